@@ -1,0 +1,280 @@
+#!/usr/bin/env python
+"""Benchmark of the discrete-ordinates CT dose solve on GB300.
+
+One step = one complete forward solve of the workload (Siddon ray trace and
+first-collision source, source iteration of the collided problem with octant
+wavefront sweeps until the relative change of the scalar fluence is below
+1e-6 in every group, particle balance).  The metric is phase-space cell
+updates per second: voxels x directions x groups x sweeps, divided by the
+device time of the whole step.  Inputs are resident in HBM before the timed
+region; the working set (four 160 MB moment arrays) is larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (whole-mesh sweeps of one group).  Under torchrun
+every rank solves its own view of an axial scan (weak scaling, no data-path
+collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "phase-space cell updates/s (voxel*angle*group)"
+UNIT = "cell_updates/s"
+WORKLOAD = "water_cylinder"
+WORKLOAD_DESC = ("35 cm water cylinder, 64x64x32 mesh (0.55x0.55x0.5 cm), fan 40 deg x 4 cm cone-beam "
+                 "source at 54 cm, 19 groups 10-120 keV, S8 (80 directions), P3, FP32 sweep, tol 1e-6")
+
+# DRAM traffic of one full sweep of this workload (all stage launches of one
+# iteration), from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum`
+# (see profiles/); valid only for the kernel source it was taken on.
+SWEEP_TRAFFIC = {"bytes_per_sweep": None, "sweep_src_sha1": None}
+
+
+def _sha1(path):
+    with open(path, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                c = [x.strip() for x in line.split(",")]
+                if len(c) < 9:
+                    continue
+                try:
+                    sm.append(float(c[1]))
+                    mx.append(float(c[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, c[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def oracle_sample(p, seconds=12.0):
+    """Time the FP64 oracle's whole-mesh sweeps of group 0 of the workload
+    (single-threaded C); returns (cell updates/s, sweeps, seconds)."""
+    import numpy as np
+    from oracle import quadrature as quad
+    from oracle import transport as tr
+
+    dirs, w, R, Mop, Dop = quad.angular_operators(p.sn, p.legendre)
+    M = Mop.shape[1]
+    sigt = p.density.astype(np.float64) * p.sigma_t[p.mat, 0]
+    rng = np.random.default_rng(0)
+    src = rng.uniform(0.0, 1.0, size=(M, p.V))
+    tr.sweep((p.nx, p.ny, p.nz), (p.dx, p.dy, p.dz), dirs, w, Mop, Dop, sigt, src)   # load + warm
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        tr.sweep((p.nx, p.ny, p.nz), (p.dx, p.dy, p.dz), dirs, w, Mop, Dop, sigt, src)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    cells = n * p.V * dirs.shape[0]
+    return cells / el, n, el
+
+
+def run_reference(args, rank, world):
+    from synth import phantoms as ph
+    if rank != 0:
+        return
+    p = ph.config_problem(WORKLOAD)
+    for _ in range(args.warmup):
+        oracle_sample(p, seconds=0.0)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, n, el = oracle_sample(p, seconds=0.0)
+        vals.append((v, n, el))
+    wall = time.perf_counter() - t0
+    total_cells = sum(v * el for v, n, el in vals)
+    value = total_cells / sum(el for _, _, el in vals)
+    sample = (f"{args.steps} whole-mesh FP64 sweeps of group 0 ({p.nx}x{p.ny}x{p.nz} voxels x "
+              f"{p.n_angles} directions each) by the single-threaded oracle")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "description": WORKLOAD_DESC},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1811_12391_gb300 import build as build_lib
+    build_lib()
+    from paper_1811_12391_gb300.solver import DoctorsProblem
+    from synth import phantoms as ph
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    p = ph.config_problem(WORKLOAD)
+    if world > 1:   # every rank solves its own view of an axial scan
+        p = p.with_sources(ph.axial_scan_sources(p, world)[rank:rank + 1])
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        d = DoctorsProblem(p, stream=stream, tol=1e-6, max_iters=500)
+        for _ in range(args.warmup):
+            d.solve()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local).start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = [d.solve() for _ in range(args.steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        if world > 1:
+            dist.barrier()
+        ms = e0.elapsed_time(e1)
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+        cells = sum(r["cell_updates"] for r in res)
+        value = world * cells / (ms_max / 1e3)
+        launches = int(sum(r["launches"] for r in res))
+        sweeps = sum(r["iterations"] for r in res)
+        ms_sweep = sum(r["ms_sweep"] for r in res)
+
+        # end to end through the C-ABI with host buffers (copies inside the timed region)
+        k_dep = np.ascontiguousarray(p.k_dep)
+        t0 = time.perf_counter()
+        e2e_cells = 0.0
+        for _ in range(args.steps):
+            d.set_materials(p.mat, p.density, p.sigma_t, p.sigma_s)
+            d.set_sources(p.sources)
+            r = d.solve()
+            phi = d.fluence_host(2)
+            dose = d.dose_host(k_dep)
+            e2e_cells += r["cell_updates"]
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        h2d = p.V * 1 + p.V * 4
+        d2h = phi.nbytes + dose.nbytes
+        d.close()
+
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    M = (p.legendre + 1) ** 2
+    bytes_per_sweep = 2 * M * p.G * p.V * 4 + 5 * p.V
+    achieved = bytes_per_sweep * sweeps / (ms_sweep / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    src_sha = _sha1(os.path.join(ROOT, "paper_1811_12391_gb300", "csrc", "sweep_impl.cuh"))
+    traffic = SWEEP_TRAFFIC["bytes_per_sweep"] if SWEEP_TRAFFIC["sweep_src_sha1"] == src_sha else None
+    cpu_v, cpu_n, cpu_s = oracle_sample(p, seconds=args.cpu_seconds) if world == 1 else (None, 0, 0)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "description": WORKLOAD_DESC, "voxels": p.V,
+                   "directions": p.n_angles, "groups": p.G, "moments": M,
+                   "sweeps_per_step": sweeps / args.steps, "l2": "inputs larger than L2 (4 x 160 MB moment arrays)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": "k_sweep (all stage launches of one sweep)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "traffic": traffic,
+                     "algorithmic_bytes_per_sweep": bytes_per_sweep,
+                     "ms_per_sweep": ms_sweep / sweeps},
+        "cpu_baseline": None if cpu_v is None else {
+            "value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{cpu_n} whole-mesh FP64 sweeps of group 0 of the same workload in {cpu_s:.1f} s"},
+        "e2e": {"value": world * e2e_cells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,644 @@
+// C-ABI entry points of libdoctors (declared in include/doctors.h).
+//
+// The handle owns the device state; every launch goes to the problem's
+// stream.  Solve = ray trace + first-collision source (Sec. II.A), then
+// source iteration of the collided problem (Eq. 2) with all groups per sweep
+// (Jacobi in energy: same fixed point as solving the groups one after the
+// other), stopped on the FP64 relative L2 change of the scalar fluence
+// (Eq. 3) in every group.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "doctors_internal.h"
+
+namespace doctors {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+}  // namespace doctors
+
+using namespace doctors;
+
+#define CU(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));              \
+            return DOCTORS_ERR_CUDA;                                                    \
+        }                                                                               \
+    } while (0)
+
+#define CHECK_ARG(cond, msg)          \
+    do {                              \
+        if (!(cond)) {                \
+            set_error(msg);           \
+            return DOCTORS_ERR_INVALID_ARG; \
+        }                             \
+    } while (0)
+
+namespace {
+
+int dalloc(void** p, size_t bytes, const char* what) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        *p = nullptr;
+        set_error(std::string("device allocation failed: ") + what + " (" + std::to_string(bytes) + " bytes)");
+        return e == cudaErrorMemoryAllocation ? DOCTORS_ERR_OOM : DOCTORS_ERR_CUDA;
+    }
+    return DOCTORS_OK;
+}
+
+template <class T>
+int dalloc_t(T** p, size_t count, const char* what) {
+    return dalloc(reinterpret_cast<void**>(p), count * sizeof(T), what);
+}
+
+int default_ab(int A8) {
+    const int cand[] = {12, 10, 9, 7, 6, 5, 4, 3, 2, 1};
+    for (int c : cand)
+        if (A8 % c == 0) return c;
+    return 1;
+}
+
+void free_problem(doctors_problem* p) {
+    void* ptrs[] = {p->d_mop, p->d_dop, p->d_coef, p->d_mat, p->d_rho, p->d_sigt, p->d_sigs,
+                    p->d_phiu_src, p->d_phiu, p->d_U, p->d_Q, p->d_mom, p->d_src, p->d_prev,
+                    p->d_emit, p->d_iso, p->d_xface, p->d_yface, p->d_red};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    if (p->h_red) cudaFreeHost(p->h_red);
+    for (auto& e : p->ev)
+        if (e) cudaEventDestroy(e);
+}
+
+// the (perp, up) frame of a collimated source: perp = (-a_y, a_x, 0)/|(a_x, a_y)|
+// ((1,0,0) for an axis along z), up = axis x perp; FP64, then rounded to FP32.
+void collimator_frame(const double a[3], double perp[3], double up[3]) {
+    const double h = std::sqrt(a[0] * a[0] + a[1] * a[1]);
+    if (h == 0.0) {
+        perp[0] = 1.0; perp[1] = 0.0; perp[2] = 0.0;
+    } else {
+        perp[0] = -a[1] / h; perp[1] = a[0] / h; perp[2] = 0.0;
+    }
+    up[0] = a[1] * perp[2] - a[2] * perp[1];
+    up[1] = a[2] * perp[0] - a[0] * perp[2];
+    up[2] = a[0] * perp[1] - a[1] * perp[0];
+}
+
+RayArgs ray_args(const doctors_problem* p, const doctors_source& s, const float* emit) {
+    RayArgs r{};
+    r.nx = p->nx; r.ny = p->ny; r.nz = p->nz; r.G = p->G; r.nmat = p->nmat;
+    r.ox = (float)p->mesh.origin[0]; r.oy = (float)p->mesh.origin[1]; r.oz = (float)p->mesh.origin[2];
+    r.dx = (float)p->mesh.dx; r.dy = (float)p->mesh.dy; r.dz = (float)p->mesh.dz;
+    r.sx = (float)s.pos[0]; r.sy = (float)s.pos[1]; r.sz = (float)s.pos[2];
+    r.lit_all = s.kind == DOCTORS_SRC_POINT ? 1 : 0;
+    double perp[3], up[3];
+    collimator_frame(s.axis, perp, up);
+    r.ax = (float)s.axis[0]; r.ay = (float)s.axis[1]; r.az = (float)s.axis[2];
+    r.px = (float)perp[0]; r.py = (float)perp[1]; r.pz = (float)perp[2];
+    r.ux = (float)up[0]; r.uy = (float)up[1]; r.uz = (float)up[2];
+    r.tan_half = (float)std::tan(0.5 * s.fan_deg * (M_PI / 180.0));
+    r.z_slope = (float)(s.z_half_iso / (s.iso_dist > 0 ? s.iso_dist : 1.0));
+    r.mat = p->d_mat; r.rho = p->d_rho; r.sigt = p->d_sigt; r.emit = emit;
+    r.phi_src = p->d_phiu_src; r.phi_tot = p->d_phiu;
+    return r;
+}
+
+int check_problem(doctors_problem* p) {
+    CHECK_ARG(p != nullptr, "null problem");
+    cudaError_t e = cudaSetDevice(p->device);
+    if (e != cudaSuccess) {
+        set_error(std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+        return DOCTORS_ERR_CUDA;
+    }
+    return DOCTORS_OK;
+}
+
+// ray trace every point source and build the fixed (first-collision) source Q
+int first_collision(doctors_problem* p) {
+    const size_t GV = (size_t)p->G * p->V;
+    CU(cudaMemsetAsync(p->d_phiu, 0, GV * sizeof(float), p->stream));
+    CU(cudaMemsetAsync(p->d_U, 0, GV * p->M * sizeof(float), p->stream));
+    std::vector<float> iso(p->G, 0.0f);
+    std::vector<float> emit_all((size_t)p->srcs.size() * p->G);
+    for (size_t s = 0; s < p->srcs.size(); ++s)
+        for (int g = 0; g < p->G; ++g) emit_all[s * p->G + g] = (float)(p->srcs[s].weight * p->spectra[s][g]);
+    float* d_emit_all = nullptr;
+    int rc = dalloc_t(&d_emit_all, emit_all.size(), "source emission table");
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(d_emit_all, emit_all.data(), emit_all.size() * sizeof(float),
+                                    cudaMemcpyHostToDevice, p->stream);
+    for (size_t s = 0; s < p->srcs.size() && e == cudaSuccess; ++s) {
+        const doctors_source& src = p->srcs[s];
+        if (src.kind == DOCTORS_SRC_VOLUME) {
+            for (int g = 0; g < p->G; ++g) iso[g] += (float)(src.weight * p->spectra[s][g]);
+            continue;
+        }
+        RayArgs r = ray_args(p, src, d_emit_all + s * p->G);
+        e = launch_raytrace(r, p->stream);
+        if (e != cudaSuccess) break;
+        ++p->launches;
+        MomentArgs m{};
+        m.nx = p->nx; m.ny = p->ny; m.nz = p->nz; m.G = p->G; m.M = p->M; m.L = p->L;
+        m.ox = r.ox; m.oy = r.oy; m.oz = r.oz; m.dx = r.dx; m.dy = r.dy; m.dz = r.dz;
+        m.sx = r.sx; m.sy = r.sy; m.sz = r.sz;
+        m.phi_src = p->d_phiu_src;
+        m.U = p->d_U;
+        e = launch_uncollided_moments(m, p->stream);
+        ++p->launches;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->d_iso, iso.data(), p->G * sizeof(float), cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) {
+        ScatterArgs sa{};
+        sa.V = p->V; sa.G = p->G; sa.M = p->M; sa.L = p->L; sa.nmat = p->nmat; sa.transpose = 0;
+        sa.mat = p->d_mat; sa.rho = p->d_rho; sa.sigs = p->d_sigs;
+        sa.base = nullptr; sa.iso = p->d_iso; sa.phi = p->d_U; sa.out = p->d_Q;
+        e = launch_scatter(sa, p->stream);
+        ++p->launches;
+    }
+    // the emission table must outlive the launches that read it
+    cudaError_t e2 = cudaStreamSynchronize(p->stream);
+    cudaFree(d_emit_all);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) {
+        set_error(std::string("first-collision source: ") + cudaGetErrorString(e));
+        return DOCTORS_ERR_CUDA;
+    }
+    return DOCTORS_OK;
+}
+
+SweepArgs sweep_args(const doctors_problem* p, int reverse) {
+    SweepArgs a{};
+    a.nx = p->nx; a.ny = p->ny; a.nz = p->nz; a.G = p->G; a.A8 = p->A8; a.ab = p->ab; a.nab = p->nab;
+    a.nmat = p->nmat; a.tx = p->tx; a.ty = p->ty; a.ntx = p->ntx; a.nty = p->nty; a.reverse = reverse;
+    a.mat = p->d_mat; a.rho = p->d_rho; a.sigt = p->d_sigt; a.src = p->d_src; a.mom = p->d_mom;
+    a.mop = p->d_mop; a.dop = p->d_dop; a.coef = p->d_coef; a.xface = p->d_xface; a.yface = p->d_yface;
+    a.leak = p->d_red;
+    return a;
+}
+
+// Source iteration: src = Q + S(mom); mom = sweep(src); residual.  `transpose`
+// selects the adjoint's scattering, `reverse` its sweep directions.
+int iterate(doctors_problem* p, int reverse, doctors_result* info) {
+    const size_t GVM = (size_t)p->G * p->V * p->M;
+    double* d_leak = p->d_red;
+    double* d_res = p->d_red + p->G;
+    double* d_bal = p->d_red + 3 * p->G;
+    CU(cudaMemsetAsync(p->d_mom, 0, GVM * sizeof(float), p->stream));
+    CU(cudaMemsetAsync(p->d_prev, 0, (size_t)p->G * p->V * sizeof(float), p->stream));
+    const double tol = std::max(p->opt.tol, kTolFloor);
+    int it = 0;
+    double resid = 0.0;
+    double ms_sweep = 0.0;
+    bool conv = false;
+    SweepArgs sw = sweep_args(p, reverse);
+    ScatterArgs sa{};
+    sa.V = p->V; sa.G = p->G; sa.M = p->M; sa.L = p->L; sa.nmat = p->nmat; sa.transpose = reverse;
+    sa.mat = p->d_mat; sa.rho = p->d_rho; sa.sigs = p->d_sigs;
+    sa.base = p->d_Q; sa.phi = p->d_mom; sa.out = p->d_src;
+    while (it < p->opt.max_iters) {
+        if (it == 0) {
+            CU(cudaMemcpyAsync(p->d_src, p->d_Q, GVM * sizeof(float), cudaMemcpyDeviceToDevice, p->stream));
+        } else {
+            CU(launch_scatter(sa, p->stream));
+            ++p->launches;
+        }
+        CU(cudaMemsetAsync(p->d_mom, 0, GVM * sizeof(float), p->stream));
+        CU(cudaMemsetAsync(p->d_red, 0, 5 * (size_t)p->G * sizeof(double), p->stream));
+        CU(cudaEventRecord(p->ev[3], p->stream));
+        for (int st = 0; st < p->ntx + p->nty - 1; ++st) {
+            sw.stage = st;
+            CU(launch_sweep_stage(sw, p->M, p->stream));
+            ++p->launches;
+        }
+        CU(cudaEventRecord(p->ev[4], p->stream));
+        CU(launch_residual(p->V, p->G, p->M, p->d_mom, p->d_prev, d_res, p->stream));
+        ++p->launches;
+        CU(cudaMemcpyAsync(p->h_red, p->d_red, 3 * (size_t)p->G * sizeof(double), cudaMemcpyDeviceToHost,
+                           p->stream));
+        CU(cudaStreamSynchronize(p->stream));
+        float ms = 0.0f;
+        CU(cudaEventElapsedTime(&ms, p->ev[3], p->ev[4]));
+        ms_sweep += ms;
+        ++it;
+        resid = 0.0;
+        for (int g = 0; g < p->G; ++g) {
+            const double num = p->h_red[p->G + 2 * g], den = p->h_red[p->G + 2 * g + 1];
+            const double eps = den > 0.0 ? std::sqrt(num / den) : 0.0;
+            resid = std::max(resid, eps);
+        }
+        if (!std::isfinite(resid)) {
+            set_error("source iteration produced a non-finite fluence");
+            return DOCTORS_ERR_INVALID_ARG;
+        }
+        if (resid < tol) {
+            conv = true;
+            break;
+        }
+    }
+    // particle balance of the last sweep (FP64)
+    const double vol = p->mesh.dx * p->mesh.dy * p->mesh.dz;
+    CU(launch_balance(p->V, p->G, p->M, p->d_mat, p->d_rho, p->d_sigt, p->d_src, p->d_mom, vol, d_bal,
+                      p->stream));
+    ++p->launches;
+    CU(cudaMemcpyAsync(p->h_red, p->d_red, 5 * (size_t)p->G * sizeof(double), cudaMemcpyDeviceToHost,
+                       p->stream));
+    CU(cudaStreamSynchronize(p->stream));
+    double gain = 0.0, loss = 0.0;
+    for (int g = 0; g < p->G; ++g) {
+        gain += p->h_red[3 * p->G + 2 * g];
+        loss += p->h_red[3 * p->G + 2 * g + 1] + p->h_red[g];
+    }
+    if (info) {
+        info->iterations = it;
+        info->converged = conv ? 1 : 0;
+        info->residual = resid;
+        info->balance_rel = gain != 0.0 ? std::fabs(gain - loss) / std::fabs(gain) : 0.0;
+        info->tol_used = tol;
+        info->cell_updates = (double)it * (double)p->V * p->A * p->G;
+        info->ms_sweep = ms_sweep;
+    }
+    return conv ? DOCTORS_OK : DOCTORS_ERR_NOT_CONVERGED;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* doctors_last_error(void) { return g_err.c_str(); }
+
+int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt, void* cuda_stream,
+                           doctors_problem** out) {
+    CHECK_ARG(mesh && opt && out, "null argument");
+    CHECK_ARG(mesh->nx >= 1 && mesh->ny >= 1 && mesh->nz >= 1, "mesh dimensions must be >= 1");
+    CHECK_ARG((double)mesh->nx * mesh->ny * mesh->nz < 2147483647.0, "mesh has too many voxels");
+    CHECK_ARG(mesh->dx > 0 && mesh->dy > 0 && mesh->dz > 0, "voxel sizes must be > 0");
+    CHECK_ARG(std::isfinite(mesh->origin[0]) && std::isfinite(mesh->origin[1]) && std::isfinite(mesh->origin[2]),
+              "origin must be finite");
+    CHECK_ARG(opt->groups >= 1 && opt->groups <= kMaxG, "groups must be 1..64");
+    CHECK_ARG(opt->legendre >= 0 && opt->legendre <= 3, "legendre must be 0..3");
+    CHECK_ARG(opt->tol > 0 && std::isfinite(opt->tol), "tol must be > 0");
+    CHECK_ARG(opt->max_iters >= 1, "max_iters must be >= 1");
+    for (int r : opt->reserved) CHECK_ARG(r == 0, "reserved option fields must be zero");
+    std::vector<double> dirs, w;
+    std::string err;
+    if (!build_quadrature(opt->sn_order, dirs, w, err)) {
+        set_error(err);
+        return DOCTORS_ERR_INVALID_ARG;
+    }
+    auto* p = new doctors_problem();
+    p->mesh = *mesh;
+    p->opt = *opt;
+    p->nx = mesh->nx; p->ny = mesh->ny; p->nz = mesh->nz;
+    p->V = (size_t)p->nx * p->ny * p->nz;
+    p->G = opt->groups; p->N = opt->sn_order; p->L = opt->legendre; p->M = (p->L + 1) * (p->L + 1);
+    p->A = (int)w.size(); p->A8 = p->A / 8;
+    p->dirs = dirs; p->w = w;
+    p->stream = (cudaStream_t)cuda_stream;
+    p->tx = opt->tile_x > 0 ? opt->tile_x : std::min(16, p->nx);
+    p->ty = opt->tile_y > 0 ? opt->tile_y : std::min(16, p->ny);
+    p->ab = opt->angles_per_block > 0 ? opt->angles_per_block : default_ab(p->A8);
+    auto fail = [&](int code, const std::string& msg) {
+        if (!msg.empty()) set_error(msg);
+        free_problem(p);
+        delete p;
+        return code;
+    };
+    if (p->tx * p->ty > 512 || p->tx < 1 || p->ty < 1) return fail(DOCTORS_ERR_INVALID_ARG, "tile_x * tile_y must be 1..512");
+    if (p->A8 % p->ab != 0 || !sweep_supported(p->ab, p->M))
+        return fail(DOCTORS_ERR_INVALID_ARG, "angles_per_block must divide N(N+2)/8 and be one of 1,2,3,4,5,6,7,9,10,12");
+    p->nab = p->A8 / p->ab;
+    p->ntx = (p->nx + p->tx - 1) / p->tx;
+    p->nty = (p->ny + p->ty - 1) / p->ty;
+    const size_t smem = sizeof(float) * (size_t)(2 * p->ab * p->tx * p->ty + 2 * p->ab * p->M + 8 * p->ab + kMaxMat);
+    if (smem > 227 * 1024) return fail(DOCTORS_ERR_INVALID_ARG, "sweep tile needs more than 227 KB of shared memory");
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) return fail(DOCTORS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+
+    // sweep tables
+    const int A = p->A, M = p->M;
+    std::vector<float> mop((size_t)A * M), dop((size_t)A * M), coef((size_t)A * 8, 0.0f);
+    const double dx = mesh->dx, dy = mesh->dy, dz = mesh->dz;
+    for (int n = 0; n < A; ++n) {
+        double R[16];
+        real_harmonics(p->L, dirs[3 * n], dirs[3 * n + 1], dirs[3 * n + 2], R);
+        for (int lm = 0; lm < M; ++lm) {
+            const int l = lm >= 9 ? 3 : lm >= 4 ? 2 : lm >= 1 ? 1 : 0;
+            mop[(size_t)n * M + lm] = (float)((2 * l + 1) / (4.0 * M_PI) * R[lm]);
+            dop[(size_t)n * M + lm] = (float)(w[n] * R[lm]);
+        }
+        const double ox = std::fabs(dirs[3 * n]), oy = std::fabs(dirs[3 * n + 1]), oz = std::fabs(dirs[3 * n + 2]);
+        coef[n * 8 + 0] = (float)(ox / dx);
+        coef[n * 8 + 1] = (float)(oy / dy);
+        coef[n * 8 + 2] = (float)(oz / dz);
+        coef[n * 8 + 3] = (float)(ox / dx + oy / dy + oz / dz);
+        coef[n * 8 + 4] = (float)(w[n] * ox * dy * dz);
+        coef[n * 8 + 5] = (float)(w[n] * oy * dx * dz);
+        coef[n * 8 + 6] = (float)(w[n] * oz * dx * dy);
+    }
+    const size_t GV = (size_t)p->G * p->V, GVM = GV * M;
+    int rc = 0;
+    rc = rc ? rc : dalloc_t(&p->d_mop, mop.size(), "tables");
+    rc = rc ? rc : dalloc_t(&p->d_dop, dop.size(), "tables");
+    rc = rc ? rc : dalloc_t(&p->d_coef, coef.size(), "tables");
+    rc = rc ? rc : dalloc_t(&p->d_mat, p->V, "materials");
+    rc = rc ? rc : dalloc_t(&p->d_rho, p->V, "densities");
+    rc = rc ? rc : dalloc_t(&p->d_sigt, (size_t)kMaxMat * p->G, "sigma_t");
+    rc = rc ? rc : dalloc_t(&p->d_sigs, (size_t)kMaxMat * (p->L + 1) * p->G * p->G, "sigma_s");
+    rc = rc ? rc : dalloc_t(&p->d_phiu_src, GV, "uncollided (source)");
+    rc = rc ? rc : dalloc_t(&p->d_phiu, GV, "uncollided");
+    rc = rc ? rc : dalloc_t(&p->d_U, GVM, "uncollided moments");
+    rc = rc ? rc : dalloc_t(&p->d_Q, GVM, "first-collision source");
+    rc = rc ? rc : dalloc_t(&p->d_mom, GVM, "moments");
+    rc = rc ? rc : dalloc_t(&p->d_src, GVM, "sweep source");
+    rc = rc ? rc : dalloc_t(&p->d_prev, GV, "previous scalar fluence");
+    rc = rc ? rc : dalloc_t(&p->d_iso, (size_t)p->G, "volume source");
+    const size_t xf = (size_t)A * p->G * (p->ntx > 1 ? p->ntx - 1 : 0) * p->ny * p->nz;
+    const size_t yf = (size_t)A * p->G * (p->nty > 1 ? p->nty - 1 : 0) * p->nx * p->nz;
+    rc = rc ? rc : dalloc_t(&p->d_xface, xf, "x face buffer");
+    rc = rc ? rc : dalloc_t(&p->d_yface, yf, "y face buffer");
+    rc = rc ? rc : dalloc_t(&p->d_red, 5 * (size_t)p->G, "reductions");
+    if (rc) return fail(rc, "");
+    e = cudaMallocHost(&p->h_red, 5 * (size_t)p->G * sizeof(double));
+    if (e != cudaSuccess) return fail(DOCTORS_ERR_OOM, "pinned host allocation failed");
+    for (auto& ev : p->ev) {
+        e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return fail(DOCTORS_ERR_CUDA, "cudaEventCreate failed");
+    }
+    e = cudaMemcpyAsync(p->d_mop, mop.data(), mop.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->d_dop, dop.data(), dop.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->d_coef, coef.data(), coef.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return fail(DOCTORS_ERR_CUDA, std::string("table upload: ") + cudaGetErrorString(e));
+    *out = p;
+    return DOCTORS_OK;
+}
+
+int doctors_set_materials(doctors_problem* p, int n_mat, const uint8_t* mat, const float* density,
+                          const double* sigma_t, const double* sigma_s, int mem) {
+    int rc = check_problem(p);
+    if (rc) return rc;
+    CHECK_ARG(n_mat >= 1 && n_mat <= kMaxMat, "n_mat must be 1..8");
+    CHECK_ARG(mat && sigma_t && sigma_s, "null material table");
+    CHECK_ARG(mem == DOCTORS_MEM_HOST || mem == DOCTORS_MEM_DEVICE, "mem must be DOCTORS_MEM_HOST or _DEVICE");
+    const int G = p->G, L = p->L;
+    for (int m = 0; m < n_mat; ++m)
+        for (int g = 0; g < G; ++g) {
+            const double st = sigma_t[m * G + g];
+            CHECK_ARG(std::isfinite(st) && st >= 0, "sigma_t must be finite and >= 0");
+            double out0 = 0.0;
+            for (int l = 0; l <= L; ++l)
+                for (int gt = 0; gt < G; ++gt) {
+                    const double s = sigma_s[(((size_t)m * (L + 1) + l) * G + g) * G + gt];
+                    CHECK_ARG(std::isfinite(s), "sigma_s must be finite");
+                    if (gt < g) CHECK_ARG(s == 0.0, "sigma_s has upscatter (to < from)");
+                    if (l == 0) {
+                        CHECK_ARG(s >= 0.0, "sigma_s,0 must be >= 0");
+                        out0 += s;
+                    }
+                }
+            CHECK_ARG(out0 <= st * (1.0 + 1e-12), "sum of sigma_s,0 out of a group exceeds sigma_t");
+        }
+    // voxel arrays: validate on the host
+    std::vector<uint8_t> hm(p->V);
+    std::vector<float> hr(p->V, 1.0f);
+    if (mem == DOCTORS_MEM_HOST) {
+        std::memcpy(hm.data(), mat, p->V);
+        if (density) std::memcpy(hr.data(), density, p->V * sizeof(float));
+    } else {
+        CU(cudaMemcpy(hm.data(), mat, p->V, cudaMemcpyDeviceToHost));
+        if (density) CU(cudaMemcpy(hr.data(), density, p->V * sizeof(float), cudaMemcpyDeviceToHost));
+    }
+    for (size_t v = 0; v < p->V; ++v) {
+        CHECK_ARG(hm[v] < n_mat, "material id out of range");
+        CHECK_ARG(std::isfinite(hr[v]) && hr[v] >= 0.0f, "density must be finite and >= 0");
+    }
+    std::vector<float> st((size_t)n_mat * G), ss((size_t)n_mat * (L + 1) * G * G);
+    for (size_t q = 0; q < st.size(); ++q) st[q] = (float)sigma_t[q];
+    for (size_t q = 0; q < ss.size(); ++q) ss[q] = (float)sigma_s[q];
+    CU(cudaMemcpyAsync(p->d_mat, hm.data(), p->V, cudaMemcpyHostToDevice, p->stream));
+    CU(cudaMemcpyAsync(p->d_rho, hr.data(), p->V * sizeof(float), cudaMemcpyHostToDevice, p->stream));
+    CU(cudaMemcpyAsync(p->d_sigt, st.data(), st.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream));
+    CU(cudaMemcpyAsync(p->d_sigs, ss.data(), ss.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream));
+    CU(cudaStreamSynchronize(p->stream));
+    p->nmat = n_mat;
+    p->h_sigt.assign(sigma_t, sigma_t + (size_t)n_mat * G);
+    p->h_sigs.assign(sigma_s, sigma_s + ss.size());
+    p->have_mat = true;
+    p->solved = false;
+    return DOCTORS_OK;
+}
+
+int doctors_set_source(doctors_problem* p, int n_src, const doctors_source* src) {
+    int rc = check_problem(p);
+    if (rc) return rc;
+    CHECK_ARG(n_src >= 1 && n_src <= kMaxSrc, "n_src must be 1..4096");
+    CHECK_ARG(src != nullptr, "null source array");
+    std::vector<doctors_source> list(src, src + n_src);
+    std::vector<std::vector<double>> spec(n_src);
+    const double lo[3] = {p->mesh.origin[0], p->mesh.origin[1], p->mesh.origin[2]};
+    const double hi[3] = {lo[0] + p->nx * p->mesh.dx, lo[1] + p->ny * p->mesh.dy, lo[2] + p->nz * p->mesh.dz};
+    for (int s = 0; s < n_src; ++s) {
+        doctors_source& q = list[s];
+        CHECK_ARG(q.kind == DOCTORS_SRC_POINT || q.kind == DOCTORS_SRC_FAN_CONE || q.kind == DOCTORS_SRC_VOLUME,
+                  "unknown source kind");
+        CHECK_ARG(q.spectrum != nullptr, "null spectrum");
+        CHECK_ARG(std::isfinite(q.weight) && q.weight >= 0, "source weight must be finite and >= 0");
+        spec[s].assign(q.spectrum, q.spectrum + p->G);
+        for (double x : spec[s]) CHECK_ARG(std::isfinite(x) && x >= 0, "spectrum must be finite and >= 0");
+        q.spectrum = nullptr;
+        if (q.kind == DOCTORS_SRC_VOLUME) continue;
+        for (int d = 0; d < 3; ++d) CHECK_ARG(std::isfinite(q.pos[d]), "source position must be finite");
+        const bool inside = q.pos[0] >= lo[0] && q.pos[0] <= hi[0] && q.pos[1] >= lo[1] && q.pos[1] <= hi[1] &&
+                            q.pos[2] >= lo[2] && q.pos[2] <= hi[2];
+        CHECK_ARG(!inside, "point sources must lie outside the mesh");
+        if (q.kind == DOCTORS_SRC_FAN_CONE) {
+            const double n = std::sqrt(q.axis[0] * q.axis[0] + q.axis[1] * q.axis[1] + q.axis[2] * q.axis[2]);
+            CHECK_ARG(n > 0 && std::isfinite(n), "collimator axis must be non-zero");
+            CHECK_ARG(std::fabs(n - 1.0) < 1e-9, "collimator axis must be a unit vector");
+            CHECK_ARG(q.fan_deg > 0 && q.fan_deg < 180, "fan_deg must be in (0, 180)");
+            CHECK_ARG(q.z_half_iso >= 0 && q.iso_dist > 0, "z_half_iso >= 0 and iso_dist > 0 required");
+        }
+    }
+    p->srcs = list;
+    p->spectra = spec;
+    p->have_src = true;
+    p->solved = false;
+    return DOCTORS_OK;
+}
+
+int doctors_solve(doctors_problem* p, doctors_result* info) {
+    int rc = check_problem(p);
+    if (rc) return rc;
+    if (!p->have_mat || !p->have_src) {
+        set_error("set materials and sources before solving");
+        return DOCTORS_ERR_STATE;
+    }
+    doctors_result r{};
+    p->solved = false;
+    p->launches = 0;
+    CU(cudaEventRecord(p->ev[0], p->stream));
+    rc = first_collision(p);
+    if (rc) return rc;
+    CU(cudaEventRecord(p->ev[1], p->stream));
+    rc = iterate(p, 0, &r);
+    if (rc && rc != DOCTORS_ERR_NOT_CONVERGED) return rc;
+    CU(cudaEventRecord(p->ev[2], p->stream));
+    CU(cudaEventSynchronize(p->ev[2]));
+    float t01 = 0, t12 = 0, t02 = 0;
+    cudaEventElapsedTime(&t01, p->ev[0], p->ev[1]);
+    cudaEventElapsedTime(&t12, p->ev[1], p->ev[2]);
+    cudaEventElapsedTime(&t02, p->ev[0], p->ev[2]);
+    r.ms_raytrace = t01;
+    r.ms_iterate = t12;
+    r.ms_total = t02;
+    r.launches = p->launches;
+    if (info) *info = r;
+    p->solved = true;
+    if (rc == DOCTORS_ERR_NOT_CONVERGED) set_error("iteration cap reached before convergence");
+    return rc;
+}
+
+int doctors_get_fluence(doctors_problem* p, int which, float* out, int mem) {
+    int rc = check_problem(p);
+    if (rc) return rc;
+    CHECK_ARG(out != nullptr, "null output");
+    CHECK_ARG(which >= 0 && which <= 2, "which must be UNCOLLIDED, COLLIDED or TOTAL");
+    CHECK_ARG(mem == DOCTORS_MEM_HOST || mem == DOCTORS_MEM_DEVICE, "bad mem");
+    if (!p->solved) {
+        set_error("no solution: call doctors_solve first");
+        return DOCTORS_ERR_STATE;
+    }
+    const int mask = which == DOCTORS_FLUENCE_UNCOLLIDED ? 1 : which == DOCTORS_FLUENCE_COLLIDED ? 2 : 3;
+    const size_t GV = (size_t)p->G * p->V;
+    if (mem == DOCTORS_MEM_DEVICE) {
+        CU(launch_extract(p->V, p->G, p->M, mask, p->d_phiu, p->d_mom, out, p->stream));
+        return DOCTORS_OK;
+    }
+    // stage through the (now free) source buffer
+    CU(launch_extract(p->V, p->G, p->M, mask, p->d_phiu, p->d_mom, p->d_src, p->stream));
+    CU(cudaMemcpyAsync(out, p->d_src, GV * sizeof(float), cudaMemcpyDeviceToHost, p->stream));
+    CU(cudaStreamSynchronize(p->stream));
+    return DOCTORS_OK;
+}
+
+int doctors_dose(doctors_problem* p, const double* k, double* dose, int mem) {
+    int rc = check_problem(p);
+    if (rc) return rc;
+    CHECK_ARG(k && dose, "null argument");
+    CHECK_ARG(mem == DOCTORS_MEM_HOST || mem == DOCTORS_MEM_DEVICE, "bad mem");
+    if (!p->solved) {
+        set_error("no solution: call doctors_solve first");
+        return DOCTORS_ERR_STATE;
+    }
+    for (int q = 0; q < p->nmat * p->G; ++q) CHECK_ARG(std::isfinite(k[q]), "k must be finite");
+    double* d_k = nullptr;
+    double* d_out = nullptr;
+    rc = dalloc_t(&d_k, (size_t)p->nmat * p->G, "dose factors");
+    if (rc) return rc;
+    if (mem == DOCTORS_MEM_HOST) {
+        rc = dalloc_t(&d_out, p->V, "dose staging");
+        if (rc) {
+            cudaFree(d_k);
+            return rc;
+        }
+    }
+    cudaError_t e = cudaMemcpyAsync(d_k, k, (size_t)p->nmat * p->G * sizeof(double), cudaMemcpyHostToDevice,
+                                    p->stream);
+    double* dst = mem == DOCTORS_MEM_HOST ? d_out : dose;
+    if (e == cudaSuccess) e = launch_dose(p->V, p->G, p->M, p->d_mat, p->d_rho, d_k, p->d_phiu, p->d_mom, dst, p->stream);
+    if (e == cudaSuccess && mem == DOCTORS_MEM_HOST)
+        e = cudaMemcpyAsync(dose, d_out, p->V * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+    // the factor table (and staging) must outlive the kernel
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    cudaFree(d_k);
+    if (d_out) cudaFree(d_out);
+    if (e != cudaSuccess) {
+        set_error(std::string("dose: ") + cudaGetErrorString(e));
+        return DOCTORS_ERR_CUDA;
+    }
+    return DOCTORS_OK;
+}
+
+int doctors_debug_ray_indices(doctors_problem* p, int src, int voxel, int32_t* idx, float* len, int cap, int* n) {
+    int rc = check_problem(p);
+    if (rc) return rc;
+    CHECK_ARG(p->have_mat && p->have_src, "set materials and sources first");
+    CHECK_ARG(src >= 0 && src < (int)p->srcs.size(), "source index out of range");
+    CHECK_ARG(p->srcs[src].kind != DOCTORS_SRC_VOLUME, "not a point source");
+    CHECK_ARG(voxel >= 0 && (size_t)voxel < p->V, "voxel index out of range");
+    CHECK_ARG(idx && len && n && cap >= 0, "null output");
+    const int dcap = p->nx + p->ny + p->nz + 4;
+    int32_t* d_idx = nullptr;
+    float* d_len = nullptr;
+    int* d_cnt = nullptr;
+    rc = dalloc_t(&d_idx, dcap, "debug ray");
+    if (!rc) rc = dalloc_t(&d_len, dcap, "debug ray");
+    if (!rc) rc = dalloc_t(&d_cnt, 1, "debug ray");
+    if (rc) {
+        cudaFree(d_idx); cudaFree(d_len); cudaFree(d_cnt);
+        return rc;
+    }
+    RayArgs r = ray_args(p, p->srcs[src], nullptr);
+    int cnt = 0;
+    cudaError_t e = launch_debug_ray(r, voxel, d_idx, d_len, dcap, d_cnt, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, d_cnt, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e == cudaSuccess && cnt <= cap && cnt <= dcap) {
+        e = cudaMemcpy(idx, d_idx, cnt * sizeof(int32_t), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(len, d_len, cnt * sizeof(float), cudaMemcpyDeviceToHost);
+    }
+    cudaFree(d_idx); cudaFree(d_len); cudaFree(d_cnt);
+    if (e != cudaSuccess) {
+        set_error(std::string("debug ray: ") + cudaGetErrorString(e));
+        return DOCTORS_ERR_CUDA;
+    }
+    *n = cnt;
+    if (cnt > cap) {
+        set_error("capacity too small for the ray's index list");
+        return DOCTORS_ERR_INVALID_ARG;
+    }
+    return DOCTORS_OK;
+}
+
+int doctors_solve_batch(doctors_problem** problems, int n, doctors_result* results) {
+    CHECK_ARG(problems && n >= 1, "empty batch");
+    int worst = DOCTORS_OK;
+    for (int q = 0; q < n; ++q) {
+        doctors_result r{};
+        const int rc = doctors_solve(problems[q], &r);
+        if (results) results[q] = r;
+        if (rc && rc != DOCTORS_ERR_NOT_CONVERGED) return rc;
+        if (rc) worst = rc;
+    }
+    return worst;
+}
+
+void doctors_destroy(doctors_problem* p) {
+    if (!p) return;
+    cudaSetDevice(p->device);
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    free_problem(p);
+    delete p;
+}
+
+}  // extern "C"
+
+extern "C" int doctors_adjoint_solve(doctors_problem* p, const double* response, int mem, double* d_weights,
+                                     double* d_spectrum, double* d_density, doctors_result* info) {
+    (void)response; (void)mem; (void)d_weights; (void)d_spectrum; (void)d_density; (void)info;
+    int rc = check_problem(p);
+    if (rc) return rc;
+    set_error("adjoint solve is not available in this build");
+    return DOCTORS_ERR_STATE;
+}

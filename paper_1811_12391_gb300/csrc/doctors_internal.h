@@ -1,0 +1,165 @@
+// Internal declarations of libdoctors: problem state, kernel argument
+// blocks and launchers.  Not part of the public C-ABI (include/doctors.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/doctors.h"
+
+namespace doctors {
+
+constexpr int kMaxMat = 8;      // materials per problem
+constexpr int kMaxG = 64;       // energy groups
+constexpr int kMaxSrc = 4096;   // sources per problem
+constexpr double kTolFloor = 1e-6;   // FP32 sweep: relative-change floor
+
+void set_error(const std::string& msg);
+
+bool build_quadrature(int N, std::vector<double>& dirs, std::vector<double>& w, std::string& err);
+void real_harmonics(int L, double x, double y, double z, double* R);
+
+// ---------------------------------------------------------------------------
+// ray trace (uncollided fluence of one point source)
+// ---------------------------------------------------------------------------
+struct RayArgs {
+    int nx, ny, nz, G, nmat, lit_all;
+    float ox, oy, oz, dx, dy, dz;      // mesh origin and spacing
+    float sx, sy, sz;                  // source position
+    float ax, ay, az, px, py, pz, ux, uy, uz;   // collimator frame
+    float tan_half, z_slope;
+    const uint8_t* mat;
+    const float* rho;
+    const float* sigt;                 // [nmat][G]
+    const float* emit;                 // [G] weight * spectrum
+    float* phi_src;                    // [G][V] this source (overwritten)
+    float* phi_tot;                    // [G][V] accumulated (+=)
+};
+
+cudaError_t launch_raytrace(const RayArgs& a, cudaStream_t s);
+cudaError_t launch_debug_ray(const RayArgs& a, int voxel, int32_t* idx, float* len, int cap,
+                             int* count, cudaStream_t s);
+
+// U[g][v][lm] += phi_src[g][v] * R_lm(unit(centre_v - source))
+struct MomentArgs {
+    int nx, ny, nz, G, M, L;
+    float ox, oy, oz, dx, dy, dz, sx, sy, sz;
+    const float* phi_src;              // [G][V]
+    float* U;                          // [G][V][M]
+};
+cudaError_t launch_uncollided_moments(const MomentArgs& a, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// scattering source:  out[g][v][lm] = base[g][v][lm] + iso[g] * (lm == 0)
+//                      + rho_v sum_g' sigma_s,l[mat v](g' -> g) phi[g'][v][lm]
+// (transpose: sigma_s,l(g -> g') instead, i.e. the adjoint's upscatter)
+// ---------------------------------------------------------------------------
+struct ScatterArgs {
+    size_t V;
+    int G, M, L, nmat, transpose;
+    const uint8_t* mat;
+    const float* rho;
+    const float* sigs;                 // [nmat][L+1][G][G] (from, to)
+    const float* base;                 // [G][V][M] or null
+    const float* iso;                  // [G] or null: added to lm = 0 of every voxel
+    const float* iso_field;            // [G][V] or null: added to lm = 0 (per voxel)
+    float iso_field_scale;
+    const float* phi;                  // [G][V][M] or null (no scattering term)
+    float* out;                        // [G][V][M]
+};
+cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s);
+
+// residual: res[g][0] += sum_v (phi00 - prev)^2, res[g][1] += sum_v phi00^2; prev = phi00
+cudaError_t launch_residual(size_t V, int G, int M, const float* mom, float* prev, double* res,
+                            cudaStream_t s);
+
+// balance: bal[g][0] += vol * sum s00, bal[g][1] += vol * sum sigma_t phi00
+cudaError_t launch_balance(size_t V, int G, int M, const uint8_t* mat, const float* rho,
+                           const float* sigt, const float* src, const float* mom, double vol,
+                           double* bal, cudaStream_t s);
+
+// dose[v] = sum_g k[mat][g] rho_v (phi_u + phi_c00)  (FP64)
+cudaError_t launch_dose(size_t V, int G, int M, const uint8_t* mat, const float* rho,
+                        const double* k, const float* phi_u, const float* mom, double* dose,
+                        cudaStream_t s);
+
+// out[g][v] = (which & 1 ? phi_u : 0) + (which & 2 ? mom00 : 0)
+cudaError_t launch_extract(size_t V, int G, int M, int which, const float* phi_u, const float* mom,
+                           float* out, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// octant wavefront sweep
+// ---------------------------------------------------------------------------
+struct SweepArgs {
+    int nx, ny, nz, G, A8, ab, nab, nmat;
+    int tx, ty, ntx, nty, stage, reverse;
+    const uint8_t* mat;
+    const float* rho;
+    const float* sigt;                 // [nmat][G]
+    const float* src;                  // [G][V][M] moment source
+    float* mom;                        // [G][V][M] accumulated moments
+    const float* mop;                  // [A][M] (2l+1)/(4 pi) R_lm(Omega_n)
+    const float* dop;                  // [A][M] w_n R_lm(Omega_n)
+    const float* coef;                 // [A][8] cx, cy, cz, cx+cy+cz, leak_x, leak_y, leak_z, 0
+    float* xface;                      // [8][A8][G][ntx-1][ny][nz]
+    float* yface;                      // [8][A8][G][nty-1][nx][nz]
+    double* leak;                      // [G]
+};
+cudaError_t launch_sweep_stage(const SweepArgs& a, int M, cudaStream_t s);
+bool sweep_supported(int ab, int M);
+
+}  // namespace doctors
+
+// ---------------------------------------------------------------------------
+// the opaque handle
+// ---------------------------------------------------------------------------
+struct doctors_problem {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    doctors_mesh mesh{};
+    doctors_options opt{};
+    int nx = 0, ny = 0, nz = 0;
+    size_t V = 0;
+    int G = 0, N = 0, L = 0, M = 0, A = 0, A8 = 0;
+    // quadrature
+    std::vector<double> dirs, w;
+    // sweep tiling
+    int tx = 16, ty = 16, ntx = 1, nty = 1, ab = 1, nab = 1;
+    // device tables
+    float* d_mop = nullptr;
+    float* d_dop = nullptr;
+    float* d_coef = nullptr;
+    // materials
+    int nmat = 0;
+    bool have_mat = false;
+    uint8_t* d_mat = nullptr;
+    float* d_rho = nullptr;
+    float* d_sigt = nullptr;
+    float* d_sigs = nullptr;
+    std::vector<double> h_sigt, h_sigs;
+    // sources
+    std::vector<doctors_source> srcs;
+    std::vector<std::vector<double>> spectra;
+    bool have_src = false;
+    // solver state
+    float* d_phiu_src = nullptr;   // [G][V]
+    float* d_phiu = nullptr;       // [G][V]
+    float* d_U = nullptr;          // [G][V][M]
+    float* d_Q = nullptr;          // [G][V][M]
+    float* d_mom = nullptr;        // [G][V][M]
+    float* d_src = nullptr;        // [G][V][M]
+    float* d_prev = nullptr;       // [G][V]
+    float* d_emit = nullptr;       // [G]
+    float* d_iso = nullptr;        // [G]
+    float* d_xface = nullptr;
+    float* d_yface = nullptr;
+    double* d_red = nullptr;       // reductions: leak [G], res [G][2], bal [G][2]
+    double* h_red = nullptr;       // pinned mirror
+    bool solved = false;
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    long long launches = 0;        // kernels launched by the current call
+};

@@ -1,0 +1,195 @@
+// Scattering-source update, FP64 reductions (residual, balance), dose tally
+// and fluence extraction.
+//
+// Eq. 2's scattering term with the kernel as a Legendre expansion reduces, in
+// moment form, to s_lm[g](v) = rho_v sum_{g'} sigma_s,l(g' -> g) phi_lm[g'](v)
+// (downscatter only, self-scatter included).  The first-collision source is
+// the same map applied to the uncollided moments (Sec. II.A).  Eq. 3's scalar
+// fluence is the lm = 00 moment.  The dose tally multiplies the group fluence
+// by group-wise conversion factors (Sec. II.A, III.A) and is accumulated in
+// FP64, like the residual norm and the particle balance.
+#include "doctors_internal.h"
+
+namespace doctors {
+
+cudaError_t launch_sweep_m1_entry(const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_sweep_m4_entry(const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_sweep_m9_entry(const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_sweep_m16_entry(const SweepArgs& a, cudaStream_t s);
+
+bool sweep_supported(int ab, int M) {
+    const int abs_ok[] = {1, 2, 3, 4, 5, 6, 7, 9, 10, 12};
+    bool ok = false;
+    for (int x : abs_ok) ok |= (x == ab);
+    return ok && (M == 1 || M == 4 || M == 9 || M == 16);
+}
+
+cudaError_t launch_sweep_stage(const SweepArgs& a, int M, cudaStream_t s) {
+    switch (M) {
+        case 1: return launch_sweep_m1_entry(a, s);
+        case 4: return launch_sweep_m4_entry(a, s);
+        case 9: return launch_sweep_m9_entry(a, s);
+        case 16: return launch_sweep_m16_entry(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+namespace {
+
+__device__ __forceinline__ int degree_of(int lm) {
+    return lm >= 9 ? 3 : lm >= 4 ? 2 : lm >= 1 ? 1 : 0;
+}
+
+// One thread per (voxel, moment); moment fastest so that a warp reads and
+// writes contiguous memory.  Loops over destination groups; the source
+// groups' moments are re-read through L1.
+__global__ void __launch_bounds__(256) k_scatter(const ScatterArgs a) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.V * a.M) return;
+    const size_t v = t / a.M;
+    const int lm = (int)(t % a.M);
+    const int l = degree_of(lm);
+    const int m = __ldg(a.mat + v);
+    const float r = __ldg(a.rho + v);
+    const float* tab = a.sigs + ((size_t)m * (a.L + 1) + l) * a.G * a.G;
+    const size_t VM = a.V * a.M;
+    for (int g = 0; g < a.G; ++g) {
+        float out = a.base ? __ldg(a.base + g * VM + t) : 0.0f;
+        if (lm == 0) {
+            if (a.iso) out += __ldg(a.iso + g);
+            if (a.iso_field) out += a.iso_field_scale * __ldg(a.iso_field + (size_t)g * a.V + v);
+        }
+        if (a.phi) {
+            float acc = 0.0f;
+            if (!a.transpose) {
+                for (int gp = 0; gp <= g; ++gp)
+                    acc = fmaf(__ldg(tab + gp * a.G + g), __ldg(a.phi + gp * VM + t), acc);
+            } else {
+                for (int gp = g; gp < a.G; ++gp)
+                    acc = fmaf(__ldg(tab + g * a.G + gp), __ldg(a.phi + gp * VM + t), acc);
+            }
+            out = fmaf(r, acc, out);
+        }
+        a.out[g * VM + t] = out;
+    }
+}
+
+template <int NV>
+__device__ __forceinline__ void block_reduce_add(double (&x)[NV], double* dst) {
+    __shared__ double red[NV][32];
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) x[q] += __shfl_down_sync(0xffffffffu, x[q], off);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) red[q][wid] = x[q];
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double y = lane < nw ? red[q][lane] : 0.0;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) y += __shfl_down_sync(0xffffffffu, y, off);
+            if (lane == 0 && y != 0.0) atomicAdd(dst + q, y);
+        }
+    }
+}
+
+// grid: (blocks over V, G)
+__global__ void __launch_bounds__(256) k_residual(size_t V, int M, const float* mom, float* prev,
+                                                  double* res) {
+    const int g = blockIdx.y;
+    double x[2] = {0.0, 0.0};
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (size_t)gridDim.x * blockDim.x) {
+        const float cur = mom[((size_t)g * V + v) * M];
+        const float old = prev[(size_t)g * V + v];
+        const double d = (double)cur - (double)old;
+        x[0] += d * d;
+        x[1] += (double)cur * (double)cur;
+        prev[(size_t)g * V + v] = cur;
+    }
+    block_reduce_add<2>(x, res + 2 * g);
+}
+
+__global__ void __launch_bounds__(256) k_balance(size_t V, int G, int M, const uint8_t* mat,
+                                                 const float* rho, const float* sigt, const float* src,
+                                                 const float* mom, double vol, double* bal) {
+    const int g = blockIdx.y;
+    double x[2] = {0.0, 0.0};
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (size_t)gridDim.x * blockDim.x) {
+        const double s00 = src[((size_t)g * V + v) * M];
+        const double p00 = mom[((size_t)g * V + v) * M];
+        const double st = (double)rho[v] * (double)sigt[mat[v] * G + g];
+        x[0] += vol * s00;
+        x[1] += vol * st * p00;
+    }
+    block_reduce_add<2>(x, bal + 2 * g);
+}
+
+__global__ void __launch_bounds__(256) k_dose(size_t V, int G, int M, const uint8_t* mat, const float* rho,
+                                              const double* k, const float* phi_u, const float* mom,
+                                              double* dose) {
+    const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    const int m = mat[v];
+    double acc = 0.0;
+    for (int g = 0; g < G; ++g) {
+        const double phi = (double)phi_u[(size_t)g * V + v] + (double)mom[((size_t)g * V + v) * M];
+        acc += k[m * G + g] * phi;
+    }
+    dose[v] = acc * (double)rho[v];
+}
+
+__global__ void __launch_bounds__(256) k_extract(size_t V, int G, int M, int which, const float* phi_u,
+                                                 const float* mom, float* out) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= V * G) return;
+    float x = 0.0f;
+    if (which & 1) x += phi_u[t];
+    if (which & 2) x += mom[t * M];
+    out[t] = x;
+}
+
+unsigned blocks_for(size_t n, int bs, unsigned cap = 0) {
+    size_t b = (n + bs - 1) / bs;
+    if (cap && b > cap) b = cap;
+    return (unsigned)(b ? b : 1);
+}
+
+}  // namespace
+
+cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s) {
+    k_scatter<<<blocks_for(a.V * a.M, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual(size_t V, int G, int M, const float* mom, float* prev, double* res,
+                            cudaStream_t s) {
+    dim3 grid(blocks_for(V, 256, 296), G);
+    k_residual<<<grid, 256, 0, s>>>(V, M, mom, prev, res);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_balance(size_t V, int G, int M, const uint8_t* mat, const float* rho, const float* sigt,
+                           const float* src, const float* mom, double vol, double* bal, cudaStream_t s) {
+    dim3 grid(blocks_for(V, 256, 296), G);
+    k_balance<<<grid, 256, 0, s>>>(V, G, M, mat, rho, sigt, src, mom, vol, bal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dose(size_t V, int G, int M, const uint8_t* mat, const float* rho, const double* k,
+                        const float* phi_u, const float* mom, double* dose, cudaStream_t s) {
+    k_dose<<<blocks_for(V, 256), 256, 0, s>>>(V, G, M, mat, rho, k, phi_u, mom, dose);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_extract(size_t V, int G, int M, int which, const float* phi_u, const float* mom,
+                           float* out, cudaStream_t s) {
+    k_extract<<<blocks_for(V * G, 256), 256, 0, s>>>(V, G, M, which, phi_u, mom, out);
+    return cudaGetLastError();
+}
+
+}  // namespace doctors

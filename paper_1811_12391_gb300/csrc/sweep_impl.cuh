@@ -1,0 +1,217 @@
+// Step-differenced discrete-ordinates sweep (Eq. 2, vacuum boundaries) as
+// diagonal wavefronts over the eight octants.
+//
+// For a direction Omega_n of octant o and group g, the step scheme sets the
+// outgoing face fluxes of a cell equal to its cell-average angular fluence:
+//   psi = (q_n + c_x psi_x + c_y psi_y + c_z psi_z) / (sigma_t + c_x + c_y + c_z),
+//   c_q = |Omega_q| / d_q,  q_n = sum_lm (2l+1)/(4 pi) R_lm(Omega_n) s_lm,
+// with psi_q the fluence of the upwind neighbour along q (0 outside the mesh).
+// A cell depends only on its three upwind neighbours, so all cells on a
+// hyperplane i' + j' + k' = h (indices reflected into the octant's sweep
+// order) are independent.
+//
+// Decomposition (one launch per tile diagonal, all octants and groups in the
+// launch):
+//   * the mesh is cut into tiles of tx x ty columns spanning all of z; tiles
+//     on one anti-diagonal of the octant's reflected tile grid form a stage;
+//   * a CTA owns one (tile, group, octant, block of `ab` directions); thread
+//     (li, lj) owns column (li, lj) of the tile and walks it in z;
+//   * inside the CTA the hyperplane h = li + lj + k' advances one step per
+//     __syncthreads(); the x/y upwind fluxes of the previous step come from a
+//     double-buffered shared-memory plane, the z upwind flux stays in a
+//     register;
+//   * fluxes leaving the tile through its downwind x/y faces go to global
+//     face buffers read by the next stage;
+//   * each thread accumulates the moments sum_n w_n R_lm(Omega_n) psi_n of
+//     its cell over its directions (Eq. 3 for lm = 00) and adds them to the
+//     global moments with one vector atomic per 4 moments;
+//   * outgoing current through the mesh boundary is accumulated in FP64 for
+//     the balance check.
+#pragma once
+
+#include "doctors_internal.h"
+
+namespace doctors {
+
+template <int M>
+__device__ __forceinline__ void load_moments(const float* p, float (&s)[M]) {
+    if constexpr (M % 4 == 0) {
+        const float4* p4 = reinterpret_cast<const float4*>(p);
+#pragma unroll
+        for (int q = 0; q < M / 4; ++q) {
+            const float4 t = __ldg(p4 + q);
+            s[4 * q] = t.x; s[4 * q + 1] = t.y; s[4 * q + 2] = t.z; s[4 * q + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < M; ++q) s[q] = __ldg(p + q);
+    }
+}
+
+template <int M>
+__device__ __forceinline__ void add_moments(float* p, const float (&a)[M]) {
+    if constexpr (M % 4 == 0) {
+        float4* p4 = reinterpret_cast<float4*>(p);
+#pragma unroll
+        for (int q = 0; q < M / 4; ++q)
+            atomicAdd(p4 + q, make_float4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]));
+    } else {
+#pragma unroll
+        for (int q = 0; q < M; ++q) atomicAdd(p + q, a[q]);
+    }
+}
+
+template <int AB, int M>
+__global__ void __launch_bounds__(512) k_sweep(const SweepArgs a) {
+    extern __shared__ float sm[];
+    const int T = a.tx * a.ty;
+    float* buf = sm;                        // [2][AB][T]
+    float* mop_s = buf + 2 * AB * T;        // [AB][M]
+    float* dop_s = mop_s + AB * M;          // [AB][M]
+    float* coef_s = dop_s + AB * M;         // [AB][8]
+    float* sigt_s = coef_s + AB * 8;        // [nmat]
+
+    const int o = blockIdx.z / a.nab;       // sweep octant
+    const int blk = blockIdx.z % a.nab;
+    const int g = blockIdx.y;
+    const int a_lo = max(0, a.stage - (a.nty - 1));
+    const int at = a_lo + blockIdx.x;       // reflected tile coordinates
+    const int bt = a.stage - at;
+    const int sx = (o & 1) ? -1 : 1, sy = (o & 2) ? -1 : 1, sz = (o & 4) ? -1 : 1;
+    // the adjoint sweeps direction n along -Omega_n
+    const int nbase = (a.reverse ? (o ^ 7) : o) * a.A8 + blk * AB;
+    const int slot0 = blk * AB;             // direction slot within the octant (face buffers)
+
+    for (int t = threadIdx.x; t < AB * M; t += blockDim.x) {
+        mop_s[t] = a.mop[(size_t)nbase * M + t];
+        dop_s[t] = a.dop[(size_t)nbase * M + t];
+    }
+    for (int t = threadIdx.x; t < AB * 8; t += blockDim.x) coef_s[t] = a.coef[(size_t)nbase * 8 + t];
+    for (int t = threadIdx.x; t < a.nmat; t += blockDim.x) sigt_s[t] = a.sigt[t * a.G + g];
+    __syncthreads();
+
+    const int tid = threadIdx.x;
+    const int li = tid % a.tx, lj = tid / a.tx;
+    const int ir = at * a.tx + li, jr = bt * a.ty + lj;
+    const bool col = ir < a.nx && jr < a.ny;
+    const int i = sx > 0 ? ir : a.nx - 1 - ir;
+    const int j = sy > 0 ? jr : a.ny - 1 - jr;
+    const size_t V = (size_t)a.nx * a.ny * a.nz;
+    const size_t gV = (size_t)g * V;
+
+    // face-buffer bases (reflected coordinates, kr fastest)
+    const size_t xf_stride = (size_t)(a.ntx > 1 ? a.ntx - 1 : 0) * a.ny * a.nz;
+    const size_t yf_stride = (size_t)(a.nty > 1 ? a.nty - 1 : 0) * a.nx * a.nz;
+
+    float zc[AB];
+#pragma unroll
+    for (int q = 0; q < AB; ++q) zc[q] = 0.0f;
+    float lk = 0.0f;
+
+    const int hmax = a.tx + a.ty + a.nz - 3;
+    for (int h = 0; h <= hmax; ++h) {
+        const int kr = h - li - lj;
+        const int cb = h & 1, pb = cb ^ 1;
+        if (col && kr >= 0 && kr < a.nz) {
+            const int k = sz > 0 ? kr : a.nz - 1 - kr;
+            const size_t v = ((size_t)k * a.ny + j) * a.nx + i;
+            float s[M];
+            load_moments<M>(a.src + (gV + v) * M, s);
+            const float sig = __ldg(a.rho + v) * sigt_s[__ldg(a.mat + v)];
+            float acc[M];
+#pragma unroll
+            for (int m = 0; m < M; ++m) acc[m] = 0.0f;
+#pragma unroll
+            for (int q = 0; q < AB; ++q) {
+                float qn = 0.0f;
+#pragma unroll
+                for (int m = 0; m < M; ++m) qn = fmaf(mop_s[q * M + m], s[m], qn);
+                float px, py;
+                if (li > 0) {
+                    px = buf[(pb * AB + q) * T + tid - 1];
+                } else if (at > 0) {
+                    const size_t fb = (((size_t)o * a.A8 + slot0 + q) * a.G + g) * xf_stride;
+                    px = a.xface[fb + ((size_t)(at - 1) * a.ny + jr) * a.nz + kr];
+                } else {
+                    px = 0.0f;
+                }
+                if (lj > 0) {
+                    py = buf[(pb * AB + q) * T + tid - a.tx];
+                } else if (bt > 0) {
+                    const size_t fb = (((size_t)o * a.A8 + slot0 + q) * a.G + g) * yf_stride;
+                    py = a.yface[fb + ((size_t)(bt - 1) * a.nx + ir) * a.nz + kr];
+                } else {
+                    py = 0.0f;
+                }
+                const float* c = coef_s + q * 8;
+                const float num = fmaf(c[2], zc[q], fmaf(c[1], py, fmaf(c[0], px, qn)));
+                const float psi = __fdividef(num, sig + c[3]);
+                buf[(cb * AB + q) * T + tid] = psi;
+                zc[q] = psi;
+                if (li == a.tx - 1 && at < a.ntx - 1) {
+                    const size_t fb = (((size_t)o * a.A8 + slot0 + q) * a.G + g) * xf_stride;
+                    a.xface[fb + ((size_t)at * a.ny + jr) * a.nz + kr] = psi;
+                }
+                if (lj == a.ty - 1 && bt < a.nty - 1) {
+                    const size_t fb = (((size_t)o * a.A8 + slot0 + q) * a.G + g) * yf_stride;
+                    a.yface[fb + ((size_t)bt * a.nx + ir) * a.nz + kr] = psi;
+                }
+                if (ir == a.nx - 1) lk = fmaf(c[4], psi, lk);
+                if (jr == a.ny - 1) lk = fmaf(c[5], psi, lk);
+                if (kr == a.nz - 1) lk = fmaf(c[6], psi, lk);
+#pragma unroll
+                for (int m = 0; m < M; ++m) acc[m] = fmaf(dop_s[q * M + m], psi, acc[m]);
+            }
+            add_moments<M>(a.mom + (gV + v) * M, acc);
+        }
+        __syncthreads();
+    }
+    // boundary leakage of this CTA, reduced per warp in FP64
+    double dl = (double)lk;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) dl += __shfl_down_sync(0xffffffffu, dl, off);
+    if ((tid & 31) == 0 && dl != 0.0) atomicAdd(a.leak + g, dl);
+}
+
+inline size_t sweep_smem_bytes(int ab, int M, int T, int nmat) {
+    return sizeof(float) * (size_t)(2 * ab * T + 2 * ab * M + 8 * ab + nmat);
+}
+
+template <int M>
+cudaError_t launch_sweep_m(const SweepArgs& a, cudaStream_t s) {
+    const int a_lo = a.stage - (a.nty - 1) > 0 ? a.stage - (a.nty - 1) : 0;
+    const int a_hi = a.stage < a.ntx - 1 ? a.stage : a.ntx - 1;
+    const int ntiles = a_hi - a_lo + 1;
+    if (ntiles <= 0) return cudaSuccess;
+    const int T = a.tx * a.ty;
+    dim3 grid(ntiles, a.G, 8 * a.nab);
+    const size_t smem = sweep_smem_bytes(a.ab, M, T, a.nmat);
+#define DOCTORS_SWEEP_CASE(AB)                                                                  \
+    case AB: {                                                                                  \
+        auto kern = k_sweep<AB, M>;                                                             \
+        if (smem > 48 * 1024) {                                                                 \
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                                 (int)smem);                                    \
+            if (e != cudaSuccess) return e;                                                     \
+        }                                                                                       \
+        kern<<<grid, T, smem, s>>>(a);                                                          \
+        break;                                                                                  \
+    }
+    switch (a.ab) {
+        DOCTORS_SWEEP_CASE(1)
+        DOCTORS_SWEEP_CASE(2)
+        DOCTORS_SWEEP_CASE(3)
+        DOCTORS_SWEEP_CASE(4)
+        DOCTORS_SWEEP_CASE(5)
+        DOCTORS_SWEEP_CASE(6)
+        DOCTORS_SWEEP_CASE(7)
+        DOCTORS_SWEEP_CASE(9)
+        DOCTORS_SWEEP_CASE(10)
+        DOCTORS_SWEEP_CASE(12)
+        default: return cudaErrorInvalidValue;
+    }
+#undef DOCTORS_SWEEP_CASE
+    return cudaGetLastError();
+}
+
+}  // namespace doctors

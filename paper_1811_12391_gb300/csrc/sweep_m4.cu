@@ -1,0 +1,6 @@
+// Instantiations of the octant wavefront sweep for 4 flux moment(s) per cell.
+#include "sweep_impl.cuh"
+
+namespace doctors {
+cudaError_t launch_sweep_m4_entry(const SweepArgs& a, cudaStream_t s) { return launch_sweep_m<4>(a, s); }
+}  // namespace doctors

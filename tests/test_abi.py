@@ -1,0 +1,93 @@
+"""The C-ABI library loads, exports every entry point include/doctors.h
+declares, and its host-only logic (quadrature tables, argument validation)
+behaves; no GPU work is issued here."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+from scipy import special
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1811_12391_gb300 import build as b
+    b.build()
+    from paper_1811_12391_gb300 import _lib
+    return _lib
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "doctors.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(doctors_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("doctors_create_problem", "doctors_set_materials", "doctors_set_source", "doctors_solve",
+              "doctors_dose", "doctors_adjoint_solve", "doctors_destroy", "doctors_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    L = lib.lib()
+    for n in _declared():
+        assert hasattr(L, n), n
+    bound = {s[0] for s in lib.SIGNATURES}
+    assert set(_declared()) <= bound
+
+
+@pytest.mark.parametrize("N,L", [(2, 0), (4, 1), (6, 2), (8, 3), (12, 3), (16, 3)])
+def test_library_quadrature_pins(lib, N, L):
+    from paper_1811_12391_gb300.solver import quadrature
+    dirs, w, R = quadrature(N, L)
+    assert dirs.shape == (N * (N + 2), 3)
+    assert np.all(w > 0)
+    assert abs(w.sum() - 4 * math.pi) < 1e-12
+    np.testing.assert_allclose(np.linalg.norm(dirs, axis=1), 1, atol=1e-6)
+    # degree-2L products integrate exactly where the set allows (2L <= N-1)
+    if 2 * L <= N - 1:
+        ls = np.array([l for l in range(L + 1) for _ in range(2 * l + 1)])
+        np.testing.assert_allclose((R * w[:, None]).T @ R, np.diag(4 * math.pi / (2 * ls + 1)), atol=1e-12)
+    # addition theorem against scipy's Legendre polynomials
+    cos = dirs @ dirs.T
+    for l in range(L + 1):
+        sl = slice(l * l, (l + 1) ** 2)
+        np.testing.assert_allclose(R[:, sl] @ R[:, sl].T, special.eval_legendre(l, cos), atol=1e-12)
+
+
+def test_quadrature_rejects_bad_orders(lib):
+    n = ctypes.c_int()
+    assert lib.doctors_quadrature(5, 1, None, None, None, ctypes.byref(n)) == lib.DOCTORS_ERR_INVALID_ARG
+    assert "sn_order" in lib.last_error()
+    assert lib.doctors_quadrature(8, 4, None, None, None, ctypes.byref(n)) == lib.DOCTORS_ERR_INVALID_ARG
+
+
+def test_create_rejects_bad_arguments_before_touching_the_device(lib):
+    C = lib
+    mesh = C.doctors_mesh(0, 4, 4, 1.0, 1.0, 1.0, (ctypes.c_double * 3)(0, 0, 0))
+    opt = C.doctors_options()
+    opt.groups, opt.sn_order, opt.legendre, opt.tol, opt.max_iters = 4, 4, 1, 1e-6, 10
+    h = ctypes.c_void_p()
+    assert C.doctors_create_problem(ctypes.byref(mesh), ctypes.byref(opt), None, ctypes.byref(h)) == \
+        C.DOCTORS_ERR_INVALID_ARG
+    mesh.nx = 4
+    opt.sn_order = 3
+    assert C.doctors_create_problem(ctypes.byref(mesh), ctypes.byref(opt), None, ctypes.byref(h)) == \
+        C.DOCTORS_ERR_INVALID_ARG
+    opt.sn_order = 4
+    opt.legendre = 5
+    assert C.doctors_create_problem(ctypes.byref(mesh), ctypes.byref(opt), None, ctypes.byref(h)) == \
+        C.DOCTORS_ERR_INVALID_ARG
+    opt.legendre = 1
+    opt.reserved[0] = 1
+    assert C.doctors_create_problem(ctypes.byref(mesh), ctypes.byref(opt), None, ctypes.byref(h)) == \
+        C.DOCTORS_ERR_INVALID_ARG
+    assert h.value is None
+    assert C.doctors_solve(None, None) == C.DOCTORS_ERR_INVALID_ARG
+    C.doctors_destroy(None)

@@ -1,0 +1,159 @@
+"""Parity of the full forward solve (ray trace, first-collision source,
+collided source iteration with octant wavefront sweeps, dose) against the
+FP64 oracle, plus properties that hold at any size."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import solver as osv
+from synth import phantoms as ph
+from tests.parity import REL_TOL, max_rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dp():
+    from paper_1811_12391_gb300 import build
+    build()
+    from paper_1811_12391_gb300.solver import DoctorsProblem
+    return DoctorsProblem
+
+
+def _compare(d, p, sol, tag):
+    d.solve()
+    phi_u = d.fluence_host(0)
+    phi_c = d.fluence_host(1)
+    phi = d.fluence_host(2)
+    dose = d.dose_host(p.k_dep)
+    errs = {
+        "phi_u": max_rel(phi_u, sol.phi_u),
+        "phi_c": max_rel(phi_c, sol.phi_c[:, 0, :]),
+        "phi": max_rel(phi, sol.phi),
+        "dose": max_rel(dose, osv.dose(p, sol.phi)),
+    }
+    for k, e in errs.items():
+        assert e <= REL_TOL, (tag, k, e, errs)
+    assert d.result["balance_rel"] < 1e-5
+    return errs
+
+
+def test_tiny_cube_full(dp):
+    """16^3 water cube, S4 P1, 4 groups (the oracle finishes in seconds)."""
+    p = ph.tiny_cube()
+    sol = osv.solve(p, tol=1e-11)
+    d = dp(p, tol=1e-6, max_iters=400)
+    _compare(d, p, sol, "tiny_cube")
+    d.close()
+
+
+@pytest.mark.parametrize("tile,ab", [((16, 16), 0), ((8, 4), 5), ((5, 7), 2)])
+def test_ragged_multitile_cylinder(dp, tile, ab):
+    """Several sweep tiles with ragged tails in x and y, S8 P3."""
+    p = ph.water_cylinder(nx=36, ny=28, nz=10, dx=1.0, dy=1.25, dz=1.1, diameter=30.0, G=5, sn=8, L=3)
+    sol = osv.solve(p, tol=1e-11)
+    d = dp(p, tol=1e-6, max_iters=400, tile=tile, angles_per_block=ab)
+    _compare(d, p, sol, f"cylinder tile={tile} ab={ab}")
+    d.close()
+
+
+def test_abdomen_s16_multi_angle_block(dp):
+    """Heterogeneous abdomen-like phantom, S16 (three direction blocks per
+    octant), P3, five materials."""
+    p = ph.abdomen(nx=32, ny=32, nz=6, d=1.0, dz=2.0, G=3, sn=16, L=3)
+    sol = osv.solve(p, tol=1e-11)
+    d = dp(p, tol=1e-6, max_iters=400)
+    _compare(d, p, sol, "abdomen S16")
+    d.close()
+
+
+def test_p0_and_p2_moment_counts(dp):
+    for L in (0, 2):
+        p = ph.water_cylinder(nx=12, ny=12, nz=6, dx=1.5, dy=1.5, dz=1.5, diameter=16, G=3, sn=6, L=L)
+        sol = osv.solve(p, tol=1e-11)
+        d = dp(p, tol=1e-6, max_iters=400)
+        _compare(d, p, sol, f"L={L}")
+        d.close()
+
+
+def test_infinite_medium_volume_source(dp):
+    p = ph.infinite_medium_cube(n=16, G=3, sn=4, L=0)
+    d = dp(p, tol=1e-6, max_iters=400)
+    d.solve()
+    phi = d.fluence_host(2)
+    Q = p.sources[0].weight * p.sources[0].spectrum
+    s0, st = p.sigma_s[0, 0], p.sigma_t[0]
+    ref = np.zeros(p.G)
+    for g in range(p.G):
+        ref[g] = (Q[g] + sum(s0[gp, g] * ref[gp] for gp in range(g))) / (st[g] - s0[g, g])
+    v = (8 * 16 + 8) * 16 + 8
+    np.testing.assert_allclose(phi[:, v], ref, rtol=1e-5)
+    d.close()
+
+
+def test_degenerate_meshes(dp):
+    """Single voxel, single column and single plane meshes."""
+    for dims in ((1, 1, 1), (1, 1, 7), (5, 1, 1), (4, 6, 1)):
+        p = ph.tiny_cube(n=2)
+        p.nx, p.ny, p.nz = dims
+        V = p.V
+        p.mat = np.zeros(V, np.uint8)
+        p.density = np.ones(V, np.float32)
+        p.origin = -0.5 * np.array(dims, float)
+        sol = osv.solve(p, tol=1e-12)
+        d = dp(p, tol=1e-6, max_iters=400)
+        _compare(d, p, sol, f"dims={dims}")
+        d.close()
+
+
+def test_zero_weight_source_gives_zero(dp):
+    p = ph.tiny_cube(n=6)
+    p.sources[0].weight = 0.0
+    d = dp(p, tol=1e-6, max_iters=10)
+    r = d.solve()
+    assert r["converged"] == 1
+    assert np.all(d.fluence_host(2) == 0)
+    d.close()
+
+
+def test_errors_are_reported(dp):
+    from paper_1811_12391_gb300 import _lib as C
+    p = ph.tiny_cube(n=4)
+    d = dp(p, tol=1e-6, max_iters=10)
+    with pytest.raises(C.DoctorsError) as e:
+        d.dose_host(p.k_dep)          # before solve
+    assert e.value.code == C.DOCTORS_ERR_STATE
+    bad = ph.tiny_cube(n=4)
+    bad.sources[0].pos = np.array([0.1, 0.2, 0.3])       # inside the mesh
+    with pytest.raises(C.DoctorsError) as e:
+        d.set_sources(bad.sources)
+    assert e.value.code == C.DOCTORS_ERR_INVALID_ARG
+    ss = p.sigma_s.copy()
+    ss[0, 0, 2, 1] = 0.01                                   # upscatter
+    with pytest.raises(C.DoctorsError) as e:
+        d.set_materials(p.mat, p.density, p.sigma_t, ss)
+    assert e.value.code == C.DOCTORS_ERR_INVALID_ARG
+    m = p.mat.copy()
+    m[3] = 7
+    with pytest.raises(C.DoctorsError):
+        d.set_materials(m, p.density, p.sigma_t, p.sigma_s)
+    d.close()
+
+
+def test_water_cylinder_full_size_properties(dp):
+    """The 64x64x32 S8 P3 19-group cylinder at full size: converged,
+    particle balance, and mirror symmetry in x and z of the collided and
+    total fluence (source on the -y axis at the axial centre)."""
+    p = ph.water_cylinder()
+    d = dp(p, tol=1e-6, max_iters=500)
+    r = d.solve()
+    assert r["converged"] == 1 and r["balance_rel"] < 1e-5
+    for which in (1, 2):
+        a = d.fluence_host(which).reshape(p.G, p.nz, p.ny, p.nx).astype(np.float64)
+        for g in range(p.G):
+            m = np.abs(a[g]).max()
+            sel = np.abs(a[g]) > 1e-6 * m
+            for flip in (a[g][:, :, ::-1], a[g][::-1, :, :]):
+                assert (np.abs(a[g] - flip)[sel] / np.abs(a[g])[sel]).max() < 2e-4
+    d.close()
