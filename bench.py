@@ -183,7 +183,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_1811_12391_gb300 import build as build_lib
+    from paper_1811_12391_gb300.build import build as build_lib
     build_lib()
     from paper_1811_12391_gb300.solver import DoctorsProblem
     from synth import phantoms as ph

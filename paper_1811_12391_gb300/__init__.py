@@ -11,14 +11,11 @@ marshals arguments and uses PyTorch for device memory and streams.
 from . import _lib  # noqa: F401
 from ._lib import DoctorsError  # noqa: F401
 
-__all__ = ["DoctorsError", "DoctorsProblem", "quadrature", "build"]
+__all__ = ["DoctorsError", "DoctorsProblem", "quadrature"]
 
 
 def __getattr__(name):
     if name in ("DoctorsProblem", "quadrature"):
         from . import solver
         return getattr(solver, name)
-    if name == "build":
-        from .build import build
-        return build
     raise AttributeError(name)

@@ -15,8 +15,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_1811_12391_gb300 import build as b
-    b.build()
+    from paper_1811_12391_gb300.build import build
+    build()
     from paper_1811_12391_gb300 import _lib
     return _lib
 

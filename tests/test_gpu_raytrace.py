@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 
 @pytest.fixture(scope="module")
 def dp():
-    from paper_1811_12391_gb300 import build
+    from paper_1811_12391_gb300.build import build
     build()
     from paper_1811_12391_gb300.solver import DoctorsProblem
     return DoctorsProblem
