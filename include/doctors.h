@@ -82,7 +82,7 @@ typedef struct doctors_options {
     double tol;              /* stop when, in every group, ||phi00_new - phi00_old||_2 / ||phi00_new||_2 < tol;
                                 values below 1e-6 are raised to 1e-6 (FP32 sweep) */
     int max_iters;           /* source-iteration cap, >= 1 */
-    int tile_x, tile_y;      /* sweep tile in voxels (0 = default 16 x 16); tile_x*tile_y <= 512 */
+    int tile_x, tile_y;      /* sweep tile in voxels (0 = default 16 x 16); tile_x*tile_y <= 256 */
     int angles_per_block;    /* directions per sweep block (0 = default); must divide N(N+2)/8 */
     int reserved[8];         /* must be zero */
 } doctors_options;

@@ -312,13 +312,14 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
         delete p;
         return code;
     };
-    if (p->tx * p->ty > 512 || p->tx < 1 || p->ty < 1) return fail(DOCTORS_ERR_INVALID_ARG, "tile_x * tile_y must be 1..512");
+    if (p->tx * p->ty > 256 || p->tx < 1 || p->ty < 1) return fail(DOCTORS_ERR_INVALID_ARG, "tile_x * tile_y must be 1..256");
     if (p->A8 % p->ab != 0 || !sweep_supported(p->ab, p->M))
         return fail(DOCTORS_ERR_INVALID_ARG, "angles_per_block must divide N(N+2)/8 and be one of 1,2,3,4,5,6,7,9,10,12");
     p->nab = p->A8 / p->ab;
     p->ntx = (p->nx + p->tx - 1) / p->tx;
     p->nty = (p->ny + p->ty - 1) / p->ty;
-    const size_t smem = sizeof(float) * (size_t)(2 * p->ab * p->tx * p->ty + 2 * p->ab * p->M + 8 * p->ab + kMaxMat);
+    const size_t smem = sizeof(float) * (size_t)(2 * p->ab * p->tx * p->ty + p->ab * (p->tx + p->ty) * p->nz +
+                                                 2 * p->ab * p->M + 8 * p->ab + kMaxMat);
     if (smem > 227 * 1024) return fail(DOCTORS_ERR_INVALID_ARG, "sweep tile needs more than 227 KB of shared memory");
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) return fail(DOCTORS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));

@@ -19,9 +19,12 @@
 //   * inside the CTA the hyperplane h = li + lj + k' advances one step per
 //     __syncthreads(); the x/y upwind fluxes of the previous step come from a
 //     double-buffered shared-memory plane, the z upwind flux stays in a
-//     register;
+//     register, and the cell's source moments are prefetched one step ahead;
 //   * fluxes leaving the tile through its downwind x/y faces go to global
-//     face buffers read by the next stage;
+//     face buffers; the next stage loads its incoming face strips into
+//     shared memory once, before its first step;
+//   * the group is the slowest grid dimension, so the CTAs resident at one
+//     time work on few groups and their moment slabs stay in L2;
 //   * each thread accumulates the moments sum_n w_n R_lm(Omega_n) psi_n of
 //     its cell over its directions (Eq. 3 for lm = 00) and adds them to the
 //     global moments with one vector atomic per 4 moments;
@@ -62,18 +65,20 @@ __device__ __forceinline__ void add_moments(float* p, const float (&a)[M]) {
 }
 
 template <int AB, int M>
-__global__ void __launch_bounds__(512) k_sweep(const SweepArgs a) {
+__global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs a) {
     extern __shared__ float sm[];
     const int T = a.tx * a.ty;
-    float* buf = sm;                        // [2][AB][T]
-    float* mop_s = buf + 2 * AB * T;        // [AB][M]
+    float* buf = sm;                        // [2][AB][T]    previous/current hyperplane
+    float* xin = buf + 2 * AB * T;          // [AB][ty][nz]  incoming x-face strip
+    float* yin = xin + AB * a.ty * a.nz;    // [AB][tx][nz]  incoming y-face strip
+    float* mop_s = yin + AB * a.tx * a.nz;  // [AB][M]
     float* dop_s = mop_s + AB * M;          // [AB][M]
     float* coef_s = dop_s + AB * M;         // [AB][8]
     float* sigt_s = coef_s + AB * 8;        // [nmat]
 
-    const int o = blockIdx.z / a.nab;       // sweep octant
-    const int blk = blockIdx.z % a.nab;
-    const int g = blockIdx.y;
+    const int g = blockIdx.z;               // group slowest: resident CTAs share a few groups in L2
+    const int o = blockIdx.y / a.nab;       // sweep octant
+    const int blk = blockIdx.y % a.nab;
     const int a_lo = max(0, a.stage - (a.nty - 1));
     const int at = a_lo + blockIdx.x;       // reflected tile coordinates
     const int bt = a.stage - at;
@@ -81,6 +86,8 @@ __global__ void __launch_bounds__(512) k_sweep(const SweepArgs a) {
     // the adjoint sweeps direction n along -Omega_n
     const int nbase = (a.reverse ? (o ^ 7) : o) * a.A8 + blk * AB;
     const int slot0 = blk * AB;             // direction slot within the octant (face buffers)
+    const size_t xf_stride = (size_t)(a.ntx > 1 ? a.ntx - 1 : 0) * a.ny * a.nz;
+    const size_t yf_stride = (size_t)(a.nty > 1 ? a.nty - 1 : 0) * a.nx * a.nz;
 
     for (int t = threadIdx.x; t < AB * M; t += blockDim.x) {
         mop_s[t] = a.mop[(size_t)nbase * M + t];
@@ -88,6 +95,31 @@ __global__ void __launch_bounds__(512) k_sweep(const SweepArgs a) {
     }
     for (int t = threadIdx.x; t < AB * 8; t += blockDim.x) coef_s[t] = a.coef[(size_t)nbase * 8 + t];
     for (int t = threadIdx.x; t < a.nmat; t += blockDim.x) sigt_s[t] = a.sigt[t * a.G + g];
+    // incoming face strips (contiguous in the face buffers), zero on the mesh boundary
+    {
+        const int nxs = AB * a.ty * a.nz;
+        for (int t = threadIdx.x; t < nxs; t += blockDim.x) {
+            const int q = t / (a.ty * a.nz), r = t % (a.ty * a.nz);
+            const int jr = bt * a.ty + r / a.nz;
+            float val = 0.0f;
+            if (at > 0 && jr < a.ny) {
+                const size_t fb = (((size_t)o * a.A8 + slot0 + q) * a.G + g) * xf_stride;
+                val = a.xface[fb + (size_t)(at - 1) * a.ny * a.nz + (size_t)bt * a.ty * a.nz + r];
+            }
+            xin[t] = val;
+        }
+        const int nys = AB * a.tx * a.nz;
+        for (int t = threadIdx.x; t < nys; t += blockDim.x) {
+            const int q = t / (a.tx * a.nz), r = t % (a.tx * a.nz);
+            const int ir = at * a.tx + r / a.nz;
+            float val = 0.0f;
+            if (bt > 0 && ir < a.nx) {
+                const size_t fb = (((size_t)o * a.A8 + slot0 + q) * a.G + g) * yf_stride;
+                val = a.yface[fb + (size_t)(bt - 1) * a.nx * a.nz + (size_t)at * a.tx * a.nz + r];
+            }
+            yin[t] = val;
+        }
+    }
     __syncthreads();
 
     const int tid = threadIdx.x;
@@ -98,26 +130,46 @@ __global__ void __launch_bounds__(512) k_sweep(const SweepArgs a) {
     const int j = sy > 0 ? jr : a.ny - 1 - jr;
     const size_t V = (size_t)a.nx * a.ny * a.nz;
     const size_t gV = (size_t)g * V;
-
-    // face-buffer bases (reflected coordinates, kr fastest)
-    const size_t xf_stride = (size_t)(a.ntx > 1 ? a.ntx - 1 : 0) * a.ny * a.nz;
-    const size_t yf_stride = (size_t)(a.nty > 1 ? a.nty - 1 : 0) * a.nx * a.nz;
+    const size_t plane = (size_t)a.nx * a.ny;
+    const size_t vcol = (size_t)j * a.nx + i;      // voxel index of k = 0 in this column
+    const bool xout = li == a.tx - 1 && at < a.ntx - 1;
+    const bool yout = lj == a.ty - 1 && bt < a.nty - 1;
+    float* xo = a.xface + (((size_t)o * a.A8 + slot0) * a.G + g) * xf_stride + ((size_t)at * a.ny + jr) * a.nz;
+    float* yo = a.yface + (((size_t)o * a.A8 + slot0) * a.G + g) * yf_stride + ((size_t)bt * a.nx + ir) * a.nz;
+    const size_t xo_q = (size_t)a.G * xf_stride, yo_q = (size_t)a.G * yf_stride;
 
     float zc[AB];
 #pragma unroll
     for (int q = 0; q < AB; ++q) zc[q] = 0.0f;
     float lk = 0.0f;
 
+    // software pipeline: the source moments and material of the next cell
+    // are loaded one hyperplane step ahead
+    float sn[M];
+    float sig_n = 0.0f;
+    auto prefetch = [&](int kr) {
+        if (col && kr >= 0 && kr < a.nz) {
+            const int k = sz > 0 ? kr : a.nz - 1 - kr;
+            const size_t v = (size_t)k * plane + vcol;
+            load_moments<M>(a.src + (gV + v) * M, sn);
+            sig_n = __ldg(a.rho + v) * sigt_s[__ldg(a.mat + v)];
+        }
+    };
+    prefetch(-li - lj);
+
     const int hmax = a.tx + a.ty + a.nz - 3;
     for (int h = 0; h <= hmax; ++h) {
         const int kr = h - li - lj;
         const int cb = h & 1, pb = cb ^ 1;
-        if (col && kr >= 0 && kr < a.nz) {
+        const bool act = col && kr >= 0 && kr < a.nz;
+        float s[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) s[m] = sn[m];
+        const float sig = sig_n;
+        prefetch(kr + 1);
+        if (act) {
             const int k = sz > 0 ? kr : a.nz - 1 - kr;
-            const size_t v = ((size_t)k * a.ny + j) * a.nx + i;
-            float s[M];
-            load_moments<M>(a.src + (gV + v) * M, s);
-            const float sig = __ldg(a.rho + v) * sigt_s[__ldg(a.mat + v)];
+            const size_t v = (size_t)k * plane + vcol;
             float acc[M];
 #pragma unroll
             for (int m = 0; m < M; ++m) acc[m] = 0.0f;
@@ -126,36 +178,15 @@ __global__ void __launch_bounds__(512) k_sweep(const SweepArgs a) {
                 float qn = 0.0f;
 #pragma unroll
                 for (int m = 0; m < M; ++m) qn = fmaf(mop_s[q * M + m], s[m], qn);
-                float px, py;
-                if (li > 0) {
-                    px = buf[(pb * AB + q) * T + tid - 1];
-                } else if (at > 0) {
-                    const size_t fb = (((size_t)o * a.A8 + slot0 + q) * a.G + g) * xf_stride;
-                    px = a.xface[fb + ((size_t)(at - 1) * a.ny + jr) * a.nz + kr];
-                } else {
-                    px = 0.0f;
-                }
-                if (lj > 0) {
-                    py = buf[(pb * AB + q) * T + tid - a.tx];
-                } else if (bt > 0) {
-                    const size_t fb = (((size_t)o * a.A8 + slot0 + q) * a.G + g) * yf_stride;
-                    py = a.yface[fb + ((size_t)(bt - 1) * a.nx + ir) * a.nz + kr];
-                } else {
-                    py = 0.0f;
-                }
+                const float px = li > 0 ? buf[(pb * AB + q) * T + tid - 1] : xin[(q * a.ty + lj) * a.nz + kr];
+                const float py = lj > 0 ? buf[(pb * AB + q) * T + tid - a.tx] : yin[(q * a.tx + li) * a.nz + kr];
                 const float* c = coef_s + q * 8;
                 const float num = fmaf(c[2], zc[q], fmaf(c[1], py, fmaf(c[0], px, qn)));
                 const float psi = __fdividef(num, sig + c[3]);
                 buf[(cb * AB + q) * T + tid] = psi;
                 zc[q] = psi;
-                if (li == a.tx - 1 && at < a.ntx - 1) {
-                    const size_t fb = (((size_t)o * a.A8 + slot0 + q) * a.G + g) * xf_stride;
-                    a.xface[fb + ((size_t)at * a.ny + jr) * a.nz + kr] = psi;
-                }
-                if (lj == a.ty - 1 && bt < a.nty - 1) {
-                    const size_t fb = (((size_t)o * a.A8 + slot0 + q) * a.G + g) * yf_stride;
-                    a.yface[fb + ((size_t)bt * a.nx + ir) * a.nz + kr] = psi;
-                }
+                if (xout) xo[q * xo_q + kr] = psi;
+                if (yout) yo[q * yo_q + kr] = psi;
                 if (ir == a.nx - 1) lk = fmaf(c[4], psi, lk);
                 if (jr == a.ny - 1) lk = fmaf(c[5], psi, lk);
                 if (kr == a.nz - 1) lk = fmaf(c[6], psi, lk);
@@ -173,8 +204,8 @@ __global__ void __launch_bounds__(512) k_sweep(const SweepArgs a) {
     if ((tid & 31) == 0 && dl != 0.0) atomicAdd(a.leak + g, dl);
 }
 
-inline size_t sweep_smem_bytes(int ab, int M, int T, int nmat) {
-    return sizeof(float) * (size_t)(2 * ab * T + 2 * ab * M + 8 * ab + nmat);
+inline size_t sweep_smem_bytes(int ab, int M, int tx, int ty, int nz, int nmat) {
+    return sizeof(float) * (size_t)(2 * ab * tx * ty + ab * (tx + ty) * nz + 2 * ab * M + 8 * ab + nmat);
 }
 
 template <int M>
@@ -184,8 +215,8 @@ cudaError_t launch_sweep_m(const SweepArgs& a, cudaStream_t s) {
     const int ntiles = a_hi - a_lo + 1;
     if (ntiles <= 0) return cudaSuccess;
     const int T = a.tx * a.ty;
-    dim3 grid(ntiles, a.G, 8 * a.nab);
-    const size_t smem = sweep_smem_bytes(a.ab, M, T, a.nmat);
+    dim3 grid(ntiles, 8 * a.nab, a.G);
+    const size_t smem = sweep_smem_bytes(a.ab, M, a.tx, a.ty, a.nz, a.nmat);
 #define DOCTORS_SWEEP_CASE(AB)                                                                  \
     case AB: {                                                                                  \
         auto kern = k_sweep<AB, M>;                                                             \
