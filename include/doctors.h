@@ -167,6 +167,22 @@ int doctors_get_fluence(doctors_problem *p, int which, float *out, int mem);
  * in `mem`.  DOCTORS_ERR_STATE before a successful solve. */
 int doctors_dose(doctors_problem *p, const double *k, double *dose, int mem);
 
+/* Dose tally that allocates nothing (the paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc, such as code
+ * inside a framework whose caching allocator owns the device memory, or
+ * real-time and embedded callers that forbid allocation after start-up).
+ * Same result as doctors_dose, written to `dose` [V] float64, which must be
+ * device memory on the problem's device; k [n_mat][G] is host memory.  The
+ * factor table is staged in a fixed array inside the library's device image
+ * (at most 256 = n_mat * G entries; larger tables are rejected with
+ * DOCTORS_ERR_INVALID_ARG), held by every GPU that loads the library until
+ * the process exits.  All calls share that array: calls that overlap on the
+ * GPU race on it.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, once per device); make that first call
+ * before any stream capture.  Stream-ordered, does not synchronise.
+ * DOCTORS_ERR_STATE before a successful solve. */
+int doctors_dose_noalloc(doctors_problem *p, const double *k, double *dose);
+
 /* Adjoint solve and gradients (no counterpart in the paper; the discrete
  * adjoint of the operator above).  For J = sum_{g,v} response[g][v] *
  * (phi_u + phi_c)[g][v] with response [G][V] float64 in `mem`, solves the

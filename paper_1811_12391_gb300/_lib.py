@@ -80,6 +80,7 @@ SIGNATURES = [
     ("doctors_solve", _int, [_vp, _P(doctors_result)]),
     ("doctors_get_fluence", _int, [_vp, _int, _vp, _int]),
     ("doctors_dose", _int, [_vp, _P(ctypes.c_double), _vp, _int]),
+    ("doctors_dose_noalloc", _int, [_vp, _P(ctypes.c_double), _vp]),
     ("doctors_adjoint_solve", _int, [_vp, _vp, _int, _vp, _vp, _vp, _P(doctors_result)]),
     ("doctors_debug_ray_indices", _int, [_vp, _int, _int, _P(ctypes.c_int32), _P(ctypes.c_float), _int,
                                          _P(_int)]),
@@ -140,6 +141,7 @@ doctors_set_source = _fwd("doctors_set_source")
 doctors_solve = _fwd("doctors_solve")
 doctors_get_fluence = _fwd("doctors_get_fluence")
 doctors_dose = _fwd("doctors_dose")
+doctors_dose_noalloc = _fwd("doctors_dose_noalloc")
 doctors_adjoint_solve = _fwd("doctors_adjoint_solve")
 doctors_debug_ray_indices = _fwd("doctors_debug_ray_indices")
 doctors_quadrature = _fwd("doctors_quadrature")
