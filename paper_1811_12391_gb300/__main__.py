@@ -1,0 +1,41 @@
+"""Command line: solve a named synthetic workload and print the report.
+
+  python -m paper_1811_12391_gb300 <workload> [--iters N] [--tol T] [--tile X Y] [--ab K] [--repeat R]
+
+Workloads: tiny_cube, water_cylinder, abdomen, axial_scan, differentiable_abdomen
+(see synth/phantoms.py).  Used as the profiled command in profiles/.
+"""
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser(prog="python -m paper_1811_12391_gb300")
+    ap.add_argument("workload")
+    ap.add_argument("--iters", type=int, default=500)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--tile", type=int, nargs=2, default=(0, 0))
+    ap.add_argument("--ab", type=int, default=0)
+    ap.add_argument("--repeat", type=int, default=1)
+    args = ap.parse_args()
+    from paper_1811_12391_gb300.build import build
+    build()
+    from paper_1811_12391_gb300.solver import DoctorsProblem
+    from synth import phantoms as ph
+
+    p = ph.config_problem(args.workload)
+    d = DoctorsProblem(p, tol=args.tol, max_iters=args.iters, tile=tuple(args.tile), angles_per_block=args.ab)
+    for _ in range(args.repeat):
+        r = d.solve(allow_not_converged=True)
+        print(json.dumps(r), flush=True)
+    d.close()
+
+
+if __name__ == "__main__":
+    main()
