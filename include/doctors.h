@@ -66,6 +66,7 @@ extern "C" {
 #define DOCTORS_FLUENCE_UNCOLLIDED  0
 #define DOCTORS_FLUENCE_COLLIDED    1
 #define DOCTORS_FLUENCE_TOTAL       2
+#define DOCTORS_FLUENCE_ADJOINT     3   /* adjoint scalar fluence (importance) of the last adjoint solve */
 
 /* Voxel mesh (Sec. II.D: Cartesian voxel phantoms). */
 typedef struct doctors_mesh {
@@ -157,8 +158,9 @@ int doctors_set_source(doctors_problem *p, int n_src, const doctors_source *src)
 int doctors_solve(doctors_problem *p, doctors_result *info);
 
 /* Copy a group fluence [G][V] float32 (Eq. 3's scalar fluence; uncollided,
- * collided or their sum) into `out` in `mem`.  DOCTORS_ERR_STATE before a
- * successful solve. */
+ * collided or their sum, or the adjoint scalar fluence of the last adjoint
+ * solve) into `out` in `mem`.  DOCTORS_ERR_STATE before a successful solve
+ * (or, for DOCTORS_FLUENCE_ADJOINT, before an adjoint solve). */
 int doctors_get_fluence(doctors_problem *p, int which, float *out, int mem);
 
 /* Dose tally (Sec. II.A, III.A): dose[v] = sum_g k[mat v][g] * density[v] *

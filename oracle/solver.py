@@ -279,6 +279,10 @@ def gradients(p, roi_weights: np.ndarray, tol: float = 1e-12, density: bool = Tr
     J = float((roi_weights * dose(p, sol.phi)).sum())
     for si, s in enumerate(p.sources):
         if s.kind == SRC_VOLUME:
+            # J depends on a volume source through <q_00 / (4 pi), Z_00>
+            z00 = adj.Z[:, 0, :].sum(axis=1) / (4.0 * math.pi)
+            d_w[si] = float(s.spectrum @ z00)
+            d_chi += s.weight * z00
             continue
         u = unit_uncollided(p, s)                                     # [G][V]
         Rs = quad.real_harmonics(L, source_directions(p, s))          # [V][M]

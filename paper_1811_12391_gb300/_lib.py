@@ -31,6 +31,7 @@ DOCTORS_SRC_VOLUME = 2
 DOCTORS_FLUENCE_UNCOLLIDED = 0
 DOCTORS_FLUENCE_COLLIDED = 1
 DOCTORS_FLUENCE_TOTAL = 2
+DOCTORS_FLUENCE_ADJOINT = 3
 
 ERROR_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "TIMEOUT",
                6: "STATE"}

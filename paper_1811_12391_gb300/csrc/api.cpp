@@ -70,10 +70,13 @@ int default_ab(int A8) {
 void free_problem(doctors_problem* p) {
     void* ptrs[] = {p->d_mop, p->d_dop, p->d_coef, p->d_mat, p->d_rho, p->d_sigt, p->d_sigs,
                     p->d_phiu_src, p->d_phiu, p->d_U, p->d_Q, p->d_mom, p->d_src, p->d_prev,
-                    p->d_emit, p->d_iso, p->d_xface, p->d_yface, p->d_red};
+                    p->d_emit, p->d_iso, p->d_xface, p->d_yface, p->d_red,
+                    p->d_Z, p->d_Qa, p->d_T, p->d_rf, p->d_r, p->d_acc, p->d_grad, p->d_H,
+                    p->d_ones, p->d_psi, p->d_prod};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (p->h_red) cudaFreeHost(p->h_red);
+    if (p->h_acc) cudaFreeHost(p->h_acc);
     for (auto& e : p->ev)
         if (e) cudaEventDestroy(e);
 }
@@ -175,52 +178,53 @@ int first_collision(doctors_problem* p) {
     return DOCTORS_OK;
 }
 
-SweepArgs sweep_args(const doctors_problem* p, int reverse) {
+SweepArgs sweep_args(const doctors_problem* p, int reverse, const float* src, float* mom) {
     SweepArgs a{};
     a.nx = p->nx; a.ny = p->ny; a.nz = p->nz; a.G = p->G; a.A8 = p->A8; a.ab = p->ab; a.nab = p->nab;
     a.nmat = p->nmat; a.tx = p->tx; a.ty = p->ty; a.ntx = p->ntx; a.nty = p->nty; a.reverse = reverse;
-    a.mat = p->d_mat; a.rho = p->d_rho; a.sigt = p->d_sigt; a.src = p->d_src; a.mom = p->d_mom;
+    a.mat = p->d_mat; a.rho = p->d_rho; a.sigt = p->d_sigt; a.src = src; a.mom = mom;
     a.mop = p->d_mop; a.dop = p->d_dop; a.coef = p->d_coef; a.xface = p->d_xface; a.yface = p->d_yface;
     a.leak = p->d_red;
+    a.A = p->A;
     return a;
 }
 
-// Source iteration: src = Q + S(mom); mom = sweep(src); residual.  `transpose`
-// selects the adjoint's scattering, `reverse` its sweep directions.
-int iterate(doctors_problem* p, int reverse, doctors_result* info) {
+// Source iteration: src = Q + S(mom); mom = sweep(src); residual.  `reverse`
+// selects the adjoint: sweep directions reversed and scattering transposed.
+int iterate(doctors_problem* p, int reverse, const float* Q, float* mom, doctors_result* info) {
     const size_t GVM = (size_t)p->G * p->V * p->M;
     double* d_leak = p->d_red;
     double* d_res = p->d_red + p->G;
     double* d_bal = p->d_red + 3 * p->G;
-    CU(cudaMemsetAsync(p->d_mom, 0, GVM * sizeof(float), p->stream));
+    CU(cudaMemsetAsync(mom, 0, GVM * sizeof(float), p->stream));
     CU(cudaMemsetAsync(p->d_prev, 0, (size_t)p->G * p->V * sizeof(float), p->stream));
     const double tol = std::max(p->opt.tol, kTolFloor);
     int it = 0;
     double resid = 0.0;
     double ms_sweep = 0.0;
     bool conv = false;
-    SweepArgs sw = sweep_args(p, reverse);
+    SweepArgs sw = sweep_args(p, reverse, p->d_src, mom);
     ScatterArgs sa{};
     sa.V = p->V; sa.G = p->G; sa.M = p->M; sa.L = p->L; sa.nmat = p->nmat; sa.transpose = reverse;
     sa.mat = p->d_mat; sa.rho = p->d_rho; sa.sigs = p->d_sigs;
-    sa.base = p->d_Q; sa.phi = p->d_mom; sa.out = p->d_src;
+    sa.base = Q; sa.phi = mom; sa.out = p->d_src;
     while (it < p->opt.max_iters) {
         if (it == 0) {
-            CU(cudaMemcpyAsync(p->d_src, p->d_Q, GVM * sizeof(float), cudaMemcpyDeviceToDevice, p->stream));
+            CU(cudaMemcpyAsync(p->d_src, Q, GVM * sizeof(float), cudaMemcpyDeviceToDevice, p->stream));
         } else {
             CU(launch_scatter(sa, p->stream));
             ++p->launches;
         }
-        CU(cudaMemsetAsync(p->d_mom, 0, GVM * sizeof(float), p->stream));
+        CU(cudaMemsetAsync(mom, 0, GVM * sizeof(float), p->stream));
         CU(cudaMemsetAsync(p->d_red, 0, 5 * (size_t)p->G * sizeof(double), p->stream));
         CU(cudaEventRecord(p->ev[3], p->stream));
         for (int st = 0; st < p->ntx + p->nty - 1; ++st) {
             sw.stage = st;
-            CU(launch_sweep_stage(sw, p->M, p->stream));
+            CU(launch_sweep_stage(sw, p->M, 0, p->stream));
             ++p->launches;
         }
         CU(cudaEventRecord(p->ev[4], p->stream));
-        CU(launch_residual(p->V, p->G, p->M, p->d_mom, p->d_prev, d_res, p->stream));
+        CU(launch_residual(p->V, p->G, p->M, mom, p->d_prev, d_res, p->stream));
         ++p->launches;
         CU(cudaMemcpyAsync(p->h_red, p->d_red, 3 * (size_t)p->G * sizeof(double), cudaMemcpyDeviceToHost,
                            p->stream));
@@ -246,7 +250,7 @@ int iterate(doctors_problem* p, int reverse, doctors_result* info) {
     }
     // particle balance of the last sweep (FP64)
     const double vol = p->mesh.dx * p->mesh.dy * p->mesh.dz;
-    CU(launch_balance(p->V, p->G, p->M, p->d_mat, p->d_rho, p->d_sigt, p->d_src, p->d_mom, vol, d_bal,
+    CU(launch_balance(p->V, p->G, p->M, p->d_mat, p->d_rho, p->d_sigt, p->d_src, mom, vol, d_bal,
                       p->stream));
     ++p->launches;
     CU(cudaMemcpyAsync(p->h_red, p->d_red, 5 * (size_t)p->G * sizeof(double), cudaMemcpyDeviceToHost,
@@ -344,6 +348,7 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
         coef[n * 8 + 4] = (float)(w[n] * ox * dy * dz);
         coef[n * 8 + 5] = (float)(w[n] * oy * dx * dz);
         coef[n * 8 + 6] = (float)(w[n] * oz * dx * dy);
+        coef[n * 8 + 7] = (float)w[n];
     }
     const size_t GV = (size_t)p->G * p->V, GVM = GV * M;
     int rc = 0;
@@ -437,6 +442,7 @@ int doctors_set_materials(doctors_problem* p, int n_mat, const uint8_t* mat, con
     p->h_sigs.assign(sigma_s, sigma_s + ss.size());
     p->have_mat = true;
     p->solved = false;
+    p->adjoint_done = false;
     return DOCTORS_OK;
 }
 
@@ -475,6 +481,7 @@ int doctors_set_source(doctors_problem* p, int n_src, const doctors_source* src)
     p->spectra = spec;
     p->have_src = true;
     p->solved = false;
+    p->adjoint_done = false;
     return DOCTORS_OK;
 }
 
@@ -487,12 +494,13 @@ int doctors_solve(doctors_problem* p, doctors_result* info) {
     }
     doctors_result r{};
     p->solved = false;
+    p->adjoint_done = false;
     p->launches = 0;
     CU(cudaEventRecord(p->ev[0], p->stream));
     rc = first_collision(p);
     if (rc) return rc;
     CU(cudaEventRecord(p->ev[1], p->stream));
-    rc = iterate(p, 0, &r);
+    rc = iterate(p, 0, p->d_Q, p->d_mom, &r);
     if (rc && rc != DOCTORS_ERR_NOT_CONVERGED) return rc;
     CU(cudaEventRecord(p->ev[2], p->stream));
     CU(cudaEventSynchronize(p->ev[2]));
@@ -514,20 +522,25 @@ int doctors_get_fluence(doctors_problem* p, int which, float* out, int mem) {
     int rc = check_problem(p);
     if (rc) return rc;
     CHECK_ARG(out != nullptr, "null output");
-    CHECK_ARG(which >= 0 && which <= 2, "which must be UNCOLLIDED, COLLIDED or TOTAL");
+    CHECK_ARG(which >= 0 && which <= 3, "which must be UNCOLLIDED, COLLIDED, TOTAL or ADJOINT");
     CHECK_ARG(mem == DOCTORS_MEM_HOST || mem == DOCTORS_MEM_DEVICE, "bad mem");
     if (!p->solved) {
         set_error("no solution: call doctors_solve first");
         return DOCTORS_ERR_STATE;
     }
-    const int mask = which == DOCTORS_FLUENCE_UNCOLLIDED ? 1 : which == DOCTORS_FLUENCE_COLLIDED ? 2 : 3;
+    if (which == DOCTORS_FLUENCE_ADJOINT && !p->adjoint_done) {
+        set_error("no adjoint solution: call doctors_adjoint_solve first");
+        return DOCTORS_ERR_STATE;
+    }
+    const int mask = which == DOCTORS_FLUENCE_UNCOLLIDED ? 1 : which == DOCTORS_FLUENCE_TOTAL ? 3 : 2;
+    const float* mom = which == DOCTORS_FLUENCE_ADJOINT ? p->d_Z : p->d_mom;
     const size_t GV = (size_t)p->G * p->V;
     if (mem == DOCTORS_MEM_DEVICE) {
-        CU(launch_extract(p->V, p->G, p->M, mask, p->d_phiu, p->d_mom, out, p->stream));
+        CU(launch_extract(p->V, p->G, p->M, mask, p->d_phiu, mom, out, p->stream));
         return DOCTORS_OK;
     }
     // stage through the (now free) source buffer
-    CU(launch_extract(p->V, p->G, p->M, mask, p->d_phiu, p->d_mom, p->d_src, p->stream));
+    CU(launch_extract(p->V, p->G, p->M, mask, p->d_phiu, mom, p->d_src, p->stream));
     CU(cudaMemcpyAsync(out, p->d_src, GV * sizeof(float), cudaMemcpyDeviceToHost, p->stream));
     CU(cudaStreamSynchronize(p->stream));
     return DOCTORS_OK;
@@ -635,11 +648,207 @@ void doctors_destroy(doctors_problem* p) {
 
 }  // extern "C"
 
+namespace {
+
+// one full sweep (all stages) of `src` into the zeroed accumulator `mom`
+int sweep_once(doctors_problem* p, int reverse, int mode, const float* src, float* mom) {
+    CU(cudaMemsetAsync(mom, 0, (size_t)p->G * p->V * p->M * sizeof(float), p->stream));
+    CU(cudaMemsetAsync(p->d_red, 0, 5 * (size_t)p->G * sizeof(double), p->stream));
+    SweepArgs sw = sweep_args(p, reverse, src, mom);
+    sw.psi = p->d_psi;
+    sw.prod = p->d_prod;
+    for (int st = 0; st < p->ntx + p->nty - 1; ++st) {
+        sw.stage = st;
+        CU(launch_sweep_stage(sw, p->M, mode, p->stream));
+        ++p->launches;
+    }
+    return DOCTORS_OK;
+}
+
+int ensure_adjoint_buffers(doctors_problem* p, bool density) {
+    const size_t GV = (size_t)p->G * p->V, GVM = GV * p->M;
+    int rc = 0;
+    if (!p->d_Z) rc = rc ? rc : dalloc_t(&p->d_Z, GVM, "adjoint moments");
+    if (!p->d_Qa) rc = rc ? rc : dalloc_t(&p->d_Qa, GVM, "adjoint source");
+    if (!p->d_T) rc = rc ? rc : dalloc_t(&p->d_T, GVM, "adjoint scattering");
+    if (!p->d_rf) rc = rc ? rc : dalloc_t(&p->d_rf, GV, "response");
+    if (!p->d_r) rc = rc ? rc : dalloc_t(&p->d_r, GV, "response");
+    if (!p->d_acc) rc = rc ? rc : dalloc_t(&p->d_acc, 2 * (size_t)p->G, "gradient sums");
+    if (!p->d_ones) rc = rc ? rc : dalloc_t(&p->d_ones, (size_t)p->G, "unit emission");
+    if (!p->d_grad) rc = rc ? rc : dalloc_t(&p->d_grad, p->V, "density gradient");
+    if (density) {
+        if (!p->d_H) rc = rc ? rc : dalloc_t(&p->d_H, (size_t)kMaxMat * p->V, "ray importance");
+        if (!p->d_psi) rc = rc ? rc : dalloc_t(&p->d_psi, GV * p->A, "stored angular fluence");
+        if (!p->d_prod) rc = rc ? rc : dalloc_t(&p->d_prod, GV, "angular product");
+    }
+    if (rc) return rc;
+    if (!p->h_acc) {
+        cudaError_t e = cudaMallocHost(&p->h_acc, 2 * (size_t)p->G * sizeof(double));
+        if (e != cudaSuccess) {
+            set_error("pinned host allocation failed");
+            return DOCTORS_ERR_OOM;
+        }
+    }
+    return DOCTORS_OK;
+}
+
+int copy_out(doctors_problem* p, double* dst, const double* src_host_or_dev, size_t n, int mem, bool src_is_dev) {
+    cudaMemcpyKind kind;
+    if (src_is_dev) kind = mem == DOCTORS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    else kind = mem == DOCTORS_MEM_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+    CU(cudaMemcpyAsync(dst, src_host_or_dev, n * sizeof(double), kind, p->stream));
+    return DOCTORS_OK;
+}
+
+}  // namespace
+
 extern "C" int doctors_adjoint_solve(doctors_problem* p, const double* response, int mem, double* d_weights,
                                      double* d_spectrum, double* d_density, doctors_result* info) {
-    (void)response; (void)mem; (void)d_weights; (void)d_spectrum; (void)d_density; (void)info;
     int rc = check_problem(p);
     if (rc) return rc;
-    set_error("adjoint solve is not available in this build");
-    return DOCTORS_ERR_STATE;
+    CHECK_ARG(response != nullptr, "null response");
+    CHECK_ARG(mem == DOCTORS_MEM_HOST || mem == DOCTORS_MEM_DEVICE, "bad mem");
+    if (!p->solved) {
+        set_error("no forward solution: call doctors_solve first");
+        return DOCTORS_ERR_STATE;
+    }
+    const bool density = d_density != nullptr;
+    rc = ensure_adjoint_buffers(p, density);
+    if (rc) return rc;
+    const size_t GV = (size_t)p->G * p->V, GVM = GV * p->M;
+    p->launches = 0;
+    CU(cudaEventRecord(p->ev[0], p->stream));
+    CU(cudaMemcpyAsync(p->d_r, response, GV * sizeof(double),
+                       mem == DOCTORS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
+    CU(launch_to_float(GV, p->d_r, p->d_rf, p->stream));
+    ++p->launches;
+    {
+        std::vector<float> ones(p->G, 1.0f);
+        CU(cudaMemcpyAsync(p->d_ones, ones.data(), p->G * sizeof(float), cudaMemcpyHostToDevice, p->stream));
+        CU(cudaStreamSynchronize(p->stream));
+    }
+    ScatterArgs sa{};
+    sa.V = p->V; sa.G = p->G; sa.M = p->M; sa.L = p->L; sa.nmat = p->nmat;
+    sa.mat = p->d_mat; sa.rho = p->d_rho; sa.sigs = p->d_sigs;
+    // 1. store the converged forward angular fluence (one extra forward sweep)
+    if (density) {
+        sa.transpose = 0; sa.base = p->d_Q; sa.iso = nullptr; sa.iso_field = nullptr; sa.phi = p->d_mom;
+        sa.out = p->d_src;
+        CU(launch_scatter(sa, p->stream));
+        ++p->launches;
+        rc = sweep_once(p, 0, 1, p->d_src, p->d_T);
+        if (rc) return rc;
+    }
+    // 2. adjoint fixed source 4 pi r in the l = 0 moment
+    sa.transpose = 1; sa.base = nullptr; sa.iso = nullptr; sa.iso_field = p->d_rf;
+    sa.iso_field_scale = (float)(4.0 * M_PI); sa.phi = nullptr; sa.out = p->d_Qa;
+    CU(launch_scatter(sa, p->stream));
+    ++p->launches;
+    CU(cudaEventRecord(p->ev[1], p->stream));
+    // 3. adjoint source iteration
+    doctors_result r{};
+    const long long l0 = p->launches;
+    int irc = iterate(p, 1, p->d_Qa, p->d_Z, &r);
+    if (irc && irc != DOCTORS_ERR_NOT_CONVERGED) return irc;
+    (void)l0;
+    // 4. angular product against the stored forward fluence
+    if (density) {
+        sa.transpose = 1; sa.base = p->d_Qa; sa.iso_field = nullptr; sa.phi = p->d_Z; sa.out = p->d_src;
+        CU(launch_scatter(sa, p->stream));
+        ++p->launches;
+        CU(cudaMemsetAsync(p->d_prod, 0, GV * sizeof(float), p->stream));
+        rc = sweep_once(p, 1, 2, p->d_src, p->d_T);
+        if (rc) return rc;
+    }
+    // 5. T = S^T Z
+    sa.transpose = 1; sa.base = nullptr; sa.iso_field = nullptr; sa.phi = p->d_Z; sa.out = p->d_T;
+    CU(launch_scatter(sa, p->stream));
+    ++p->launches;
+    // 6. per-source view-weight, spectrum and ray terms
+    std::vector<double> gw(p->srcs.size(), 0.0), gs(p->G, 0.0);
+    if (density) CU(cudaMemsetAsync(p->d_grad, 0, p->V * sizeof(double), p->stream));
+    bool have_z00 = false;
+    for (size_t s = 0; s < p->srcs.size(); ++s) {
+        const doctors_source& src = p->srcs[s];
+        CU(cudaMemsetAsync(p->d_acc, 0, 2 * (size_t)p->G * sizeof(double), p->stream));
+        if (src.kind == DOCTORS_SRC_VOLUME) {
+            // J depends on a volume source through <q00 / (4 pi), Z00>
+            if (!have_z00) {
+                CU(launch_sum00(p->V, p->G, p->M, p->d_Z, p->d_acc + p->G, p->stream));
+                ++p->launches;
+                CU(cudaMemcpyAsync(p->h_acc, p->d_acc, 2 * (size_t)p->G * sizeof(double), cudaMemcpyDeviceToHost,
+                                   p->stream));
+                CU(cudaStreamSynchronize(p->stream));
+                have_z00 = true;
+            }
+            for (int g = 0; g < p->G; ++g) {
+                const double a = p->h_acc[p->G + g] / (4.0 * M_PI);
+                gw[s] += p->spectra[s][g] * a;
+                gs[g] += src.weight * a;
+            }
+            continue;
+        }
+        std::vector<float> emit(p->G);
+        for (int g = 0; g < p->G; ++g) emit[g] = (float)(src.weight * p->spectra[s][g]);
+        CU(cudaMemcpyAsync(p->d_iso, emit.data(), p->G * sizeof(float), cudaMemcpyHostToDevice, p->stream));
+        RayArgs ra = ray_args(p, src, p->d_ones);
+        ra.phi_tot = nullptr;
+        CU(launch_raytrace(ra, p->stream));
+        ++p->launches;
+        SourceGradArgs ga{};
+        ga.nx = p->nx; ga.ny = p->ny; ga.nz = p->nz; ga.G = p->G; ga.M = p->M; ga.nmat = p->nmat;
+        ga.ox = ra.ox; ga.oy = ra.oy; ga.oz = ra.oz; ga.dx = ra.dx; ga.dy = ra.dy; ga.dz = ra.dz;
+        ga.sx = ra.sx; ga.sy = ra.sy; ga.sz = ra.sz;
+        ga.r = p->d_r; ga.T = p->d_T; ga.u = p->d_phiu_src; ga.emit = p->d_iso; ga.sigt = p->d_sigt;
+        ga.acc = p->d_acc; ga.H = density ? p->d_H : nullptr;
+        CU(launch_source_grad(ga, p->stream));
+        ++p->launches;
+        if (density) {
+            CU(launch_backproject(ra, p->d_H, p->d_grad, p->stream));
+            ++p->launches;
+        }
+        CU(cudaMemcpyAsync(p->h_acc, p->d_acc, (size_t)p->G * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+        CU(cudaStreamSynchronize(p->stream));
+        for (int g = 0; g < p->G; ++g) {
+            gw[s] += p->spectra[s][g] * p->h_acc[g];
+            gs[g] += src.weight * p->h_acc[g];
+        }
+    }
+    // 7. collision and scattering terms of the density gradient
+    if (density) {
+        DensityGradArgs da{};
+        da.V = p->V; da.G = p->G; da.M = p->M; da.L = p->L; da.nmat = p->nmat;
+        da.mat = p->d_mat; da.sigt = p->d_sigt; da.sigs = p->d_sigs;
+        da.Z = p->d_Z; da.phic = p->d_mom; da.U = p->d_U; da.prod = p->d_prod; da.grad = p->d_grad;
+        CU(launch_density_grad(da, p->stream));
+        ++p->launches;
+    }
+    // 8. outputs
+    if (d_weights) {
+        rc = copy_out(p, d_weights, gw.data(), gw.size(), mem, false);
+        if (rc) return rc;
+    }
+    if (d_spectrum) {
+        rc = copy_out(p, d_spectrum, gs.data(), gs.size(), mem, false);
+        if (rc) return rc;
+    }
+    if (density) {
+        rc = copy_out(p, d_density, p->d_grad, p->V, mem, true);
+        if (rc) return rc;
+    }
+    CU(cudaEventRecord(p->ev[2], p->stream));
+    CU(cudaStreamSynchronize(p->stream));
+    float t01 = 0, t12 = 0, t02 = 0;
+    cudaEventElapsedTime(&t01, p->ev[0], p->ev[1]);
+    cudaEventElapsedTime(&t12, p->ev[1], p->ev[2]);
+    cudaEventElapsedTime(&t02, p->ev[0], p->ev[2]);
+    r.ms_raytrace = t01;
+    r.ms_iterate = t12;
+    r.ms_total = t02;
+    r.launches = p->launches;
+    if (info) *info = r;
+    (void)GVM;
+    p->adjoint_done = true;
+    if (irc == DOCTORS_ERR_NOT_CONVERGED) set_error("adjoint iteration cap reached before convergence");
+    return irc;
 }

@@ -37,12 +37,52 @@ struct RayArgs {
     const float* sigt;                 // [nmat][G]
     const float* emit;                 // [G] weight * spectrum
     float* phi_src;                    // [G][V] this source (overwritten)
-    float* phi_tot;                    // [G][V] accumulated (+=)
+    float* phi_tot;                    // [G][V] accumulated (+=), or null
 };
 
 cudaError_t launch_raytrace(const RayArgs& a, cudaStream_t s);
 cudaError_t launch_debug_ray(const RayArgs& a, int voxel, int32_t* idx, float* len, int cap,
                              int* count, cudaStream_t s);
+cudaError_t launch_backproject(const RayArgs& a, const float* H, double* grad, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// adjoint gradients
+// ---------------------------------------------------------------------------
+// Per point source: imp[g](v) = r[g](v) + sum_lm (2l+1)/(4 pi) R_lm(Omega_sv) T[g][v][lm]
+// (dJ/dphi_u of this source), acc[g] += sum_v u[g](v) imp[g](v) with u the unit
+// uncollided fluence, and (if H) H[m][v] = sum_g sigma_t[m][g] imp emit[g] u.
+struct SourceGradArgs {
+    int nx, ny, nz, G, M, nmat;
+    float ox, oy, oz, dx, dy, dz, sx, sy, sz;
+    const double* r;                   // [G][V]
+    const float* T;                    // [G][V][M]
+    const float* u;                    // [G][V]
+    const float* emit;                 // [G] weight * spectrum of this source
+    const float* sigt;                 // [nmat][G]
+    double* acc;                       // [G]
+    float* H;                          // [nmat][V] or null
+};
+cudaError_t launch_source_grad(const SourceGradArgs& a, cudaStream_t s);
+
+// grad[v] += sum_{g,lm} (2l+1)/(4 pi) Z[g][v][lm] rho-free sigma_s,l(g'->g) (phi_c + U)[g'][v][lm]
+//            - sum_g sigma_t[mat][g] prod[g][v]     (prod may be null)
+struct DensityGradArgs {
+    size_t V;
+    int G, M, L, nmat;
+    const uint8_t* mat;
+    const float* sigt;                 // [nmat][G]
+    const float* sigs;                 // [nmat][L+1][G][G]
+    const float* Z;                    // [G][V][M] adjoint moments
+    const float* phic;                 // [G][V][M] forward collided moments
+    const float* U;                    // [G][V][M] uncollided moments
+    const float* prod;                 // [G][V] or null
+    double* grad;                      // [V]
+};
+cudaError_t launch_density_grad(const DensityGradArgs& a, cudaStream_t s);
+// out[g] += sum_v mom[g][v][0]
+cudaError_t launch_sum00(size_t V, int G, int M, const float* mom, double* out, cudaStream_t s);
+// out[i] = (float) in[i]
+cudaError_t launch_to_float(size_t n, const double* in, float* out, cudaStream_t s);
 
 // U[g][v][lm] += phi_src[g][v] * R_lm(unit(centre_v - source))
 struct MomentArgs {
@@ -104,12 +144,16 @@ struct SweepArgs {
     float* mom;                        // [G][V][M] accumulated moments
     const float* mop;                  // [A][M] (2l+1)/(4 pi) R_lm(Omega_n)
     const float* dop;                  // [A][M] w_n R_lm(Omega_n)
-    const float* coef;                 // [A][8] cx, cy, cz, cx+cy+cz, leak_x, leak_y, leak_z, 0
+    const float* coef;                 // [A][8] cx, cy, cz, cx+cy+cz, leak_x, leak_y, leak_z, w
     float* xface;                      // [8][A8][G][ntx-1][ny][nz]
     float* yface;                      // [8][A8][G][nty-1][nx][nz]
     double* leak;                      // [G]
+    int A;                             // directions (psi indexing)
+    float* psi;                        // [G][A][V]: written (mode 1) or read (mode 2)
+    float* prod;                       // [G][V]: mode 2 accumulator
 };
-cudaError_t launch_sweep_stage(const SweepArgs& a, int M, cudaStream_t s);
+// mode 0: plain; 1: store psi; 2: accumulate sum_n w_n psi_n psi_stored_n into prod
+cudaError_t launch_sweep_stage(const SweepArgs& a, int M, int mode, cudaStream_t s);
 bool sweep_supported(int ab, int M);
 
 }  // namespace doctors
@@ -159,7 +203,21 @@ struct doctors_problem {
     float* d_yface = nullptr;
     double* d_red = nullptr;       // reductions: leak [G], res [G][2], bal [G][2]
     double* h_red = nullptr;       // pinned mirror
+    // adjoint state (allocated on the first adjoint solve)
+    float* d_Z = nullptr;          // [G][V][M] adjoint moments
+    float* d_Qa = nullptr;         // [G][V][M] adjoint fixed source
+    float* d_T = nullptr;          // [G][V][M] S^T Z (also a throwaway accumulator)
+    float* d_rf = nullptr;         // [G][V] response (FP32)
+    double* d_r = nullptr;         // [G][V] response (FP64)
+    double* d_acc = nullptr;       // [2G] per-group sums
+    double* d_grad = nullptr;      // [V] density gradient
+    float* d_H = nullptr;          // [kMaxMat][V]
+    float* d_ones = nullptr;       // [G]
+    float* d_psi = nullptr;        // [G][A][V] stored forward angular fluence
+    float* d_prod = nullptr;       // [G][V] angular product
+    double* h_acc = nullptr;       // pinned [2G]
     bool solved = false;
+    bool adjoint_done = false;
     cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     long long launches = 0;        // kernels launched by the current call
 };

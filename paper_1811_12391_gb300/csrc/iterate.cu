@@ -12,10 +12,10 @@
 
 namespace doctors {
 
-cudaError_t launch_sweep_m1_entry(const SweepArgs& a, cudaStream_t s);
-cudaError_t launch_sweep_m4_entry(const SweepArgs& a, cudaStream_t s);
-cudaError_t launch_sweep_m9_entry(const SweepArgs& a, cudaStream_t s);
-cudaError_t launch_sweep_m16_entry(const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_sweep_m1_entry(const SweepArgs& a, int mode, cudaStream_t s);
+cudaError_t launch_sweep_m4_entry(const SweepArgs& a, int mode, cudaStream_t s);
+cudaError_t launch_sweep_m9_entry(const SweepArgs& a, int mode, cudaStream_t s);
+cudaError_t launch_sweep_m16_entry(const SweepArgs& a, int mode, cudaStream_t s);
 
 bool sweep_supported(int ab, int M) {
     const int abs_ok[] = {1, 2, 3, 4, 5, 6, 7, 9, 10, 12};
@@ -24,12 +24,12 @@ bool sweep_supported(int ab, int M) {
     return ok && (M == 1 || M == 4 || M == 9 || M == 16);
 }
 
-cudaError_t launch_sweep_stage(const SweepArgs& a, int M, cudaStream_t s) {
+cudaError_t launch_sweep_stage(const SweepArgs& a, int M, int mode, cudaStream_t s) {
     switch (M) {
-        case 1: return launch_sweep_m1_entry(a, s);
-        case 4: return launch_sweep_m4_entry(a, s);
-        case 9: return launch_sweep_m9_entry(a, s);
-        case 16: return launch_sweep_m16_entry(a, s);
+        case 1: return launch_sweep_m1_entry(a, mode, s);
+        case 4: return launch_sweep_m4_entry(a, mode, s);
+        case 9: return launch_sweep_m9_entry(a, mode, s);
+        case 16: return launch_sweep_m16_entry(a, mode, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -134,8 +134,36 @@ __global__ void __launch_bounds__(256) k_raytrace(const RayArgs r) {
             if (m < r.nmat) tau = fmaf(s_sigt[m * r.G + g], lam[m], tau);
         const float phi = __ldg(r.emit + g) * expf(-tau) * inv;
         r.phi_src[(size_t)g * V + v] = phi;
-        r.phi_tot[(size_t)g * V + v] += phi;
+        if (r.phi_tot) r.phi_tot[(size_t)g * V + v] += phi;
     }
+}
+
+// Density gradient of the uncollided fluence, back-projected along the rays:
+// d phi_u[g](t) / d rho_u = -sigma_t[mat u][g] * length(u on ray t) * phi_u[g](t),
+// so grad[u] -= length * H[mat u][t] with H[m][t] = sum_g sigma_t[m][g] *
+// dJ/dphi_u[g](t) * phi_u[g](t).  One thread per target voxel t; FP64 atomics.
+__global__ void __launch_bounds__(256) k_backproject(const RayArgs r, const float* H, double* grad) {
+    const size_t V = (size_t)r.nx * r.ny * r.nz;
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= V) return;
+    float h[kMaxMat];
+    bool any = false;
+#pragma unroll
+    for (int m = 0; m < kMaxMat; ++m) {
+        h[m] = m < r.nmat ? H[(size_t)m * V + t] : 0.0f;
+        any |= h[m] != 0.0f;
+    }
+    if (!any) return;
+    const int i = (int)(t % r.nx);
+    const int j = (int)((t / r.nx) % r.ny);
+    const int k = (int)(t / ((size_t)r.nx * r.ny));
+    walk_ray(r, i, j, k, [&](int u, float len) {
+        const int mu = __ldg(r.mat + u);
+        float hm = 0.0f;
+#pragma unroll
+        for (int m = 0; m < kMaxMat; ++m) hm = (mu == m) ? h[m] : hm;
+        if (hm != 0.0f) atomicAdd(grad + u, -(double)len * (double)hm);
+    });
 }
 
 __global__ void k_debug_ray(const RayArgs r, int voxel, int32_t* idx, float* len, int cap, int* count) {
@@ -196,6 +224,13 @@ cudaError_t launch_raytrace(const RayArgs& a, cudaStream_t s) {
     const int bs = 256;
     const unsigned grid = (unsigned)((V + bs - 1) / bs);
     k_raytrace<<<grid, bs, sizeof(float) * a.nmat * a.G, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backproject(const RayArgs& a, const float* H, double* grad, cudaStream_t s) {
+    const size_t V = (size_t)a.nx * a.ny * a.nz;
+    const int bs = 256;
+    k_backproject<<<(unsigned)((V + bs - 1) / bs), bs, 0, s>>>(a, H, grad);
     return cudaGetLastError();
 }
 

@@ -64,7 +64,11 @@ __device__ __forceinline__ void add_moments(float* p, const float (&a)[M]) {
     }
 }
 
-template <int AB, int M>
+// MODE 0: plain sweep.  MODE 1: also store every angular fluence psi[g][n][v]
+// (forward fluence kept for the density gradient).  MODE 2: also accumulate
+// prod[g][v] += sum_n w_n psi_n psi_store[g][n][v] (adjoint sweep against the
+// stored forward fluence).
+template <int AB, int M, int MODE>
 __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs a) {
     extern __shared__ float sm[];
     const int T = a.tx * a.ty;
@@ -173,6 +177,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs a) {
             float acc[M];
 #pragma unroll
             for (int m = 0; m < M; ++m) acc[m] = 0.0f;
+            float pacc = 0.0f;
 #pragma unroll
             for (int q = 0; q < AB; ++q) {
                 float qn = 0.0f;
@@ -185,6 +190,9 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs a) {
                 const float psi = __fdividef(num, sig + c[3]);
                 buf[(cb * AB + q) * T + tid] = psi;
                 zc[q] = psi;
+                if constexpr (MODE == 1) a.psi[((size_t)g * a.A + nbase + q) * V + v] = psi;
+                if constexpr (MODE == 2)
+                    pacc = fmaf(c[7] * psi, __ldg(a.psi + ((size_t)g * a.A + nbase + q) * V + v), pacc);
                 if (xout) xo[q * xo_q + kr] = psi;
                 if (yout) yo[q * yo_q + kr] = psi;
                 if (ir == a.nx - 1) lk = fmaf(c[4], psi, lk);
@@ -194,6 +202,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs a) {
                 for (int m = 0; m < M; ++m) acc[m] = fmaf(dop_s[q * M + m], psi, acc[m]);
             }
             add_moments<M>(a.mom + (gV + v) * M, acc);
+            if constexpr (MODE == 2) atomicAdd(a.prod + gV + v, pacc);
         }
         __syncthreads();
     }
@@ -208,7 +217,7 @@ inline size_t sweep_smem_bytes(int ab, int M, int tx, int ty, int nz, int nmat) 
     return sizeof(float) * (size_t)(2 * ab * tx * ty + ab * (tx + ty) * nz + 2 * ab * M + 8 * ab + nmat);
 }
 
-template <int M>
+template <int M, int MODE>
 cudaError_t launch_sweep_m(const SweepArgs& a, cudaStream_t s) {
     const int a_lo = a.stage - (a.nty - 1) > 0 ? a.stage - (a.nty - 1) : 0;
     const int a_hi = a.stage < a.ntx - 1 ? a.stage : a.ntx - 1;
@@ -219,7 +228,7 @@ cudaError_t launch_sweep_m(const SweepArgs& a, cudaStream_t s) {
     const size_t smem = sweep_smem_bytes(a.ab, M, a.tx, a.ty, a.nz, a.nmat);
 #define DOCTORS_SWEEP_CASE(AB)                                                                  \
     case AB: {                                                                                  \
-        auto kern = k_sweep<AB, M>;                                                             \
+        auto kern = k_sweep<AB, M, MODE>;                                                             \
         if (smem > 48 * 1024) {                                                                 \
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                                  (int)smem);                                    \

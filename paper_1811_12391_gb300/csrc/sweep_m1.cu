@@ -2,5 +2,12 @@
 #include "sweep_impl.cuh"
 
 namespace doctors {
-cudaError_t launch_sweep_m1_entry(const SweepArgs& a, cudaStream_t s) { return launch_sweep_m<1>(a, s); }
+cudaError_t launch_sweep_m1_entry(const SweepArgs& a, int mode, cudaStream_t s) {
+    switch (mode) {
+        case 0: return launch_sweep_m<1, 0>(a, s);
+        case 1: return launch_sweep_m<1, 1>(a, s);
+        case 2: return launch_sweep_m<1, 2>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
 }  // namespace doctors

@@ -95,3 +95,28 @@ def test_gradients_match_central_differences():
         q2.density[v] = np.float32(p.density[v] * (1 - rel))
         fd = (_J(q1, roi) - _J(q2, roi)) / (float(q1.density[v]) - float(q2.density[v]))
         assert abs(fd - gr["d_density"][v]) <= 1e-5 * max(abs(fd), 1e-3 * scale), (v, fd, gr["d_density"][v])
+
+
+def test_volume_source_gradients_match_central_differences():
+    p = ph.infinite_medium_cube(n=5, G=2, sn=4, L=1, sigma_t=0.8)
+    p.sources.append(ph.Source(kind=ph.SRC_POINT, pos=np.array([0.3, -0.2, -9.0]), axis=np.array([0, 0, 1.0]),
+                               weight=2.0, spectrum=p.sources[0].spectrum.copy()))
+    roi = np.zeros(p.V)
+    roi[p.V // 2] = 1.0
+    gr = osv.gradients(p, roi, tol=1e-13, density=False)
+    for s in range(2):
+        q1, q2 = copy.deepcopy(p), copy.deepcopy(p)
+        h = 1e-3 * p.sources[s].weight
+        q1.sources[s].weight += h
+        q2.sources[s].weight -= h
+        fd = (_J(q1, roi) - _J(q2, roi)) / (2 * h)
+        assert abs(fd - gr["d_weights"][s]) <= 1e-8 * abs(fd)
+    for g in range(p.G):
+        q1, q2 = copy.deepcopy(p), copy.deepcopy(p)
+        h = 1e-3 * p.sources[0].spectrum[g]
+        for q, sg in ((q1, 1), (q2, -1)):
+            for s in q.sources:
+                s.spectrum = s.spectrum.copy()
+                s.spectrum[g] += sg * h
+        fd = (_J(q1, roi) - _J(q2, roi)) / (2 * h)
+        assert abs(fd - gr["d_spectrum"][g]) <= 1e-8 * abs(fd)
