@@ -68,7 +68,7 @@ int default_ab(int A8) {
 }
 
 void free_problem(doctors_problem* p) {
-    void* ptrs[] = {p->d_mop, p->d_dop, p->d_coef, p->d_mat, p->d_rho, p->d_sigt, p->d_sigs,
+    void* ptrs[] = {p->d_coef, p->d_mat, p->d_rho, p->d_sigt, p->d_sigs,
                     p->d_phiu_src, p->d_phiu, p->d_U, p->d_Q, p->d_mom, p->d_src, p->d_prev,
                     p->d_emit, p->d_iso, p->d_xface, p->d_yface, p->d_red,
                     p->d_Z, p->d_Qa, p->d_T, p->d_rf, p->d_r, p->d_acc, p->d_grad, p->d_H,
@@ -183,7 +183,7 @@ SweepArgs sweep_args(const doctors_problem* p, int reverse, const float* src, fl
     a.nx = p->nx; a.ny = p->ny; a.nz = p->nz; a.G = p->G; a.A8 = p->A8; a.ab = p->ab; a.nab = p->nab;
     a.nmat = p->nmat; a.tx = p->tx; a.ty = p->ty; a.ntx = p->ntx; a.nty = p->nty; a.reverse = reverse;
     a.mat = p->d_mat; a.rho = p->d_rho; a.sigt = p->d_sigt; a.src = src; a.mom = mom;
-    a.mop = p->d_mop; a.dop = p->d_dop; a.coef = p->d_coef; a.xface = p->d_xface; a.yface = p->d_yface;
+    a.table_base = p->table_base; a.coef = p->d_coef; a.xface = p->d_xface; a.yface = p->d_yface;
     a.leak = p->d_red;
     a.A = p->A;
     return a;
@@ -323,23 +323,16 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     p->ntx = (p->nx + p->tx - 1) / p->tx;
     p->nty = (p->ny + p->ty - 1) / p->ty;
     const size_t smem = sizeof(float) * (size_t)(2 * p->ab * p->tx * p->ty + p->ab * (p->tx + p->ty) * p->nz +
-                                                 2 * p->ab * p->M + 8 * p->ab + kMaxMat);
+                                                 21 * p->ab + kMaxMat);
     if (smem > 227 * 1024) return fail(DOCTORS_ERR_INVALID_ARG, "sweep tile needs more than 227 KB of shared memory");
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) return fail(DOCTORS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
 
     // sweep tables
     const int A = p->A, M = p->M;
-    std::vector<float> mop((size_t)A * M), dop((size_t)A * M), coef((size_t)A * 8, 0.0f);
+    std::vector<float> coef((size_t)A * 8, 0.0f);
     const double dx = mesh->dx, dy = mesh->dy, dz = mesh->dz;
     for (int n = 0; n < A; ++n) {
-        double R[16];
-        real_harmonics(p->L, dirs[3 * n], dirs[3 * n + 1], dirs[3 * n + 2], R);
-        for (int lm = 0; lm < M; ++lm) {
-            const int l = lm >= 9 ? 3 : lm >= 4 ? 2 : lm >= 1 ? 1 : 0;
-            mop[(size_t)n * M + lm] = (float)((2 * l + 1) / (4.0 * M_PI) * R[lm]);
-            dop[(size_t)n * M + lm] = (float)(w[n] * R[lm]);
-        }
         const double ox = std::fabs(dirs[3 * n]), oy = std::fabs(dirs[3 * n + 1]), oz = std::fabs(dirs[3 * n + 2]);
         coef[n * 8 + 0] = (float)(ox / dx);
         coef[n * 8 + 1] = (float)(oy / dy);
@@ -352,8 +345,6 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     }
     const size_t GV = (size_t)p->G * p->V, GVM = GV * M;
     int rc = 0;
-    rc = rc ? rc : dalloc_t(&p->d_mop, mop.size(), "tables");
-    rc = rc ? rc : dalloc_t(&p->d_dop, dop.size(), "tables");
     rc = rc ? rc : dalloc_t(&p->d_coef, coef.size(), "tables");
     rc = rc ? rc : dalloc_t(&p->d_mat, p->V, "materials");
     rc = rc ? rc : dalloc_t(&p->d_rho, p->V, "densities");
@@ -379,9 +370,7 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
         e = cudaEventCreate(&ev);
         if (e != cudaSuccess) return fail(DOCTORS_ERR_CUDA, "cudaEventCreate failed");
     }
-    e = cudaMemcpyAsync(p->d_mop, mop.data(), mop.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(p->d_dop, dop.data(), dop.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream);
+    e = ensure_direction_tables(p->device, p->N, &p->table_base);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p->d_coef, coef.data(), coef.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);

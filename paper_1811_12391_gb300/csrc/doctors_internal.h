@@ -142,8 +142,7 @@ struct SweepArgs {
     const float* sigt;                 // [nmat][G]
     const float* src;                  // [G][V][M] moment source
     float* mom;                        // [G][V][M] accumulated moments
-    const float* mop;                  // [A][M] (2l+1)/(4 pi) R_lm(Omega_n)
-    const float* dop;                  // [A][M] w_n R_lm(Omega_n)
+    int table_base;                    // first row of this S_N set in the constant direction tables
     const float* coef;                 // [A][8] cx, cy, cz, cx+cy+cz, leak_x, leak_y, leak_z, w
     float* xface;                      // [8][A8][G][ntx-1][ny][nz]
     float* yface;                      // [8][A8][G][nty-1][nx][nz]
@@ -155,6 +154,9 @@ struct SweepArgs {
 // mode 0: plain; 1: store psi; 2: accumulate sum_n w_n psi_n psi_stored_n into prod
 cudaError_t launch_sweep_stage(const SweepArgs& a, int M, int mode, cudaStream_t s);
 bool sweep_supported(int ab, int M);
+// Upload the shared direction tables (all S_N sets) to the current device,
+// once per device; returns the first table row of order N in *base.
+cudaError_t ensure_direction_tables(int device, int N, int* base);
 
 }  // namespace doctors
 
@@ -174,9 +176,8 @@ struct doctors_problem {
     // sweep tiling
     int tx = 16, ty = 16, ntx = 1, nty = 1, ab = 1, nab = 1;
     // device tables
-    float* d_mop = nullptr;
-    float* d_dop = nullptr;
     float* d_coef = nullptr;
+    int table_base = 0;
     // materials
     int nmat = 0;
     bool have_mat = false;

@@ -8,6 +8,10 @@
 // fluence is the lm = 00 moment.  The dose tally multiplies the group fluence
 // by group-wise conversion factors (Sec. II.A, III.A) and is accumulated in
 // FP64, like the residual norm and the particle balance.
+#include <mutex>
+#include <string>
+#include <vector>
+
 #include "doctors_internal.h"
 
 namespace doctors {
@@ -16,6 +20,49 @@ cudaError_t launch_sweep_m1_entry(const SweepArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_sweep_m4_entry(const SweepArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_sweep_m9_entry(const SweepArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_sweep_m16_entry(const SweepArgs& a, int mode, cudaStream_t s);
+
+cudaError_t upload_tables_m1(const float* R, const float* w);
+cudaError_t upload_tables_m4(const float* R, const float* w);
+cudaError_t upload_tables_m9(const float* R, const float* w);
+cudaError_t upload_tables_m16(const float* R, const float* w);
+
+namespace {
+std::mutex g_table_mu;
+bool g_table_done[64] = {};
+const int kOrders[6] = {2, 4, 6, 8, 12, 16};
+}  // namespace
+
+// The level-symmetric sets and their harmonics depend only on N, so one
+// concatenated table (S2, S4, S6, S8, S12, S16) serves every problem.
+cudaError_t ensure_direction_tables(int device, int N, int* base) {
+    int off = 0, found = -1;
+    for (int q = 0; q < 6; ++q) {
+        if (kOrders[q] == N) found = off;
+        off += kOrders[q] * (kOrders[q] + 2);
+    }
+    if (found < 0 || device < 0 || device >= 64) return cudaErrorInvalidValue;
+    *base = found;
+    std::lock_guard<std::mutex> lock(g_table_mu);
+    if (g_table_done[device]) return cudaSuccess;
+    std::vector<float> R, w;
+    for (int q = 0; q < 6; ++q) {
+        std::vector<double> dirs, wt;
+        std::string err;
+        if (!build_quadrature(kOrders[q], dirs, wt, err)) return cudaErrorInvalidValue;
+        for (size_t n = 0; n < wt.size(); ++n) {
+            double r[16];
+            real_harmonics(3, dirs[3 * n], dirs[3 * n + 1], dirs[3 * n + 2], r);
+            for (int m = 0; m < 16; ++m) R.push_back((float)r[m]);
+            w.push_back((float)wt[n]);
+        }
+    }
+    cudaError_t e = upload_tables_m1(R.data(), w.data());
+    if (e == cudaSuccess) e = upload_tables_m4(R.data(), w.data());
+    if (e == cudaSuccess) e = upload_tables_m9(R.data(), w.data());
+    if (e == cudaSuccess) e = upload_tables_m16(R.data(), w.data());
+    if (e == cudaSuccess) g_table_done[device] = true;
+    return e;
+}
 
 bool sweep_supported(int ab, int M) {
     const int abs_ok[] = {1, 2, 3, 4, 5, 6, 7, 9, 10, 12};

@@ -64,21 +64,32 @@ __device__ __forceinline__ void add_moments(float* p, const float (&a)[M]) {
     }
 }
 
+// Direction tables shared by every problem: R_lm(Omega_n) (Schmidt real
+// harmonics, 16 per direction, l <= 3) and w_n of every supported S_N set,
+// concatenated (S2, S4, S6, S8, S12, S16: 616 directions).  They depend only
+// on N, so they are uploaded once per device; each CTA copies the rows of its
+// directions into shared memory (re-read after every barrier, so the compiler
+// keeps them out of registers).
+constexpr int kTableDirs = 616;
+__constant__ float c_R[kTableDirs * 16];
+__constant__ float c_w[kTableDirs];
+
 // MODE 0: plain sweep.  MODE 1: also store every angular fluence psi[g][n][v]
 // (forward fluence kept for the density gradient).  MODE 2: also accumulate
 // prod[g][v] += sum_n w_n psi_n psi_store[g][n][v] (adjoint sweep against the
 // stored forward fluence).
 template <int AB, int M, int MODE>
 __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs a) {
-    extern __shared__ float sm[];
+    // float4 arrays first: the dynamic shared block is 16-byte aligned
+    extern __shared__ float4 sm4[];
     const int T = a.tx * a.ty;
-    float* buf = sm;                        // [2][AB][T]    previous/current hyperplane
+    float4* coef_s = sm4;                   // [AB]: cx, cy, cz, cx+cy+cz
+    float4* R_s = coef_s + AB;              // [AB][4]: R_lm, 16 per direction
+    float* buf = reinterpret_cast<float*>(R_s + 4 * AB);   // [2][AB][T] previous/current hyperplane
     float* xin = buf + 2 * AB * T;          // [AB][ty][nz]  incoming x-face strip
     float* yin = xin + AB * a.ty * a.nz;    // [AB][tx][nz]  incoming y-face strip
-    float* mop_s = yin + AB * a.tx * a.nz;  // [AB][M]
-    float* dop_s = mop_s + AB * M;          // [AB][M]
-    float* coef_s = dop_s + AB * M;         // [AB][8]
-    float* sigt_s = coef_s + AB * 8;        // [nmat]
+    float* w_s = yin + AB * a.tx * a.nz;    // [AB]
+    float* sigt_s = w_s + AB;               // [nmat]
 
     const int g = blockIdx.z;               // group slowest: resident CTAs share a few groups in L2
     const int o = blockIdx.y / a.nab;       // sweep octant
@@ -89,15 +100,20 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs a) {
     const int sx = (o & 1) ? -1 : 1, sy = (o & 2) ? -1 : 1, sz = (o & 4) ? -1 : 1;
     // the adjoint sweeps direction n along -Omega_n
     const int nbase = (a.reverse ? (o ^ 7) : o) * a.A8 + blk * AB;
+    const int tb = a.table_base + nbase;    // row of direction nbase in the constant tables
     const int slot0 = blk * AB;             // direction slot within the octant (face buffers)
     const size_t xf_stride = (size_t)(a.ntx > 1 ? a.ntx - 1 : 0) * a.ny * a.nz;
     const size_t yf_stride = (size_t)(a.nty > 1 ? a.nty - 1 : 0) * a.nx * a.nz;
 
-    for (int t = threadIdx.x; t < AB * M; t += blockDim.x) {
-        mop_s[t] = a.mop[(size_t)nbase * M + t];
-        dop_s[t] = a.dop[(size_t)nbase * M + t];
+    for (int t = threadIdx.x; t < AB; t += blockDim.x) {
+        const float* c = a.coef + (size_t)(nbase + t) * 8;
+        coef_s[t] = make_float4(c[0], c[1], c[2], c[3]);
+        w_s[t] = c_w[tb + t];
     }
-    for (int t = threadIdx.x; t < AB * 8; t += blockDim.x) coef_s[t] = a.coef[(size_t)nbase * 8 + t];
+    for (int t = threadIdx.x; t < 4 * AB; t += blockDim.x) {
+        const float* r = c_R + (size_t)(tb + t / 4) * 16 + 4 * (t % 4);
+        R_s[t] = make_float4(r[0], r[1], r[2], r[3]);
+    }
     for (int t = threadIdx.x; t < a.nmat; t += blockDim.x) sigt_s[t] = a.sigt[t * a.G + g];
     // incoming face strips (contiguous in the face buffers), zero on the mesh boundary
     {
@@ -138,6 +154,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs a) {
     const size_t vcol = (size_t)j * a.nx + i;      // voxel index of k = 0 in this column
     const bool xout = li == a.tx - 1 && at < a.ntx - 1;
     const bool yout = lj == a.ty - 1 && bt < a.nty - 1;
+    const bool xleak = ir == a.nx - 1, yleak = jr == a.ny - 1;
     float* xo = a.xface + (((size_t)o * a.A8 + slot0) * a.G + g) * xf_stride + ((size_t)at * a.ny + jr) * a.nz;
     float* yo = a.yface + (((size_t)o * a.A8 + slot0) * a.G + g) * yf_stride + ((size_t)bt * a.nx + ir) * a.nz;
     const size_t xo_q = (size_t)a.G * xf_stride, yo_q = (size_t)a.G * yf_stride;
@@ -167,42 +184,91 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs a) {
         const int cb = h & 1, pb = cb ^ 1;
         const bool act = col && kr >= 0 && kr < a.nz;
         float s[M];
+        // (2l+1)/(4 pi) folded into the source moments
 #pragma unroll
-        for (int m = 0; m < M; ++m) s[m] = sn[m];
+        for (int m = 0; m < M; ++m) {
+            const int l = m >= 9 ? 3 : m >= 4 ? 2 : m >= 1 ? 1 : 0;
+            s[m] = sn[m] * ((2 * l + 1) * 0.07957747154594767f);
+        }
         const float sig = sig_n;
         prefetch(kr + 1);
         if (act) {
             const int k = sz > 0 ? kr : a.nz - 1 - kr;
             const size_t v = (size_t)k * plane + vcol;
+            // moments -> directions: AB independent dot products
+            float psi[AB];
+#pragma unroll
+            for (int q = 0; q < AB; ++q) {
+                float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f, t3 = 0.0f;
+#pragma unroll
+                for (int m = 0; m < M; m += 4) {
+                    const float4 R = R_s[4 * q + m / 4];
+                    t0 = fmaf(R.x, s[m], t0);
+                    if (m + 1 < M) t1 = fmaf(R.y, s[m + 1], t1);
+                    if (m + 2 < M) t2 = fmaf(R.z, s[m + 2], t2);
+                    if (m + 3 < M) t3 = fmaf(R.w, s[m + 3], t3);
+                }
+                psi[q] = (t0 + t1) + (t2 + t3);
+            }
+            // step-differenced cell solve per direction
+#pragma unroll
+            for (int q = 0; q < AB; ++q) {
+                const float px = li > 0 ? buf[(pb * AB + q) * T + tid - 1] : xin[(q * a.ty + lj) * a.nz + kr];
+                const float py = lj > 0 ? buf[(pb * AB + q) * T + tid - a.tx] : yin[(q * a.tx + li) * a.nz + kr];
+                const float4 c = coef_s[q];
+                const float num = fmaf(c.z, zc[q], fmaf(c.y, py, fmaf(c.x, px, psi[q])));
+                psi[q] = __fdividef(num, sig + c.w);
+                buf[(cb * AB + q) * T + tid] = psi[q];
+                zc[q] = psi[q];
+            }
+            if constexpr (MODE == 1) {
+#pragma unroll
+                for (int q = 0; q < AB; ++q) a.psi[((size_t)g * a.A + nbase + q) * V + v] = psi[q];
+            }
+            if constexpr (MODE == 2) {
+                float pacc = 0.0f;
+#pragma unroll
+                for (int q = 0; q < AB; ++q)
+                    pacc = fmaf(w_s[q] * psi[q], __ldg(a.psi + ((size_t)g * a.A + nbase + q) * V + v), pacc);
+                atomicAdd(a.prod + gV + v, pacc);
+            }
+            // faces leaving the tile and current leaving the mesh
+            if (xout) {
+#pragma unroll
+                for (int q = 0; q < AB; ++q) xo[q * xo_q + kr] = psi[q];
+            }
+            if (yout) {
+#pragma unroll
+                for (int q = 0; q < AB; ++q) yo[q * yo_q + kr] = psi[q];
+            }
+            if (xleak || yleak || kr == a.nz - 1) {
+#pragma unroll
+                for (int q = 0; q < AB; ++q) {
+                    const float* c = a.coef + (size_t)(nbase + q) * 8;
+                    float f = 0.0f;
+                    if (xleak) f += __ldg(c + 4);
+                    if (yleak) f += __ldg(c + 5);
+                    if (kr == a.nz - 1) f += __ldg(c + 6);
+                    lk = fmaf(f, psi[q], lk);
+                }
+            }
+            // directions -> moments (Eq. 3 for lm = 00)
             float acc[M];
 #pragma unroll
             for (int m = 0; m < M; ++m) acc[m] = 0.0f;
-            float pacc = 0.0f;
 #pragma unroll
             for (int q = 0; q < AB; ++q) {
-                float qn = 0.0f;
+                const float wp = w_s[q] * psi[q];
 #pragma unroll
-                for (int m = 0; m < M; ++m) qn = fmaf(mop_s[q * M + m], s[m], qn);
-                const float px = li > 0 ? buf[(pb * AB + q) * T + tid - 1] : xin[(q * a.ty + lj) * a.nz + kr];
-                const float py = lj > 0 ? buf[(pb * AB + q) * T + tid - a.tx] : yin[(q * a.tx + li) * a.nz + kr];
-                const float* c = coef_s + q * 8;
-                const float num = fmaf(c[2], zc[q], fmaf(c[1], py, fmaf(c[0], px, qn)));
-                const float psi = __fdividef(num, sig + c[3]);
-                buf[(cb * AB + q) * T + tid] = psi;
-                zc[q] = psi;
-                if constexpr (MODE == 1) a.psi[((size_t)g * a.A + nbase + q) * V + v] = psi;
-                if constexpr (MODE == 2)
-                    pacc = fmaf(c[7] * psi, __ldg(a.psi + ((size_t)g * a.A + nbase + q) * V + v), pacc);
-                if (xout) xo[q * xo_q + kr] = psi;
-                if (yout) yo[q * yo_q + kr] = psi;
-                if (ir == a.nx - 1) lk = fmaf(c[4], psi, lk);
-                if (jr == a.ny - 1) lk = fmaf(c[5], psi, lk);
-                if (kr == a.nz - 1) lk = fmaf(c[6], psi, lk);
-#pragma unroll
-                for (int m = 0; m < M; ++m) acc[m] = fmaf(dop_s[q * M + m], psi, acc[m]);
+                for (int m = 0; m < M; m += 4) {
+                    const float4 R = R_s[4 * q + m / 4];
+                    acc[m] = fmaf(R.x, wp, acc[m]);
+                    if (m + 1 < M) acc[m + 1] = fmaf(R.y, wp, acc[m + 1]);
+                    if (m + 2 < M) acc[m + 2] = fmaf(R.z, wp, acc[m + 2]);
+                    if (m + 3 < M) acc[m + 3] = fmaf(R.w, wp, acc[m + 3]);
+                }
             }
             add_moments<M>(a.mom + (gV + v) * M, acc);
-            if constexpr (MODE == 2) atomicAdd(a.prod + gV + v, pacc);
         }
         __syncthreads();
     }
@@ -214,7 +280,15 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs a) {
 }
 
 inline size_t sweep_smem_bytes(int ab, int M, int tx, int ty, int nz, int nmat) {
-    return sizeof(float) * (size_t)(2 * ab * tx * ty + ab * (tx + ty) * nz + 2 * ab * M + 8 * ab + nmat);
+    (void)M;
+    return sizeof(float) * (size_t)(2 * ab * tx * ty + ab * (tx + ty) * nz + 4 * ab + 16 * ab + ab + nmat);
+}
+
+// upload the direction tables of this translation unit's constant bank
+inline cudaError_t upload_direction_tables(const float* R, const float* w) {
+    cudaError_t e = cudaMemcpyToSymbol(c_R, R, sizeof(float) * kTableDirs * 16);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w, w, sizeof(float) * kTableDirs);
+    return e;
 }
 
 template <int M, int MODE>

@@ -10,4 +10,5 @@ cudaError_t launch_sweep_m1_entry(const SweepArgs& a, int mode, cudaStream_t s) 
         default: return cudaErrorInvalidValue;
     }
 }
+cudaError_t upload_tables_m1(const float* R, const float* w) { return upload_direction_tables(R, w); }
 }  // namespace doctors

@@ -10,4 +10,5 @@ cudaError_t launch_sweep_m9_entry(const SweepArgs& a, int mode, cudaStream_t s) 
         default: return cudaErrorInvalidValue;
     }
 }
+cudaError_t upload_tables_m9(const float* R, const float* w) { return upload_direction_tables(R, w); }
 }  // namespace doctors
