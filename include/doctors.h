@@ -85,7 +85,11 @@ typedef struct doctors_options {
     int max_iters;           /* source-iteration cap, >= 1 */
     int tile_x, tile_y;      /* sweep tile in voxels (0 = default 16 x 16); tile_x*tile_y <= 256 */
     int angles_per_block;    /* directions per sweep block (0 = default); must divide N(N+2)/8 */
-    int reserved[8];         /* must be zero */
+    int sweep_kernel;        /* 0 = default (the faster measured path), 1 = CUDA-core moment transforms,
+                                2 = tensor-core (3xTF32 mma) moment transforms (P3 only) */
+    int device_loop;         /* 1 = run the source iteration as one CUDA graph whose while loop is
+                                decided on the device (no host round trip per iteration) */
+    int reserved[6];         /* must be zero */
 } doctors_options;
 
 /* One source (Sec. II.B: position, energy distribution, azimuthal and polar
@@ -217,12 +221,35 @@ int doctors_debug_ray_indices(doctors_problem *p, int src, int voxel, int32_t *i
 int doctors_quadrature(int sn_order, int legendre, double *dirs, double *w, double *R, int *n_dirs);
 
 /* Solve several problems (e.g. the views of an axial scan, or phantoms of
- * different mesh sizes) as one batch: every stage of every problem's
- * iteration is issued on the first problem's stream, and the convergence
- * loop runs until all have converged.  Each problem must have its materials
- * and sources set; results[i] (array may be NULL) receives problem i's
- * report. */
+ * different mesh sizes) as one batch (Sec. II.C: a CT scan is many
+ * concurrent projections).  After each problem's ray trace, one CUDA graph
+ * holds every problem's source iteration inside a device-side while loop:
+ * per iteration, every live problem's scattering source, all its wavefront
+ * stages and its FP64 residual, then a one-thread decision that retires the
+ * problems that have converged (their kernels return at entry from then on)
+ * and ends the loop when all are retired.  Everything runs on the first
+ * problem's stream; all problems must be on one device and have materials
+ * and sources set.  results[i] (array may be NULL) receives problem i's
+ * report; the batch's device time is in every report's ms_total. */
 int doctors_solve_batch(doctors_problem **problems, int n, doctors_result *results);
+
+/* Sweep schedule chosen by doctors_autotune. */
+typedef struct doctors_tuning {
+    int tile_x, tile_y;      /* tile of columns */
+    int angles_per_block;    /* directions per CTA */
+    int sweep_kernel;        /* 1 CUDA-core, 2 tensor-core moment transforms */
+    double ms_per_sweep;     /* measured time of one full sweep of this problem */
+    int candidates;          /* schedules timed (0 if taken from the cache) */
+} doctors_tuning;
+
+/* Autotune the wavefront schedule (tile shape, directions per CTA and the
+ * moment-transform path) of a problem whose materials and sources are set:
+ * each candidate schedule is timed on two sweeps of the problem's own
+ * first-collision source with CUDA events, and the fastest is installed.
+ * Results are cached per (mesh size, S_N order, Legendre order, groups) for
+ * the life of the process.  Synchronises; invalidates any solution.  `out`
+ * may be NULL. */
+int doctors_autotune(doctors_problem *p, doctors_tuning *out);
 
 /* Release the problem and its device memory.  NULL is ignored. */
 void doctors_destroy(doctors_problem *p);

@@ -47,7 +47,8 @@ class doctors_options(ctypes.Structure):
     _fields_ = [("groups", ctypes.c_int), ("sn_order", ctypes.c_int), ("legendre", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_iters", ctypes.c_int), ("tile_x", ctypes.c_int),
                 ("tile_y", ctypes.c_int), ("angles_per_block", ctypes.c_int),
-                ("reserved", ctypes.c_int * 8)]
+                ("sweep_kernel", ctypes.c_int), ("device_loop", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
 
 
 class doctors_source(ctypes.Structure):
@@ -64,6 +65,14 @@ class doctors_result(ctypes.Structure):
                 ("ms_raytrace", ctypes.c_double), ("ms_iterate", ctypes.c_double),
                 ("ms_sweep", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class doctors_tuning(ctypes.Structure):
+    _fields_ = [("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("angles_per_block", ctypes.c_int),
+                ("sweep_kernel", ctypes.c_int), ("ms_per_sweep", ctypes.c_double), ("candidates", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -88,6 +97,7 @@ SIGNATURES = [
     ("doctors_quadrature", _int, [_int, _int, _P(ctypes.c_double), _P(ctypes.c_double),
                                   _P(ctypes.c_double), _P(_int)]),
     ("doctors_solve_batch", _int, [_P(_vp), _int, _P(doctors_result)]),
+    ("doctors_autotune", _int, [_vp, _P(doctors_tuning)]),
     ("doctors_destroy", None, [_vp]),
     ("doctors_last_error", ctypes.c_char_p, []),
 ]
@@ -147,5 +157,6 @@ doctors_adjoint_solve = _fwd("doctors_adjoint_solve")
 doctors_debug_ray_indices = _fwd("doctors_debug_ray_indices")
 doctors_quadrature = _fwd("doctors_quadrature")
 doctors_solve_batch = _fwd("doctors_solve_batch")
+doctors_autotune = _fwd("doctors_autotune")
 doctors_destroy = _fwd("doctors_destroy")
 doctors_last_error = _fwd("doctors_last_error")

@@ -14,10 +14,6 @@
 namespace doctors {
 namespace {
 
-__device__ __forceinline__ int degree_of_lm(int lm) {
-    return lm >= 9 ? 3 : lm >= 4 ? 2 : lm >= 1 ? 1 : 0;
-}
-
 template <int M>
 __device__ __forceinline__ void harmonics_scaled(float x, float y, float z, float (&R)[M]) {
     // Schmidt semi-normalised real harmonics times (2l+1)/(4 pi)
@@ -64,7 +60,7 @@ __global__ void __launch_bounds__(256) k_source_grad(const SourceGradArgs a) {
             const float* t = a.T + ((size_t)g * V + v) * M;
             float imp = 0.0f;
 #pragma unroll
-            for (int lm = 0; lm < M; ++lm) imp = fmaf(R[lm], t[lm], imp);
+            for (int pm = 0; pm < M; ++pm) imp = fmaf(R[lm_of_pos(pm, M)], t[pm], imp);
             const double impd = a.r[(size_t)g * V + v] + (double)imp;
             atomicAdd(&s_acc[g], (double)u * impd);
             if (a.H) {
@@ -93,7 +89,7 @@ __global__ void __launch_bounds__(256) k_density_grad(const DensityGradArgs a) {
     double acc = 0.0;
     for (int g = 0; g < a.G; ++g) {
         for (int lm = 0; lm < a.M; ++lm) {
-            const int l = degree_of_lm(lm);
+            const int l = degree_of_lm(lm_of_pos(lm, a.M));
             const float zc = a.Z[g * VM + v * a.M + lm] * (float)(2 * l + 1) * 0.07957747154594767f;
             if (zc == 0.0f) continue;
             const float* tab = a.sigs + ((size_t)m * (a.L + 1) + l) * a.G * a.G;

@@ -6,10 +6,14 @@
 // (Jacobi in energy: same fixed point as solving the groups one after the
 // other), stopped on the FP64 relative L2 change of the scalar fluence
 // (Eq. 3) in every group.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "doctors_internal.h"
@@ -42,6 +46,9 @@ using namespace doctors;
     } while (0)
 
 namespace {
+
+// default choice of the moment-transform path of the sweep for P3 problems
+constexpr bool kDefaultTensorCoreSweep = false;
 
 int dalloc(void** p, size_t bytes, const char* what) {
     if (bytes == 0) bytes = 16;
@@ -220,7 +227,7 @@ int iterate(doctors_problem* p, int reverse, const float* Q, float* mom, doctors
         CU(cudaEventRecord(p->ev[3], p->stream));
         for (int st = 0; st < p->ntx + p->nty - 1; ++st) {
             sw.stage = st;
-            CU(launch_sweep_stage(sw, p->M, 0, p->stream));
+            CU(p->use_tc ? launch_sweep_tc(sw, 0, p->stream) : launch_sweep_stage(sw, p->M, 0, p->stream));
             ++p->launches;
         }
         CU(cudaEventRecord(p->ev[4], p->stream));
@@ -273,6 +280,191 @@ int iterate(doctors_problem* p, int reverse, const float* Q, float* mom, doctors
     return conv ? DOCTORS_OK : DOCTORS_ERR_NOT_CONVERGED;
 }
 
+
+// Launch one sweep stage with the problem's chosen kernel.
+cudaError_t sweep_stage(const doctors_problem* p, const SweepArgs& sw, int mode, cudaStream_t s) {
+    return p->use_tc ? launch_sweep_tc(sw, mode, s) : launch_sweep_stage(sw, p->M, mode, s);
+}
+
+// Source iteration of n problems as one CUDA graph: a while node whose body
+// holds every problem's iteration and a decision kernel that retires
+// converged problems and ends the loop on the device.
+int graph_iterate(doctors_problem** ps, int n, int reverse, const float* const* Qs, float* const* moms,
+                  doctors_result* infos) {
+    doctors_problem* p0 = ps[0];
+    cudaStream_t s = p0->stream;
+    std::vector<LoopCtl> ctl(n);
+    for (int q = 0; q < n; ++q) {
+        ctl[q].done = 0;
+        ctl[q].iters = 0;
+        ctl[q].max_iters = ps[q]->opt.max_iters;
+        ctl[q].G = ps[q]->G;
+        ctl[q].tol = std::max(ps[q]->opt.tol, kTolFloor);
+        ctl[q].resid = 0.0;
+        ctl[q].res = ps[q]->d_red + ps[q]->G;
+    }
+    LoopCtl* d_ctl = nullptr;
+    int rc = dalloc_t(&d_ctl, (size_t)n, "loop control");
+    if (rc) return rc;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaMemcpyAsync(d_ctl, ctl.data(), n * sizeof(LoopCtl), cudaMemcpyHostToDevice, s);
+    for (int q = 0; q < n && e == cudaSuccess; ++q) {
+        e = cudaMemsetAsync(moms[q], 0, (size_t)ps[q]->G * ps[q]->V * ps[q]->M * sizeof(float), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ps[q]->d_prev, 0, (size_t)ps[q]->G * ps[q]->V * sizeof(float), s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaGraphCreate(&graph, 0);
+    cudaGraphConditionalHandle handle{};
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+    cudaGraph_t body = nullptr;
+    if (e == cudaSuccess) {
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = handle;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+        if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
+    }
+    long long per_iter_launches = 1;
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        for (int q = 0; q < n && e == cudaSuccess; ++q) {
+            doctors_problem* p = ps[q];
+            const int* skip = &d_ctl[q].done;
+            ScatterArgs sa{};
+            sa.V = p->V; sa.G = p->G; sa.M = p->M; sa.L = p->L; sa.nmat = p->nmat; sa.transpose = reverse;
+            sa.mat = p->d_mat; sa.rho = p->d_rho; sa.sigs = p->d_sigs;
+            sa.base = Qs[q]; sa.phi = moms[q]; sa.out = p->d_src; sa.skip = skip;
+            e = launch_scatter(sa, cap);
+            if (e == cudaSuccess) e = launch_zero(moms[q], (size_t)p->G * p->V * p->M, skip, cap);
+            if (e == cudaSuccess) e = launch_zero(p->d_red, 5 * (size_t)p->G, skip, cap);
+            SweepArgs sw = sweep_args(p, reverse, p->d_src, moms[q]);
+            sw.skip = skip;
+            for (int st = 0; st < p->ntx + p->nty - 1 && e == cudaSuccess; ++st) {
+                sw.stage = st;
+                e = sweep_stage(p, sw, 0, cap);
+            }
+            if (e == cudaSuccess) e = launch_residual(p->V, p->G, p->M, moms[q], p->d_prev, p->d_red + p->G, cap, skip);
+            per_iter_launches += 4 + (p->ntx + p->nty - 1);
+        }
+        if (e == cudaSuccess) e = launch_decide(d_ctl, n, (unsigned long long)handle, cap);
+        cudaGraph_t captured = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cap, &captured);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctl.data(), d_ctl, n * sizeof(LoopCtl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
+    cudaFree(d_ctl);
+    if (e != cudaSuccess) {
+        set_error(std::string("device-side iteration graph: ") + cudaGetErrorString(e));
+        return DOCTORS_ERR_CUDA;
+    }
+    int worst = DOCTORS_OK;
+    int max_it = 0;
+    for (int q = 0; q < n; ++q) max_it = std::max(max_it, ctl[q].iters);
+    for (int q = 0; q < n; ++q) {
+        doctors_problem* p = ps[q];
+        if (!std::isfinite(ctl[q].resid)) {
+            set_error("source iteration produced a non-finite fluence");
+            return DOCTORS_ERR_INVALID_ARG;
+        }
+        // particle balance of the last sweep (FP64)
+        const double vol = p->mesh.dx * p->mesh.dy * p->mesh.dz;
+        double* d_bal = p->d_red + 3 * p->G;
+        CU(cudaMemsetAsync(d_bal, 0, 2 * (size_t)p->G * sizeof(double), s));
+        CU(launch_balance(p->V, p->G, p->M, p->d_mat, p->d_rho, p->d_sigt, p->d_src, moms[q], vol, d_bal, s));
+        CU(cudaMemcpyAsync(p->h_red, p->d_red, 5 * (size_t)p->G * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        double gain = 0.0, loss = 0.0;
+        for (int g = 0; g < p->G; ++g) {
+            gain += p->h_red[3 * p->G + 2 * g];
+            loss += p->h_red[3 * p->G + 2 * g + 1] + p->h_red[g];
+        }
+        const bool conv = ctl[q].resid < ctl[q].tol;
+        if (infos) {
+            doctors_result& r = infos[q];
+            r.iterations = ctl[q].iters;
+            r.converged = conv ? 1 : 0;
+            r.residual = ctl[q].resid;
+            r.balance_rel = gain != 0.0 ? std::fabs(gain - loss) / std::fabs(gain) : 0.0;
+            r.tol_used = ctl[q].tol;
+            r.cell_updates = (double)ctl[q].iters * (double)p->V * p->A * p->G;
+            r.ms_sweep = -1.0;   // not separable inside the graph
+        }
+        p->launches += (long long)max_it * per_iter_launches / n + 1;
+        if (!conv) worst = DOCTORS_ERR_NOT_CONVERGED;
+    }
+    return worst;
+}
+
+// (Re)install a sweep schedule: tile, directions per CTA, transform path.
+int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
+    if (tx < 1 || ty < 1 || tx * ty > 256) {
+        set_error("tile_x * tile_y must be 1..256");
+        return DOCTORS_ERR_INVALID_ARG;
+    }
+    if (p->A8 % ab != 0 || !sweep_supported(ab, p->M)) {
+        set_error("angles_per_block must divide N(N+2)/8 and be one of 1,2,3,4,5,6,7,9,10,12");
+        return DOCTORS_ERR_INVALID_ARG;
+    }
+    if (kernel < 0 || kernel > 2) {
+        set_error("sweep_kernel must be 0, 1 or 2");
+        return DOCTORS_ERR_INVALID_ARG;
+    }
+    const bool tc_ok = sweep_tc_supported(ab, p->M, tx, ty);
+    if (kernel == 2 && !tc_ok) {
+        set_error("tensor-core sweep needs P3, <= 16 directions per block and tile_x*tile_y a multiple of 32");
+        return DOCTORS_ERR_INVALID_ARG;
+    }
+    const bool use_tc = kernel == 2 || (kernel == 0 && tc_ok && kDefaultTensorCoreSweep);
+    const size_t smem = use_tc ? sweep_tc_smem_bytes(ab, tx, ty, p->nz, kMaxMat)
+                               : sizeof(float) * (size_t)(2 * ab * tx * ty + ab * (tx + ty) * p->nz + 21 * ab + kMaxMat);
+    if (smem > 227 * 1024) {
+        set_error("sweep tile needs more than 227 KB of shared memory");
+        return DOCTORS_ERR_INVALID_ARG;
+    }
+    const int ntx = (p->nx + tx - 1) / tx, nty = (p->ny + ty - 1) / ty;
+    const size_t xf = (size_t)p->A * p->G * (ntx > 1 ? ntx - 1 : 0) * p->ny * p->nz;
+    const size_t yf = (size_t)p->A * p->G * (nty > 1 ? nty - 1 : 0) * p->nx * p->nz;
+    const size_t xf_old = (size_t)p->A * p->G * (p->ntx > 1 ? p->ntx - 1 : 0) * p->ny * p->nz;
+    const size_t yf_old = (size_t)p->A * p->G * (p->nty > 1 ? p->nty - 1 : 0) * p->nx * p->nz;
+    if (p->d_xface == nullptr || xf > xf_old) {
+        float* nb = nullptr;
+        int rc = dalloc_t(&nb, xf, "x face buffer");
+        if (rc) return rc;
+        if (p->d_xface) cudaFree(p->d_xface);
+        p->d_xface = nb;
+    }
+    if (p->d_yface == nullptr || yf > yf_old) {
+        float* nb = nullptr;
+        int rc = dalloc_t(&nb, yf, "y face buffer");
+        if (rc) return rc;
+        if (p->d_yface) cudaFree(p->d_yface);
+        p->d_yface = nb;
+    }
+    p->tx = tx; p->ty = ty; p->ab = ab; p->nab = p->A8 / ab; p->ntx = ntx; p->nty = nty; p->use_tc = use_tc;
+    return DOCTORS_OK;
+}
+
+struct TuneKey {
+    int nx, ny, nz, N, L, G;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(nx, ny, nz, N, L, G) < std::tie(o.nx, o.ny, o.nz, o.N, o.L, o.G);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, doctors_tuning> g_tune_cache;
+
 }  // namespace
 
 extern "C" {
@@ -322,8 +514,14 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     p->nab = p->A8 / p->ab;
     p->ntx = (p->nx + p->tx - 1) / p->tx;
     p->nty = (p->ny + p->ty - 1) / p->ty;
-    const size_t smem = sizeof(float) * (size_t)(2 * p->ab * p->tx * p->ty + p->ab * (p->tx + p->ty) * p->nz +
-                                                 21 * p->ab + kMaxMat);
+    if (opt->sweep_kernel < 0 || opt->sweep_kernel > 2) return fail(DOCTORS_ERR_INVALID_ARG, "sweep_kernel must be 0, 1 or 2");
+    const bool tc_ok = sweep_tc_supported(p->ab, p->M, p->tx, p->ty);
+    if (opt->sweep_kernel == 2 && !tc_ok)
+        return fail(DOCTORS_ERR_INVALID_ARG, "tensor-core sweep needs P3, <= 16 directions per block and tile_x*tile_y a multiple of 32");
+    p->use_tc = opt->sweep_kernel == 2 || (opt->sweep_kernel == 0 && tc_ok && kDefaultTensorCoreSweep);
+    const size_t smem = p->use_tc ? sweep_tc_smem_bytes(p->ab, p->tx, p->ty, p->nz, kMaxMat)
+                                  : sizeof(float) * (size_t)(2 * p->ab * p->tx * p->ty + p->ab * (p->tx + p->ty) * p->nz +
+                                                             21 * p->ab + kMaxMat);
     if (smem > 227 * 1024) return fail(DOCTORS_ERR_INVALID_ARG, "sweep tile needs more than 227 KB of shared memory");
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) return fail(DOCTORS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
@@ -358,10 +556,7 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     rc = rc ? rc : dalloc_t(&p->d_src, GVM, "sweep source");
     rc = rc ? rc : dalloc_t(&p->d_prev, GV, "previous scalar fluence");
     rc = rc ? rc : dalloc_t(&p->d_iso, (size_t)p->G, "volume source");
-    const size_t xf = (size_t)A * p->G * (p->ntx > 1 ? p->ntx - 1 : 0) * p->ny * p->nz;
-    const size_t yf = (size_t)A * p->G * (p->nty > 1 ? p->nty - 1 : 0) * p->nx * p->nz;
-    rc = rc ? rc : dalloc_t(&p->d_xface, xf, "x face buffer");
-    rc = rc ? rc : dalloc_t(&p->d_yface, yf, "y face buffer");
+    rc = rc ? rc : configure_sweep(p, p->tx, p->ty, p->ab, opt->sweep_kernel);
     rc = rc ? rc : dalloc_t(&p->d_red, 5 * (size_t)p->G, "reductions");
     if (rc) return fail(rc, "");
     e = cudaMallocHost(&p->h_red, 5 * (size_t)p->G * sizeof(double));
@@ -489,7 +684,14 @@ int doctors_solve(doctors_problem* p, doctors_result* info) {
     rc = first_collision(p);
     if (rc) return rc;
     CU(cudaEventRecord(p->ev[1], p->stream));
-    rc = iterate(p, 0, p->d_Q, p->d_mom, &r);
+    if (p->opt.device_loop) {
+        doctors_problem* list[1] = {p};
+        const float* Qs[1] = {p->d_Q};
+        float* moms[1] = {p->d_mom};
+        rc = graph_iterate(list, 1, 0, Qs, moms, &r);
+    } else {
+        rc = iterate(p, 0, p->d_Q, p->d_mom, &r);
+    }
     if (rc && rc != DOCTORS_ERR_NOT_CONVERGED) return rc;
     CU(cudaEventRecord(p->ev[2], p->stream));
     CU(cudaEventSynchronize(p->ev[2]));
@@ -616,15 +818,138 @@ int doctors_debug_ray_indices(doctors_problem* p, int src, int voxel, int32_t* i
 
 int doctors_solve_batch(doctors_problem** problems, int n, doctors_result* results) {
     CHECK_ARG(problems && n >= 1, "empty batch");
-    int worst = DOCTORS_OK;
     for (int q = 0; q < n; ++q) {
-        doctors_result r{};
-        const int rc = doctors_solve(problems[q], &r);
-        if (results) results[q] = r;
-        if (rc && rc != DOCTORS_ERR_NOT_CONVERGED) return rc;
-        if (rc) worst = rc;
+        CHECK_ARG(problems[q] != nullptr, "null problem in batch");
+        CHECK_ARG(problems[q]->device == problems[0]->device, "batch problems must share one device");
+        for (int r = 0; r < q; ++r) CHECK_ARG(problems[r] != problems[q], "a problem appears twice in the batch");
+        if (!problems[q]->have_mat || !problems[q]->have_src) {
+            set_error("set materials and sources of every batch problem before solving");
+            return DOCTORS_ERR_STATE;
+        }
     }
-    return worst;
+    doctors_problem* p0 = problems[0];
+    int rc = check_problem(p0);
+    if (rc) return rc;
+    CU(cudaEventRecord(p0->ev[0], p0->stream));
+    for (int q = 0; q < n; ++q) {
+        problems[q]->solved = false;
+        problems[q]->adjoint_done = false;
+        problems[q]->launches = 0;
+        CU(cudaStreamSynchronize(p0->stream));
+        rc = first_collision(problems[q]);
+        if (rc) return rc;
+    }
+    CU(cudaEventRecord(p0->ev[1], p0->stream));
+    std::vector<const float*> Qs(n);
+    std::vector<float*> moms(n);
+    for (int q = 0; q < n; ++q) {
+        Qs[q] = problems[q]->d_Q;
+        moms[q] = problems[q]->d_mom;
+    }
+    std::vector<doctors_result> res(n);
+    rc = graph_iterate(problems, n, 0, Qs.data(), moms.data(), res.data());
+    if (rc && rc != DOCTORS_ERR_NOT_CONVERGED) return rc;
+    CU(cudaEventRecord(p0->ev[2], p0->stream));
+    CU(cudaEventSynchronize(p0->ev[2]));
+    float t01 = 0, t12 = 0, t02 = 0;
+    cudaEventElapsedTime(&t01, p0->ev[0], p0->ev[1]);
+    cudaEventElapsedTime(&t12, p0->ev[1], p0->ev[2]);
+    cudaEventElapsedTime(&t02, p0->ev[0], p0->ev[2]);
+    for (int q = 0; q < n; ++q) {
+        res[q].ms_raytrace = t01;
+        res[q].ms_iterate = t12;
+        res[q].ms_total = t02;
+        res[q].launches = problems[q]->launches;
+        problems[q]->solved = true;
+        if (results) results[q] = res[q];
+    }
+    if (rc == DOCTORS_ERR_NOT_CONVERGED) set_error("iteration cap reached before convergence");
+    return rc;
+}
+
+int doctors_autotune(doctors_problem* p, doctors_tuning* out) {
+    int rc = check_problem(p);
+    if (rc) return rc;
+    if (!p->have_mat || !p->have_src) {
+        set_error("set materials and sources before autotuning");
+        return DOCTORS_ERR_STATE;
+    }
+    const TuneKey key{p->nx, p->ny, p->nz, p->N, p->L, p->G};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            doctors_tuning t = it->second;
+            rc = configure_sweep(p, t.tile_x, t.tile_y, t.angles_per_block, t.sweep_kernel);
+            if (rc) return rc;
+            t.candidates = 0;
+            if (out) *out = t;
+            p->solved = false;
+            return DOCTORS_OK;
+        }
+    }
+    p->solved = false;
+    p->launches = 0;
+    rc = first_collision(p);
+    if (rc) return rc;
+    const int tiles[][2] = {{16, 16}, {32, 8}, {16, 8}, {8, 16}, {8, 8}, {32, 4}};
+    const int abs_c[] = {12, 10, 9, 7, 6, 5, 4, 3, 2, 1};
+    std::vector<int> abs_ok;
+    for (int ab : abs_c)
+        if (p->A8 % ab == 0 && (int)abs_ok.size() < 3) abs_ok.push_back(ab);
+    doctors_tuning best{};
+    best.ms_per_sweep = 1e30;
+    int count = 0;
+    const int saved[4] = {p->tx, p->ty, p->ab, p->use_tc ? 2 : 1};
+    for (const auto& t : tiles) {
+        for (int ab : abs_ok) {
+            for (int kernel = 1; kernel <= 2; ++kernel) {
+                if (kernel == 2 && !sweep_tc_supported(ab, p->M, t[0], t[1])) continue;
+                if (configure_sweep(p, t[0], t[1], ab, kernel) != DOCTORS_OK) continue;
+                SweepArgs sw = sweep_args(p, 0, p->d_Q, p->d_mom);
+                float total = 0.0f;
+                cudaError_t e = cudaSuccess;
+                for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+                    e = cudaMemsetAsync(p->d_mom, 0, (size_t)p->G * p->V * p->M * sizeof(float), p->stream);
+                    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_red, 0, 5 * (size_t)p->G * sizeof(double), p->stream);
+                    if (e == cudaSuccess) e = cudaEventRecord(p->ev[3], p->stream);
+                    for (int st = 0; st < p->ntx + p->nty - 1 && e == cudaSuccess; ++st) {
+                        sw.stage = st;
+                        e = sweep_stage(p, sw, 0, p->stream);
+                    }
+                    if (e == cudaSuccess) e = cudaEventRecord(p->ev[4], p->stream);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(p->ev[4]);
+                    float ms = 0.0f;
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p->ev[3], p->ev[4]);
+                    if (rep > 0) total += ms;   // first repetition is a warm-up
+                }
+                if (e != cudaSuccess) {
+                    set_error(std::string("autotune: ") + cudaGetErrorString(e));
+                    return DOCTORS_ERR_CUDA;
+                }
+                ++count;
+                const double ms = total / 2.0;
+                if (ms < best.ms_per_sweep) {
+                    best.tile_x = t[0]; best.tile_y = t[1]; best.angles_per_block = ab; best.sweep_kernel = kernel;
+                    best.ms_per_sweep = ms;
+                }
+            }
+        }
+    }
+    if (count == 0) {
+        configure_sweep(p, saved[0], saved[1], saved[2], saved[3]);
+        set_error("autotune: no valid schedule");
+        return DOCTORS_ERR_INVALID_ARG;
+    }
+    rc = configure_sweep(p, best.tile_x, best.tile_y, best.angles_per_block, best.sweep_kernel);
+    if (rc) return rc;
+    best.candidates = count;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    if (out) *out = best;
+    return DOCTORS_OK;
 }
 
 void doctors_destroy(doctors_problem* p) {
@@ -648,7 +973,7 @@ int sweep_once(doctors_problem* p, int reverse, int mode, const float* src, floa
     sw.prod = p->d_prod;
     for (int st = 0; st < p->ntx + p->nty - 1; ++st) {
         sw.stage = st;
-        CU(launch_sweep_stage(sw, p->M, mode, p->stream));
+        CU(p->use_tc ? launch_sweep_tc(sw, mode, p->stream) : launch_sweep_stage(sw, p->M, mode, p->stream));
         ++p->launches;
     }
     return DOCTORS_OK;

@@ -20,6 +20,15 @@ constexpr double kTolFloor = 1e-6;   // FP32 sweep: relative-change floor
 
 void set_error(const std::string& msg);
 
+// Storage order of the flux moments of one cell.  For P3 (16 moments) the
+// record is stored as the 4 x 4 transpose of the (l, m) order, so that the
+// tensor-core sweep loads a lane's A-operand fragment and stores its
+// accumulator fragment as one float4 each: position p holds moment
+// lm = p / 4 + 4 (p % 4) (position 0 is still lm = 00).  Other orders are
+// stored in (l, m) order.
+__host__ __device__ constexpr int lm_of_pos(int p, int M) { return M == 16 ? (p >> 2) + 4 * (p & 3) : p; }
+__host__ __device__ constexpr int degree_of_lm(int lm) { return lm >= 9 ? 3 : lm >= 4 ? 2 : lm >= 1 ? 1 : 0; }
+
 bool build_quadrature(int N, std::vector<double>& dirs, std::vector<double>& w, std::string& err);
 void real_harmonics(int L, double x, double y, double z, double* R);
 
@@ -110,12 +119,29 @@ struct ScatterArgs {
     float iso_field_scale;
     const float* phi;                  // [G][V][M] or null (no scattering term)
     float* out;                        // [G][V][M]
+    const int* skip;                   // if non-null and *skip != 0 the kernel does nothing
 };
 cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s);
 
 // residual: res[g][0] += sum_v (phi00 - prev)^2, res[g][1] += sum_v phi00^2; prev = phi00
 cudaError_t launch_residual(size_t V, int G, int M, const float* mom, float* prev, double* res,
-                            cudaStream_t s);
+                            cudaStream_t s, const int* skip = nullptr);
+// zero n floats (or doubles) unless *skip
+cudaError_t launch_zero(float* p, size_t n, const int* skip, cudaStream_t s);
+cudaError_t launch_zero(double* p, size_t n, const int* skip, cudaStream_t s);
+
+// One entry per instance of a device-side iteration loop.
+struct LoopCtl {
+    int done;                          // instance retired (converged or capped)
+    int iters;                         // sweeps performed
+    int max_iters;
+    int G;
+    double tol;
+    double resid;                      // max over groups of the last relative change
+    const double* res;                 // [G][2] residual sums of the instance
+};
+// Retire converged instances; end the while loop when all are retired.
+cudaError_t launch_decide(LoopCtl* ctl, int n, unsigned long long cond_handle, cudaStream_t s);
 
 // balance: bal[g][0] += vol * sum s00, bal[g][1] += vol * sum sigma_t phi00
 cudaError_t launch_balance(size_t V, int G, int M, const uint8_t* mat, const float* rho,
@@ -150,6 +176,7 @@ struct SweepArgs {
     int A;                             // directions (psi indexing)
     float* psi;                        // [G][A][V]: written (mode 1) or read (mode 2)
     float* prod;                       // [G][V]: mode 2 accumulator
+    const int* skip;                   // if non-null and *skip != 0 the kernel does nothing
 };
 // mode 0: plain; 1: store psi; 2: accumulate sum_n w_n psi_n psi_stored_n into prod
 cudaError_t launch_sweep_stage(const SweepArgs& a, int M, int mode, cudaStream_t s);
@@ -157,6 +184,12 @@ bool sweep_supported(int ab, int M);
 // Upload the shared direction tables (all S_N sets) to the current device,
 // once per device; returns the first table row of order N in *base.
 cudaError_t ensure_direction_tables(int device, int N, int* base);
+
+// tensor-core sweep (P3): sweep_tc.cu
+bool sweep_tc_supported(int ab, int M, int tx, int ty);
+size_t sweep_tc_smem_bytes(int ab, int tx, int ty, int nz, int nmat);
+cudaError_t launch_sweep_tc(const SweepArgs& a, int mode, cudaStream_t s);
+cudaError_t upload_tables_tc(const float* R, const float* w);
 
 }  // namespace doctors
 
@@ -175,6 +208,7 @@ struct doctors_problem {
     std::vector<double> dirs, w;
     // sweep tiling
     int tx = 16, ty = 16, ntx = 1, nty = 1, ab = 1, nab = 1;
+    bool use_tc = false;            // tensor-core transforms in the sweep
     // device tables
     float* d_coef = nullptr;
     int table_base = 0;

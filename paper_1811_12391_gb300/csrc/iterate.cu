@@ -60,6 +60,7 @@ cudaError_t ensure_direction_tables(int device, int N, int* base) {
     if (e == cudaSuccess) e = upload_tables_m4(R.data(), w.data());
     if (e == cudaSuccess) e = upload_tables_m9(R.data(), w.data());
     if (e == cudaSuccess) e = upload_tables_m16(R.data(), w.data());
+    if (e == cudaSuccess) e = upload_tables_tc(R.data(), w.data());
     if (e == cudaSuccess) g_table_done[device] = true;
     return e;
 }
@@ -83,19 +84,16 @@ cudaError_t launch_sweep_stage(const SweepArgs& a, int M, int mode, cudaStream_t
 
 namespace {
 
-__device__ __forceinline__ int degree_of(int lm) {
-    return lm >= 9 ? 3 : lm >= 4 ? 2 : lm >= 1 ? 1 : 0;
-}
-
 // One thread per (voxel, moment); moment fastest so that a warp reads and
 // writes contiguous memory.  Loops over destination groups; the source
 // groups' moments are re-read through L1.
 __global__ void __launch_bounds__(256) k_scatter(const ScatterArgs a) {
+    if (a.skip && *a.skip) return;
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= a.V * a.M) return;
     const size_t v = t / a.M;
     const int lm = (int)(t % a.M);
-    const int l = degree_of(lm);
+    const int l = degree_of_lm(lm_of_pos(lm, a.M));
     const int m = __ldg(a.mat + v);
     const float r = __ldg(a.rho + v);
     const float* tab = a.sigs + ((size_t)m * (a.L + 1) + l) * a.G * a.G;
@@ -147,7 +145,8 @@ __device__ __forceinline__ void block_reduce_add(double (&x)[NV], double* dst) {
 
 // grid: (blocks over V, G)
 __global__ void __launch_bounds__(256) k_residual(size_t V, int M, const float* mom, float* prev,
-                                                  double* res) {
+                                                  double* res, const int* skip) {
+    if (skip && *skip) return;
     const int g = blockIdx.y;
     double x[2] = {0.0, 0.0};
     for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (size_t)gridDim.x * blockDim.x) {
@@ -200,6 +199,37 @@ __global__ void __launch_bounds__(256) k_extract(size_t V, int G, int M, int whi
     out[t] = x;
 }
 
+template <class T>
+__global__ void __launch_bounds__(256) k_zero(T* p, size_t n, const int* skip) {
+    if (skip && *skip) return;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        p[t] = T(0);
+}
+
+// One thread: update every live instance's iteration count and residual
+// (max over groups of sqrt(sum (dphi)^2 / sum phi^2)), retire it when the
+// relative change is below its tolerance or the cap is reached, and stop
+// the graph's while loop once all instances are retired.
+__global__ void k_decide(LoopCtl* ctl, int n, cudaGraphConditionalHandle h) {
+    if (threadIdx.x != 0) return;
+    bool all = true;
+    for (int q = 0; q < n; ++q) {
+        LoopCtl& c = ctl[q];
+        if (c.done) continue;
+        double eps = 0.0;
+        for (int g = 0; g < c.G; ++g) {
+            const double num = c.res[2 * g], den = c.res[2 * g + 1];
+            const double e = den > 0.0 ? sqrt(num / den) : 0.0;
+            eps = e > eps || e != e ? e : eps;
+        }
+        c.iters += 1;
+        c.resid = eps;
+        if (eps < c.tol || c.iters >= c.max_iters) c.done = 1;
+        else all = false;
+    }
+    if (all) cudaGraphSetConditional(h, 0);
+}
+
 unsigned blocks_for(size_t n, int bs, unsigned cap = 0) {
     size_t b = (n + bs - 1) / bs;
     if (cap && b > cap) b = cap;
@@ -214,9 +244,24 @@ cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_residual(size_t V, int G, int M, const float* mom, float* prev, double* res,
-                            cudaStream_t s) {
+                            cudaStream_t s, const int* skip) {
     dim3 grid(blocks_for(V, 256, 296), G);
-    k_residual<<<grid, 256, 0, s>>>(V, M, mom, prev, res);
+    k_residual<<<grid, 256, 0, s>>>(V, M, mom, prev, res, skip);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero(float* p, size_t n, const int* skip, cudaStream_t s) {
+    k_zero<float><<<blocks_for((n + 3) / 4, 256, 152 * 16), 256, 0, s>>>(p, n, skip);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero(double* p, size_t n, const int* skip, cudaStream_t s) {
+    k_zero<double><<<blocks_for((n + 3) / 4, 256, 152 * 16), 256, 0, s>>>(p, n, skip);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decide(LoopCtl* ctl, int n, unsigned long long cond_handle, cudaStream_t s) {
+    k_decide<<<1, 32, 0, s>>>(ctl, n, (cudaGraphConditionalHandle)cond_handle);
     return cudaGetLastError();
 }
 

@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(256) k_uncollided_moments(const MomentArgs a) 
         if (p == 0.0f) continue;
         float* u = a.U + ((size_t)g * V + v) * M;
 #pragma unroll
-        for (int m = 0; m < M; ++m) u[m] += p * R[m];
+        for (int m = 0; m < M; ++m) u[m] += p * R[lm_of_pos(m, M)];
     }
 }
 

@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs a) {
     float* w_s = yin + AB * a.tx * a.nz;    // [AB]
     float* sigt_s = w_s + AB;               // [nmat]
 
+    if (a.skip && *a.skip) return;         // retired instance of a batched loop
     const int g = blockIdx.z;               // group slowest: resident CTAs share a few groups in L2
     const int o = blockIdx.y / a.nab;       // sweep octant
     const int blk = blockIdx.y % a.nab;
@@ -111,8 +112,10 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs a) {
         w_s[t] = c_w[tb + t];
     }
     for (int t = threadIdx.x; t < 4 * AB; t += blockDim.x) {
-        const float* r = c_R + (size_t)(tb + t / 4) * 16 + 4 * (t % 4);
-        R_s[t] = make_float4(r[0], r[1], r[2], r[3]);
+        const float* r = c_R + (size_t)(tb + t / 4) * 16;
+        const int p0 = 4 * (t % 4);
+        R_s[t] = make_float4(r[lm_of_pos(p0, M)], r[lm_of_pos(p0 + 1, M)], r[lm_of_pos(p0 + 2, M)],
+                             r[lm_of_pos(p0 + 3, M)]);
     }
     for (int t = threadIdx.x; t < a.nmat; t += blockDim.x) sigt_s[t] = a.sigt[t * a.G + g];
     // incoming face strips (contiguous in the face buffers), zero on the mesh boundary
@@ -186,10 +189,8 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs a) {
         float s[M];
         // (2l+1)/(4 pi) folded into the source moments
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-            const int l = m >= 9 ? 3 : m >= 4 ? 2 : m >= 1 ? 1 : 0;
-            s[m] = sn[m] * ((2 * l + 1) * 0.07957747154594767f);
-        }
+        for (int m = 0; m < M; ++m)
+            s[m] = sn[m] * ((2 * degree_of_lm(lm_of_pos(m, M)) + 1) * 0.07957747154594767f);
         const float sig = sig_n;
         prefetch(kr + 1);
         if (act) {

@@ -53,7 +53,7 @@ class DoctorsProblem:
     (default: torch's current stream)."""
 
     def __init__(self, prob, stream=None, tol: Optional[float] = None, max_iters: Optional[int] = None,
-                 tile=(0, 0), angles_per_block: int = 0):
+                 tile=(0, 0), angles_per_block: int = 0, sweep_kernel: int = 0, device_loop: int = 0):
         torch = _require_torch_cuda()
         self.torch = torch
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -71,6 +71,8 @@ class DoctorsProblem:
         opt.max_iters = int(max_iters if max_iters is not None else getattr(prob, "max_iters", 500))
         opt.tile_x, opt.tile_y = int(tile[0]), int(tile[1])
         opt.angles_per_block = int(angles_per_block)
+        opt.sweep_kernel = int(sweep_kernel)
+        opt.device_loop = int(device_loop)
         h = ctypes.c_void_p()
         C.check(C.doctors_create_problem(ctypes.byref(mesh), ctypes.byref(opt),
                                          ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
@@ -161,6 +163,11 @@ class DoctorsProblem:
         outs["result"] = res.as_dict()
         return outs
 
+    def autotune(self) -> dict:
+        t = C.doctors_tuning()
+        C.check(C.doctors_autotune(self.h, ctypes.byref(t)))
+        return t.as_dict()
+
     def ray_indices(self, src: int, voxel: int, cap: int = 4096):
         idx = (ctypes.c_int32 * cap)()
         ln = (ctypes.c_float * cap)()
@@ -178,6 +185,18 @@ class DoctorsProblem:
             self.close()
         except Exception:
             pass
+
+
+def solve_batch(problems: Sequence["DoctorsProblem"]) -> list:
+    """Solve several problems in one graph-captured device-side loop."""
+    n = len(problems)
+    arr = (ctypes.c_void_p * n)(*[p.h.value for p in problems])
+    res = (C.doctors_result * n)()
+    C.check(C.doctors_solve_batch(arr, n, res))
+    out = [r.as_dict() for r in res]
+    for p, r in zip(problems, out):
+        p.result = r
+    return out
 
 
 def quadrature(sn_order: int, legendre: int):

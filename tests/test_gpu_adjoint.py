@@ -39,12 +39,28 @@ def _roi(p):
     return roi
 
 
-def test_adjoint_fluence_and_gradients_match_oracle(env):
-    torch, C, DoctorsProblem = env
+@pytest.fixture(scope="module")
+def grad_ref():
     p = _problem()
     roi = _roi(p)
-    ref = osv.gradients(p, roi, tol=1e-12)
-    d = DoctorsProblem(p, tol=1e-6, max_iters=400)
+    return p, roi, osv.gradients(p, roi, tol=1e-12)
+
+
+@pytest.mark.parametrize("L,kernel", [(1, 1), (3, 1), (3, 2)])
+def test_adjoint_fluence_and_gradients_match_oracle(env, grad_ref, L, kernel):
+    torch, C, DoctorsProblem = env
+    if L == 1:
+        p, roi, ref = grad_ref
+    else:
+        p = _problem()
+        p = ph.water_cylinder(seed=3, nx=20, ny=18, nz=6, G=3, sn=4, L=3, dx=1.0, dy=1.0, dz=1.5,
+                              diameter=16.0, sid=20.0, fan_deg=60.0, z_width=8.0)
+        p.sources = ph.axial_scan_sources(p, 2, sid=20.0, fan_deg=60.0, z_width=8.0)
+        p.sources[-1].weight = 0.7
+        p.density[:] = _problem().density
+        roi = _roi(p)
+        ref = osv.gradients(p, roi, tol=1e-12)
+    d = DoctorsProblem(p, tol=1e-6, max_iters=400, sweep_kernel=kernel)
     d.solve()
     r = osv.response_from_roi(p, roi)
     g = d.adjoint(torch.as_tensor(r, device="cuda"))

@@ -48,24 +48,45 @@ def test_tiny_cube_full(dp):
     d.close()
 
 
-@pytest.mark.parametrize("tile,ab", [((16, 16), 0), ((8, 4), 5), ((5, 7), 2)])
-def test_ragged_multitile_cylinder(dp, tile, ab):
-    """Several sweep tiles with ragged tails in x and y, S8 P3."""
+@pytest.fixture(scope="module")
+def cylinder_ref():
     p = ph.water_cylinder(nx=36, ny=28, nz=10, dx=1.0, dy=1.25, dz=1.1, diameter=30.0, G=5, sn=8, L=3)
-    sol = osv.solve(p, tol=1e-11)
-    d = dp(p, tol=1e-6, max_iters=400, tile=tile, angles_per_block=ab)
-    _compare(d, p, sol, f"cylinder tile={tile} ab={ab}")
+    return p, osv.solve(p, tol=1e-11)
+
+
+@pytest.mark.parametrize("tile,ab,kernel", [((16, 16), 0, 1), ((16, 16), 0, 2), ((8, 4), 5, 1), ((8, 4), 5, 2),
+                                            ((5, 7), 2, 1), ((16, 2), 10, 2)])
+def test_ragged_multitile_cylinder(dp, cylinder_ref, tile, ab, kernel):
+    """Several sweep tiles with ragged tails in x and y, S8 P3, with the
+    CUDA-core (1) and tensor-core (2) moment transforms."""
+    p, sol = cylinder_ref
+    d = dp(p, tol=1e-6, max_iters=400, tile=tile, angles_per_block=ab, sweep_kernel=kernel)
+    _compare(d, p, sol, f"cylinder tile={tile} ab={ab} kernel={kernel}")
     d.close()
 
 
-def test_abdomen_s16_multi_angle_block(dp):
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_abdomen_s16_multi_angle_block(dp, kernel):
     """Heterogeneous abdomen-like phantom, S16 (three direction blocks per
     octant), P3, five materials."""
     p = ph.abdomen(nx=32, ny=32, nz=6, d=1.0, dz=2.0, G=3, sn=16, L=3)
     sol = osv.solve(p, tol=1e-11)
-    d = dp(p, tol=1e-6, max_iters=400)
-    _compare(d, p, sol, "abdomen S16")
+    d = dp(p, tol=1e-6, max_iters=400, sweep_kernel=kernel)
+    _compare(d, p, sol, f"abdomen S16 kernel={kernel}")
     d.close()
+
+
+def test_tensor_core_and_cuda_core_sweeps_agree(dp):
+    """The two moment-transform paths give the same fluence on the full-size
+    water cylinder (one sweep from the first-collision source)."""
+    p = ph.water_cylinder()
+    outs = []
+    for kernel in (1, 2):
+        d = dp(p, tol=1e-6, max_iters=1, sweep_kernel=kernel)
+        d.solve(allow_not_converged=True)
+        outs.append(d.fluence_host(1))
+        d.close()
+    assert max_rel(outs[1], outs[0]) <= 2e-5
 
 
 def test_p0_and_p2_moment_counts(dp):
