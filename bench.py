@@ -138,6 +138,41 @@ def oracle_sample(p, seconds=12.0):
     return cells / el, n, el
 
 
+def bench_batched(torch, DoctorsProblem, ph, stream):
+    """Axial-scan batch: 64 views on the water-cylinder mesh plus 16 extra
+    cylinders (6 x 48^3, 5 x 64x64x32, 5 x 96x96x32), solved as one
+    graph-captured batch and, for comparison, one instance at a time."""
+    from paper_1811_12391_gb300.solver import solve_batch
+    base = ph.config_problem("water_cylinder")
+    inst = [base.with_sources([v]) for v in ph.axial_scan_sources(base, 64)] + ph.extra_cylinders()
+    ds = [DoctorsProblem(q, stream=stream, tol=1e-6, max_iters=500) for q in inst]
+    for d in ds[:1]:
+        d.autotune()
+    solve_batch(ds)                      # warm-up
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = solve_batch(ds)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1)
+    dose_sum = float(sum(d.dose(q.k_dep).sum().item() for d, q in zip(ds, inst)))
+    e0.record(stream)
+    single = [d.solve() for d in ds]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_single = e0.elapsed_time(e1)
+    cells = sum(r["cell_updates"] for r in res)
+    for d in ds:
+        d.close()
+    return {"instances": len(inst), "ms_batch": ms_batch, "ms_one_at_a_time": ms_single,
+            "speedup_vs_single_instance_solves": ms_single / ms_batch,
+            "cell_updates_per_s": cells / (ms_batch / 1e3), "summed_dose": dose_sum,
+            "iterations_max": max(r["iterations"] for r in res),
+            "converged": all(r["converged"] for r in res)}
+
+
 def run_reference(args, rank, world):
     from synth import phantoms as ph
     if rank != 0:
@@ -172,6 +207,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="omit the adjoint and batched-scan measurements (the headline line is unchanged)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -197,6 +234,7 @@ def main():
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         d = DoctorsProblem(p, stream=stream, tol=1e-6, max_iters=500)
+        tuning = d.autotune()
         for _ in range(args.warmup):
             d.solve()
         torch.cuda.synchronize()
@@ -239,7 +277,22 @@ def main():
         e2e_s = time.perf_counter() - t0
         h2d = p.V * 1 + p.V * 4
         d2h = phi.nbytes + dose.nbytes
+
+        # adjoint (backward) solve of the mean dose in a central region
+        adjoint = None
+        if not args.no_extra:
+            roi = np.zeros(p.V)
+            roi.reshape(p.nz, p.ny, p.nx)[p.nz // 2 - 2:p.nz // 2 + 2, p.ny // 2 - 4:p.ny // 2 + 4,
+                                          p.nx // 2 - 4:p.nx // 2 + 4] = 1.0 / 256.0
+            resp = torch.as_tensor(p.k_dep[p.mat].T * (p.density.astype(np.float64) * roi)[None, :],
+                                   device="cuda")
+            d.solve()
+            g = d.adjoint(resp)
+            g = d.adjoint(resp)
+            adjoint = {"ms_per_solve": g["result"]["ms_total"], "iterations": g["result"]["iterations"],
+                       "gradients": "view weights, spectrum, densities"}
         d.close()
+        batched = None if (args.no_extra or world > 1) else bench_batched(torch, DoctorsProblem, ph, stream)
 
     if world > 1:
         dist.destroy_process_group()
@@ -272,6 +325,9 @@ def main():
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clocks,
+        "autotune": tuning,
+        "adjoint": adjoint,
+        "batched_axial_scan": batched,
     }
     print(json.dumps(line), flush=True)
 

@@ -331,32 +331,60 @@ int graph_iterate(doctors_problem** ps, int n, int reverse, const float* const* 
         if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
     }
     long long per_iter_launches = 1;
+    // independent instances run on parallel branches of the body: the
+    // capture forks onto up to kBranches side streams and joins before the
+    // decision kernel
+    constexpr int kBranches = 8;
+    const int nb = std::min(n, kBranches);
+    cudaStream_t side[kBranches] = {};
+    cudaEvent_t fork = nullptr, join[kBranches] = {};
+    for (int b = 0; b < nb && e == cudaSuccess; ++b) {
+        e = cudaStreamCreateWithFlags(&side[b], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[b], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
+        if (nb > 1) {
+            e = cudaEventRecord(fork, cap);
+            for (int b = 0; b < nb && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(side[b], fork, 0);
+        }
         for (int q = 0; q < n && e == cudaSuccess; ++q) {
             doctors_problem* p = ps[q];
             const int* skip = &d_ctl[q].done;
+            cudaStream_t cs = nb > 1 ? side[q % nb] : cap;
             ScatterArgs sa{};
             sa.V = p->V; sa.G = p->G; sa.M = p->M; sa.L = p->L; sa.nmat = p->nmat; sa.transpose = reverse;
             sa.mat = p->d_mat; sa.rho = p->d_rho; sa.sigs = p->d_sigs;
             sa.base = Qs[q]; sa.phi = moms[q]; sa.out = p->d_src; sa.skip = skip;
-            e = launch_scatter(sa, cap);
-            if (e == cudaSuccess) e = launch_zero(moms[q], (size_t)p->G * p->V * p->M, skip, cap);
-            if (e == cudaSuccess) e = launch_zero(p->d_red, 5 * (size_t)p->G, skip, cap);
+            e = launch_scatter(sa, cs);
+            if (e == cudaSuccess) e = launch_zero(moms[q], (size_t)p->G * p->V * p->M, skip, cs);
+            if (e == cudaSuccess) e = launch_zero(p->d_red, 5 * (size_t)p->G, skip, cs);
             SweepArgs sw = sweep_args(p, reverse, p->d_src, moms[q]);
             sw.skip = skip;
             for (int st = 0; st < p->ntx + p->nty - 1 && e == cudaSuccess; ++st) {
                 sw.stage = st;
-                e = sweep_stage(p, sw, 0, cap);
+                e = sweep_stage(p, sw, 0, cs);
             }
-            if (e == cudaSuccess) e = launch_residual(p->V, p->G, p->M, moms[q], p->d_prev, p->d_red + p->G, cap, skip);
+            if (e == cudaSuccess) e = launch_residual(p->V, p->G, p->M, moms[q], p->d_prev, p->d_red + p->G, cs, skip);
             per_iter_launches += 4 + (p->ntx + p->nty - 1);
+        }
+        if (nb > 1) {
+            for (int b = 0; b < nb && e == cudaSuccess; ++b) {
+                e = cudaEventRecord(join[b], side[b]);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, join[b], 0);
+            }
         }
         if (e == cudaSuccess) e = launch_decide(d_ctl, n, (unsigned long long)handle, cap);
         cudaGraph_t captured = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(cap, &captured);
         if (e == cudaSuccess) e = e2;
     }
+    for (int b = 0; b < nb; ++b) {
+        if (join[b]) cudaEventDestroy(join[b]);
+        if (side[b]) cudaStreamDestroy(side[b]);
+    }
+    if (fork) cudaEventDestroy(fork);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
     if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ctl.data(), d_ctl, n * sizeof(LoopCtl), cudaMemcpyDeviceToHost, s);

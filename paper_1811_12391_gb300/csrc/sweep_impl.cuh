@@ -146,7 +146,25 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs a) {
     __syncthreads();
 
     const int tid = threadIdx.x;
-    const int li = tid % a.tx, lj = tid / a.tx;
+    // threads own the tile's columns in diagonal order (li + lj ascending):
+    // the columns active at a hyperplane step are then a contiguous range of
+    // threads, so warps are either busy or skip the step entirely
+    int li = 0, lj = 0;
+    {
+        int base = 0;
+        for (int d = 0; d <= a.tx + a.ty - 2; ++d) {
+            const int lo = d > a.ty - 1 ? d - (a.ty - 1) : 0;
+            const int hi = d < a.tx - 1 ? d : a.tx - 1;
+            const int cnt = hi - lo + 1;
+            if (tid < base + cnt) {
+                li = lo + (tid - base);
+                lj = d - li;
+                break;
+            }
+            base += cnt;
+        }
+    }
+    const int col_id = lj * a.tx + li;          // column slot in the plane buffers
     const int ir = at * a.tx + li, jr = bt * a.ty + lj;
     const bool col = ir < a.nx && jr < a.ny;
     const int i = sx > 0 ? ir : a.nx - 1 - ir;
@@ -179,21 +197,21 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs a) {
             sig_n = __ldg(a.rho + v) * sigt_s[__ldg(a.mat + v)];
         }
     };
-    prefetch(-li - lj);
+    prefetch(0);      // first cell of this column
 
     const int hmax = a.tx + a.ty + a.nz - 3;
     for (int h = 0; h <= hmax; ++h) {
         const int kr = h - li - lj;
         const int cb = h & 1, pb = cb ^ 1;
         const bool act = col && kr >= 0 && kr < a.nz;
-        float s[M];
-        // (2l+1)/(4 pi) folded into the source moments
-#pragma unroll
-        for (int m = 0; m < M; ++m)
-            s[m] = sn[m] * ((2 * degree_of_lm(lm_of_pos(m, M)) + 1) * 0.07957747154594767f);
-        const float sig = sig_n;
-        prefetch(kr + 1);
         if (act) {
+            float s[M];
+            // (2l+1)/(4 pi) folded into the source moments
+#pragma unroll
+            for (int m = 0; m < M; ++m)
+                s[m] = sn[m] * ((2 * degree_of_lm(lm_of_pos(m, M)) + 1) * 0.07957747154594767f);
+            const float sig = sig_n;
+            prefetch(kr + 1);
             const int k = sz > 0 ? kr : a.nz - 1 - kr;
             const size_t v = (size_t)k * plane + vcol;
             // moments -> directions: AB independent dot products
@@ -214,12 +232,12 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs a) {
             // step-differenced cell solve per direction
 #pragma unroll
             for (int q = 0; q < AB; ++q) {
-                const float px = li > 0 ? buf[(pb * AB + q) * T + tid - 1] : xin[(q * a.ty + lj) * a.nz + kr];
-                const float py = lj > 0 ? buf[(pb * AB + q) * T + tid - a.tx] : yin[(q * a.tx + li) * a.nz + kr];
+                const float px = li > 0 ? buf[(pb * AB + q) * T + col_id - 1] : xin[(q * a.ty + lj) * a.nz + kr];
+                const float py = lj > 0 ? buf[(pb * AB + q) * T + col_id - a.tx] : yin[(q * a.tx + li) * a.nz + kr];
                 const float4 c = coef_s[q];
                 const float num = fmaf(c.z, zc[q], fmaf(c.y, py, fmaf(c.x, px, psi[q])));
                 psi[q] = __fdividef(num, sig + c.w);
-                buf[(cb * AB + q) * T + tid] = psi[q];
+                buf[(cb * AB + q) * T + col_id] = psi[q];
                 zc[q] = psi[q];
             }
             if constexpr (MODE == 1) {
