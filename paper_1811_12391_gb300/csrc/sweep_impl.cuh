@@ -291,11 +291,16 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs a) {
         }
         __syncthreads();
     }
-    // boundary leakage of this CTA, reduced per warp in FP64
+    // boundary leakage of this CTA, reduced per full warp in FP64 (the last
+    // warp of a block whose size is not a multiple of 32 adds lane by lane)
     double dl = (double)lk;
+    if ((int)blockDim.x - (tid & ~31) >= 32) {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) dl += __shfl_down_sync(0xffffffffu, dl, off);
-    if ((tid & 31) == 0 && dl != 0.0) atomicAdd(a.leak + g, dl);
+        for (int off = 16; off > 0; off >>= 1) dl += __shfl_down_sync(0xffffffffu, dl, off);
+        if ((tid & 31) == 0 && dl != 0.0) atomicAdd(a.leak + g, dl);
+    } else if (dl != 0.0) {
+        atomicAdd(a.leak + g, dl);
+    }
 }
 
 inline size_t sweep_smem_bytes(int ab, int M, int tx, int ty, int nz, int nmat) {
