@@ -178,3 +178,29 @@ def test_water_cylinder_full_size_properties(dp):
             for flip in (a[g][:, :, ::-1], a[g][::-1, :, :]):
                 assert (np.abs(a[g] - flip)[sel] / np.abs(a[g])[sel]).max() < 2e-4
     d.close()
+
+
+@pytest.mark.parametrize("name", ["water_cylinder", "abdomen"])
+def test_full_size_against_stored_oracle_samples(dp, name):
+    """Full-size workloads in the configuration the benchmark times: the
+    fluences and dose at 600 seeded voxels, and every group's fluence summed
+    over the mesh, against FP64 oracle values stored by
+    tests/golden/make_full_size_samples.py."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", f"{name}_samples.npz")
+    if not os.path.exists(path):
+        pytest.skip(f"{path} not generated")
+    ref = np.load(path)
+    p = ph.config_problem(name)
+    d = dp(p, tol=1e-6, max_iters=500)
+    d.autotune()
+    r = d.solve()
+    assert r["converged"] == 1
+    idx = ref["voxels"]
+    phi = d.fluence_host(2)
+    assert max_rel(d.fluence_host(0)[:, idx], ref["phi_u"]) <= REL_TOL
+    assert max_rel(d.fluence_host(1)[:, idx], ref["phi_c"]) <= REL_TOL
+    assert max_rel(phi[:, idx], ref["phi"]) <= REL_TOL
+    assert max_rel(d.dose_host(p.k_dep)[idx], ref["dose"]) <= REL_TOL
+    np.testing.assert_allclose(phi.astype(np.float64).sum(axis=1), ref["phi_total"], rtol=REL_TOL)
+    d.close()
