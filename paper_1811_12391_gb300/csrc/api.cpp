@@ -451,7 +451,7 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
     }
     const bool tc_ok = sweep_tc_supported(ab, p->M, tx, ty);
     if (kernel == 2 && !tc_ok) {
-        set_error("tensor-core sweep needs P3, <= 16 directions per block and tile_x*tile_y a multiple of 32");
+        set_error("tensor-core sweep needs P3, <= 16 directions per block and a 16x16, 32x8, 16x8, 8x16, 8x8 or 8x4 tile");
         return DOCTORS_ERR_INVALID_ARG;
     }
     const bool use_tc = kernel == 2 || (kernel == 0 && tc_ok && kDefaultTensorCoreSweep);
@@ -545,7 +545,7 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     if (opt->sweep_kernel < 0 || opt->sweep_kernel > 2) return fail(DOCTORS_ERR_INVALID_ARG, "sweep_kernel must be 0, 1 or 2");
     const bool tc_ok = sweep_tc_supported(p->ab, p->M, p->tx, p->ty);
     if (opt->sweep_kernel == 2 && !tc_ok)
-        return fail(DOCTORS_ERR_INVALID_ARG, "tensor-core sweep needs P3, <= 16 directions per block and tile_x*tile_y a multiple of 32");
+        return fail(DOCTORS_ERR_INVALID_ARG, "tensor-core sweep needs P3, <= 16 directions per block and a 16x16, 32x8, 16x8, 8x16, 8x8 or 8x4 tile");
     p->use_tc = opt->sweep_kernel == 2 || (opt->sweep_kernel == 0 && tc_ok && kDefaultTensorCoreSweep);
     const size_t smem = p->use_tc ? sweep_tc_smem_bytes(p->ab, p->tx, p->ty, p->nz, kMaxMat)
                                   : sizeof(float) * (size_t)(2 * p->ab * p->tx * p->ty + p->ab * (p->tx + p->ty) * p->nz +

@@ -17,14 +17,16 @@
 //   A (16x8):  a0 = A[g][t]  a1 = A[g+8][t]  a2 = A[g][t+4]  a3 = A[g+8][t+4]
 //   B (8x8):   b0 = B[t][g]  b1 = B[t+4][g]
 //   C (16x8):  c0 = C[g][2t] c1 = C[g][2t+1] c2 = C[g+8][2t] c3 = C[g+8][2t+1]
-// Rows are cells: lane (g, t) owns the fragment rows of cells g, g+8, 16+g,
-// 24+g of its warp.  With the moment record stored in the transposed order
-// of lm_of_pos(), a lane's A-fragment entries of one cell are one float4
-// (positions 4t..4t+3), and so are its accumulator entries after the second
-// product.  The step solve runs directly on the C fragment of the first
-// product (cells x direction slots 2t, 2t+1, 8+2t, 9+2t), and that fragment
-// is reused as the A operand of the second product by ordering the summed
-// direction index as (2t, 2t+1) <-> (t, t+4).
+// Rows are cells: fragment row r of a warp is the cell of lane r, so lane
+// (g, t) loads and accumulates the rows g, g+8, 16+g, 24+g.  With the moment
+// record stored in the transposed order of lm_of_pos(), a lane's A-fragment
+// entries of one cell are one float4 (positions 4t..4t+3), and so are its
+// accumulator entries after the second product.  Between the two products a
+// per-warp shared-memory block turns the C fragment (cells x direction slots)
+// into one row per thread: each thread runs the step solve of its own cell
+// (as in the CUDA-core sweep), writes its row of Psi back, and the second
+// product reads the rows as A fragments with the summed direction index
+// ordered as (2t, 2t+1) <-> (t, t+4).
 #include <cstdint>
 
 #include "doctors_internal.h"
@@ -38,6 +40,7 @@ __constant__ float tc_w[kTcDirs];        // w_n
 namespace {
 
 constexpr int kSlots = 16;               // direction slots per CTA (padded)
+constexpr int kQS = 20;                  // row stride (floats) of the per-warp Q/Psi rows
 constexpr float kInv4Pi = 0.07957747154594767f;
 
 __device__ __forceinline__ uint32_t tf32_of(float x) {
@@ -49,6 +52,14 @@ __device__ __forceinline__ uint32_t tf32_of(float x) {
 __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
     hi = tf32_of(x);
     lo = tf32_of(x - __uint_as_float(hi));
+}
+
+// Split for the per-step operands: hi keeps the TF32 bits of x (truncated),
+// lo = x - hi is exact in FP32 and is truncated to TF32 by the mma itself;
+// the product error stays below ~2^-20 |a b|.
+__device__ __forceinline__ void split_fast(float x, uint32_t& hi, uint32_t& lo) {
+    hi = __float_as_uint(x) & 0xffffe000u;
+    lo = __float_as_uint(x - __uint_as_float(hi));
 }
 
 __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
@@ -77,22 +88,29 @@ __device__ __forceinline__ float4 split_pair(float b0, float b1) {
 }
 
 // MODE 0: plain; 1: store psi[g][n][v]; 2: prod[g][v] += sum_n w_n psi_n psi_stored_n
-template <int MODE>
-__global__ void __launch_bounds__(256, 2) k_sweep_tc(const SweepArgs a) {
+// The upwind planes carry a one-column halo (x = -1, y = -1) that the
+// boundary threads fill from the incoming face strips one step ahead, so the
+// cell solve reads its x and y upwind values at fixed offsets.
+template <int TX, int TY, int MODE>
+__global__ void __launch_bounds__(TX * TY, 2) k_sweep_tc(const SweepArgs a) {
+    if (a.skip && *a.skip) return;         // retired instance of a batched loop
+    constexpr int T = TX * TY;              // columns = threads (multiple of 32)
+    // plane pitch with the x halo, plus one spare column so that the stride
+    // between consecutive diagonal-order threads (PX - 1) is odd: no bank conflicts
+    constexpr int PX = TX + 2;
+    constexpr int P = PX * (TY + 1);        // plane size with both halos
     extern __shared__ float4 sm4[];
-    const int T = a.tx * a.ty;
-    const int SA = T + 4;                   // slot stride of the plane buffers (bank-conflict free)
     const int AB = a.ab;
     float4* tabM = sm4;                     // [2 kt][2 nt][32 lanes]  moments -> directions
     float4* tabD = tabM + 128;              // [2 kt][2 nt][32 lanes]  directions -> moments
     float4* coefs = tabD + 128;             // [16 slots]: cx, cy, cz, cx+cy+cz
     float4* leakc = coefs + kSlots;         // [16 slots]: leak_x, leak_y, leak_z, w
-    float* buf = reinterpret_cast<float*>(leakc + kSlots);   // [2][16][SA]
-    float* xin = buf + 2 * kSlots * SA;     // [AB][ty][nz]
-    float* yin = xin + AB * a.ty * a.nz;    // [AB][tx][nz]
-    float* sigt_s = yin + AB * a.tx * a.nz; // [nmat]
+    float* qs = reinterpret_cast<float*>(leakc + kSlots);   // per warp [32 rows][kQS]: Q, then Psi
+    float* buf = qs + T * kQS;              // [2][16 slots][P] previous/current hyperplane
+    float* xin = buf + 2 * kSlots * P;      // [AB][TY][nz]
+    float* yin = xin + AB * TY * a.nz;      // [AB][TX][nz]
+    float* sigt_s = yin + AB * TX * a.nz;   // [nmat]
 
-    if (a.skip && *a.skip) return;         // retired instance of a batched loop
     const int g = blockIdx.z;
     const int o = blockIdx.y / a.nab;
     const int blk = blockIdx.y % a.nab;
@@ -110,7 +128,6 @@ __global__ void __launch_bounds__(256, 2) k_sweep_tc(const SweepArgs a) {
     for (int idx = threadIdx.x; idx < 128; idx += blockDim.x) {
         const int kt = idx >> 6, nt = (idx >> 5) & 1, ln = idx & 31;
         const int gq = ln >> 2, tq = ln & 3;
-        // moments -> directions: B[k = lm][n = slot] = (2l+1)/(4 pi) R_lm(Omega_slot)
         {
             const int n = 8 * nt + gq;
             const int k0 = 8 * kt + tq, k1 = k0 + 4;
@@ -121,9 +138,8 @@ __global__ void __launch_bounds__(256, 2) k_sweep_tc(const SweepArgs a) {
             }
             tabM[idx] = split_pair(b0, b1);
         }
-        // directions -> moments: B'[k' = (slot 8kt+2t, 8kt+2t+1) <-> (t, t+4)][n' = output column]
         {
-            const int col = gq;                              // column within the n' tile
+            const int col = gq;
             const int lm = col / 2 + 4 * ((col & 1) + 2 * nt);
             const int s0 = 8 * kt + 2 * tq, s1 = s0 + 1;
             const float b0 = s0 < AB ? tc_w[tb + s0] * tc_R[(tb + s0) * 16 + lm] : 0.0f;
@@ -136,226 +152,229 @@ __global__ void __launch_bounds__(256, 2) k_sweep_tc(const SweepArgs a) {
             const float* c = a.coef + (size_t)(nbase + t) * 8;
             coefs[t] = make_float4(c[0], c[1], c[2], c[3]);
             leakc[t] = make_float4(c[4], c[5], c[6], c[7]);
-        } else {   // padded slot: psi = 0 whatever the cell
+        } else {
             coefs[t] = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
             leakc[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
     }
     for (int t = threadIdx.x; t < a.nmat; t += blockDim.x) sigt_s[t] = a.sigt[t * a.G + g];
+    for (int t = threadIdx.x; t < 2 * kSlots * P; t += blockDim.x) buf[t] = 0.0f;
     {
-        const int nxs = AB * a.ty * a.nz;
+        const int nxs = AB * TY * a.nz;
         for (int t = threadIdx.x; t < nxs; t += blockDim.x) {
-            const int q = t / (a.ty * a.nz), r = t % (a.ty * a.nz);
-            const int jr = bt * a.ty + r / a.nz;
+            const int q = t / (TY * a.nz), r = t % (TY * a.nz);
+            const int jr = bt * TY + r / a.nz;
             float val = 0.0f;
             if (at > 0 && jr < a.ny) {
                 const size_t fb = (((size_t)o * a.A8 + slot0 + q) * a.G + g) * xf_stride;
-                val = a.xface[fb + (size_t)(at - 1) * a.ny * a.nz + (size_t)bt * a.ty * a.nz + r];
+                val = a.xface[fb + (size_t)(at - 1) * a.ny * a.nz + (size_t)bt * TY * a.nz + r];
             }
             xin[t] = val;
         }
-        const int nys = AB * a.tx * a.nz;
+        const int nys = AB * TX * a.nz;
         for (int t = threadIdx.x; t < nys; t += blockDim.x) {
-            const int q = t / (a.tx * a.nz), r = t % (a.tx * a.nz);
-            const int ir = at * a.tx + r / a.nz;
+            const int q = t / (TX * a.nz), r = t % (TX * a.nz);
+            const int ir = at * TX + r / a.nz;
             float val = 0.0f;
             if (bt > 0 && ir < a.nx) {
                 const size_t fb = (((size_t)o * a.A8 + slot0 + q) * a.G + g) * yf_stride;
-                val = a.yface[fb + (size_t)(bt - 1) * a.nx * a.nz + (size_t)at * a.tx * a.nz + r];
+                val = a.yface[fb + (size_t)(bt - 1) * a.nx * a.nz + (size_t)at * TX * a.nz + r];
             }
             yin[t] = val;
         }
     }
     __syncthreads();
 
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
     const int gq = lane >> 2, tq = lane & 3;
+    float* wq = qs + (tid >> 5) * 32 * kQS;        // this warp's Q/Psi rows
+    // threads own the tile's columns in diagonal order (li + lj ascending)
+    int li = 0, lj = 0;
+    {
+        int base = 0;
+        for (int d = 0; d <= TX + TY - 2; ++d) {
+            const int lo = d > TY - 1 ? d - (TY - 1) : 0;
+            const int hi = d < TX - 1 ? d : TX - 1;
+            const int cnt = hi - lo + 1;
+            if (tid < base + cnt) {
+                li = lo + (tid - base);
+                lj = d - li;
+                break;
+            }
+            base += cnt;
+        }
+    }
+    const int pc = (lj + 1) * PX + (li + 1);       // plane cell of this column
+    const int ir = at * TX + li, jr = bt * TY + lj;
+    const bool col = ir < a.nx && jr < a.ny;
+    const int i = sx > 0 ? ir : a.nx - 1 - ir;
+    const int j = sy > 0 ? jr : a.ny - 1 - jr;
     const size_t V = (size_t)a.nx * a.ny * a.nz;
     const size_t gV = (size_t)g * V;
     const size_t plane = (size_t)a.nx * a.ny;
+    const size_t vcol = (size_t)j * a.nx + i;
+    const bool xout = li == TX - 1 && at < a.ntx - 1;
+    const bool yout = lj == TY - 1 && bt < a.nty - 1;
+    const bool xleak = ir == a.nx - 1, yleak = jr == a.ny - 1;
+    float* xo = a.xface + (((size_t)o * a.A8 + slot0) * a.G + g) * xf_stride + ((size_t)at * a.ny + jr) * a.nz;
+    float* yo = a.yface + (((size_t)o * a.A8 + slot0) * a.G + g) * yf_stride + ((size_t)bt * a.nx + ir) * a.nz;
+    const size_t xo_q = (size_t)a.G * xf_stride, yo_q = (size_t)a.G * yf_stride;
 
-    // the four cells (fragment rows gq, gq+8, 16+gq, 24+gq) of this lane
-    int cc[4], li[4], lj[4], ir[4], jr[4];
-    size_t vcol[4];
-    bool colok[4];
+    // halo values of step hh (incoming faces of the tile's first column/row)
+    auto fill_halo = [&](int hh, float* dst) {
+        if (li == 0) {
+            const int kq = hh - lj;
+            if (kq >= 0 && kq < a.nz)
+                for (int s = 0; s < AB; ++s) dst[s * P + (lj + 1) * PX] = xin[(s * TY + lj) * a.nz + kq];
+        }
+        if (lj == 0) {
+            const int kq = hh - li;
+            if (kq >= 0 && kq < a.nz)
+                for (int s = 0; s < AB; ++s) dst[s * P + li + 1] = yin[(s * TX + li) * a.nz + kq];
+        }
+    };
+    fill_halo(0, buf + kSlots * P);                 // step 0 reads plane 1
+    __syncthreads();
+
+    float zc[kSlots];
 #pragma unroll
-    for (int ci = 0; ci < 4; ++ci) {
-        cc[ci] = 32 * warp + gq + 8 * ci;
-        li[ci] = cc[ci] % a.tx;
-        lj[ci] = cc[ci] / a.tx;
-        ir[ci] = at * a.tx + li[ci];
-        jr[ci] = bt * a.ty + lj[ci];
-        colok[ci] = ir[ci] < a.nx && jr[ci] < a.ny;
-        const int i = sx > 0 ? ir[ci] : a.nx - 1 - ir[ci];
-        const int j = sy > 0 ? jr[ci] : a.ny - 1 - jr[ci];
-        vcol[ci] = colok[ci] ? (size_t)j * a.nx + i : 0;
-    }
-    // direction slot of fragment entry (nt, e): 8 nt + 2 tq + (e & 1); zc index si = 2 nt + (e & 1)
-    float zc[4][4];
-#pragma unroll
-    for (int ci = 0; ci < 4; ++ci)
-#pragma unroll
-        for (int si = 0; si < 4; ++si) zc[ci][si] = 0.0f;
+    for (int q = 0; q < kSlots; ++q) zc[q] = 0.0f;
     float lk = 0.0f;
 
-    const int hmax = a.tx + a.ty + a.nz - 3;
+    const int hmax = TX + TY + a.nz - 3;
     for (int h = 0; h <= hmax; ++h) {
-        const int cb = h & 1, pb = cb ^ 1;
-        int kr[4];
-        bool act[4];
-        size_t v[4];
-        float4 sv[4];
-        float sig[4];
-#pragma unroll
-        for (int ci = 0; ci < 4; ++ci) {
-            kr[ci] = h - li[ci] - lj[ci];
-            act[ci] = colok[ci] && kr[ci] >= 0 && kr[ci] < a.nz;
-            const int k = sz > 0 ? kr[ci] : a.nz - 1 - kr[ci];
-            v[ci] = act[ci] ? (size_t)k * plane + vcol[ci] : 0;
-            sv[ci] = act[ci] ? __ldg(reinterpret_cast<const float4*>(a.src + (gV + v[ci]) * 16) + tq)
-                             : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            sig[ci] = act[ci] ? __ldg(a.rho + v[ci]) * sigt_s[__ldg(a.mat + v[ci])] : 1.0f;
-        }
-        // ---- moments -> directions ----------------------------------------------
-        float q[2][2][4];
-#pragma unroll
-        for (int rt = 0; rt < 2; ++rt)
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) q[rt][nt][e] = 0.0f;
-#pragma unroll
-        for (int rt = 0; rt < 2; ++rt) {
-            const float4 s0 = sv[2 * rt], s1 = sv[2 * rt + 1];
-#pragma unroll
-            for (int kt = 0; kt < 2; ++kt) {
-                float af[4];
-                af[0] = kt == 0 ? s0.x : s0.z;
-                af[1] = kt == 0 ? s1.x : s1.z;
-                af[2] = kt == 0 ? s0.y : s0.w;
-                af[3] = kt == 0 ? s1.y : s1.w;
-                uint32_t ah[4], al[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) split_tf32(af[e], ah[e], al[e]);
-#pragma unroll
-                for (int nt = 0; nt < 2; ++nt) mma_3xtf32(q[rt][nt], ah, al, tabM[(kt * 2 + nt) * 32 + lane]);
-            }
-        }
-        // ---- step-differenced cell solve on the fragment --------------------------
-#pragma unroll
-        for (int rt = 0; rt < 2; ++rt)
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int ci = 2 * rt + (e >> 1);
-                    const int slot = 8 * nt + 2 * tq + (e & 1);
-                    const int si = 2 * nt + (e & 1);
-                    float psi = 0.0f;
-                    if (act[ci]) {
-                        const float px = li[ci] > 0 ? buf[(pb * kSlots + slot) * SA + cc[ci] - 1]
-                                         : (slot < AB ? xin[(slot * a.ty + lj[ci]) * a.nz + kr[ci]] : 0.0f);
-                        const float py = lj[ci] > 0 ? buf[(pb * kSlots + slot) * SA + cc[ci] - a.tx]
-                                         : (slot < AB ? yin[(slot * a.tx + li[ci]) * a.nz + kr[ci]] : 0.0f);
-                        const float4 cf = coefs[slot];
-                        const float num = fmaf(cf.z, zc[ci][si], fmaf(cf.y, py, fmaf(cf.x, px, q[rt][nt][e])));
-                        psi = __fdividef(num, sig[ci] + cf.w);
-                    }
-                    buf[(cb * kSlots + slot) * SA + cc[ci]] = psi;
-                    zc[ci][si] = psi;
-                    q[rt][nt][e] = psi;
-                }
-        // faces leaving the tile, current leaving the mesh, stored fluence: only
-        // cells on a tile or mesh boundary (or in store mode) take this path
-        {
-            bool bnd[4];
-            bool anyb = false;
+        const int kr = h - li - lj;
+        const float* prev = buf + ((h & 1) ^ 1) * kSlots * P;
+        float* cur = buf + (h & 1) * kSlots * P;
+        const bool act = col && kr >= 0 && kr < a.nz;
+        const unsigned amask = __ballot_sync(0xffffffffu, act);
+        if (amask) {
+            const int k = sz > 0 ? kr : a.nz - 1 - kr;
+            const unsigned vme = act ? (unsigned)((size_t)k * plane + vcol) : 0u;   // V < 2^31
+            unsigned vr[4];
+            bool ar[4];
 #pragma unroll
             for (int ci = 0; ci < 4; ++ci) {
-                bnd[ci] = act[ci] && (MODE == 1 || (li[ci] == a.tx - 1 && at < a.ntx - 1) ||
-                                      (lj[ci] == a.ty - 1 && bt < a.nty - 1) || ir[ci] == a.nx - 1 ||
-                                      jr[ci] == a.ny - 1 || kr[ci] == a.nz - 1);
-                anyb |= bnd[ci];
+                vr[ci] = __shfl_sync(0xffffffffu, vme, gq + 8 * ci);
+                ar[ci] = (amask >> (gq + 8 * ci)) & 1u;
             }
-            if (__any_sync(0xffffffffu, anyb)) {
+            // ---- moments -> directions (3xTF32 mma) ---------------------------------
 #pragma unroll
-                for (int ci = 0; ci < 4; ++ci) {
-                    if (!bnd[ci]) continue;
-                    const int rt = ci >> 1;
-#pragma unroll
-                    for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-                        for (int b = 0; b < 2; ++b) {
-                            const int slot = 8 * nt + 2 * tq + b;
-                            if (slot >= AB) continue;
-                            const float psi = q[rt][nt][2 * (ci & 1) + b];
-                            if (li[ci] == a.tx - 1 && at < a.ntx - 1) {
-                                const size_t fb = (((size_t)o * a.A8 + slot0 + slot) * a.G + g) * xf_stride;
-                                a.xface[fb + ((size_t)at * a.ny + jr[ci]) * a.nz + kr[ci]] = psi;
-                            }
-                            if (lj[ci] == a.ty - 1 && bt < a.nty - 1) {
-                                const size_t fb = (((size_t)o * a.A8 + slot0 + slot) * a.G + g) * yf_stride;
-                                a.yface[fb + ((size_t)bt * a.nx + ir[ci]) * a.nz + kr[ci]] = psi;
-                            }
-                            if (ir[ci] == a.nx - 1 || jr[ci] == a.ny - 1 || kr[ci] == a.nz - 1) {
-                                const float4 lc = leakc[slot];
-                                float f = 0.0f;
-                                if (ir[ci] == a.nx - 1) f += lc.x;
-                                if (jr[ci] == a.ny - 1) f += lc.y;
-                                if (kr[ci] == a.nz - 1) f += lc.z;
-                                lk = fmaf(f, psi, lk);
-                            }
-                            if constexpr (MODE == 1) a.psi[((size_t)g * a.A + nbase + slot) * V + v[ci]] = psi;
-                        }
-                }
-            }
-        }
-        if constexpr (MODE == 2) {
-            // prod[g][v] += sum over this cell's real slots of w psi psi_stored
-#pragma unroll
-            for (int ci = 0; ci < 4; ++ci) {
-                const int rt = ci >> 1;
-                float pacc = 0.0f;
+            for (int rt = 0; rt < 2; ++rt) {
+                const float4 s0 = ar[2 * rt] ? __ldg(reinterpret_cast<const float4*>(a.src + (gV + vr[2 * rt]) * 16) + tq)
+                                             : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                const float4 s1 = ar[2 * rt + 1]
+                                      ? __ldg(reinterpret_cast<const float4*>(a.src + (gV + vr[2 * rt + 1]) * 16) + tq)
+                                      : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                float q[2][4];
 #pragma unroll
                 for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-                    for (int b = 0; b < 2; ++b) {
-                        const int e = 2 * (ci & 1) + b;
-                        const int slot = 8 * nt + 2 * tq + b;
-                        if (act[ci] && slot < AB)
-                            pacc = fmaf(leakc[slot].w * q[rt][nt][e],
-                                        __ldg(a.psi + ((size_t)g * a.A + nbase + slot) * V + v[ci]), pacc);
+                    for (int e = 0; e < 4; ++e) q[nt][e] = 0.0f;
+#pragma unroll
+                for (int kt = 0; kt < 2; ++kt) {
+                    const float af[4] = {kt == 0 ? s0.x : s0.z, kt == 0 ? s1.x : s1.z,
+                                         kt == 0 ? s0.y : s0.w, kt == 0 ? s1.y : s1.w};
+                    uint32_t ah[4], al[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) split_fast(af[e], ah[e], al[e]);
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt) mma_3xtf32(q[nt], ah, al, tabM[(kt * 2 + nt) * 32 + lane]);
+                }
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    const int c = 8 * nt + 2 * tq;
+                    *reinterpret_cast<float2*>(wq + (16 * rt + gq) * kQS + c) = make_float2(q[nt][0], q[nt][1]);
+                    *reinterpret_cast<float2*>(wq + (16 * rt + gq + 8) * kQS + c) = make_float2(q[nt][2], q[nt][3]);
+                }
+            }
+            __syncwarp();
+            // ---- step-differenced cell solve, one thread per column ---------------------
+            float* my = wq + lane * kQS;
+            if (act) {
+                const float sig = __ldg(a.rho + vme) * sigt_s[__ldg(a.mat + vme)];
+                float psi[kSlots];
+#pragma unroll
+                for (int c4 = 0; c4 < kSlots / 4; ++c4) {
+                    const float4 t4 = *reinterpret_cast<const float4*>(my + 4 * c4);
+                    psi[4 * c4] = t4.x; psi[4 * c4 + 1] = t4.y; psi[4 * c4 + 2] = t4.z; psi[4 * c4 + 3] = t4.w;
+                }
+                const float* px = prev + pc - 1;
+                const float* py = prev + pc - PX;
+                float* pw = cur + pc;
+#pragma unroll
+                for (int s = 0; s < kSlots; ++s) {
+                    const float4 cf = coefs[s];
+                    const float num = fmaf(cf.z, zc[s], fmaf(cf.y, py[s * P], fmaf(cf.x, px[s * P], psi[s])));
+                    psi[s] = __fdividef(num, sig + cf.w);
+                    pw[s * P] = psi[s];
+                    zc[s] = psi[s];
+                }
+#pragma unroll
+                for (int c4 = 0; c4 < kSlots / 4; ++c4)
+                    *reinterpret_cast<float4*>(my + 4 * c4) =
+                        make_float4(psi[4 * c4], psi[4 * c4 + 1], psi[4 * c4 + 2], psi[4 * c4 + 3]);
+                // rare paths read this cell's Psi row back from shared memory
+                if (xout)
+                    for (int s = 0; s < AB; ++s) xo[s * xo_q + kr] = my[s];
+                if (yout)
+                    for (int s = 0; s < AB; ++s) yo[s * yo_q + kr] = my[s];
+                if (xleak || yleak || kr == a.nz - 1) {
+                    for (int s = 0; s < AB; ++s) {
+                        const float4 lc = leakc[s];
+                        float f = 0.0f;
+                        if (xleak) f += lc.x;
+                        if (yleak) f += lc.y;
+                        if (kr == a.nz - 1) f += lc.z;
+                        lk = fmaf(f, my[s], lk);
                     }
-                pacc += __shfl_xor_sync(0xffffffffu, pacc, 1);
-                pacc += __shfl_xor_sync(0xffffffffu, pacc, 2);
-                if (tq == 0 && act[ci]) atomicAdd(a.prod + gV + v[ci], pacc);
+                }
+                if constexpr (MODE == 1) {
+                    for (int s = 0; s < AB; ++s) a.psi[((size_t)g * a.A + nbase + s) * V + vme] = my[s];
+                }
+                if constexpr (MODE == 2) {
+                    float pacc = 0.0f;
+                    for (int s = 0; s < AB; ++s)
+                        pacc = fmaf(leakc[s].w * my[s], __ldg(a.psi + ((size_t)g * a.A + nbase + s) * V + vme), pacc);
+                    atomicAdd(a.prod + gV + vme, pacc);
+                }
+            } else {
+#pragma unroll
+                for (int c4 = 0; c4 < kSlots / 4; ++c4)
+                    *reinterpret_cast<float4*>(my + 4 * c4) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+            __syncwarp();
+            // ---- directions -> moments (3xTF32 mma) ---------------------------------
+#pragma unroll
+            for (int rt = 0; rt < 2; ++rt) {
+                float acc[2][4];
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[nt][e] = 0.0f;
+#pragma unroll
+                for (int kt = 0; kt < 2; ++kt) {
+                    const int c = 8 * kt + 2 * tq;
+                    const float2 p0 = *reinterpret_cast<const float2*>(wq + (16 * rt + gq) * kQS + c);
+                    const float2 p1 = *reinterpret_cast<const float2*>(wq + (16 * rt + gq + 8) * kQS + c);
+                    const float af[4] = {p0.x, p1.x, p0.y, p1.y};
+                    uint32_t ah[4], al[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) split_fast(af[e], ah[e], al[e]);
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt) mma_3xtf32(acc[nt], ah, al, tabD[(kt * 2 + nt) * 32 + lane]);
+                }
+                if (ar[2 * rt])
+                    atomicAdd(reinterpret_cast<float4*>(a.mom + (gV + vr[2 * rt]) * 16) + tq,
+                              make_float4(acc[0][0], acc[0][1], acc[1][0], acc[1][1]));
+                if (ar[2 * rt + 1])
+                    atomicAdd(reinterpret_cast<float4*>(a.mom + (gV + vr[2 * rt + 1]) * 16) + tq,
+                              make_float4(acc[0][2], acc[0][3], acc[1][2], acc[1][3]));
             }
         }
-        // ---- directions -> moments ----------------------------------------------
-#pragma unroll
-        for (int rt = 0; rt < 2; ++rt) {
-            float acc[2][4];
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) acc[nt][e] = 0.0f;
-#pragma unroll
-            for (int kt = 0; kt < 2; ++kt) {
-                const float af[4] = {q[rt][kt][0], q[rt][kt][2], q[rt][kt][1], q[rt][kt][3]};
-                uint32_t ah[4], al[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) split_tf32(af[e], ah[e], al[e]);
-#pragma unroll
-                for (int nt = 0; nt < 2; ++nt) mma_3xtf32(acc[nt], ah, al, tabD[(kt * 2 + nt) * 32 + lane]);
-            }
-            const int c0 = 2 * rt, c1 = 2 * rt + 1;
-            if (act[c0])
-                atomicAdd(reinterpret_cast<float4*>(a.mom + (gV + v[c0]) * 16) + tq,
-                          make_float4(acc[0][0], acc[0][1], acc[1][0], acc[1][1]));
-            if (act[c1])
-                atomicAdd(reinterpret_cast<float4*>(a.mom + (gV + v[c1]) * 16) + tq,
-                          make_float4(acc[0][2], acc[0][3], acc[1][2], acc[1][3]));
-        }
+        // incoming face values of the next step go into this step's plane
+        fill_halo(h + 1, cur);
         __syncthreads();
     }
     double dl = (double)lk;
@@ -369,11 +388,36 @@ __global__ void __launch_bounds__(256, 2) k_sweep_tc(const SweepArgs a) {
 size_t sweep_tc_smem_bytes(int ab, int tx, int ty, int nz, int nmat) {
     const int T = tx * ty;
     return sizeof(float4) * (256 + 2 * kSlots) +
-           sizeof(float) * ((size_t)2 * kSlots * (T + 4) + (size_t)ab * (tx + ty) * nz + nmat);
+           sizeof(float) * ((size_t)T * kQS + (size_t)2 * kSlots * (tx + 2) * (ty + 1) + (size_t)ab * (tx + ty) * nz +
+                            nmat);
 }
 
 bool sweep_tc_supported(int ab, int M, int tx, int ty) {
-    return M == 16 && ab >= 1 && ab <= kSlots && (tx * ty) % 32 == 0 && tx * ty <= 256;
+    const bool tile = (tx == 16 && ty == 16) || (tx == 32 && ty == 8) || (tx == 16 && ty == 8) || (tx == 8 && ty == 16) ||
+                      (tx == 8 && ty == 8) || (tx == 8 && ty == 4);
+    return M == 16 && ab >= 1 && ab <= kSlots && tile;
+}
+
+template <int TX, int TY>
+cudaError_t launch_tc_tile(const SweepArgs& a, int mode, dim3 grid, size_t smem, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    switch (mode) {
+        case 0:
+            e = cudaFuncSetAttribute(k_sweep_tc<TX, TY, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess) k_sweep_tc<TX, TY, 0><<<grid, TX * TY, smem, s>>>(a);
+            break;
+        case 1:
+            e = cudaFuncSetAttribute(k_sweep_tc<TX, TY, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess) k_sweep_tc<TX, TY, 1><<<grid, TX * TY, smem, s>>>(a);
+            break;
+        case 2:
+            e = cudaFuncSetAttribute(k_sweep_tc<TX, TY, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess) k_sweep_tc<TX, TY, 2><<<grid, TX * TY, smem, s>>>(a);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return e;
 }
 
 cudaError_t launch_sweep_tc(const SweepArgs& a, int mode, cudaStream_t s) {
@@ -383,24 +427,14 @@ cudaError_t launch_sweep_tc(const SweepArgs& a, int mode, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     dim3 grid(ntiles, 8 * a.nab, a.G);
     const size_t smem = sweep_tc_smem_bytes(a.ab, a.tx, a.ty, a.nz, a.nmat);
-    const int T = a.tx * a.ty;
-    cudaError_t e = cudaSuccess;
-    switch (mode) {
-        case 0:
-            e = cudaFuncSetAttribute(k_sweep_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess) k_sweep_tc<0><<<grid, T, smem, s>>>(a);
-            break;
-        case 1:
-            e = cudaFuncSetAttribute(k_sweep_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess) k_sweep_tc<1><<<grid, T, smem, s>>>(a);
-            break;
-        case 2:
-            e = cudaFuncSetAttribute(k_sweep_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess) k_sweep_tc<2><<<grid, T, smem, s>>>(a);
-            break;
-        default:
-            return cudaErrorInvalidValue;
-    }
+    cudaError_t e;
+    if (a.tx == 16 && a.ty == 16) e = launch_tc_tile<16, 16>(a, mode, grid, smem, s);
+    else if (a.tx == 32 && a.ty == 8) e = launch_tc_tile<32, 8>(a, mode, grid, smem, s);
+    else if (a.tx == 16 && a.ty == 8) e = launch_tc_tile<16, 8>(a, mode, grid, smem, s);
+    else if (a.tx == 8 && a.ty == 16) e = launch_tc_tile<8, 16>(a, mode, grid, smem, s);
+    else if (a.tx == 8 && a.ty == 8) e = launch_tc_tile<8, 8>(a, mode, grid, smem, s);
+    else if (a.tx == 8 && a.ty == 4) e = launch_tc_tile<8, 4>(a, mode, grid, smem, s);
+    else return cudaErrorInvalidValue;
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -55,7 +55,7 @@ def cylinder_ref():
 
 
 @pytest.mark.parametrize("tile,ab,kernel", [((16, 16), 0, 1), ((16, 16), 0, 2), ((8, 4), 5, 1), ((8, 4), 5, 2),
-                                            ((5, 7), 2, 1), ((16, 2), 10, 2)])
+                                            ((5, 7), 2, 1), ((32, 8), 10, 2), ((8, 16), 10, 2)])
 def test_ragged_multitile_cylinder(dp, cylinder_ref, tile, ab, kernel):
     """Several sweep tiles with ragged tails in x and y, S8 P3, with the
     CUDA-core (1) and tensor-core (2) moment transforms."""
