@@ -38,10 +38,20 @@ WORKLOAD = "water_cylinder"
 WORKLOAD_DESC = ("35 cm water cylinder, 64x64x32 mesh (0.55x0.55x0.5 cm), fan 40 deg x 4 cm cone-beam "
                  "source at 54 cm, 19 groups 10-120 keV, S8 (80 directions), P3, FP32 sweep, tol 1e-6")
 
-# DRAM traffic of one full sweep of this workload (all stage launches of one
-# iteration), from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum`
-# (see profiles/); valid only for the kernel source it was taken on.
-SWEEP_TRAFFIC = {"bytes_per_sweep": None, "sweep_src_sha1": None}
+# DRAM traffic (read + write) of one full sweep of this workload (the seven
+# stage launches of one iteration) per sweep schedule (tile_x, tile_y,
+# directions per block, kernel), from `ncu --metrics
+# dram__bytes_read.sum,dram__bytes_write.sum` (profiles/k_sweep_water_cylinder.md);
+# valid only for the kernel source it was taken on.
+SWEEP_TRAFFIC = {
+    (16, 16, 10, 1): (2254.0e6, "sweep_impl.cuh", "78800eef8cd25340afa9ec42509ed47d5aa3943c"),
+    (16, 16, 5, 1): (1693.8e6, "sweep_impl.cuh", "78800eef8cd25340afa9ec42509ed47d5aa3943c"),
+    (16, 16, 10, 2): (2123.4e6, "sweep_tc.cu", "8cb389a75cfaf79df5262a211cc474444061941a"),
+}
+
+# FP32 lanes per SM and SMs of a GB300 (the ALU roofline of the CUDA-core sweep)
+FP32_LANES_PER_SM = 128
+SMS = 152
 
 
 def _sha1(path):
@@ -299,11 +309,24 @@ def main():
     if rank != 0:
         return
     M = (p.legendre + 1) ** 2
+    # algorithmic work of one sweep: per cell update 2M flops (moments ->
+    # direction), 2M (direction -> moments) and 8 for the step solve; bytes:
+    # read the moment source and write the moments once, plus material/density
+    flops_per_update = 4 * M + 8
+    flops_per_sweep = flops_per_update * p.V * p.n_angles * p.G
     bytes_per_sweep = 2 * M * p.G * p.V * 4 + 5 * p.V
-    achieved = bytes_per_sweep * sweeps / (ms_sweep / 1e3) / 1e9
-    peak, peak_kind = measured_peaks()
-    src_sha = _sha1(os.path.join(ROOT, "paper_1811_12391_gb300", "csrc", "sweep_impl.cuh"))
-    traffic = SWEEP_TRAFFIC["bytes_per_sweep"] if SWEEP_TRAFFIC["sweep_src_sha1"] == src_sha else None
+    sec_per_sweep = (ms_sweep / 1e3) / sweeps
+    achieved_tflops = flops_per_sweep / sec_per_sweep / 1e12
+    achieved_gbs = bytes_per_sweep / sec_per_sweep / 1e9
+    hbm_peak, peak_kind = measured_peaks()
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    alu_peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    key = (tuning["tile_x"], tuning["tile_y"], tuning["angles_per_block"], tuning["sweep_kernel"])
+    traffic = None
+    if key in SWEEP_TRAFFIC:
+        tbytes, fname, sha = SWEEP_TRAFFIC[key]
+        if _sha1(os.path.join(ROOT, "paper_1811_12391_gb300", "csrc", fname)) == sha:
+            traffic = tbytes
     cpu_v, cpu_n, cpu_s = oracle_sample(p, seconds=args.cpu_seconds) if world == 1 else (None, 0, 0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -313,11 +336,14 @@ def main():
                    "directions": p.n_angles, "groups": p.G, "moments": M,
                    "sweeps_per_step": sweeps / args.steps, "l2": "inputs larger than L2 (4 x 160 MB moment arrays)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": "k_sweep (all stage launches of one sweep)",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_kind": peak_kind, "traffic": traffic,
-                     "algorithmic_bytes_per_sweep": bytes_per_sweep,
-                     "ms_per_sweep": ms_sweep / sweeps},
+        "roofline": {"bound": "alu", "kernel": "k_sweep (the stage launches of one sweep)",
+                     "achieved": achieved_tflops, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / alu_peak,
+                     "peak_kind": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_mhz:.0f} MHz",
+                     "traffic": traffic, "algorithmic_flops_per_sweep": flops_per_sweep,
+                     "algorithmic_bytes_per_sweep": bytes_per_sweep, "ms_per_sweep": 1e3 * sec_per_sweep,
+                     "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": achieved_gbs / hbm_peak, "peak_kind": peak_kind + " (MEASURED_PEAKS.json)"}},
         "cpu_baseline": None if cpu_v is None else {
             "value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{cpu_n} whole-mesh FP64 sweeps of group 0 of the same workload in {cpu_s:.1f} s"},
