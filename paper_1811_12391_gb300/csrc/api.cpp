@@ -193,6 +193,8 @@ SweepArgs sweep_args(const doctors_problem* p, int reverse, const float* src, fl
     a.table_base = p->table_base; a.coef = p->d_coef; a.xface = p->d_xface; a.yface = p->d_yface;
     a.leak = p->d_red;
     a.A = p->A;
+    a.g0 = 0;
+    a.gcount = p->G;
     return a;
 }
 
@@ -200,38 +202,52 @@ SweepArgs sweep_args(const doctors_problem* p, int reverse, const float* src, fl
 // selects the adjoint: sweep directions reversed and scattering transposed.
 int iterate(doctors_problem* p, int reverse, const float* Q, float* mom, doctors_result* info) {
     const size_t GVM = (size_t)p->G * p->V * p->M;
-    double* d_leak = p->d_red;
+    const size_t VM = p->V * p->M;
     double* d_res = p->d_red + p->G;
     double* d_bal = p->d_red + 3 * p->G;
     CU(cudaMemsetAsync(mom, 0, GVM * sizeof(float), p->stream));
     CU(cudaMemsetAsync(p->d_prev, 0, (size_t)p->G * p->V * sizeof(float), p->stream));
+    CU(cudaMemsetAsync(p->d_red, 0, 5 * (size_t)p->G * sizeof(double), p->stream));
     const double tol = std::max(p->opt.tol, kTolFloor);
     int it = 0;
     double resid = 0.0;
     double ms_sweep = 0.0;
+    double updates = 0.0;
     bool conv = false;
+    // Active group window [g0, g1).  A group whose relative change is below
+    // tol and whose sources are all final is final itself: in the forward
+    // problem (downscatter) the window's leading groups retire, in the adjoint
+    // (transposed scattering, upward in energy) its trailing groups.
+    int g0 = 0, g1 = p->G;
+    std::vector<double> eps(p->G, 0.0);
     SweepArgs sw = sweep_args(p, reverse, p->d_src, mom);
     ScatterArgs sa{};
     sa.V = p->V; sa.G = p->G; sa.M = p->M; sa.L = p->L; sa.nmat = p->nmat; sa.transpose = reverse;
     sa.mat = p->d_mat; sa.rho = p->d_rho; sa.sigs = p->d_sigs;
     sa.base = Q; sa.phi = mom; sa.out = p->d_src;
     while (it < p->opt.max_iters) {
+        const int gc = g1 - g0;
         if (it == 0) {
             CU(cudaMemcpyAsync(p->d_src, Q, GVM * sizeof(float), cudaMemcpyDeviceToDevice, p->stream));
         } else {
+            sa.g0 = g0;
+            sa.g1 = g1;
             CU(launch_scatter(sa, p->stream));
             ++p->launches;
         }
-        CU(cudaMemsetAsync(mom, 0, GVM * sizeof(float), p->stream));
-        CU(cudaMemsetAsync(p->d_red, 0, 5 * (size_t)p->G * sizeof(double), p->stream));
+        CU(cudaMemsetAsync(mom + (size_t)g0 * VM, 0, (size_t)gc * VM * sizeof(float), p->stream));
+        CU(cudaMemsetAsync(p->d_red + g0, 0, (size_t)gc * sizeof(double), p->stream));
+        CU(cudaMemsetAsync(d_res + 2 * g0, 0, 2 * (size_t)gc * sizeof(double), p->stream));
         CU(cudaEventRecord(p->ev[3], p->stream));
+        sw.g0 = g0;
+        sw.gcount = gc;
         for (int st = 0; st < p->ntx + p->nty - 1; ++st) {
             sw.stage = st;
             CU(p->use_tc ? launch_sweep_tc(sw, 0, p->stream) : launch_sweep_stage(sw, p->M, 0, p->stream));
             ++p->launches;
         }
         CU(cudaEventRecord(p->ev[4], p->stream));
-        CU(launch_residual(p->V, p->G, p->M, mom, p->d_prev, d_res, p->stream));
+        CU(launch_residual(p->V, p->G, p->M, mom, p->d_prev, d_res, p->stream, nullptr, g0, gc));
         ++p->launches;
         CU(cudaMemcpyAsync(p->h_red, p->d_red, 3 * (size_t)p->G * sizeof(double), cudaMemcpyDeviceToHost,
                            p->stream));
@@ -239,21 +255,26 @@ int iterate(doctors_problem* p, int reverse, const float* Q, float* mom, doctors
         float ms = 0.0f;
         CU(cudaEventElapsedTime(&ms, p->ev[3], p->ev[4]));
         ms_sweep += ms;
+        updates += (double)p->V * p->A * gc;
         ++it;
         resid = 0.0;
-        for (int g = 0; g < p->G; ++g) {
+        for (int g = g0; g < g1; ++g) {
             const double num = p->h_red[p->G + 2 * g], den = p->h_red[p->G + 2 * g + 1];
-            const double eps = den > 0.0 ? std::sqrt(num / den) : 0.0;
-            resid = std::max(resid, eps);
-        }
-        if (!std::isfinite(resid)) {
-            set_error("source iteration produced a non-finite fluence");
-            return DOCTORS_ERR_INVALID_ARG;
+            eps[g] = den > 0.0 ? std::sqrt(num / den) : 0.0;
+            if (!std::isfinite(eps[g])) {
+                set_error("source iteration produced a non-finite fluence");
+                return DOCTORS_ERR_INVALID_ARG;
+            }
+            resid = std::max(resid, eps[g]);
         }
         if (resid < tol) {
             conv = true;
             break;
         }
+        if (!reverse)
+            while (g0 < g1 - 1 && eps[g0] < tol) ++g0;
+        else
+            while (g1 - 1 > g0 && eps[g1 - 1] < tol) --g1;
     }
     // particle balance of the last sweep (FP64)
     const double vol = p->mesh.dx * p->mesh.dy * p->mesh.dz;
@@ -274,7 +295,7 @@ int iterate(doctors_problem* p, int reverse, const float* Q, float* mom, doctors
         info->residual = resid;
         info->balance_rel = gain != 0.0 ? std::fabs(gain - loss) / std::fabs(gain) : 0.0;
         info->tol_used = tol;
-        info->cell_updates = (double)it * (double)p->V * p->A * p->G;
+        info->cell_updates = updates;
         info->ms_sweep = ms_sweep;
     }
     return conv ? DOCTORS_OK : DOCTORS_ERR_NOT_CONVERGED;

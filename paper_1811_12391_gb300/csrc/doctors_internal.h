@@ -120,12 +120,13 @@ struct ScatterArgs {
     const float* phi;                  // [G][V][M] or null (no scattering term)
     float* out;                        // [G][V][M]
     const int* skip;                   // if non-null and *skip != 0 the kernel does nothing
+    int g0, g1;                        // destination groups updated: g0 .. g1 - 1 (g1 = 0: all)
 };
 cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s);
 
 // residual: res[g][0] += sum_v (phi00 - prev)^2, res[g][1] += sum_v phi00^2; prev = phi00
 cudaError_t launch_residual(size_t V, int G, int M, const float* mom, float* prev, double* res,
-                            cudaStream_t s, const int* skip = nullptr);
+                            cudaStream_t s, const int* skip = nullptr, int g0 = 0, int gcount = -1);
 // zero n floats (or doubles) unless *skip
 cudaError_t launch_zero(float* p, size_t n, const int* skip, cudaStream_t s);
 cudaError_t launch_zero(double* p, size_t n, const int* skip, cudaStream_t s);
@@ -163,6 +164,7 @@ cudaError_t launch_extract(size_t V, int G, int M, int which, const float* phi_u
 struct SweepArgs {
     int nx, ny, nz, G, A8, ab, nab, nmat;
     int tx, ty, ntx, nty, stage, reverse;
+    int g0, gcount;                    // groups swept: g0 .. g0 + gcount - 1
     const uint8_t* mat;
     const float* rho;
     const float* sigt;                 // [nmat][G]

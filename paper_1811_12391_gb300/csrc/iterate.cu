@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(256) k_scatter(const ScatterArgs a) {
     const float r = __ldg(a.rho + v);
     const float* tab = a.sigs + ((size_t)m * (a.L + 1) + l) * a.G * a.G;
     const size_t VM = a.V * a.M;
-    for (int g = 0; g < a.G; ++g) {
+    const int g_end = a.g1 > 0 ? a.g1 : a.G;
+    for (int g = a.g0; g < g_end; ++g) {
         float out = a.base ? __ldg(a.base + g * VM + t) : 0.0f;
         if (lm == 0) {
             if (a.iso) out += __ldg(a.iso + g);
@@ -145,9 +146,9 @@ __device__ __forceinline__ void block_reduce_add(double (&x)[NV], double* dst) {
 
 // grid: (blocks over V, G)
 __global__ void __launch_bounds__(256) k_residual(size_t V, int M, const float* mom, float* prev,
-                                                  double* res, const int* skip) {
+                                                  double* res, const int* skip, int g0) {
     if (skip && *skip) return;
-    const int g = blockIdx.y;
+    const int g = g0 + blockIdx.y;
     double x[2] = {0.0, 0.0};
     for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (size_t)gridDim.x * blockDim.x) {
         const float cur = mom[((size_t)g * V + v) * M];
@@ -244,9 +245,9 @@ cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_residual(size_t V, int G, int M, const float* mom, float* prev, double* res,
-                            cudaStream_t s, const int* skip) {
-    dim3 grid(blocks_for(V, 256, 296), G);
-    k_residual<<<grid, 256, 0, s>>>(V, M, mom, prev, res, skip);
+                            cudaStream_t s, const int* skip, int g0, int gcount) {
+    dim3 grid(blocks_for(V, 256, 296), gcount < 0 ? G : gcount);
+    k_residual<<<grid, 256, 0, s>>>(V, M, mom, prev, res, skip, g0);
     return cudaGetLastError();
 }
 

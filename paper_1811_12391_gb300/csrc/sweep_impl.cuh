@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs a) {
     float* sigt_s = w_s + AB;               // [nmat]
 
     if (a.skip && *a.skip) return;         // retired instance of a batched loop
-    const int g = blockIdx.z;               // group slowest: resident CTAs share a few groups in L2
+    const int g = a.g0 + blockIdx.z;               // group slowest: resident CTAs share a few groups in L2
     const int o = blockIdx.y / a.nab;       // sweep octant
     const int blk = blockIdx.y % a.nab;
     const int a_lo = max(0, a.stage - (a.nty - 1));
@@ -322,7 +322,7 @@ cudaError_t launch_sweep_m(const SweepArgs& a, cudaStream_t s) {
     const int ntiles = a_hi - a_lo + 1;
     if (ntiles <= 0) return cudaSuccess;
     const int T = a.tx * a.ty;
-    dim3 grid(ntiles, 8 * a.nab, a.G);
+    dim3 grid(ntiles, 8 * a.nab, a.gcount);
     const size_t smem = sweep_smem_bytes(a.ab, M, a.tx, a.ty, a.nz, a.nmat);
 #define DOCTORS_SWEEP_CASE(AB)                                                                  \
     case AB: {                                                                                  \

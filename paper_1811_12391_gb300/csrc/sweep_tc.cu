@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(TX * TY, 2) k_sweep_tc(const SweepArgs a) {
     float* yin = xin + AB * TY * a.nz;      // [AB][TX][nz]
     float* sigt_s = yin + AB * TX * a.nz;   // [nmat]
 
-    const int g = blockIdx.z;
+    const int g = a.g0 + blockIdx.z;
     const int o = blockIdx.y / a.nab;
     const int blk = blockIdx.y % a.nab;
     const int a_lo = max(0, a.stage - (a.nty - 1));
@@ -425,7 +425,7 @@ cudaError_t launch_sweep_tc(const SweepArgs& a, int mode, cudaStream_t s) {
     const int a_hi = a.stage < a.ntx - 1 ? a.stage : a.ntx - 1;
     const int ntiles = a_hi - a_lo + 1;
     if (ntiles <= 0) return cudaSuccess;
-    dim3 grid(ntiles, 8 * a.nab, a.G);
+    dim3 grid(ntiles, 8 * a.nab, a.gcount);
     const size_t smem = sweep_tc_smem_bytes(a.ab, a.tx, a.ty, a.nz, a.nmat);
     cudaError_t e;
     if (a.tx == 16 && a.ty == 16) e = launch_tc_tile<16, 16>(a, mode, grid, smem, s);
