@@ -232,6 +232,7 @@ def main():
 
     from paper_1811_12391_gb300.build import build as build_lib
     build_lib()
+    from paper_1811_12391_gb300 import sharding
     from paper_1811_12391_gb300.solver import DoctorsProblem
     from synth import phantoms as ph
 
@@ -239,8 +240,8 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     p = ph.config_problem(WORKLOAD)
-    if world > 1:   # every rank solves its own view of an axial scan
-        p = p.with_sources(ph.axial_scan_sources(p, world)[rank:rank + 1])
+    if world > 1:   # every rank solves its own block of the views of an axial scan
+        p = p.with_sources(sharding.my_items(ph.axial_scan_sources(p, world), rank, world))
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         d = DoctorsProblem(p, stream=stream, tol=1e-6, max_iters=500)
@@ -261,11 +262,7 @@ def main():
         clocks = sampler.stop()
         if world > 1:
             dist.barrier()
-        ms = e0.elapsed_time(e1)
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+        ms_max = sharding.max_time(e0.elapsed_time(e1), device="cuda")
         cells = sum(r["cell_updates"] for r in res)
         value = world * cells / (ms_max / 1e3)
         launches = int(sum(r["launches"] for r in res))
