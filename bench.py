@@ -44,9 +44,9 @@ WORKLOAD_DESC = ("35 cm water cylinder, 64x64x32 mesh (0.55x0.55x0.5 cm), fan 40
 # dram__bytes_read.sum,dram__bytes_write.sum` (profiles/k_sweep_water_cylinder.md);
 # valid only for the kernel source it was taken on.
 SWEEP_TRAFFIC = {
-    (16, 16, 10, 1): (2254.0e6, "sweep_impl.cuh", "78800eef8cd25340afa9ec42509ed47d5aa3943c"),
-    (16, 16, 5, 1): (1693.8e6, "sweep_impl.cuh", "78800eef8cd25340afa9ec42509ed47d5aa3943c"),
-    (16, 16, 10, 2): (2123.4e6, "sweep_tc.cu", "8cb389a75cfaf79df5262a211cc474444061941a"),
+    (16, 16, 10, 1): (2246.4e6, "sweep_impl.cuh", "592eff4d10129e1bde8b55aecdf9fbf52f768e8c"),
+    (16, 16, 5, 1): (1687.6e6, "sweep_impl.cuh", "592eff4d10129e1bde8b55aecdf9fbf52f768e8c"),
+    (16, 16, 10, 2): (2121.9e6, "sweep_tc.cu", "79ec5703826b205c1bdc9d4f7ff57c205fec428a"),
 }
 
 # FP32 lanes per SM and SMs of a GB300 (the ALU roofline of the CUDA-core sweep)

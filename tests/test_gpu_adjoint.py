@@ -140,3 +140,27 @@ def test_autograd_roi_dose_matches_finite_differences(env):
         # FD noise of FP32 solves converged to 1e-6 relative: ~1e-6 |J| / step
         noise = 4e-6 * Jv / (2 * e[v].item())
         assert abs(fd - gr[v]) <= 2e-2 * abs(fd) + noise, (v, fd, gr[v], noise)
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_gradients_satisfy_euler_identity(env, kernel):
+    """J is linear in every view weight and in every spectrum entry, so
+    sum_s w_s dJ/dw_s = J and sum_g chi_g dJ/dchi_g = J (Euler's identity for
+    homogeneous functions of degree one): the adjoint gradients against the
+    forward dose of the same GPU solve, with no oracle involved."""
+    torch, C, DoctorsProblem = env
+    p = ph.water_cylinder(seed=3, nx=20, ny=18, nz=6, G=3, sn=4, L=3, dx=1.0, dy=1.0, dz=1.5,
+                          diameter=16.0, sid=20.0, fan_deg=60.0, z_width=8.0)
+    p.sources = ph.axial_scan_sources(p, 3, sid=20.0, fan_deg=60.0, z_width=8.0)
+    p.sources[1].weight = 0.6
+    p.sources[2].weight = 1.3
+    roi = _roi(p)
+    d = DoctorsProblem(p, tol=1e-6, max_iters=400, sweep_kernel=kernel)
+    d.solve()
+    J = float((roi * d.dose_host(p.k_dep)).sum())
+    g = d.adjoint(torch.as_tensor(osv.response_from_roi(p, roi), device="cuda"), want=("weights", "spectrum"))
+    w = np.array([s.weight for s in p.sources])
+    chi = np.asarray(p.sources[0].spectrum, dtype=np.float64)
+    assert abs(float(w @ g["weights"].cpu().numpy()) - J) <= 2 * REL_TOL * abs(J)
+    assert abs(float(chi @ g["spectrum"].cpu().numpy()) - J) <= 2 * REL_TOL * abs(J)
+    d.close()

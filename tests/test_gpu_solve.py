@@ -162,6 +162,31 @@ def test_errors_are_reported(dp):
     d.close()
 
 
+def test_iteration_cap_reports_not_converged(dp):
+    """A cap below the iterations the problem needs returns
+    DOCTORS_ERR_NOT_CONVERGED with the partial results still readable (host
+    loop and graph-captured device loop alike); a later solve with a larger
+    cap on the same problem converges to the oracle."""
+    from paper_1811_12391_gb300 import _lib as C
+    p = ph.tiny_cube(n=8)
+    ref = osv.solve(p, tol=1e-11)
+    for device_loop in (0, 1):
+        d = dp(p, tol=1e-6, max_iters=3, device_loop=device_loop)
+        with pytest.raises(C.DoctorsError) as e:
+            d.solve()
+        assert e.value.code == C.DOCTORS_ERR_NOT_CONVERGED
+        r = d.solve(allow_not_converged=True)
+        assert r["converged"] == 0 and r["iterations"] == 3
+        phi = d.fluence_host(2)
+        assert np.all(np.isfinite(phi)) and phi.max() > 0
+        d.dose_host(p.k_dep)                                  # results kept
+        d.close()
+        d = dp(p, tol=1e-6, max_iters=300, device_loop=device_loop)
+        assert d.solve()["converged"] == 1
+        assert max_rel(d.fluence_host(2), ref.phi) <= REL_TOL
+        d.close()
+
+
 def test_water_cylinder_full_size_properties(dp):
     """The 64x64x32 S8 P3 19-group cylinder at full size: converged,
     particle balance, and mirror symmetry in x and z of the collided and
