@@ -85,8 +85,11 @@ typedef struct doctors_options {
     int max_iters;           /* source-iteration cap, >= 1 */
     int tile_x, tile_y;      /* sweep tile in voxels (0 = default 16 x 16); tile_x*tile_y <= 256 */
     int angles_per_block;    /* directions per sweep block (0 = default); must divide N(N+2)/8 */
-    int sweep_kernel;        /* 0 = default (the faster measured path), 1 = CUDA-core moment transforms,
-                                2 = tensor-core (3xTF32 mma) moment transforms (P3 only) */
+    int sweep_kernel;        /* 0 = default (the chained CUDA-core sweep, the fastest measured),
+                                1 = CUDA-core transforms, one task (tile, octant, direction block,
+                                group) per CTA, 2 = tensor-core (3xTF32 mma) moment transforms
+                                (P3 only), 3 = CUDA-core transforms, each CTA running a chain of
+                                tasks of a stage back to back in one hyperplane pipeline */
     int device_loop;         /* 1 = run the source iteration as one CUDA graph whose while loop is
                                 decided on the device (no host round trip per iteration) */
     int reserved[6];         /* must be zero */
@@ -237,7 +240,7 @@ int doctors_solve_batch(doctors_problem **problems, int n, doctors_result *resul
 typedef struct doctors_tuning {
     int tile_x, tile_y;      /* tile of columns */
     int angles_per_block;    /* directions per CTA */
-    int sweep_kernel;        /* 1 CUDA-core, 2 tensor-core moment transforms */
+    int sweep_kernel;        /* 1 CUDA-core, 2 tensor-core, 3 chained CUDA-core (as doctors_options) */
     double ms_per_sweep;     /* measured time of one full sweep of this problem */
     int candidates;          /* schedules timed (0 if taken from the cache) */
 } doctors_tuning;

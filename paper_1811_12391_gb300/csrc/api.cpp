@@ -49,6 +49,7 @@ namespace {
 
 // default choice of the moment-transform path of the sweep for P3 problems
 constexpr bool kDefaultTensorCoreSweep = false;
+constexpr bool kDefaultChainedSweep = true;
 
 int dalloc(void** p, size_t bytes, const char* what) {
     if (bytes == 0) bytes = 16;
@@ -195,6 +196,7 @@ SweepArgs sweep_args(const doctors_problem* p, int reverse, const float* src, fl
     a.A = p->A;
     a.g0 = 0;
     a.gcount = p->G;
+    a.chain_slots = p->use_tc ? 0 : p->chain_slots;
     return a;
 }
 
@@ -466,8 +468,8 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
         set_error("angles_per_block must divide N(N+2)/8 and be one of 1,2,3,4,5,6,7,9,10,12");
         return DOCTORS_ERR_INVALID_ARG;
     }
-    if (kernel < 0 || kernel > 2) {
-        set_error("sweep_kernel must be 0, 1 or 2");
+    if (kernel < 0 || kernel > 3) {
+        set_error("sweep_kernel must be 0, 1, 2 or 3");
         return DOCTORS_ERR_INVALID_ARG;
     }
     const bool tc_ok = sweep_tc_supported(ab, p->M, tx, ty);
@@ -476,13 +478,36 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
         return DOCTORS_ERR_INVALID_ARG;
     }
     const bool use_tc = kernel == 2 || (kernel == 0 && tc_ok && kDefaultTensorCoreSweep);
-    const size_t smem = use_tc ? sweep_tc_smem_bytes(ab, tx, ty, p->nz, kMaxMat)
-                               : sizeof(float) * (size_t)(2 * ab * tx * ty + ab * (tx + ty) * p->nz + 21 * ab + kMaxMat);
+    const bool use_chain = !use_tc && (kernel == 3 || (kernel == 0 && kDefaultChainedSweep));
+    const int ntx = (p->nx + tx - 1) / tx, nty = (p->ny + ty - 1) / ty;
+    int chain_slots = 0;
+    size_t smem = 0;
+    if (use_tc) {
+        smem = sweep_tc_smem_bytes(ab, tx, ty, p->nz, kMaxMat);
+    } else if (use_chain) {
+        // CTA slots from the occupancy at the largest chain a stage can need
+        // (every chain is at most ceil(tasks / SMs) long once there is at
+        // least one CTA per SM)
+        int sms = 0;
+        CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+        const int max_tasks = std::min(ntx, nty) * 8 * (p->A8 / ab) * p->G;
+        const int cmax = (max_tasks + sms - 1) / sms;
+        smem = sweep_chain_smem_bytes(ab, tx, ty, cmax, p->G, kMaxMat);
+        if (smem <= 227 * 1024) {
+            const int per_sm = sweep_chain_blocks_per_sm(ab, p->M, tx * ty, smem);
+            if (per_sm < 1) {
+                set_error("chained sweep cannot be resident with this tile");
+                return DOCTORS_ERR_INVALID_ARG;
+            }
+            chain_slots = sms * per_sm;
+        }
+    } else {
+        smem = sizeof(float) * (size_t)(2 * ab * tx * ty + ab * (tx + ty) * p->nz + 21 * ab + kMaxMat);
+    }
     if (smem > 227 * 1024) {
         set_error("sweep tile needs more than 227 KB of shared memory");
         return DOCTORS_ERR_INVALID_ARG;
     }
-    const int ntx = (p->nx + tx - 1) / tx, nty = (p->ny + ty - 1) / ty;
     const size_t xf = (size_t)p->A * p->G * (ntx > 1 ? ntx - 1 : 0) * p->ny * p->nz;
     const size_t yf = (size_t)p->A * p->G * (nty > 1 ? nty - 1 : 0) * p->nx * p->nz;
     const size_t xf_old = (size_t)p->A * p->G * (p->ntx > 1 ? p->ntx - 1 : 0) * p->ny * p->nz;
@@ -502,6 +527,7 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
         p->d_yface = nb;
     }
     p->tx = tx; p->ty = ty; p->ab = ab; p->nab = p->A8 / ab; p->ntx = ntx; p->nty = nty; p->use_tc = use_tc;
+    p->chain_slots = chain_slots;
     return DOCTORS_OK;
 }
 
@@ -563,15 +589,9 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     p->nab = p->A8 / p->ab;
     p->ntx = (p->nx + p->tx - 1) / p->tx;
     p->nty = (p->ny + p->ty - 1) / p->ty;
-    if (opt->sweep_kernel < 0 || opt->sweep_kernel > 2) return fail(DOCTORS_ERR_INVALID_ARG, "sweep_kernel must be 0, 1 or 2");
-    const bool tc_ok = sweep_tc_supported(p->ab, p->M, p->tx, p->ty);
-    if (opt->sweep_kernel == 2 && !tc_ok)
+    if (opt->sweep_kernel < 0 || opt->sweep_kernel > 3) return fail(DOCTORS_ERR_INVALID_ARG, "sweep_kernel must be 0, 1, 2 or 3");
+    if (opt->sweep_kernel == 2 && !sweep_tc_supported(p->ab, p->M, p->tx, p->ty))
         return fail(DOCTORS_ERR_INVALID_ARG, "tensor-core sweep needs P3, <= 16 directions per block and a 16x16, 32x8, 16x8, 8x16, 8x8 or 8x4 tile");
-    p->use_tc = opt->sweep_kernel == 2 || (opt->sweep_kernel == 0 && tc_ok && kDefaultTensorCoreSweep);
-    const size_t smem = p->use_tc ? sweep_tc_smem_bytes(p->ab, p->tx, p->ty, p->nz, kMaxMat)
-                                  : sizeof(float) * (size_t)(2 * p->ab * p->tx * p->ty + p->ab * (p->tx + p->ty) * p->nz +
-                                                             21 * p->ab + kMaxMat);
-    if (smem > 227 * 1024) return fail(DOCTORS_ERR_INVALID_ARG, "sweep tile needs more than 227 KB of shared memory");
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) return fail(DOCTORS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
 
@@ -949,10 +969,10 @@ int doctors_autotune(doctors_problem* p, doctors_tuning* out) {
     doctors_tuning best{};
     best.ms_per_sweep = 1e30;
     int count = 0;
-    const int saved[4] = {p->tx, p->ty, p->ab, p->use_tc ? 2 : 1};
+    const int saved[4] = {p->tx, p->ty, p->ab, p->use_tc ? 2 : (p->chain_slots > 0 ? 3 : 1)};
     for (const auto& t : tiles) {
         for (int ab : abs_ok) {
-            for (int kernel = 1; kernel <= 2; ++kernel) {
+            for (int kernel = 1; kernel <= 3; ++kernel) {
                 if (kernel == 2 && !sweep_tc_supported(ab, p->M, t[0], t[1])) continue;
                 if (configure_sweep(p, t[0], t[1], ab, kernel) != DOCTORS_OK) continue;
                 SweepArgs sw = sweep_args(p, 0, p->d_Q, p->d_mom);

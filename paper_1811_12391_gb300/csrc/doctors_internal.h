@@ -179,10 +179,20 @@ struct SweepArgs {
     float* psi;                        // [G][A][V]: written (mode 1) or read (mode 2)
     float* prod;                       // [G][V]: mode 2 accumulator
     const int* skip;                   // if non-null and *skip != 0 the kernel does nothing
+    int chain_slots;                   // > 0: chained kernel, at most this many CTAs per stage launch
 };
 // mode 0: plain; 1: store psi; 2: accumulate sum_n w_n psi_n psi_stored_n into prod
 cudaError_t launch_sweep_stage(const SweepArgs& a, int M, int mode, cudaStream_t s);
 bool sweep_supported(int ab, int M);
+// CTAs of the chained sweep kernel resident per SM (0 if it cannot launch)
+int sweep_chain_blocks_per_sm(int ab, int M, int threads, size_t smem);
+// shared memory of one chained-sweep CTA: per chained task the direction rows
+// (coef and R as float4, w), the per-group leakage (FP64), the two
+// halo-padded hyperplanes and sigma_t of the swept groups
+inline size_t sweep_chain_smem_bytes(int ab, int tx, int ty, int cmax, int gcount, int nmat) {
+    return 16 * (size_t)cmax * ab * 5 + 8 * (size_t)gcount +
+           4 * ((size_t)2 * ab * (tx + 1) * (ty + 1) + (size_t)cmax * ab + (size_t)gcount * nmat);
+}
 // Upload the shared direction tables (all S_N sets) to the current device,
 // once per device; returns the first table row of order N in *base.
 cudaError_t ensure_direction_tables(int device, int N, int* base);
@@ -211,6 +221,7 @@ struct doctors_problem {
     // sweep tiling
     int tx = 16, ty = 16, ntx = 1, nty = 1, ab = 1, nab = 1;
     bool use_tc = false;            // tensor-core transforms in the sweep
+    int chain_slots = 0;            // > 0: chained CUDA-core sweep with this many CTA slots
     // device tables
     float* d_coef = nullptr;
     int table_base = 0;

@@ -1,0 +1,384 @@
+// Chained octant wavefront sweep: the step-differenced cell update, tile
+// stages and face buffers of k_sweep, with one change of schedule.
+//
+// In k_sweep a CTA owns one task (tile, octant, direction block, group) and
+// its hyperplane pipeline fills and drains for every task: with a tx x ty
+// tile the thread of column (li, lj) starts li + lj steps late, so a CTA runs
+// nz + tx + ty - 2 steps for nz steps of work per thread.  Here a launch has
+// at most as many CTAs as fit on the GPU at once, and each CTA runs a chain
+// of tasks of the stage back to back: the thread of column (li, lj) works at
+// step h on position u = h - li - lj of the concatenated z columns of its
+// chain (task u / nz, plane u % nz).  Its upwind x and y neighbours worked on
+// the same position one step earlier, so the double-buffered hyperplane needs
+// no drain between tasks and the pipeline fills once per launch.  Tasks of
+// one stage are independent, so CTAs never wait on one another.
+//
+// Incoming face fluxes reach the tile's first row and column through a halo
+// of the plane buffers: the edge threads copy the value of their next cell
+// with cp.async one step ahead (zero on the mesh boundary), so every upwind
+// read is the same shared-memory load, without a branch.
+#pragma once
+
+#include "sweep_impl.cuh"
+
+namespace doctors {
+
+__device__ __forceinline__ void cp_async_f32(float* dst_smem, const float* src_gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(dst_smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src_gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// task t of a stage with `ntiles` tiles: tile fastest, then direction block,
+// octant, group
+__device__ __forceinline__ void chain_decode(int t, int ntiles, int nab, int& ti, int& blk, int& o, int& gi) {
+    ti = t % ntiles;
+    int r = t / ntiles;
+    blk = r % nab;
+    r /= nab;
+    o = r & 7;
+    gi = r >> 3;
+}
+
+template <int AB, int M, int MODE>
+__global__ void __launch_bounds__(256, 2) k_sweep_chain(const SweepArgs a) {
+    extern __shared__ float4 sm4[];
+    if (a.skip && *a.skip) return;         // retired instance of a batched loop
+    const int a_lo = max(0, a.stage - (a.nty - 1));
+    const int a_hi = min(a.stage, a.ntx - 1);
+    const int ntiles = a_hi - a_lo + 1;
+    const int ntasks = ntiles * 8 * a.nab * a.gcount;
+    const int grid = (int)gridDim.x;
+    const int cmax = (ntasks + grid - 1) / grid;
+    const int nchain = (ntasks - (int)blockIdx.x + grid - 1) / grid;   // tasks of this CTA (grid <= ntasks)
+    const int PX = a.tx + 1;                    // padded plane: halo row and column at index 0
+    const int P = PX * (a.ty + 1);
+
+    float4* coef_s = sm4;                       // [cmax][AB]: cx, cy, cz, cx+cy+cz
+    float4* R_s = coef_s + cmax * AB;           // [cmax][AB][4]: R_lm, 16 per direction
+    double* leak_s = reinterpret_cast<double*>(R_s + 4 * cmax * AB);   // [gcount]
+    float* buf = reinterpret_cast<float*>(leak_s + a.gcount);        // [2][AB][P]
+    float* w_s = buf + 2 * AB * P;              // [cmax][AB]
+    float* sigt_s = w_s + cmax * AB;            // [gcount][nmat]
+
+    for (int e = threadIdx.x; e < nchain * AB; e += blockDim.x) {
+        const int cc = e / AB, q = e % AB;
+        int ti, blk, o, gi;
+        chain_decode((int)blockIdx.x + cc * grid, ntiles, a.nab, ti, blk, o, gi);
+        const int n = (a.reverse ? (o ^ 7) : o) * a.A8 + blk * AB + q;   // adjoint: along -Omega_n
+        const float* cf = a.coef + (size_t)n * 8;
+        coef_s[e] = make_float4(cf[0], cf[1], cf[2], cf[3]);
+        w_s[e] = c_w[a.table_base + n];
+        const float* r = c_R + (size_t)(a.table_base + n) * 16;
+#pragma unroll
+        for (int p4 = 0; p4 < 4; ++p4)
+            R_s[4 * e + p4] = make_float4(r[lm_of_pos(4 * p4, M)], r[lm_of_pos(4 * p4 + 1, M)],
+                                          r[lm_of_pos(4 * p4 + 2, M)], r[lm_of_pos(4 * p4 + 3, M)]);
+    }
+    for (int e = threadIdx.x; e < a.gcount * a.nmat; e += blockDim.x)
+        sigt_s[e] = a.sigt[(e % a.nmat) * a.G + a.g0 + e / a.nmat];
+    for (int e = threadIdx.x; e < a.gcount; e += blockDim.x) leak_s[e] = 0.0;
+    for (int e = threadIdx.x; e < 2 * AB * P; e += blockDim.x) buf[e] = 0.0f;
+    __syncthreads();
+
+    // threads own the tile's columns in diagonal order (li + lj ascending):
+    // the columns active at a step are a contiguous range of threads
+    const int tid = threadIdx.x;
+    int li = 0, lj = 0;
+    {
+        int base = 0;
+        for (int dd = 0; dd <= a.tx + a.ty - 2; ++dd) {
+            const int lo = dd > a.ty - 1 ? dd - (a.ty - 1) : 0;
+            const int hi = dd < a.tx - 1 ? dd : a.tx - 1;
+            const int cnt = hi - lo + 1;
+            if (tid < base + cnt) {
+                li = lo + (tid - base);
+                lj = dd - li;
+                break;
+            }
+            base += cnt;
+        }
+    }
+    const int d = li + lj;
+    const int cs = (lj + 1) * PX + li + 1;      // this column's slot in the padded planes
+    const size_t V = (size_t)a.nx * a.ny * a.nz;
+    const size_t nxy = (size_t)a.nx * a.ny;
+    const size_t xf_stride = (size_t)(a.ntx > 1 ? a.ntx - 1 : 0) * a.ny * a.nz;
+    const size_t yf_stride = (size_t)(a.nty > 1 ? a.nty - 1 : 0) * a.nx * a.nz;
+    const size_t xo_q = (size_t)a.G * xf_stride, yo_q = (size_t)a.G * yf_stride;
+
+    // state of the task this thread works on (or starts next)
+    int gi = 0, sz = 1, nb = 0, tab = 0;
+    size_t gV = 0, vcol = 0;
+    bool col = false, xout = false, yout = false, xleak = false, yleak = false;
+    float* xo = nullptr;
+    float* yo = nullptr;
+    const float* xi = nullptr;
+    const float* yi = nullptr;
+    auto begin_task = [&](int cc) {
+        int ti, blk, o;
+        chain_decode((int)blockIdx.x + cc * grid, ntiles, a.nab, ti, blk, o, gi);
+        const int g = a.g0 + gi;
+        const int at = a_lo + ti, bt = a.stage - at;
+        const int sx = (o & 1) ? -1 : 1, sy = (o & 2) ? -1 : 1;
+        sz = (o & 4) ? -1 : 1;
+        nb = (a.reverse ? (o ^ 7) : o) * a.A8 + blk * AB;
+        tab = cc * AB;
+        const int ir = at * a.tx + li, jr = bt * a.ty + lj;
+        col = ir < a.nx && jr < a.ny;
+        const int i = sx > 0 ? ir : a.nx - 1 - ir;
+        const int j = sy > 0 ? jr : a.ny - 1 - jr;
+        vcol = (size_t)j * a.nx + i;
+        gV = (size_t)g * V;
+        xout = li == a.tx - 1 && at < a.ntx - 1;
+        yout = lj == a.ty - 1 && bt < a.nty - 1;
+        xleak = ir == a.nx - 1;
+        yleak = jr == a.ny - 1;
+        const size_t fq = ((size_t)o * a.A8 + blk * AB) * a.G + g;
+        xo = a.xface + fq * xf_stride + ((size_t)at * a.ny + jr) * a.nz;
+        yo = a.yface + fq * yf_stride + ((size_t)bt * a.nx + ir) * a.nz;
+        xi = at > 0 ? a.xface + fq * xf_stride + ((size_t)(at - 1) * a.ny + jr) * a.nz : nullptr;
+        yi = bt > 0 ? a.yface + fq * yf_stride + ((size_t)(bt - 1) * a.nx + ir) * a.nz : nullptr;
+    };
+    // incoming face values of plane kn of the current task into the halo of
+    // hyperplane buffer `pl` (read by this thread one step later)
+    auto fill_halo = [&](int pl, int kn) {
+        if (!col) return;
+        float* hb = buf + pl * AB * P;
+        if (li == 0) {
+            if (xi) {
+#pragma unroll
+                for (int q = 0; q < AB; ++q) cp_async_f32(hb + q * P + cs - 1, xi + q * xo_q + kn);
+            } else {
+#pragma unroll
+                for (int q = 0; q < AB; ++q) hb[q * P + cs - 1] = 0.0f;
+            }
+        }
+        if (lj == 0) {
+            if (yi) {
+#pragma unroll
+                for (int q = 0; q < AB; ++q) cp_async_f32(hb + q * P + cs - PX, yi + q * yo_q + kn);
+            } else {
+#pragma unroll
+                for (int q = 0; q < AB; ++q) hb[q * P + cs - PX] = 0.0f;
+            }
+        }
+    };
+    // source moments and total cross section of plane kn, one step ahead
+    float sn[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) sn[m] = 0.0f;
+    float sig_n = 0.0f;
+    auto prefetch = [&](int kn) {
+        if (col) {
+            const int k = sz > 0 ? kn : a.nz - 1 - kn;
+            const size_t v = (size_t)k * nxy + vcol;
+            load_moments<M>(a.src + (gV + v) * M, sn);
+            sig_n = __ldg(a.rho + v) * sigt_s[gi * a.nmat + __ldg(a.mat + v)];
+        }
+    };
+
+    int c = 0, kr = 0;
+    begin_task(0);
+    prefetch(0);
+    if (d == 0) fill_halo(1, 0);                // read at step 0
+    cp_async_wait_all();
+    __syncthreads();
+
+    float zc[AB];
+#pragma unroll
+    for (int q = 0; q < AB; ++q) zc[q] = 0.0f;
+    float lk = 0.0f;
+
+    const int hend = a.tx + a.ty - 2 + nchain * a.nz;
+    for (int h = 0; h < hend; ++h) {
+        const int cb = h & 1, pb = cb ^ 1;
+        if (h + 1 == d) fill_halo(cb, 0);      // this thread's first cell comes next step
+        if (h >= d && c < nchain) {
+            const bool last = kr == a.nz - 1;
+            if (col) {
+                float s[M];
+                // (2l+1)/(4 pi) folded into the source moments
+#pragma unroll
+                for (int m = 0; m < M; ++m)
+                    s[m] = sn[m] * ((2 * degree_of_lm(lm_of_pos(m, M)) + 1) * 0.07957747154594767f);
+                const float sig = sig_n;
+                const int k = sz > 0 ? kr : a.nz - 1 - kr;
+                const size_t v = (size_t)k * nxy + vcol;
+                const size_t mo = (gV + v) * M;
+                if (!last) {
+                    fill_halo(cb, kr + 1);
+                    prefetch(kr + 1);
+                }
+                // moments -> directions: AB independent dot products
+                float psi[AB];
+#pragma unroll
+                for (int q = 0; q < AB; ++q) {
+                    float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f, t3 = 0.0f;
+#pragma unroll
+                    for (int m = 0; m < M; m += 4) {
+                        const float4 R = R_s[4 * (tab + q) + m / 4];
+                        t0 = fmaf(R.x, s[m], t0);
+                        if (m + 1 < M) t1 = fmaf(R.y, s[m + 1], t1);
+                        if (m + 2 < M) t2 = fmaf(R.z, s[m + 2], t2);
+                        if (m + 3 < M) t3 = fmaf(R.w, s[m + 3], t3);
+                    }
+                    psi[q] = (t0 + t1) + (t2 + t3);
+                }
+                // step-differenced cell solve per direction
+                const float* pv = buf + pb * AB * P;
+                float* cv = buf + cb * AB * P;
+#pragma unroll
+                for (int q = 0; q < AB; ++q) {
+                    const float px = pv[q * P + cs - 1];
+                    const float py = pv[q * P + cs - PX];
+                    const float4 cq = coef_s[tab + q];
+                    const float num = fmaf(cq.z, zc[q], fmaf(cq.y, py, fmaf(cq.x, px, psi[q])));
+                    psi[q] = __fdividef(num, sig + cq.w);
+                    cv[q * P + cs] = psi[q];
+                    zc[q] = psi[q];
+                }
+                if constexpr (MODE == 1) {
+#pragma unroll
+                    for (int q = 0; q < AB; ++q) a.psi[((size_t)(a.g0 + gi) * a.A + nb + q) * V + v] = psi[q];
+                }
+                if constexpr (MODE == 2) {
+                    float pacc = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < AB; ++q)
+                        pacc = fmaf(w_s[tab + q] * psi[q],
+                                    __ldg(a.psi + ((size_t)(a.g0 + gi) * a.A + nb + q) * V + v), pacc);
+                    atomicAdd(a.prod + gV + v, pacc);
+                }
+                // faces leaving the tile and current leaving the mesh
+                if (xout) {
+#pragma unroll
+                    for (int q = 0; q < AB; ++q) xo[q * xo_q + kr] = psi[q];
+                }
+                if (yout) {
+#pragma unroll
+                    for (int q = 0; q < AB; ++q) yo[q * yo_q + kr] = psi[q];
+                }
+                if (xleak || yleak || last) {
+#pragma unroll
+                    for (int q = 0; q < AB; ++q) {
+                        const float* cf = a.coef + (size_t)(nb + q) * 8;
+                        float f = 0.0f;
+                        if (xleak) f += __ldg(cf + 4);
+                        if (yleak) f += __ldg(cf + 5);
+                        if (last) f += __ldg(cf + 6);
+                        lk = fmaf(f, psi[q], lk);
+                    }
+                }
+                // directions -> moments (Eq. 3 for lm = 00)
+                float acc[M];
+#pragma unroll
+                for (int m = 0; m < M; ++m) acc[m] = 0.0f;
+#pragma unroll
+                for (int q = 0; q < AB; ++q) {
+                    const float wp = w_s[tab + q] * psi[q];
+#pragma unroll
+                    for (int m = 0; m < M; m += 4) {
+                        const float4 R = R_s[4 * (tab + q) + m / 4];
+                        acc[m] = fmaf(R.x, wp, acc[m]);
+                        if (m + 1 < M) acc[m + 1] = fmaf(R.y, wp, acc[m + 1]);
+                        if (m + 2 < M) acc[m + 2] = fmaf(R.z, wp, acc[m + 2]);
+                        if (m + 3 < M) acc[m + 3] = fmaf(R.w, wp, acc[m + 3]);
+                    }
+                }
+                add_moments<M>(a.mom + mo, acc);
+            }
+            if (last) {                          // task done: next task of the chain
+                if (lk != 0.0f) atomicAdd(leak_s + gi, (double)lk);
+                lk = 0.0f;
+#pragma unroll
+                for (int q = 0; q < AB; ++q) zc[q] = 0.0f;
+                kr = 0;
+                ++c;
+                if (c < nchain) {
+                    begin_task(c);
+                    fill_halo(cb, 0);
+                    prefetch(0);
+                }
+            } else {
+                ++kr;
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < a.gcount; e += blockDim.x)
+        if (leak_s[e] != 0.0) atomicAdd(a.leak + a.g0 + e, leak_s[e]);
+}
+
+// CTAs of k_sweep_chain<AB, M, 0> resident per SM at this shared-memory size
+template <int M>
+int sweep_chain_blocks_per_sm(int ab, int threads, size_t smem) {
+    int b = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+#define DOCTORS_CHAIN_OCC(AB)                                                                        \
+    case AB: {                                                                                       \
+        auto kern = k_sweep_chain<AB, M, 0>;                                                         \
+        e = smem > 48 * 1024                                                                         \
+                ? cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) \
+                : cudaSuccess;                                                                       \
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, smem); \
+        break;                                                                                       \
+    }
+    switch (ab) {
+        DOCTORS_CHAIN_OCC(1)
+        DOCTORS_CHAIN_OCC(2)
+        DOCTORS_CHAIN_OCC(3)
+        DOCTORS_CHAIN_OCC(4)
+        DOCTORS_CHAIN_OCC(5)
+        DOCTORS_CHAIN_OCC(6)
+        DOCTORS_CHAIN_OCC(7)
+        DOCTORS_CHAIN_OCC(9)
+        DOCTORS_CHAIN_OCC(10)
+        DOCTORS_CHAIN_OCC(12)
+        default: break;
+    }
+#undef DOCTORS_CHAIN_OCC
+    return e == cudaSuccess ? b : 0;
+}
+
+template <int M, int MODE>
+cudaError_t launch_sweep_chain_m(const SweepArgs& a, cudaStream_t s) {
+    const int a_lo = a.stage - (a.nty - 1) > 0 ? a.stage - (a.nty - 1) : 0;
+    const int a_hi = a.stage < a.ntx - 1 ? a.stage : a.ntx - 1;
+    const int ntiles = a_hi - a_lo + 1;
+    if (ntiles <= 0 || a.gcount <= 0) return cudaSuccess;
+    const int ntasks = ntiles * 8 * a.nab * a.gcount;
+    const int grid = ntasks < a.chain_slots ? ntasks : a.chain_slots;
+    const int cmax = (ntasks + grid - 1) / grid;
+    const int T = a.tx * a.ty;
+    const size_t smem = sweep_chain_smem_bytes(a.ab, a.tx, a.ty, cmax, a.gcount, a.nmat);
+#define DOCTORS_CHAIN_CASE(AB)                                                                       \
+    case AB: {                                                                                       \
+        auto kern = k_sweep_chain<AB, M, MODE>;                                                      \
+        if (smem > 48 * 1024) {                                                                      \
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+            if (e != cudaSuccess) return e;                                                          \
+        }                                                                                            \
+        kern<<<grid, T, smem, s>>>(a);                                                               \
+        break;                                                                                       \
+    }
+    switch (a.ab) {
+        DOCTORS_CHAIN_CASE(1)
+        DOCTORS_CHAIN_CASE(2)
+        DOCTORS_CHAIN_CASE(3)
+        DOCTORS_CHAIN_CASE(4)
+        DOCTORS_CHAIN_CASE(5)
+        DOCTORS_CHAIN_CASE(6)
+        DOCTORS_CHAIN_CASE(7)
+        DOCTORS_CHAIN_CASE(9)
+        DOCTORS_CHAIN_CASE(10)
+        DOCTORS_CHAIN_CASE(12)
+        default: return cudaErrorInvalidValue;
+    }
+#undef DOCTORS_CHAIN_CASE
+    return cudaGetLastError();
+}
+
+}  // namespace doctors

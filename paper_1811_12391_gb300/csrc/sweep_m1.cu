@@ -1,8 +1,17 @@
-// Instantiations of the octant wavefront sweep for 1 flux moment(s) per cell.
-#include "sweep_impl.cuh"
+// Instantiations of the octant wavefront sweep for 1 flux moment(s) per cell:
+// the tile-stage kernel (k_sweep) and the chained kernel (k_sweep_chain).
+#include "sweep_chain.cuh"
 
 namespace doctors {
 cudaError_t launch_sweep_m1_entry(const SweepArgs& a, int mode, cudaStream_t s) {
+    if (a.chain_slots > 0) {
+        switch (mode) {
+            case 0: return launch_sweep_chain_m<1, 0>(a, s);
+            case 1: return launch_sweep_chain_m<1, 1>(a, s);
+            case 2: return launch_sweep_chain_m<1, 2>(a, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (mode) {
         case 0: return launch_sweep_m<1, 0>(a, s);
         case 1: return launch_sweep_m<1, 1>(a, s);
@@ -10,5 +19,6 @@ cudaError_t launch_sweep_m1_entry(const SweepArgs& a, int mode, cudaStream_t s) 
         default: return cudaErrorInvalidValue;
     }
 }
+int sweep_chain_blocks_m1(int ab, int threads, size_t smem) { return sweep_chain_blocks_per_sm<1>(ab, threads, smem); }
 cudaError_t upload_tables_m1(const float* R, const float* w) { return upload_direction_tables(R, w); }
 }  // namespace doctors

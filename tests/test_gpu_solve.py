@@ -54,18 +54,19 @@ def cylinder_ref():
     return p, osv.solve(p, tol=1e-11)
 
 
-@pytest.mark.parametrize("tile,ab,kernel", [((16, 16), 0, 1), ((16, 16), 0, 2), ((8, 4), 5, 1), ((8, 4), 5, 2),
-                                            ((5, 7), 2, 1), ((32, 8), 10, 2), ((8, 16), 10, 2)])
+@pytest.mark.parametrize("tile,ab,kernel", [((16, 16), 0, 1), ((16, 16), 0, 2), ((16, 16), 0, 3), ((8, 4), 5, 1),
+                                            ((8, 4), 5, 2), ((8, 4), 5, 3), ((5, 7), 2, 1), ((5, 7), 2, 3),
+                                            ((32, 8), 10, 2), ((32, 8), 10, 3), ((8, 16), 10, 2), ((16, 2), 1, 3)])
 def test_ragged_multitile_cylinder(dp, cylinder_ref, tile, ab, kernel):
     """Several sweep tiles with ragged tails in x and y, S8 P3, with the
-    CUDA-core (1) and tensor-core (2) moment transforms."""
+    CUDA-core (1), tensor-core (2) and chained CUDA-core (3) sweeps."""
     p, sol = cylinder_ref
     d = dp(p, tol=1e-6, max_iters=400, tile=tile, angles_per_block=ab, sweep_kernel=kernel)
     _compare(d, p, sol, f"cylinder tile={tile} ab={ab} kernel={kernel}")
     d.close()
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3])
 def test_abdomen_s16_multi_angle_block(dp, kernel):
     """Heterogeneous abdomen-like phantom, S16 (three direction blocks per
     octant), P3, five materials."""
@@ -76,17 +77,18 @@ def test_abdomen_s16_multi_angle_block(dp, kernel):
     d.close()
 
 
-def test_tensor_core_and_cuda_core_sweeps_agree(dp):
-    """The two moment-transform paths give the same fluence on the full-size
-    water cylinder (one sweep from the first-collision source)."""
+def test_sweep_kernels_agree(dp):
+    """The three sweep kernels give the same fluence on the full-size water
+    cylinder (one sweep from the first-collision source)."""
     p = ph.water_cylinder()
     outs = []
-    for kernel in (1, 2):
+    for kernel in (1, 2, 3):
         d = dp(p, tol=1e-6, max_iters=1, sweep_kernel=kernel)
         d.solve(allow_not_converged=True)
         outs.append(d.fluence_host(1))
         d.close()
     assert max_rel(outs[1], outs[0]) <= 2e-5
+    assert max_rel(outs[2], outs[0]) <= 2e-5
 
 
 def test_p0_and_p2_moment_counts(dp):
@@ -113,7 +115,8 @@ def test_infinite_medium_volume_source(dp):
     d.close()
 
 
-def test_degenerate_meshes(dp):
+@pytest.mark.parametrize("kernel", [1, 3])
+def test_degenerate_meshes(dp, kernel):
     """Single voxel, single column and single plane meshes."""
     for dims in ((1, 1, 1), (1, 1, 7), (5, 1, 1), (4, 6, 1)):
         p = ph.tiny_cube(n=2)
@@ -123,8 +126,8 @@ def test_degenerate_meshes(dp):
         p.density = np.ones(V, np.float32)
         p.origin = -0.5 * np.array(dims, float)
         sol = osv.solve(p, tol=1e-12)
-        d = dp(p, tol=1e-6, max_iters=400)
-        _compare(d, p, sol, f"dims={dims}")
+        d = dp(p, tol=1e-6, max_iters=400, sweep_kernel=kernel)
+        _compare(d, p, sol, f"dims={dims} kernel={kernel}")
         d.close()
 
 
