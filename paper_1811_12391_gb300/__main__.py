@@ -1,7 +1,7 @@
 """Command line: solve a named synthetic workload and print the report.
 
   python -m paper_1811_12391_gb300 <workload> [--iters N] [--tol T] [--tile X Y] [--ab K] [--kernel 1|2|3]
-                                   [--autotune] [--repeat R]
+                                   [--device-loop] [--autotune] [--repeat R]
 
 Workloads: tiny_cube, water_cylinder, abdomen, axial_scan, differentiable_abdomen
 (see synth/phantoms.py).  Used as the profiled command in profiles/.
@@ -24,6 +24,8 @@ def main():
     ap.add_argument("--tile", type=int, nargs=2, default=(0, 0))
     ap.add_argument("--ab", type=int, default=0)
     ap.add_argument("--kernel", type=int, default=0, help="sweep kernel: 0 default, 1 CUDA-core, 2 tensor-core, 3 chained CUDA-core")
+    ap.add_argument("--device-loop", action="store_true",
+                    help="run the source iteration as one CUDA graph with a device-side while loop")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--repeat", type=int, default=1)
     args = ap.parse_args()
@@ -34,7 +36,7 @@ def main():
 
     p = ph.config_problem(args.workload)
     d = DoctorsProblem(p, tol=args.tol, max_iters=args.iters, tile=tuple(args.tile), angles_per_block=args.ab,
-                       sweep_kernel=args.kernel)
+                       sweep_kernel=args.kernel, device_loop=int(args.device_loop))
     if args.autotune:
         print(json.dumps({"autotune": d.autotune()}), flush=True)
     for _ in range(args.repeat):

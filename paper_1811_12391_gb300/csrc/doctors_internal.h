@@ -186,12 +186,19 @@ cudaError_t launch_sweep_stage(const SweepArgs& a, int M, int mode, cudaStream_t
 bool sweep_supported(int ab, int M);
 // CTAs of the chained sweep kernel resident per SM (0 if it cannot launch)
 int sweep_chain_blocks_per_sm(int ab, int M, int threads, size_t smem);
+// Hyperplane plane of the chained sweep: a column's AB fluxes are one record
+// of chain_rs(AB) floats (odd), columns are laid out with a row pitch of
+// chain_px(tx) slots (even, halo column at 0) and a halo row at 0.  Threads
+// on one diagonal of the tile are then an odd number of words apart, so
+// their plane accesses fall in distinct shared-memory banks.
+__host__ __device__ inline int chain_rs(int ab) { return ab | 1; }
+__host__ __device__ inline int chain_px(int tx) { return (tx & 1) ? tx + 1 : tx + 2; }
 // shared memory of one chained-sweep CTA: per chained task the direction rows
 // (coef and R as float4, w), the per-group leakage (FP64), the two
 // halo-padded hyperplanes and sigma_t of the swept groups
 inline size_t sweep_chain_smem_bytes(int ab, int tx, int ty, int cmax, int gcount, int nmat) {
     return 16 * (size_t)cmax * ab * 5 + 8 * (size_t)gcount +
-           4 * ((size_t)2 * ab * (tx + 1) * (ty + 1) + (size_t)cmax * ab + (size_t)gcount * nmat);
+           4 * ((size_t)2 * chain_rs(ab) * chain_px(tx) * (ty + 1) + (size_t)cmax * ab + (size_t)gcount * nmat);
 }
 // Upload the shared direction tables (all S_N sets) to the current device,
 // once per device; returns the first table row of order N in *base.

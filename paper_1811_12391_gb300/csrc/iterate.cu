@@ -99,39 +99,97 @@ cudaError_t launch_sweep_stage(const SweepArgs& a, int M, int mode, cudaStream_t
 
 namespace {
 
-// One thread per (voxel, moment); moment fastest so that a warp reads and
-// writes contiguous memory.  Loops over destination groups; the source
-// groups' moments are re-read through L1.
-__global__ void __launch_bounds__(256) k_scatter(const ScatterArgs a) {
+// Threads stride over (voxel, moment) pairs, moment fastest, so that a warp reads and
+// writes contiguous memory.  A thread loads the moments of every source group
+// it needs into registers once (all loads in flight together) and forms each
+// destination group's sum from them; the group loops are unrolled up to
+// GMAX (>= G) so that the moments stay in registers.  The scattering table
+// is staged in shared memory when it fits.  Blocks stride over the
+// (voxel, moment) range, so each stages the table once.
+constexpr int kScatterThreads = 256;
+constexpr size_t kScatterTableSmem = 100 * 1024;  // largest staged table
+
+// staged table: [nmat][L+1] blocks of [GMAX (from)][GMAX (to)], so that every
+// entry a thread reads is at a compile-time offset from its (material, degree)
+// block; the block pitch GMAX^2 + 1 is odd, so the lanes of a warp (two voxels,
+// up to eight blocks) read distinct shared-memory banks
+template <int GMAX>
+__host__ __device__ constexpr int scatter_block_pitch() { return GMAX * GMAX + 1; }
+template <int GMAX>
+size_t scatter_table_bytes(const ScatterArgs& a) {
+    return (size_t)a.nmat * (a.L + 1) * scatter_block_pitch<GMAX>() * sizeof(float);
+}
+
+template <int GMAX>
+__global__ void __launch_bounds__(kScatterThreads, 4) k_scatter(const ScatterArgs a, int table_in_smem) {
+    extern __shared__ float tab_s[];
     if (a.skip && *a.skip) return;
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.V * a.M) return;
-    const size_t v = t / a.M;
-    const int lm = (int)(t % a.M);
-    const int l = degree_of_lm(lm_of_pos(lm, a.M));
-    const int m = __ldg(a.mat + v);
-    const float r = __ldg(a.rho + v);
-    const float* tab = a.sigs + ((size_t)m * (a.L + 1) + l) * a.G * a.G;
+    const int G = a.G;
+    if (table_in_smem) {
+        constexpr int BP = scatter_block_pitch<GMAX>();
+        const int nblk = a.nmat * (a.L + 1);
+        for (int e = threadIdx.x; e < nblk * BP; e += blockDim.x) {
+            const int blk = e / BP, r = e % BP, i = r / GMAX, j = r % GMAX;
+            tab_s[e] = (r < GMAX * GMAX && i < G && j < G) ? __ldg(a.sigs + ((size_t)blk * G + i) * G + j) : 0.0f;
+        }
+        __syncthreads();
+    }
     const size_t VM = a.V * a.M;
-    const int g_end = a.g1 > 0 ? a.g1 : a.G;
-    for (int g = a.g0; g < g_end; ++g) {
-        float out = a.base ? __ldg(a.base + g * VM + t) : 0.0f;
-        if (lm == 0) {
-            if (a.iso) out += __ldg(a.iso + g);
-            if (a.iso_field) out += a.iso_field_scale * __ldg(a.iso_field + (size_t)g * a.V + v);
-        }
+    const int g_beg = a.g0, g_end = a.g1 > 0 ? a.g1 : G;
+    // no barrier below: threads leave the grid-stride loop independently
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < VM; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t v = t / a.M;
+        const int lm = (int)(t % a.M);
+        const int l = degree_of_lm(lm_of_pos(lm, a.M));
+        float ph[GMAX];
+        float r = 0.0f;
+        int mb = 0;
         if (a.phi) {
-            float acc = 0.0f;
-            if (!a.transpose) {
-                for (int gp = 0; gp <= g; ++gp)
-                    acc = fmaf(__ldg(tab + gp * a.G + g), __ldg(a.phi + gp * VM + t), acc);
-            } else {
-                for (int gp = g; gp < a.G; ++gp)
-                    acc = fmaf(__ldg(tab + g * a.G + gp), __ldg(a.phi + gp * VM + t), acc);
+            mb = __ldg(a.mat + v) * (a.L + 1) + l;     // (material, degree) block of the table
+            r = __ldg(a.rho + v);
+            // every source group a destination group of the window needs
+#pragma unroll
+            for (int gp = 0; gp < GMAX; ++gp) {
+                const bool need = a.transpose ? (gp >= g_beg && gp < G) : (gp < g_end);
+                ph[gp] = need ? __ldg(a.phi + gp * VM + t) : 0.0f;
             }
-            out = fmaf(r, acc, out);
         }
-        a.out[g * VM + t] = out;
+        const float* ts = tab_s + (size_t)mb * scatter_block_pitch<GMAX>();
+        const float* tg = a.sigs + (size_t)mb * G * G;
+#pragma unroll
+        for (int g = 0; g < GMAX; ++g) {
+            if (g < g_beg || g >= g_end) continue;
+            float out = a.base ? __ldg(a.base + g * VM + t) : 0.0f;
+            if (lm == 0) {
+                if (a.iso) out += __ldg(a.iso + g);
+                if (a.iso_field) out += a.iso_field_scale * __ldg(a.iso_field + (size_t)g * a.V + v);
+            }
+            if (a.phi) {
+                float acc = 0.0f;
+                if (!a.transpose) {
+                    // downscatter: g' <= g
+                    if (table_in_smem) {
+#pragma unroll
+                        for (int gp = 0; gp <= g; ++gp) acc = fmaf(ts[gp * GMAX + g], ph[gp], acc);
+                    } else {
+#pragma unroll
+                        for (int gp = 0; gp <= g; ++gp) acc = fmaf(__ldg(tg + gp * G + g), ph[gp], acc);
+                    }
+                } else {
+                    // adjoint: g' >= g (zero padding beyond G in the staged table)
+                    if (table_in_smem) {
+#pragma unroll
+                        for (int gp = g; gp < GMAX; ++gp) acc = fmaf(ts[g * GMAX + gp], ph[gp], acc);
+                    } else {
+#pragma unroll
+                        for (int gp = g; gp < GMAX; ++gp)
+                            if (gp < G) acc = fmaf(__ldg(tg + g * G + gp), ph[gp], acc);
+                    }
+                }
+                out = fmaf(r, acc, out);
+            }
+            a.out[g * VM + t] = out;
+        }
     }
 }
 
@@ -254,9 +312,26 @@ unsigned blocks_for(size_t n, int bs, unsigned cap = 0) {
 
 }  // namespace
 
-cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s) {
-    k_scatter<<<blocks_for(a.V * a.M, 256), 256, 0, s>>>(a);
+template <int GMAX>
+cudaError_t launch_scatter_g(const ScatterArgs& a, cudaStream_t s) {
+    const size_t tab_bytes = scatter_table_bytes<GMAX>(a);
+    const int staged = tab_bytes <= kScatterTableSmem ? 1 : 0;
+    const size_t smem = staged ? tab_bytes : 0;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_scatter<GMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_scatter<GMAX><<<blocks_for(a.V * a.M, kScatterThreads, 152 * 8), kScatterThreads, smem, s>>>(a, staged);
     return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s) {
+    if (a.G <= 8) return launch_scatter_g<8>(a, s);
+    if (a.G <= 16) return launch_scatter_g<16>(a, s);
+    if (a.G <= 24) return launch_scatter_g<24>(a, s);
+    if (a.G <= 32) return launch_scatter_g<32>(a, s);
+    if (a.G <= 64) return launch_scatter_g<64>(a, s);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_residual(size_t V, int G, int M, const float* mom, float* prev, double* res,

@@ -52,14 +52,15 @@ __global__ void __launch_bounds__(256, 2) k_sweep_chain(const SweepArgs a) {
     const int grid = (int)gridDim.x;
     const int cmax = (ntasks + grid - 1) / grid;
     const int nchain = (ntasks - (int)blockIdx.x + grid - 1) / grid;   // tasks of this CTA (grid <= ntasks)
-    const int PX = a.tx + 1;                    // padded plane: halo row and column at index 0
-    const int P = PX * (a.ty + 1);
+    constexpr int RS = AB | 1;                  // floats per column record (odd: conflict-free)
+    const int PX = chain_px(a.tx);              // row pitch in columns (even), halo column at 0
+    const int P = PX * (a.ty + 1);              // columns per plane, halo row at 0
 
     float4* coef_s = sm4;                       // [cmax][AB]: cx, cy, cz, cx+cy+cz
     float4* R_s = coef_s + cmax * AB;           // [cmax][AB][4]: R_lm, 16 per direction
     double* leak_s = reinterpret_cast<double*>(R_s + 4 * cmax * AB);   // [gcount]
-    float* buf = reinterpret_cast<float*>(leak_s + a.gcount);        // [2][AB][P]
-    float* w_s = buf + 2 * AB * P;              // [cmax][AB]
+    float* buf = reinterpret_cast<float*>(leak_s + a.gcount);        // [2][P][RS]
+    float* w_s = buf + 2 * P * RS;              // [cmax][AB]
     float* sigt_s = w_s + cmax * AB;            // [gcount][nmat]
 
     for (int e = threadIdx.x; e < nchain * AB; e += blockDim.x) {
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_chain(const SweepArgs a) {
     for (int e = threadIdx.x; e < a.gcount * a.nmat; e += blockDim.x)
         sigt_s[e] = a.sigt[(e % a.nmat) * a.G + a.g0 + e / a.nmat];
     for (int e = threadIdx.x; e < a.gcount; e += blockDim.x) leak_s[e] = 0.0;
-    for (int e = threadIdx.x; e < 2 * AB * P; e += blockDim.x) buf[e] = 0.0f;
+    for (int e = threadIdx.x; e < 2 * P * RS; e += blockDim.x) buf[e] = 0.0f;
     __syncthreads();
 
     // threads own the tile's columns in diagonal order (li + lj ascending):
@@ -102,6 +103,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_chain(const SweepArgs a) {
     }
     const int d = li + lj;
     const int cs = (lj + 1) * PX + li + 1;      // this column's slot in the padded planes
+    const int xs = (cs - 1) * RS, ys = (cs - PX) * RS, os = cs * RS;   // upwind x, upwind y, own record
     const size_t V = (size_t)a.nx * a.ny * a.nz;
     const size_t nxy = (size_t)a.nx * a.ny;
     const size_t xf_stride = (size_t)(a.ntx > 1 ? a.ntx - 1 : 0) * a.ny * a.nz;
@@ -145,23 +147,23 @@ __global__ void __launch_bounds__(256, 2) k_sweep_chain(const SweepArgs a) {
     // hyperplane buffer `pl` (read by this thread one step later)
     auto fill_halo = [&](int pl, int kn) {
         if (!col) return;
-        float* hb = buf + pl * AB * P;
+        float* hb = buf + pl * P * RS;
         if (li == 0) {
             if (xi) {
 #pragma unroll
-                for (int q = 0; q < AB; ++q) cp_async_f32(hb + q * P + cs - 1, xi + q * xo_q + kn);
+                for (int q = 0; q < AB; ++q) cp_async_f32(hb + xs + q, xi + q * xo_q + kn);
             } else {
 #pragma unroll
-                for (int q = 0; q < AB; ++q) hb[q * P + cs - 1] = 0.0f;
+                for (int q = 0; q < AB; ++q) hb[xs + q] = 0.0f;
             }
         }
         if (lj == 0) {
             if (yi) {
 #pragma unroll
-                for (int q = 0; q < AB; ++q) cp_async_f32(hb + q * P + cs - PX, yi + q * yo_q + kn);
+                for (int q = 0; q < AB; ++q) cp_async_f32(hb + ys + q, yi + q * yo_q + kn);
             } else {
 #pragma unroll
-                for (int q = 0; q < AB; ++q) hb[q * P + cs - PX] = 0.0f;
+                for (int q = 0; q < AB; ++q) hb[ys + q] = 0.0f;
             }
         }
     };
@@ -226,17 +228,18 @@ __global__ void __launch_bounds__(256, 2) k_sweep_chain(const SweepArgs a) {
                     }
                     psi[q] = (t0 + t1) + (t2 + t3);
                 }
-                // step-differenced cell solve per direction
-                const float* pv = buf + pb * AB * P;
-                float* cv = buf + cb * AB * P;
+                // step-differenced cell solve per direction (branch-free
+                // upwind reads: the halo holds the incoming face values)
+                const float* pv = buf + pb * P * RS;
+                float* cv = buf + cb * P * RS;
 #pragma unroll
                 for (int q = 0; q < AB; ++q) {
-                    const float px = pv[q * P + cs - 1];
-                    const float py = pv[q * P + cs - PX];
+                    const float px = pv[xs + q];
+                    const float py = pv[ys + q];
                     const float4 cq = coef_s[tab + q];
                     const float num = fmaf(cq.z, zc[q], fmaf(cq.y, py, fmaf(cq.x, px, psi[q])));
                     psi[q] = __fdividef(num, sig + cq.w);
-                    cv[q * P + cs] = psi[q];
+                    cv[os + q] = psi[q];
                     zc[q] = psi[q];
                 }
                 if constexpr (MODE == 1) {
