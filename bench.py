@@ -49,6 +49,9 @@ SWEEP_TRAFFIC = {
     (16, 16, 10, 2): (2121.9e6, "sweep_tc.cu", "79ec5703826b205c1bdc9d4f7ff57c205fec428a"),
 }
 
+# sweep kernel by the library's sweep_kernel code
+SWEEP_KERNELS = {1: "k_sweep", 2: "k_sweep_tc", 3: "k_sweep_chain"}
+
 # FP32 lanes per SM and SMs of a GB300 (the ALU roofline of the CUDA-core sweep)
 FP32_LANES_PER_SM = 128
 SMS = 152
@@ -337,7 +340,7 @@ def main():
                    "directions": p.n_angles, "groups": p.G, "moments": M,
                    "sweeps_per_step": sweeps / args.steps, "l2": "inputs larger than L2 (4 x 160 MB moment arrays)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "roofline": {"bound": "alu", "kernel": "k_sweep (the stage launches of one sweep)",
+        "roofline": {"bound": "alu", "kernel": f"{SWEEP_KERNELS.get(tuning['sweep_kernel'], '?')} (the stage launches of one sweep)",
                      "achieved": achieved_tflops, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": achieved_tflops / alu_peak,
                      "peak_kind": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_mhz:.0f} MHz",

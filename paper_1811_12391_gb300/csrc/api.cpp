@@ -197,6 +197,7 @@ SweepArgs sweep_args(const doctors_problem* p, int reverse, const float* src, fl
     a.g0 = 0;
     a.gcount = p->G;
     a.chain_slots = p->use_tc ? 0 : p->chain_slots;
+    a.dir_table = &p->dir_table;
     return a;
 }
 
@@ -491,10 +492,12 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
         int sms = 0;
         CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
         const int max_tasks = std::min(ntx, nty) * 8 * (p->A8 / ab) * p->G;
-        const int cmax = (max_tasks + sms - 1) / sms;
+        // whole octants per CTA: direction table in the constant bank, no staged rows
+        const bool ct = p->A8 == ab && chain_const_table_ab(ab);
+        const int cmax = ct ? 0 : (max_tasks + sms - 1) / sms;
         smem = sweep_chain_smem_bytes(ab, tx, ty, cmax, p->G, kMaxMat);
         if (smem <= 227 * 1024) {
-            const int per_sm = sweep_chain_blocks_per_sm(ab, p->M, tx * ty, smem);
+            const int per_sm = sweep_chain_blocks_per_sm(ab, ct, p->M, tx * ty, smem);
             if (per_sm < 1) {
                 set_error("chained sweep cannot be resident with this tile");
                 return DOCTORS_ERR_INVALID_ARG;
@@ -609,6 +612,41 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
         coef[n * 8 + 5] = (float)(w[n] * oy * dx * dz);
         coef[n * 8 + 6] = (float)(w[n] * oz * dx * dy);
         coef[n * 8 + 7] = (float)w[n];
+    }
+    // first-octant direction table of the chained sweep; check that every
+    // octant's harmonics are the first octant's with the reflection signs
+    {
+        ChainDirTable& t = p->dir_table;
+        double Rb[16], Rn[16];
+        for (int n = 0; n < A; ++n) {
+            const int o = n / p->A8, j = n % p->A8;
+            real_harmonics(3, dirs[3 * j], dirs[3 * j + 1], dirs[3 * j + 2], Rb);
+            real_harmonics(3, dirs[3 * n], dirs[3 * n + 1], dirs[3 * n + 2], Rn);
+            for (int lm = 0; lm < 16; ++lm) {
+                const bool flip = (((o & 1) && ((kOddX >> lm) & 1u)) != 0) ^ (((o & 2) && ((kOddY >> lm) & 1u)) != 0) ^
+                                  (((o & 4) && ((kOddZ >> lm) & 1u)) != 0);
+                if (std::fabs(Rn[lm] - (flip ? -Rb[lm] : Rb[lm])) > 1e-12)
+                    return fail(DOCTORS_ERR_INVALID_ARG, "quadrature octants are not reflections of the first");
+            }
+        }
+        for (int j = 0; j < p->A8; ++j) {
+            const double ox = dirs[3 * j], oy = dirs[3 * j + 1], oz = dirs[3 * j + 2];
+            real_harmonics(3, ox, oy, oz, Rb);
+            for (int pos = 0; pos < M; ++pos) {
+                const int lm = lm_of_pos(pos, M);
+                const int l = degree_of_lm(lm);
+                t.mop[j * 16 + pos] = (float)((2 * l + 1) / (4.0 * M_PI) * Rb[lm]);
+                t.dop[j * 16 + pos] = (float)(w[j] * Rb[lm]);
+            }
+            t.cx[j] = coef[j * 8 + 0];
+            t.cy[j] = coef[j * 8 + 1];
+            t.cz[j] = coef[j * 8 + 2];
+            t.csum[j] = coef[j * 8 + 3];
+            t.lx[j] = coef[j * 8 + 4];
+            t.ly[j] = coef[j * 8 + 5];
+            t.lz[j] = coef[j * 8 + 6];
+            t.w[j] = coef[j * 8 + 7];
+        }
     }
     const size_t GV = (size_t)p->G * p->V, GVM = GV * M;
     int rc = 0;

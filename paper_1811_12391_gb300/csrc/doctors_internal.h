@@ -180,12 +180,35 @@ struct SweepArgs {
     float* prod;                       // [G][V]: mode 2 accumulator
     const int* skip;                   // if non-null and *skip != 0 the kernel does nothing
     int chain_slots;                   // > 0: chained kernel, at most this many CTAs per stage launch
+    const struct ChainDirTable* dir_table;   // host copy of the first-octant direction table (chained kernel)
 };
+
+// Direction data of the first octant for the chained sweep, passed by value
+// as a kernel parameter: the kernel reads it through the constant bank, with
+// compile-time offsets when a CTA sweeps whole octants.  Directions of octant
+// o are the first octant's reflected by the signs of o (the quadrature builds
+// them that way), and R_lm of a reflected direction is R_lm of the original
+// times (-1) to the number of reflected axes in which R_lm is odd.
+constexpr int kMaxA8 = 36;             // S16
+struct ChainDirTable {
+    float mop[kMaxA8 * 16];            // (2l+1)/(4 pi) R_lm, moment storage order
+    float dop[kMaxA8 * 16];            // w R_lm, moment storage order
+    float cx[kMaxA8], cy[kMaxA8], cz[kMaxA8], csum[kMaxA8];   // |Omega_q| / d_q and their sum
+    float lx[kMaxA8], ly[kMaxA8], lz[kMaxA8];                  // boundary current per face (w |Omega_q| area)
+    float w[kMaxA8];
+};
+// R_lm odd in x, y, z (bit lm)
+constexpr unsigned kOddX = (1u << 3) | (1u << 4) | (1u << 7) | (1u << 10) | (1u << 13) | (1u << 15);
+constexpr unsigned kOddY = (1u << 1) | (1u << 4) | (1u << 5) | (1u << 9) | (1u << 10) | (1u << 11);
+constexpr unsigned kOddZ = (1u << 2) | (1u << 5) | (1u << 7) | (1u << 10) | (1u << 12) | (1u << 14);
+// chained kernels with the direction table in the constant bank exist for
+// these directions per CTA (whole octants of S2, S4, S6, S8)
+inline bool chain_const_table_ab(int ab) { return ab == 1 || ab == 3 || ab == 6 || ab == 10; }
 // mode 0: plain; 1: store psi; 2: accumulate sum_n w_n psi_n psi_stored_n into prod
 cudaError_t launch_sweep_stage(const SweepArgs& a, int M, int mode, cudaStream_t s);
 bool sweep_supported(int ab, int M);
 // CTAs of the chained sweep kernel resident per SM (0 if it cannot launch)
-int sweep_chain_blocks_per_sm(int ab, int M, int threads, size_t smem);
+int sweep_chain_blocks_per_sm(int ab, bool ct, int M, int threads, size_t smem);
 // Hyperplane plane of the chained sweep: a column's AB fluxes are one record
 // of chain_rs(AB) floats (odd), columns are laid out with a row pitch of
 // chain_px(tx) slots (even, halo column at 0) and a halo row at 0.  Threads
@@ -229,6 +252,7 @@ struct doctors_problem {
     int tx = 16, ty = 16, ntx = 1, nty = 1, ab = 1, nab = 1;
     bool use_tc = false;            // tensor-core transforms in the sweep
     int chain_slots = 0;            // > 0: chained CUDA-core sweep with this many CTA slots
+    doctors::ChainDirTable dir_table{};   // first-octant direction table of the chained sweep
     // device tables
     float* d_coef = nullptr;
     int table_base = 0;

@@ -17,11 +17,38 @@
 // of the plane buffers: the edge threads copy the value of their next cell
 // with cp.async one step ahead (zero on the mesh boundary), so every upwind
 // read is the same shared-memory load, without a branch.
+//
+// CT = true (a CTA sweeps whole octants): the moment-to-direction and
+// direction-to-moment tables, the step coefficients and the weights of the
+// first octant come as a kernel parameter (ChainDirTable) and are read as
+// constant-bank operands at compile-time offsets, so the transforms issue no
+// shared-memory loads.  Another octant's directions are the first octant's
+// reflected, which multiplies R_lm by -1 for every reflected axis in which it
+// is odd: the kernel applies those signs to the source moments before the
+// transform and to the accumulated moments after it.  CT = false: the rows
+// of every chained task are staged in shared memory.
 #pragma once
+
+#include <type_traits>
 
 #include "sweep_impl.cuh"
 
 namespace doctors {
+
+struct ChainNoTable {
+    int unused;
+};
+
+// sign of R_lm (storage position m) under the reflections (fx, fy, fz) = +-1
+template <int M>
+__device__ __forceinline__ float octant_sign(int m, float fx, float fy, float fz) {
+    const int lm = lm_of_pos(m, M);
+    float r = 1.0f;
+    if ((kOddX >> lm) & 1u) r *= fx;
+    if ((kOddY >> lm) & 1u) r *= fy;
+    if ((kOddZ >> lm) & 1u) r *= fz;
+    return r;
+}
 
 __device__ __forceinline__ void cp_async_f32(float* dst_smem, const float* src_gmem) {
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(dst_smem));
@@ -41,8 +68,31 @@ __device__ __forceinline__ void chain_decode(int t, int ntiles, int nab, int& ti
     gi = r >> 3;
 }
 
-template <int AB, int M, int MODE>
-__global__ void __launch_bounds__(256, 2) k_sweep_chain(const SweepArgs a) {
+// field f of the direction table at index i (CT only; i and f compile-time
+// in the unrolled loops, so this is a constant-bank operand)
+template <bool CT, typename T>
+__device__ __forceinline__ float dt_at(const T& dt, int f, int i) {
+    if constexpr (CT) {
+        switch (f) {
+            case 0: return dt.mop[i];
+            case 1: return dt.dop[i];
+            case 2: return dt.cx[i];
+            case 3: return dt.cy[i];
+            case 4: return dt.cz[i];
+            case 5: return dt.csum[i];
+            case 6: return dt.lx[i];
+            case 7: return dt.ly[i];
+            case 8: return dt.lz[i];
+            default: return dt.w[i];
+        }
+    } else {
+        return 0.0f;
+    }
+}
+
+template <int AB, int M, int MODE, bool CT>
+__global__ void __launch_bounds__(256, 2)
+    k_sweep_chain(const SweepArgs a, const std::conditional_t<CT, ChainDirTable, ChainNoTable> dt) {
     extern __shared__ float4 sm4[];
     if (a.skip && *a.skip) return;         // retired instance of a batched loop
     const int a_lo = max(0, a.stage - (a.nty - 1));
@@ -50,7 +100,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_chain(const SweepArgs a) {
     const int ntiles = a_hi - a_lo + 1;
     const int ntasks = ntiles * 8 * a.nab * a.gcount;
     const int grid = (int)gridDim.x;
-    const int cmax = (ntasks + grid - 1) / grid;
+    const int cmax = CT ? 0 : (ntasks + grid - 1) / grid;   // staged table rows (CT: none)
     const int nchain = (ntasks - (int)blockIdx.x + grid - 1) / grid;   // tasks of this CTA (grid <= ntasks)
     constexpr int RS = AB | 1;                  // floats per column record (odd: conflict-free)
     const int PX = chain_px(a.tx);              // row pitch in columns (even), halo column at 0
@@ -63,7 +113,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_chain(const SweepArgs a) {
     float* w_s = buf + 2 * P * RS;              // [cmax][AB]
     float* sigt_s = w_s + cmax * AB;            // [gcount][nmat]
 
-    for (int e = threadIdx.x; e < nchain * AB; e += blockDim.x) {
+    for (int e = threadIdx.x; e < (CT ? 0 : nchain * AB); e += blockDim.x) {
         const int cc = e / AB, q = e % AB;
         int ti, blk, o, gi;
         chain_decode((int)blockIdx.x + cc * grid, ntiles, a.nab, ti, blk, o, gi);
@@ -112,6 +162,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_chain(const SweepArgs a) {
 
     // state of the task this thread works on (or starts next)
     int gi = 0, sz = 1, nb = 0, tab = 0;
+    float fx = 1.0f, fy = 1.0f, fz = 1.0f;      // reflections of the task's directions (CT)
     size_t gV = 0, vcol = 0;
     bool col = false, xout = false, yout = false, xleak = false, yleak = false;
     float* xo = nullptr;
@@ -125,8 +176,12 @@ __global__ void __launch_bounds__(256, 2) k_sweep_chain(const SweepArgs a) {
         const int at = a_lo + ti, bt = a.stage - at;
         const int sx = (o & 1) ? -1 : 1, sy = (o & 2) ? -1 : 1;
         sz = (o & 4) ? -1 : 1;
-        nb = (a.reverse ? (o ^ 7) : o) * a.A8 + blk * AB;
+        const int oe = a.reverse ? (o ^ 7) : o;          // octant of the directions
+        nb = oe * a.A8 + blk * AB;
         tab = cc * AB;
+        fx = (oe & 1) ? -1.0f : 1.0f;
+        fy = (oe & 2) ? -1.0f : 1.0f;
+        fz = (oe & 4) ? -1.0f : 1.0f;
         const int ir = at * a.tx + li, jr = bt * a.ty + lj;
         col = ir < a.nx && jr < a.ny;
         const int i = sx > 0 ? ir : a.nx - 1 - ir;
@@ -201,10 +256,11 @@ __global__ void __launch_bounds__(256, 2) k_sweep_chain(const SweepArgs a) {
             const bool last = kr == a.nz - 1;
             if (col) {
                 float s[M];
-                // (2l+1)/(4 pi) folded into the source moments
+                // CT: reflection signs; otherwise (2l+1)/(4 pi) folded into the source moments
 #pragma unroll
                 for (int m = 0; m < M; ++m)
-                    s[m] = sn[m] * ((2 * degree_of_lm(lm_of_pos(m, M)) + 1) * 0.07957747154594767f);
+                    s[m] = CT ? sn[m] * octant_sign<M>(m, fx, fy, fz)
+                              : sn[m] * ((2 * degree_of_lm(lm_of_pos(m, M)) + 1) * 0.07957747154594767f);
                 const float sig = sig_n;
                 const int k = sz > 0 ? kr : a.nz - 1 - kr;
                 const size_t v = (size_t)k * nxy + vcol;
@@ -220,7 +276,9 @@ __global__ void __launch_bounds__(256, 2) k_sweep_chain(const SweepArgs a) {
                     float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f, t3 = 0.0f;
 #pragma unroll
                     for (int m = 0; m < M; m += 4) {
-                        const float4 R = R_s[4 * (tab + q) + m / 4];
+                        const float4 R = CT ? make_float4(dt_at<CT>(dt, 0, q * 16 + m), dt_at<CT>(dt, 0, q * 16 + m + 1),
+                                                          dt_at<CT>(dt, 0, q * 16 + m + 2), dt_at<CT>(dt, 0, q * 16 + m + 3))
+                                            : R_s[4 * (tab + q) + m / 4];
                         t0 = fmaf(R.x, s[m], t0);
                         if (m + 1 < M) t1 = fmaf(R.y, s[m + 1], t1);
                         if (m + 2 < M) t2 = fmaf(R.z, s[m + 2], t2);
@@ -236,7 +294,9 @@ __global__ void __launch_bounds__(256, 2) k_sweep_chain(const SweepArgs a) {
                 for (int q = 0; q < AB; ++q) {
                     const float px = pv[xs + q];
                     const float py = pv[ys + q];
-                    const float4 cq = coef_s[tab + q];
+                    const float4 cq = CT ? make_float4(dt_at<CT>(dt, 2, q), dt_at<CT>(dt, 3, q), dt_at<CT>(dt, 4, q),
+                                                       dt_at<CT>(dt, 5, q))
+                                         : coef_s[tab + q];
                     const float num = fmaf(cq.z, zc[q], fmaf(cq.y, py, fmaf(cq.x, px, psi[q])));
                     psi[q] = __fdividef(num, sig + cq.w);
                     cv[os + q] = psi[q];
@@ -250,7 +310,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_chain(const SweepArgs a) {
                     float pacc = 0.0f;
 #pragma unroll
                     for (int q = 0; q < AB; ++q)
-                        pacc = fmaf(w_s[tab + q] * psi[q],
+                        pacc = fmaf((CT ? dt_at<CT>(dt, 9, q) : w_s[tab + q]) * psi[q],
                                     __ldg(a.psi + ((size_t)(a.g0 + gi) * a.A + nb + q) * V + v), pacc);
                     atomicAdd(a.prod + gV + v, pacc);
                 }
@@ -266,11 +326,17 @@ __global__ void __launch_bounds__(256, 2) k_sweep_chain(const SweepArgs a) {
                 if (xleak || yleak || last) {
 #pragma unroll
                     for (int q = 0; q < AB; ++q) {
-                        const float* cf = a.coef + (size_t)(nb + q) * 8;
                         float f = 0.0f;
-                        if (xleak) f += __ldg(cf + 4);
-                        if (yleak) f += __ldg(cf + 5);
-                        if (last) f += __ldg(cf + 6);
+                        if constexpr (CT) {
+                            if (xleak) f += dt_at<CT>(dt, 6, q);
+                            if (yleak) f += dt_at<CT>(dt, 7, q);
+                            if (last) f += dt_at<CT>(dt, 8, q);
+                        } else {
+                            const float* cf = a.coef + (size_t)(nb + q) * 8;
+                            if (xleak) f += __ldg(cf + 4);
+                            if (yleak) f += __ldg(cf + 5);
+                            if (last) f += __ldg(cf + 6);
+                        }
                         lk = fmaf(f, psi[q], lk);
                     }
                 }
@@ -280,15 +346,22 @@ __global__ void __launch_bounds__(256, 2) k_sweep_chain(const SweepArgs a) {
                 for (int m = 0; m < M; ++m) acc[m] = 0.0f;
 #pragma unroll
                 for (int q = 0; q < AB; ++q) {
-                    const float wp = w_s[tab + q] * psi[q];
+                    // CT: the table holds w R_lm
+                    const float wp = CT ? psi[q] : w_s[tab + q] * psi[q];
 #pragma unroll
                     for (int m = 0; m < M; m += 4) {
-                        const float4 R = R_s[4 * (tab + q) + m / 4];
+                        const float4 R = CT ? make_float4(dt_at<CT>(dt, 1, q * 16 + m), dt_at<CT>(dt, 1, q * 16 + m + 1),
+                                                          dt_at<CT>(dt, 1, q * 16 + m + 2), dt_at<CT>(dt, 1, q * 16 + m + 3))
+                                            : R_s[4 * (tab + q) + m / 4];
                         acc[m] = fmaf(R.x, wp, acc[m]);
                         if (m + 1 < M) acc[m + 1] = fmaf(R.y, wp, acc[m + 1]);
                         if (m + 2 < M) acc[m + 2] = fmaf(R.z, wp, acc[m + 2]);
                         if (m + 3 < M) acc[m + 3] = fmaf(R.w, wp, acc[m + 3]);
                     }
+                }
+                if constexpr (CT) {
+#pragma unroll
+                    for (int m = 0; m < M; ++m) acc[m] *= octant_sign<M>(m, fx, fy, fz);
                 }
                 add_moments<M>(a.mom + mo, acc);
             }
@@ -315,34 +388,39 @@ __global__ void __launch_bounds__(256, 2) k_sweep_chain(const SweepArgs a) {
         if (leak_s[e] != 0.0) atomicAdd(a.leak + a.g0 + e, leak_s[e]);
 }
 
-// CTAs of k_sweep_chain<AB, M, 0> resident per SM at this shared-memory size
+// CTAs of k_sweep_chain<AB, M, 0, CT> resident per SM at this shared-memory size
 template <int M>
-int sweep_chain_blocks_per_sm(int ab, int threads, size_t smem) {
+int sweep_chain_blocks_per_sm(int ab, bool ct, int threads, size_t smem) {
     int b = 0;
     cudaError_t e = cudaErrorInvalidValue;
-#define DOCTORS_CHAIN_OCC(AB)                                                                        \
-    case AB: {                                                                                       \
-        auto kern = k_sweep_chain<AB, M, 0>;                                                         \
-        e = smem > 48 * 1024                                                                         \
-                ? cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) \
-                : cudaSuccess;                                                                       \
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, smem); \
-        break;                                                                                       \
+    auto query = [&](auto kern) {
+        e = smem > 48 * 1024 ? cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                             : cudaSuccess;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, smem);
+    };
+    if (ct) {
+        switch (ab) {
+            case 1: query(k_sweep_chain<1, M, 0, true>); break;
+            case 3: query(k_sweep_chain<3, M, 0, true>); break;
+            case 6: query(k_sweep_chain<6, M, 0, true>); break;
+            case 10: query(k_sweep_chain<10, M, 0, true>); break;
+            default: break;
+        }
+    } else {
+        switch (ab) {
+            case 1: query(k_sweep_chain<1, M, 0, false>); break;
+            case 2: query(k_sweep_chain<2, M, 0, false>); break;
+            case 3: query(k_sweep_chain<3, M, 0, false>); break;
+            case 4: query(k_sweep_chain<4, M, 0, false>); break;
+            case 5: query(k_sweep_chain<5, M, 0, false>); break;
+            case 6: query(k_sweep_chain<6, M, 0, false>); break;
+            case 7: query(k_sweep_chain<7, M, 0, false>); break;
+            case 9: query(k_sweep_chain<9, M, 0, false>); break;
+            case 10: query(k_sweep_chain<10, M, 0, false>); break;
+            case 12: query(k_sweep_chain<12, M, 0, false>); break;
+            default: break;
+        }
     }
-    switch (ab) {
-        DOCTORS_CHAIN_OCC(1)
-        DOCTORS_CHAIN_OCC(2)
-        DOCTORS_CHAIN_OCC(3)
-        DOCTORS_CHAIN_OCC(4)
-        DOCTORS_CHAIN_OCC(5)
-        DOCTORS_CHAIN_OCC(6)
-        DOCTORS_CHAIN_OCC(7)
-        DOCTORS_CHAIN_OCC(9)
-        DOCTORS_CHAIN_OCC(10)
-        DOCTORS_CHAIN_OCC(12)
-        default: break;
-    }
-#undef DOCTORS_CHAIN_OCC
     return e == cudaSuccess ? b : 0;
 }
 
@@ -354,33 +432,41 @@ cudaError_t launch_sweep_chain_m(const SweepArgs& a, cudaStream_t s) {
     if (ntiles <= 0 || a.gcount <= 0) return cudaSuccess;
     const int ntasks = ntiles * 8 * a.nab * a.gcount;
     const int grid = ntasks < a.chain_slots ? ntasks : a.chain_slots;
-    const int cmax = (ntasks + grid - 1) / grid;
+    const bool ct = a.nab == 1 && chain_const_table_ab(a.ab) && a.dir_table != nullptr;
+    const int cmax = ct ? 0 : (ntasks + grid - 1) / grid;
     const int T = a.tx * a.ty;
     const size_t smem = sweep_chain_smem_bytes(a.ab, a.tx, a.ty, cmax, a.gcount, a.nmat);
-#define DOCTORS_CHAIN_CASE(AB)                                                                       \
-    case AB: {                                                                                       \
-        auto kern = k_sweep_chain<AB, M, MODE>;                                                      \
-        if (smem > 48 * 1024) {                                                                      \
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-            if (e != cudaSuccess) return e;                                                          \
-        }                                                                                            \
-        kern<<<grid, T, smem, s>>>(a);                                                               \
-        break;                                                                                       \
+    cudaError_t e = cudaSuccess;
+    auto launch = [&](auto kern, const auto& table) {
+        if (smem > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) kern<<<grid, T, smem, s>>>(a, table);
+    };
+    if (ct) {
+        const ChainDirTable& dt = *a.dir_table;
+        switch (a.ab) {
+            case 1: launch(k_sweep_chain<1, M, MODE, true>, dt); break;
+            case 3: launch(k_sweep_chain<3, M, MODE, true>, dt); break;
+            case 6: launch(k_sweep_chain<6, M, MODE, true>, dt); break;
+            case 10: launch(k_sweep_chain<10, M, MODE, true>, dt); break;
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        const ChainNoTable nt{0};
+        switch (a.ab) {
+            case 1: launch(k_sweep_chain<1, M, MODE, false>, nt); break;
+            case 2: launch(k_sweep_chain<2, M, MODE, false>, nt); break;
+            case 3: launch(k_sweep_chain<3, M, MODE, false>, nt); break;
+            case 4: launch(k_sweep_chain<4, M, MODE, false>, nt); break;
+            case 5: launch(k_sweep_chain<5, M, MODE, false>, nt); break;
+            case 6: launch(k_sweep_chain<6, M, MODE, false>, nt); break;
+            case 7: launch(k_sweep_chain<7, M, MODE, false>, nt); break;
+            case 9: launch(k_sweep_chain<9, M, MODE, false>, nt); break;
+            case 10: launch(k_sweep_chain<10, M, MODE, false>, nt); break;
+            case 12: launch(k_sweep_chain<12, M, MODE, false>, nt); break;
+            default: return cudaErrorInvalidValue;
+        }
     }
-    switch (a.ab) {
-        DOCTORS_CHAIN_CASE(1)
-        DOCTORS_CHAIN_CASE(2)
-        DOCTORS_CHAIN_CASE(3)
-        DOCTORS_CHAIN_CASE(4)
-        DOCTORS_CHAIN_CASE(5)
-        DOCTORS_CHAIN_CASE(6)
-        DOCTORS_CHAIN_CASE(7)
-        DOCTORS_CHAIN_CASE(9)
-        DOCTORS_CHAIN_CASE(10)
-        DOCTORS_CHAIN_CASE(12)
-        default: return cudaErrorInvalidValue;
-    }
-#undef DOCTORS_CHAIN_CASE
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
