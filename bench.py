@@ -38,15 +38,16 @@ WORKLOAD = "water_cylinder"
 WORKLOAD_DESC = ("35 cm water cylinder, 64x64x32 mesh (0.55x0.55x0.5 cm), fan 40 deg x 4 cm cone-beam "
                  "source at 54 cm, 19 groups 10-120 keV, S8 (80 directions), P3, FP32 sweep, tol 1e-6")
 
-# DRAM traffic (read + write) of one full sweep of this workload (the seven
-# stage launches of one iteration) per sweep schedule (tile_x, tile_y,
+# DRAM traffic (read + write) of one full sweep of this workload (the stage
+# launches of one iteration) per sweep schedule (tile_x, tile_y,
 # directions per block, kernel), from `ncu --metrics
-# dram__bytes_read.sum,dram__bytes_write.sum` (profiles/k_sweep_water_cylinder.md);
+# dram__bytes_read.sum,dram__bytes_write.sum` (profiles/k_sweep*_water_cylinder.md);
 # valid only for the kernel source it was taken on.
 SWEEP_TRAFFIC = {
     (16, 16, 10, 1): (2246.4e6, "sweep_impl.cuh", "592eff4d10129e1bde8b55aecdf9fbf52f768e8c"),
     (16, 16, 5, 1): (1687.6e6, "sweep_impl.cuh", "592eff4d10129e1bde8b55aecdf9fbf52f768e8c"),
     (16, 16, 10, 2): (2121.9e6, "sweep_tc.cu", "79ec5703826b205c1bdc9d4f7ff57c205fec428a"),
+    (16, 8, 10, 3): (2534.9e6, "sweep_chain.cuh", "3502773d12d37fb58b50dbc1187553785b1df685"),
 }
 
 # sweep kernel by the library's sweep_kernel code
