@@ -630,14 +630,6 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
             }
         }
         for (int j = 0; j < p->A8; ++j) {
-            const double ox = dirs[3 * j], oy = dirs[3 * j + 1], oz = dirs[3 * j + 2];
-            real_harmonics(3, ox, oy, oz, Rb);
-            for (int pos = 0; pos < M; ++pos) {
-                const int lm = lm_of_pos(pos, M);
-                const int l = degree_of_lm(lm);
-                t.mop[j * 16 + pos] = (float)((2 * l + 1) / (4.0 * M_PI) * Rb[lm]);
-                t.dop[j * 16 + pos] = (float)(w[j] * Rb[lm]);
-            }
             t.cx[j] = coef[j * 8 + 0];
             t.cy[j] = coef[j * 8 + 1];
             t.cz[j] = coef[j * 8 + 2];

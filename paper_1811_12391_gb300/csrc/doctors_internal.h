@@ -183,16 +183,14 @@ struct SweepArgs {
     const struct ChainDirTable* dir_table;   // host copy of the first-octant direction table (chained kernel)
 };
 
-// Direction data of the first octant for the chained sweep, passed by value
-// as a kernel parameter: the kernel reads it through the constant bank, with
-// compile-time offsets when a CTA sweeps whole octants.  Directions of octant
-// o are the first octant's reflected by the signs of o (the quadrature builds
-// them that way), and R_lm of a reflected direction is R_lm of the original
-// times (-1) to the number of reflected axes in which R_lm is odd.
+// Per-problem direction data of the first octant for the chained sweep,
+// passed by value as a kernel parameter and read through the constant bank
+// at compile-time offsets when a CTA sweeps whole octants.  Directions of
+// octant o are the first octant's reflected by the signs of o (the quadrature
+// builds them that way), and R_lm of a reflected direction is R_lm of the
+// original times (-1) to the number of reflected axes in which R_lm is odd.
 constexpr int kMaxA8 = 36;             // S16
 struct ChainDirTable {
-    float mop[kMaxA8 * 16];            // (2l+1)/(4 pi) R_lm, moment storage order
-    float dop[kMaxA8 * 16];            // w R_lm, moment storage order
     float cx[kMaxA8], cy[kMaxA8], cz[kMaxA8], csum[kMaxA8];   // |Omega_q| / d_q and their sum
     float lx[kMaxA8], ly[kMaxA8], lz[kMaxA8];                  // boundary current per face (w |Omega_q| area)
     float w[kMaxA8];

@@ -18,11 +18,11 @@
 // with cp.async one step ahead (zero on the mesh boundary), so every upwind
 // read is the same shared-memory load, without a branch.
 //
-// CT = true (a CTA sweeps whole octants): the moment-to-direction and
-// direction-to-moment tables, the step coefficients and the weights of the
-// first octant come as a kernel parameter (ChainDirTable) and are read as
-// constant-bank operands at compile-time offsets, so the transforms issue no
-// shared-memory loads.  Another octant's directions are the first octant's
+// CT = true (a CTA sweeps whole octants of S2..S8): the first octant's
+// moment-to-direction and direction-to-moment rows come from this unit's
+// constant bank (c_Mop1, c_Dop1) and its step coefficients and weights from a
+// kernel parameter (ChainDirTable), all read at compile-time offsets, so the
+// transforms issue no shared-memory loads.  Another octant's directions are the first octant's
 // reflected, which multiplies R_lm by -1 for every reflected axis in which it
 // is odd: the kernel applies those signs to the source moments before the
 // transform and to the accumulated moments after it.  CT = false: the rows
@@ -38,6 +38,38 @@ namespace doctors {
 struct ChainNoTable {
     int unused;
 };
+
+// First-octant transform rows of the S2, S4, S6 and S8 sets (the sets a CTA
+// can sweep as whole octants), natural (l, m) order: (2l+1)/(4 pi) R_lm for
+// moments -> direction and w R_lm for direction -> moments.  They depend only
+// on N, so they live in this translation unit's constant bank next to c_R,
+// and the kernel reads them at compile-time offsets (row base fixed by AB).
+constexpr int kChainRows = 1 + 3 + 6 + 10;
+__constant__ float c_Mop1[kChainRows * 16];
+__constant__ float c_Dop1[kChainRows * 16];
+
+__host__ __device__ constexpr int chain_row_base(int ab) { return ab == 1 ? 0 : ab == 3 ? 1 : ab == 6 ? 4 : 10; }
+
+// R, w: the concatenated direction tables (all octants of S2, S4, S6, S8,
+// S12, S16, natural order) as uploaded to c_R and c_w.  Internal linkage:
+// every translation unit including this header must fill its own copy of
+// the constant arrays (a shared inline definition would fill only one).
+static cudaError_t upload_chain_tables(const float* R, const float* w) {
+    const int first_row[4] = {0, 8, 32, 80};     // first direction of S2, S4, S6, S8
+    const int a8[4] = {1, 3, 6, 10};
+    float mop[kChainRows * 16], dop[kChainRows * 16];
+    int row = 0;
+    for (int set = 0; set < 4; ++set)
+        for (int j = 0; j < a8[set]; ++j, ++row)
+            for (int lm = 0; lm < 16; ++lm) {
+                const double r = R[(first_row[set] + j) * 16 + lm];
+                mop[row * 16 + lm] = (float)((2 * degree_of_lm(lm) + 1) / (4.0 * 3.14159265358979323846) * r);
+                dop[row * 16 + lm] = (float)((double)w[first_row[set] + j] * r);
+            }
+    cudaError_t e = cudaMemcpyToSymbol(c_Mop1, mop, sizeof(mop));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_Dop1, dop, sizeof(dop));
+    return e;
+}
 
 // sign of R_lm (storage position m) under the reflections (fx, fy, fz) = +-1
 template <int M>
@@ -74,8 +106,6 @@ template <bool CT, typename T>
 __device__ __forceinline__ float dt_at(const T& dt, int f, int i) {
     if constexpr (CT) {
         switch (f) {
-            case 0: return dt.mop[i];
-            case 1: return dt.dop[i];
             case 2: return dt.cx[i];
             case 3: return dt.cy[i];
             case 4: return dt.cz[i];
@@ -276,8 +306,11 @@ __global__ void __launch_bounds__(256, 2)
                     float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f, t3 = 0.0f;
 #pragma unroll
                     for (int m = 0; m < M; m += 4) {
-                        const float4 R = CT ? make_float4(dt_at<CT>(dt, 0, q * 16 + m), dt_at<CT>(dt, 0, q * 16 + m + 1),
-                                                          dt_at<CT>(dt, 0, q * 16 + m + 2), dt_at<CT>(dt, 0, q * 16 + m + 3))
+                        constexpr int rb = chain_row_base(AB) * 16;
+                        const float4 R = CT ? make_float4(c_Mop1[rb + q * 16 + lm_of_pos(m, M)],
+                                                          c_Mop1[rb + q * 16 + lm_of_pos(m + 1, M)],
+                                                          c_Mop1[rb + q * 16 + lm_of_pos(m + 2, M)],
+                                                          c_Mop1[rb + q * 16 + lm_of_pos(m + 3, M)])
                                             : R_s[4 * (tab + q) + m / 4];
                         t0 = fmaf(R.x, s[m], t0);
                         if (m + 1 < M) t1 = fmaf(R.y, s[m + 1], t1);
@@ -350,8 +383,11 @@ __global__ void __launch_bounds__(256, 2)
                     const float wp = CT ? psi[q] : w_s[tab + q] * psi[q];
 #pragma unroll
                     for (int m = 0; m < M; m += 4) {
-                        const float4 R = CT ? make_float4(dt_at<CT>(dt, 1, q * 16 + m), dt_at<CT>(dt, 1, q * 16 + m + 1),
-                                                          dt_at<CT>(dt, 1, q * 16 + m + 2), dt_at<CT>(dt, 1, q * 16 + m + 3))
+                        constexpr int rb = chain_row_base(AB) * 16;
+                        const float4 R = CT ? make_float4(c_Dop1[rb + q * 16 + lm_of_pos(m, M)],
+                                                          c_Dop1[rb + q * 16 + lm_of_pos(m + 1, M)],
+                                                          c_Dop1[rb + q * 16 + lm_of_pos(m + 2, M)],
+                                                          c_Dop1[rb + q * 16 + lm_of_pos(m + 3, M)])
                                             : R_s[4 * (tab + q) + m / 4];
                         acc[m] = fmaf(R.x, wp, acc[m]);
                         if (m + 1 < M) acc[m + 1] = fmaf(R.y, wp, acc[m + 1]);

@@ -309,7 +309,8 @@ inline size_t sweep_smem_bytes(int ab, int M, int tx, int ty, int nz, int nmat) 
 }
 
 // upload the direction tables of this translation unit's constant bank
-inline cudaError_t upload_direction_tables(const float* R, const float* w) {
+// (internal linkage, so that each unit's own copy is the one filled)
+static cudaError_t upload_direction_tables(const float* R, const float* w) {
     cudaError_t e = cudaMemcpyToSymbol(c_R, R, sizeof(float) * kTableDirs * 16);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w, w, sizeof(float) * kTableDirs);
     return e;

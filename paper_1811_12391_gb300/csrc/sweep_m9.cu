@@ -20,5 +20,8 @@ cudaError_t launch_sweep_m9_entry(const SweepArgs& a, int mode, cudaStream_t s) 
     }
 }
 int sweep_chain_blocks_m9(int ab, bool ct, int threads, size_t smem) { return sweep_chain_blocks_per_sm<9>(ab, ct, threads, smem); }
-cudaError_t upload_tables_m9(const float* R, const float* w) { return upload_direction_tables(R, w); }
+cudaError_t upload_tables_m9(const float* R, const float* w) {
+    cudaError_t e = upload_direction_tables(R, w);
+    return e == cudaSuccess ? upload_chain_tables(R, w) : e;
+}
 }  // namespace doctors
