@@ -89,7 +89,11 @@ typedef struct doctors_options {
                                 1 = CUDA-core transforms, one task (tile, octant, direction block,
                                 group) per CTA, 2 = tensor-core (3xTF32 mma) moment transforms
                                 (P3 only), 3 = CUDA-core transforms, each CTA running a chain of
-                                tasks of a stage back to back in one hyperplane pipeline */
+                                tasks of a stage back to back in one hyperplane pipeline,
+                                4 = dataflow: one launch per sweep, CTAs take tasks from a queue and
+                                wait (bounded) on their upstream tiles' face fluxes plane by plane;
+                                needs angles_per_block = N(N+2)/8 and N <= 8.  A wait that gives up
+                                makes the solve return DOCTORS_ERR_TIMEOUT */
     int device_loop;         /* 1 = run the source iteration as one CUDA graph whose while loop is
                                 decided on the device (no host round trip per iteration) */
     int reserved[6];         /* must be zero */
@@ -240,7 +244,7 @@ int doctors_solve_batch(doctors_problem **problems, int n, doctors_result *resul
 typedef struct doctors_tuning {
     int tile_x, tile_y;      /* tile of columns */
     int angles_per_block;    /* directions per CTA */
-    int sweep_kernel;        /* 1 CUDA-core, 2 tensor-core, 3 chained CUDA-core (as doctors_options) */
+    int sweep_kernel;        /* 1 CUDA-core, 2 tensor-core, 3 chained, 4 dataflow (as doctors_options) */
     double ms_per_sweep;     /* measured time of one full sweep of this problem */
     int candidates;          /* schedules timed (0 if taken from the cache) */
 } doctors_tuning;

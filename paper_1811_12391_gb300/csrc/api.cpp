@@ -50,6 +50,7 @@ namespace {
 // default choice of the moment-transform path of the sweep for P3 problems
 constexpr bool kDefaultTensorCoreSweep = false;
 constexpr bool kDefaultChainedSweep = true;
+constexpr bool kDefaultDataflowSweep = false;
 
 int dalloc(void** p, size_t bytes, const char* what) {
     if (bytes == 0) bytes = 16;
@@ -80,7 +81,7 @@ void free_problem(doctors_problem* p) {
                     p->d_phiu_src, p->d_phiu, p->d_U, p->d_Q, p->d_mom, p->d_src, p->d_prev,
                     p->d_emit, p->d_iso, p->d_xface, p->d_yface, p->d_red,
                     p->d_Z, p->d_Qa, p->d_T, p->d_rf, p->d_r, p->d_acc, p->d_grad, p->d_H,
-                    p->d_ones, p->d_psi, p->d_prod};
+                    p->d_ones, p->d_psi, p->d_prod, p->d_flow};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (p->h_red) cudaFreeHost(p->h_red);
@@ -198,7 +199,41 @@ SweepArgs sweep_args(const doctors_problem* p, int reverse, const float* src, fl
     a.gcount = p->G;
     a.chain_slots = p->use_tc ? 0 : p->chain_slots;
     a.dir_table = &p->dir_table;
+    a.flow = p->use_flow ? p->d_flow : nullptr;
     return a;
+}
+
+// One full sweep with the problem's chosen kernel: one launch per tile stage,
+// or one dataflow launch.  Returns the kernels launched in *count.
+cudaError_t launch_sweep(const doctors_problem* p, SweepArgs sw, int mode, cudaStream_t s, int* count) {
+    if (p->use_flow) {
+        *count = 1;
+        return launch_sweep_flow(sw, p->M, mode, s);
+    }
+    *count = 0;
+    for (int st = 0; st < p->ntx + p->nty - 1; ++st) {
+        sw.stage = st;
+        cudaError_t e = p->use_tc ? launch_sweep_tc(sw, mode, s) : launch_sweep_stage(sw, p->M, mode, s);
+        if (e != cudaSuccess) return e;
+        ++*count;
+    }
+    return cudaSuccess;
+}
+
+// After a dataflow sweep: a face wait that timed out leaves the queue and the
+// face records in an unknown state; reset them and report the failure.
+int check_flow(doctors_problem* p) {
+    if (!p->use_flow || !p->d_flow) return DOCTORS_OK;
+    int h[4] = {0, 0, 0, 0};
+    CU(cudaMemcpyAsync(h, p->d_flow, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
+    CU(cudaStreamSynchronize(p->stream));
+    if (h[2] == 0) return DOCTORS_OK;
+    CU(cudaMemsetAsync(p->d_flow, 0, 4 * sizeof(int), p->stream));
+    CU(cudaMemsetAsync(p->d_xface, 0xff, p->xface_bytes, p->stream));
+    CU(cudaMemsetAsync(p->d_yface, 0xff, p->yface_bytes, p->stream));
+    CU(cudaStreamSynchronize(p->stream));
+    set_error("dataflow sweep: a wait for an upstream face timed out");
+    return DOCTORS_ERR_TIMEOUT;
 }
 
 // Source iteration: src = Q + S(mom); mom = sweep(src); residual.  `reverse`
@@ -244,11 +279,9 @@ int iterate(doctors_problem* p, int reverse, const float* Q, float* mom, doctors
         CU(cudaEventRecord(p->ev[3], p->stream));
         sw.g0 = g0;
         sw.gcount = gc;
-        for (int st = 0; st < p->ntx + p->nty - 1; ++st) {
-            sw.stage = st;
-            CU(p->use_tc ? launch_sweep_tc(sw, 0, p->stream) : launch_sweep_stage(sw, p->M, 0, p->stream));
-            ++p->launches;
-        }
+        int nl = 0;
+        CU(launch_sweep(p, sw, 0, p->stream, &nl));
+        p->launches += nl;
         CU(cudaEventRecord(p->ev[4], p->stream));
         CU(launch_residual(p->V, p->G, p->M, mom, p->d_prev, d_res, p->stream, nullptr, g0, gc));
         ++p->launches;
@@ -305,10 +338,7 @@ int iterate(doctors_problem* p, int reverse, const float* Q, float* mom, doctors
 }
 
 
-// Launch one sweep stage with the problem's chosen kernel.
-cudaError_t sweep_stage(const doctors_problem* p, const SweepArgs& sw, int mode, cudaStream_t s) {
-    return p->use_tc ? launch_sweep_tc(sw, mode, s) : launch_sweep_stage(sw, p->M, mode, s);
-}
+
 
 // Source iteration of n problems as one CUDA graph: a while node whose body
 // holds every problem's iteration and a decision kernel that retires
@@ -386,12 +416,10 @@ int graph_iterate(doctors_problem** ps, int n, int reverse, const float* const* 
             if (e == cudaSuccess) e = launch_zero(p->d_red, 5 * (size_t)p->G, skip, cs);
             SweepArgs sw = sweep_args(p, reverse, p->d_src, moms[q]);
             sw.skip = skip;
-            for (int st = 0; st < p->ntx + p->nty - 1 && e == cudaSuccess; ++st) {
-                sw.stage = st;
-                e = sweep_stage(p, sw, 0, cs);
-            }
+            int nl = 0;
+            if (e == cudaSuccess) e = launch_sweep(p, sw, 0, cs, &nl);
             if (e == cudaSuccess) e = launch_residual(p->V, p->G, p->M, moms[q], p->d_prev, p->d_red + p->G, cs, skip);
-            per_iter_launches += 4 + (p->ntx + p->nty - 1);
+            per_iter_launches += 4 + nl;
         }
         if (nb > 1) {
             for (int b = 0; b < nb && e == cudaSuccess; ++b) {
@@ -469,8 +497,12 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
         set_error("angles_per_block must divide N(N+2)/8 and be one of 1,2,3,4,5,6,7,9,10,12");
         return DOCTORS_ERR_INVALID_ARG;
     }
-    if (kernel < 0 || kernel > 3) {
-        set_error("sweep_kernel must be 0, 1, 2 or 3");
+    if (kernel < 0 || kernel > 4) {
+        set_error("sweep_kernel must be 0, 1, 2, 3 or 4");
+        return DOCTORS_ERR_INVALID_ARG;
+    }
+    if (kernel == 4 && !(p->A8 == ab && chain_const_table_ab(ab))) {
+        set_error("dataflow sweep needs whole octants per CTA (angles_per_block = N(N+2)/8) of S2, S4, S6 or S8");
         return DOCTORS_ERR_INVALID_ARG;
     }
     const bool tc_ok = sweep_tc_supported(ab, p->M, tx, ty);
@@ -479,12 +511,26 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
         return DOCTORS_ERR_INVALID_ARG;
     }
     const bool use_tc = kernel == 2 || (kernel == 0 && tc_ok && kDefaultTensorCoreSweep);
-    const bool use_chain = !use_tc && (kernel == 3 || (kernel == 0 && kDefaultChainedSweep));
+    const bool flow_ok = p->A8 == ab && chain_const_table_ab(ab);
+    const bool use_flow = kernel == 4 || (kernel == 0 && !use_tc && flow_ok && kDefaultDataflowSweep);
+    const bool use_chain = !use_tc && !use_flow && (kernel == 3 || (kernel == 0 && kDefaultChainedSweep));
     const int ntx = (p->nx + tx - 1) / tx, nty = (p->ny + ty - 1) / ty;
     int chain_slots = 0;
     size_t smem = 0;
     if (use_tc) {
         smem = sweep_tc_smem_bytes(ab, tx, ty, p->nz, kMaxMat);
+    } else if (use_flow) {
+        int sms = 0;
+        CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+        smem = sweep_flow_smem_bytes(ab, tx, ty, p->G, kMaxMat);
+        if (smem <= 227 * 1024) {
+            const int per_sm = sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem);
+            if (per_sm < 1) {
+                set_error("dataflow sweep cannot be resident with this tile");
+                return DOCTORS_ERR_INVALID_ARG;
+            }
+            chain_slots = sms * per_sm;
+        }
     } else if (use_chain) {
         // CTA slots from the occupancy at the largest chain a stage can need
         // (every chain is at most ceil(tasks / SMs) long once there is at
@@ -511,25 +557,40 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
         set_error("sweep tile needs more than 227 KB of shared memory");
         return DOCTORS_ERR_INVALID_ARG;
     }
-    const size_t xf = (size_t)p->A * p->G * (ntx > 1 ? ntx - 1 : 0) * p->ny * p->nz;
-    const size_t yf = (size_t)p->A * p->G * (nty > 1 ? nty - 1 : 0) * p->nx * p->nz;
-    const size_t xf_old = (size_t)p->A * p->G * (p->ntx > 1 ? p->ntx - 1 : 0) * p->ny * p->nz;
-    const size_t yf_old = (size_t)p->A * p->G * (p->nty > 1 ? p->nty - 1 : 0) * p->nx * p->nz;
-    if (p->d_xface == nullptr || xf > xf_old) {
+    // face buffers: [8][A/8][G][tiles-1][ny or nx][nz] per direction for the
+    // staged kernels; [8][G][tiles-1][ny or nx][nz][A/8 padded to 4] records
+    // for the dataflow kernel
+    const size_t per_dir = std::max((size_t)p->A, (size_t)8 * flow_abp_host(p->A8));
+    const size_t xf = per_dir * p->G * (ntx > 1 ? ntx - 1 : 0) * p->ny * p->nz;
+    const size_t yf = per_dir * p->G * (nty > 1 ? nty - 1 : 0) * p->nx * p->nz;
+    if (p->d_xface == nullptr || xf * sizeof(float) > p->xface_bytes) {
         float* nb = nullptr;
         int rc = dalloc_t(&nb, xf, "x face buffer");
         if (rc) return rc;
         if (p->d_xface) cudaFree(p->d_xface);
         p->d_xface = nb;
+        p->xface_bytes = xf * sizeof(float);
     }
-    if (p->d_yface == nullptr || yf > yf_old) {
+    if (p->d_yface == nullptr || yf * sizeof(float) > p->yface_bytes) {
         float* nb = nullptr;
         int rc = dalloc_t(&nb, yf, "y face buffer");
         if (rc) return rc;
         if (p->d_yface) cudaFree(p->d_yface);
         p->d_yface = nb;
+        p->yface_bytes = yf * sizeof(float);
+    }
+    if (use_flow) {
+        // every face record starts as NaN (not yet written); the queue at zero
+        if (!p->d_flow) {
+            int rc = dalloc_t(&p->d_flow, 4, "dataflow queue");
+            if (rc) return rc;
+        }
+        CU(cudaMemsetAsync(p->d_flow, 0, 4 * sizeof(int), p->stream));
+        if (p->xface_bytes) CU(cudaMemsetAsync(p->d_xface, 0xff, p->xface_bytes, p->stream));
+        if (p->yface_bytes) CU(cudaMemsetAsync(p->d_yface, 0xff, p->yface_bytes, p->stream));
     }
     p->tx = tx; p->ty = ty; p->ab = ab; p->nab = p->A8 / ab; p->ntx = ntx; p->nty = nty; p->use_tc = use_tc;
+    p->use_flow = use_flow;
     p->chain_slots = chain_slots;
     return DOCTORS_OK;
 }
@@ -592,7 +653,7 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     p->nab = p->A8 / p->ab;
     p->ntx = (p->nx + p->tx - 1) / p->tx;
     p->nty = (p->ny + p->ty - 1) / p->ty;
-    if (opt->sweep_kernel < 0 || opt->sweep_kernel > 3) return fail(DOCTORS_ERR_INVALID_ARG, "sweep_kernel must be 0, 1, 2 or 3");
+    if (opt->sweep_kernel < 0 || opt->sweep_kernel > 4) return fail(DOCTORS_ERR_INVALID_ARG, "sweep_kernel must be 0, 1, 2, 3 or 4");
     if (opt->sweep_kernel == 2 && !sweep_tc_supported(p->ab, p->M, p->tx, p->ty))
         return fail(DOCTORS_ERR_INVALID_ARG, "tensor-core sweep needs P3, <= 16 directions per block and a 16x16, 32x8, 16x8, 8x16, 8x8 or 8x4 tile");
     cudaError_t e = cudaGetDevice(&p->device);
@@ -803,6 +864,8 @@ int doctors_solve(doctors_problem* p, doctors_result* info) {
     r.ms_total = t02;
     r.launches = p->launches;
     if (info) *info = r;
+    const int frc = check_flow(p);
+    if (frc) return frc;
     p->solved = true;
     if (rc == DOCTORS_ERR_NOT_CONVERGED) set_error("iteration cap reached before convergence");
     return rc;
@@ -959,8 +1022,12 @@ int doctors_solve_batch(doctors_problem** problems, int n, doctors_result* resul
         res[q].ms_iterate = t12;
         res[q].ms_total = t02;
         res[q].launches = problems[q]->launches;
-        problems[q]->solved = true;
         if (results) results[q] = res[q];
+    }
+    for (int q = 0; q < n; ++q) {
+        const int frc = check_flow(problems[q]);
+        if (frc) return frc;
+        problems[q]->solved = true;
     }
     if (rc == DOCTORS_ERR_NOT_CONVERGED) set_error("iteration cap reached before convergence");
     return rc;
@@ -991,7 +1058,7 @@ int doctors_autotune(doctors_problem* p, doctors_tuning* out) {
     p->launches = 0;
     rc = first_collision(p);
     if (rc) return rc;
-    const int tiles[][2] = {{16, 16}, {32, 8}, {16, 8}, {8, 16}, {8, 8}, {32, 4}};
+    const int tiles[][2] = {{16, 16}, {32, 8}, {16, 8}, {8, 16}, {8, 8}, {32, 4}, {16, 4}, {8, 4}, {4, 8}};
     const int abs_c[] = {12, 10, 9, 7, 6, 5, 4, 3, 2, 1};
     std::vector<int> abs_ok;
     for (int ab : abs_c)
@@ -999,11 +1066,12 @@ int doctors_autotune(doctors_problem* p, doctors_tuning* out) {
     doctors_tuning best{};
     best.ms_per_sweep = 1e30;
     int count = 0;
-    const int saved[4] = {p->tx, p->ty, p->ab, p->use_tc ? 2 : (p->chain_slots > 0 ? 3 : 1)};
+    const int saved[4] = {p->tx, p->ty, p->ab, p->use_tc ? 2 : p->use_flow ? 4 : (p->chain_slots > 0 ? 3 : 1)};
     for (const auto& t : tiles) {
         for (int ab : abs_ok) {
-            for (int kernel = 1; kernel <= 3; ++kernel) {
+            for (int kernel = 1; kernel <= 4; ++kernel) {
                 if (kernel == 2 && !sweep_tc_supported(ab, p->M, t[0], t[1])) continue;
+                if (kernel == 4 && !(p->A8 == ab && chain_const_table_ab(ab))) continue;
                 if (configure_sweep(p, t[0], t[1], ab, kernel) != DOCTORS_OK) continue;
                 SweepArgs sw = sweep_args(p, 0, p->d_Q, p->d_mom);
                 float total = 0.0f;
@@ -1012,10 +1080,8 @@ int doctors_autotune(doctors_problem* p, doctors_tuning* out) {
                     e = cudaMemsetAsync(p->d_mom, 0, (size_t)p->G * p->V * p->M * sizeof(float), p->stream);
                     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_red, 0, 5 * (size_t)p->G * sizeof(double), p->stream);
                     if (e == cudaSuccess) e = cudaEventRecord(p->ev[3], p->stream);
-                    for (int st = 0; st < p->ntx + p->nty - 1 && e == cudaSuccess; ++st) {
-                        sw.stage = st;
-                        e = sweep_stage(p, sw, 0, p->stream);
-                    }
+                    int nl = 0;
+                    if (e == cudaSuccess) e = launch_sweep(p, sw, 0, p->stream, &nl);
                     if (e == cudaSuccess) e = cudaEventRecord(p->ev[4], p->stream);
                     if (e == cudaSuccess) e = cudaEventSynchronize(p->ev[4]);
                     float ms = 0.0f;
@@ -1026,6 +1092,8 @@ int doctors_autotune(doctors_problem* p, doctors_tuning* out) {
                     set_error(std::string("autotune: ") + cudaGetErrorString(e));
                     return DOCTORS_ERR_CUDA;
                 }
+                const int frc = check_flow(p);
+                if (frc) return frc;
                 ++count;
                 const double ms = total / 2.0;
                 if (ms < best.ms_per_sweep) {
@@ -1070,11 +1138,9 @@ int sweep_once(doctors_problem* p, int reverse, int mode, const float* src, floa
     SweepArgs sw = sweep_args(p, reverse, src, mom);
     sw.psi = p->d_psi;
     sw.prod = p->d_prod;
-    for (int st = 0; st < p->ntx + p->nty - 1; ++st) {
-        sw.stage = st;
-        CU(p->use_tc ? launch_sweep_tc(sw, mode, p->stream) : launch_sweep_stage(sw, p->M, mode, p->stream));
-        ++p->launches;
-    }
+    int nl = 0;
+    CU(launch_sweep(p, sw, mode, p->stream, &nl));
+    p->launches += nl;
     return DOCTORS_OK;
 }
 
@@ -1261,6 +1327,8 @@ extern "C" int doctors_adjoint_solve(doctors_problem* p, const double* response,
     r.launches = p->launches;
     if (info) *info = r;
     (void)GVM;
+    const int frc = check_flow(p);
+    if (frc) return frc;
     p->adjoint_done = true;
     if (irc == DOCTORS_ERR_NOT_CONVERGED) set_error("adjoint iteration cap reached before convergence");
     return irc;

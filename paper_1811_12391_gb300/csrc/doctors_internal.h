@@ -181,6 +181,7 @@ struct SweepArgs {
     const int* skip;                   // if non-null and *skip != 0 the kernel does nothing
     int chain_slots;                   // > 0: chained kernel, at most this many CTAs per stage launch
     const struct ChainDirTable* dir_table;   // host copy of the first-octant direction table (chained kernel)
+    int* flow;                         // non-null: dataflow kernel; [0] task queue, [1] CTAs done, [2] wait timed out
 };
 
 // Per-problem direction data of the first octant for the chained sweep,
@@ -221,6 +222,16 @@ inline size_t sweep_chain_smem_bytes(int ab, int tx, int ty, int cmax, int gcoun
     return 16 * (size_t)cmax * ab * 5 + 8 * (size_t)gcount +
            4 * ((size_t)2 * chain_rs(ab) * chain_px(tx) * (ty + 1) + (size_t)cmax * ab + (size_t)gcount * nmat);
 }
+// shared memory of one dataflow-sweep CTA: the fetched face records of the
+// tile's first row and column, per-group leakage, the two halo-padded
+// hyperplanes, sigma_t of the swept groups and the task slot
+inline int flow_abp_host(int ab) { return (ab + 3) & ~3; }
+inline size_t sweep_flow_smem_bytes(int ab, int tx, int ty, int gcount, int nmat) {
+    return 4 * (size_t)(tx + ty) * flow_abp_host(ab) + 8 * (size_t)gcount +
+           4 * ((size_t)2 * chain_rs(ab) * chain_px(tx) * (ty + 1) + (size_t)gcount * nmat) + 16;
+}
+int sweep_flow_blocks_per_sm(int ab, int M, int threads, size_t smem);
+cudaError_t launch_sweep_flow(const SweepArgs& a, int M, int mode, cudaStream_t s);
 // Upload the shared direction tables (all S_N sets) to the current device,
 // once per device; returns the first table row of order N in *base.
 cudaError_t ensure_direction_tables(int device, int N, int* base);
@@ -249,7 +260,9 @@ struct doctors_problem {
     // sweep tiling
     int tx = 16, ty = 16, ntx = 1, nty = 1, ab = 1, nab = 1;
     bool use_tc = false;            // tensor-core transforms in the sweep
-    int chain_slots = 0;            // > 0: chained CUDA-core sweep with this many CTA slots
+    int chain_slots = 0;            // > 0: chained or dataflow sweep with this many CTA slots
+    bool use_flow = false;          // dataflow sweep (one launch per sweep, task queue)
+    int* d_flow = nullptr;          // [4] dataflow queue, done count, timeout flag
     doctors::ChainDirTable dir_table{};   // first-octant direction table of the chained sweep
     // device tables
     float* d_coef = nullptr;
@@ -278,6 +291,7 @@ struct doctors_problem {
     float* d_iso = nullptr;        // [G]
     float* d_xface = nullptr;
     float* d_yface = nullptr;
+    size_t xface_bytes = 0, yface_bytes = 0;
     double* d_red = nullptr;       // reductions: leak [G], res [G][2], bal [G][2]
     double* h_red = nullptr;       // pinned mirror
     // adjoint state (allocated on the first adjoint solve)

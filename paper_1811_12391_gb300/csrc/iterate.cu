@@ -26,6 +26,15 @@ int sweep_chain_blocks_m4(int ab, bool ct, int threads, size_t smem);
 int sweep_chain_blocks_m9(int ab, bool ct, int threads, size_t smem);
 int sweep_chain_blocks_m16(int ab, bool ct, int threads, size_t smem);
 
+cudaError_t launch_sweep_flow_m1_entry(const SweepArgs& a, int mode, cudaStream_t s);
+cudaError_t launch_sweep_flow_m4_entry(const SweepArgs& a, int mode, cudaStream_t s);
+cudaError_t launch_sweep_flow_m9_entry(const SweepArgs& a, int mode, cudaStream_t s);
+cudaError_t launch_sweep_flow_m16_entry(const SweepArgs& a, int mode, cudaStream_t s);
+int sweep_flow_blocks_m1(int ab, int threads, size_t smem);
+int sweep_flow_blocks_m4(int ab, int threads, size_t smem);
+int sweep_flow_blocks_m9(int ab, int threads, size_t smem);
+int sweep_flow_blocks_m16(int ab, int threads, size_t smem);
+
 cudaError_t upload_tables_m1(const float* R, const float* w);
 cudaError_t upload_tables_m4(const float* R, const float* w);
 cudaError_t upload_tables_m9(const float* R, const float* w);
@@ -84,6 +93,26 @@ int sweep_chain_blocks_per_sm(int ab, bool ct, int M, int threads, size_t smem) 
         case 9: return sweep_chain_blocks_m9(ab, ct, threads, smem);
         case 16: return sweep_chain_blocks_m16(ab, ct, threads, smem);
         default: return 0;
+    }
+}
+
+int sweep_flow_blocks_per_sm(int ab, int M, int threads, size_t smem) {
+    switch (M) {
+        case 1: return sweep_flow_blocks_m1(ab, threads, smem);
+        case 4: return sweep_flow_blocks_m4(ab, threads, smem);
+        case 9: return sweep_flow_blocks_m9(ab, threads, smem);
+        case 16: return sweep_flow_blocks_m16(ab, threads, smem);
+        default: return 0;
+    }
+}
+
+cudaError_t launch_sweep_flow(const SweepArgs& a, int M, int mode, cudaStream_t s) {
+    switch (M) {
+        case 1: return launch_sweep_flow_m1_entry(a, mode, s);
+        case 4: return launch_sweep_flow_m4_entry(a, mode, s);
+        case 9: return launch_sweep_flow_m9_entry(a, mode, s);
+        case 16: return launch_sweep_flow_m16_entry(a, mode, s);
+        default: return cudaErrorInvalidValue;
     }
 }
 

@@ -1,0 +1,374 @@
+// Dataflow octant wavefront sweep: the step-differenced cell update of
+// k_sweep_chain (whole octants per CTA, first-octant tables in the constant
+// bank) with the tile stages replaced by a task queue in one launch.
+//
+// The tasks (tile, octant, group) are numbered stage by stage (the tile
+// diagonal of the octant's reflected tile grid).  Each CTA takes the next
+// task from a global counter, sweeps it through its hyperplane pipeline and
+// takes another, until the queue is empty; there is one launch per sweep and
+// no barrier between stages.  A task needs the fluxes leaving its upstream
+// x and y tiles, which other CTAs may still be producing: every face record
+// (the AB fluxes of one column face and plane) starts the sweep as NaN, the
+// producer overwrites it with the fluxes, and the consumer's edge thread
+// fetches it one step ahead with cp.async (L2, not L1), re-fetching while any
+// value is still NaN.  Having used a record, the consumer writes NaN back, so
+// the face buffers are ready for the next sweep without a reset pass.
+//
+// Waiting is bounded and cannot deadlock: a CTA holds one task at a time and
+// waits only on tasks with smaller numbers, which are held by running CTAs
+// (a task is taken only by a running CTA) and themselves wait only on smaller
+// numbers.  A wait that exceeds kFlowSpinLimit polls records the failure in
+// the problem's flag word, uses zero fluxes and goes on; the host turns the
+// flag into DOCTORS_ERR_TIMEOUT and resets the buffers.
+#pragma once
+
+#include "sweep_chain.cuh"
+
+namespace doctors {
+
+constexpr int kFlowSpinLimit = 1 << 18;
+
+// floats per face record: AB fluxes padded to a multiple of 4 (16-byte copies)
+__host__ __device__ constexpr int flow_abp(int ab) { return (ab + 3) & ~3; }
+
+__device__ __forceinline__ void cp_async_cg16(void* dst_smem, const void* src_gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(dst_smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src_gmem) : "memory");
+}
+
+// tiles of stage s of an ntx x nty tile grid
+__device__ __forceinline__ int flow_stage_tiles(int s, int ntx, int nty) {
+    const int lo = s - (nty - 1) > 0 ? s - (nty - 1) : 0;
+    const int hi = s < ntx - 1 ? s : ntx - 1;
+    return hi - lo + 1;
+}
+
+template <int AB, int M, int MODE>
+__global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const ChainDirTable dt) {
+    constexpr int ABP = flow_abp(AB);
+    constexpr int RS = AB | 1;
+    extern __shared__ float4 sm4[];
+    if (a.skip && *a.skip) return;          // retired instance of a batched loop
+    const int PX = chain_px(a.tx);
+    const int P = PX * (a.ty + 1);
+    float4* landx = sm4;                                      // [ty][ABP/4] fetched x-face records
+    float4* landy = landx + a.ty * (ABP / 4);                 // [tx][ABP/4] fetched y-face records
+    double* leak_s = reinterpret_cast<double*>(landy + a.tx * (ABP / 4));   // [gcount]
+    float* buf = reinterpret_cast<float*>(leak_s + a.gcount);              // [2][P][RS]
+    float* sigt_s = buf + 2 * P * RS;                         // [gcount][nmat]
+    int* task_s = reinterpret_cast<int*>(sigt_s + a.gcount * a.nmat);
+
+    for (int e = threadIdx.x; e < a.gcount * a.nmat; e += blockDim.x)
+        sigt_s[e] = a.sigt[(e % a.nmat) * a.G + a.g0 + e / a.nmat];
+    for (int e = threadIdx.x; e < a.gcount; e += blockDim.x) leak_s[e] = 0.0;
+    for (int e = threadIdx.x; e < 2 * P * RS; e += blockDim.x) buf[e] = 0.0f;
+
+    // threads own the tile's columns in diagonal order (li + lj ascending)
+    const int tid = threadIdx.x;
+    int li = 0, lj = 0;
+    {
+        int base = 0;
+        for (int dd = 0; dd <= a.tx + a.ty - 2; ++dd) {
+            const int lo = dd > a.ty - 1 ? dd - (a.ty - 1) : 0;
+            const int hi = dd < a.tx - 1 ? dd : a.tx - 1;
+            const int cnt = hi - lo + 1;
+            if (tid < base + cnt) {
+                li = lo + (tid - base);
+                lj = dd - li;
+                break;
+            }
+            base += cnt;
+        }
+    }
+    const int d = li + lj;
+    const int cs = (lj + 1) * PX + li + 1;
+    const int xs = (cs - 1) * RS, ys = (cs - PX) * RS, os = cs * RS;
+    const size_t V = (size_t)a.nx * a.ny * a.nz;
+    const size_t nxy = (size_t)a.nx * a.ny;
+    const int nst = a.ntx + a.nty - 1;
+    const int ntxf = a.ntx > 1 ? a.ntx - 1 : 0, ntyf = a.nty > 1 ? a.nty - 1 : 0;
+    const size_t xslab = (size_t)a.ny * a.nz * ABP, yslab = (size_t)a.nx * a.nz * ABP;
+    int ntasks = 0;
+    for (int s = 0; s < nst; ++s) ntasks += flow_stage_tiles(s, a.ntx, a.nty) * 8 * a.gcount;
+    float4* const myland_x = landx + lj * (ABP / 4);
+    float4* const myland_y = landy + li * (ABP / 4);
+    const float qnan = __int_as_float(0x7fffffff);
+
+    float sn[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) sn[m] = 0.0f;
+    float sig_n = 0.0f;
+    float zc[AB];
+    float lk = 0.0f;
+
+    for (;;) {
+        __syncthreads();                        // previous task done with task_s and the planes
+        if (threadIdx.x == 0) *task_s = atomicAdd(a.flow + 0, 1);
+        __syncthreads();
+        const int t = *task_s;
+        if (t >= ntasks) break;
+        // task t: stage, then tile fastest, octant, group
+        int s = 0, r = t, ntiles = 1;
+        for (; s < nst; ++s) {
+            ntiles = flow_stage_tiles(s, a.ntx, a.nty);
+            if (r < ntiles * 8 * a.gcount) break;
+            r -= ntiles * 8 * a.gcount;
+        }
+        const int ti = r % ntiles;
+        r /= ntiles;
+        const int o = r & 7, gi = r >> 3;
+        const int g = a.g0 + gi;
+        const int at = max(0, s - (a.nty - 1)) + ti, bt = s - at;
+        const int sx = (o & 1) ? -1 : 1, sy = (o & 2) ? -1 : 1, sz = (o & 4) ? -1 : 1;
+        const int oe = a.reverse ? (o ^ 7) : o;     // octant of the directions
+        const float fx = (oe & 1) ? -1.0f : 1.0f, fy = (oe & 2) ? -1.0f : 1.0f, fz = (oe & 4) ? -1.0f : 1.0f;
+        const int nb = oe * a.A8;
+        const int ir = at * a.tx + li, jr = bt * a.ty + lj;
+        const bool col = ir < a.nx && jr < a.ny;
+        const int i = sx > 0 ? ir : a.nx - 1 - ir;
+        const int j = sy > 0 ? jr : a.ny - 1 - jr;
+        const size_t vcol = (size_t)j * a.nx + i;
+        const size_t gV = (size_t)g * V;
+        const bool xout = li == a.tx - 1 && at < a.ntx - 1;
+        const bool yout = lj == a.ty - 1 && bt < a.nty - 1;
+        const bool xleak = ir == a.nx - 1, yleak = jr == a.ny - 1;
+        const size_t og = (size_t)o * a.G + g;
+        float* const xo = a.xface + (og * ntxf + at) * xslab + (size_t)jr * a.nz * ABP;
+        float* const yo = a.yface + (og * ntyf + bt) * yslab + (size_t)ir * a.nz * ABP;
+        // incoming records (null on the mesh boundary: zero inflow)
+        float* const xi = (li == 0 && at > 0) ? a.xface + (og * ntxf + at - 1) * xslab + (size_t)jr * a.nz * ABP : nullptr;
+        float* const yi = (lj == 0 && bt > 0) ? a.yface + (og * ntyf + bt - 1) * yslab + (size_t)ir * a.nz * ABP : nullptr;
+        const bool xedge = col && li == 0, yedge = col && lj == 0;
+
+        auto prefetch = [&](int kn) {
+            const int k = sz > 0 ? kn : a.nz - 1 - kn;
+            const size_t v = (size_t)k * nxy + vcol;
+            load_moments<M>(a.src + (gV + v) * M, sn);
+            sig_n = __ldg(a.rho + v) * sigt_s[gi * a.nmat + __ldg(a.mat + v)];
+        };
+        if (col) prefetch(0);
+#pragma unroll
+        for (int q = 0; q < AB; ++q) zc[q] = 0.0f;
+
+        // step h = -1 only fetches the first halo of column (0, 0)
+        const int hend = a.nz + a.tx + a.ty - 2;
+        for (int h = -1; h < hend; ++h) {
+            const int cb = h & 1, pb = cb ^ 1;
+            const int kr = h - d;
+            const bool act = col && kr >= 0 && kr < a.nz;
+            // plane whose incoming faces this thread needs next step
+            const int kf = (h + 1 == d) ? 0 : (act && kr + 1 < a.nz ? kr + 1 : -1);
+            if (kf >= 0) {
+                float* hb = buf + cb * P * RS;
+                if (xedge) {
+                    if (xi) {
+#pragma unroll
+                        for (int c4 = 0; c4 < ABP / 4; ++c4) cp_async_cg16(myland_x + c4, xi + (size_t)kf * ABP + 4 * c4);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < AB; ++q) hb[xs + q] = 0.0f;
+                    }
+                }
+                if (yedge) {
+                    if (yi) {
+#pragma unroll
+                        for (int c4 = 0; c4 < ABP / 4; ++c4) cp_async_cg16(myland_y + c4, yi + (size_t)kf * ABP + 4 * c4);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < AB; ++q) hb[ys + q] = 0.0f;
+                    }
+                }
+            }
+            if (act) {
+                const bool last = kr == a.nz - 1;
+#pragma unroll
+                for (int m = 0; m < M; ++m) sn[m] *= octant_sign<M>(m, fx, fy, fz);
+                const float sig = sig_n;
+                const int k = sz > 0 ? kr : a.nz - 1 - kr;
+                const size_t v = (size_t)k * nxy + vcol;
+                const size_t mo = (gV + v) * M;
+                float s[M];
+#pragma unroll
+                for (int m = 0; m < M; ++m) s[m] = sn[m];
+                if (!last) prefetch(kr + 1);
+                constexpr int rb = chain_row_base(AB) * 16;
+                // moments -> directions
+                float psi[AB];
+#pragma unroll
+                for (int q = 0; q < AB; ++q) {
+                    float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f, t3 = 0.0f;
+#pragma unroll
+                    for (int m = 0; m < M; m += 4) {
+                        t0 = fmaf(c_Mop1[rb + q * 16 + lm_of_pos(m, M)], s[m], t0);
+                        if (m + 1 < M) t1 = fmaf(c_Mop1[rb + q * 16 + lm_of_pos(m + 1, M)], s[m + 1], t1);
+                        if (m + 2 < M) t2 = fmaf(c_Mop1[rb + q * 16 + lm_of_pos(m + 2, M)], s[m + 2], t2);
+                        if (m + 3 < M) t3 = fmaf(c_Mop1[rb + q * 16 + lm_of_pos(m + 3, M)], s[m + 3], t3);
+                    }
+                    psi[q] = (t0 + t1) + (t2 + t3);
+                }
+                // step-differenced cell solve
+                const float* pv = buf + pb * P * RS;
+                float* cv = buf + cb * P * RS;
+#pragma unroll
+                for (int q = 0; q < AB; ++q) {
+                    const float px = pv[xs + q];
+                    const float py = pv[ys + q];
+                    const float num = fmaf(dt.cz[q], zc[q], fmaf(dt.cy[q], py, fmaf(dt.cx[q], px, psi[q])));
+                    psi[q] = __fdividef(num, sig + dt.csum[q]);
+                    cv[os + q] = psi[q];
+                    zc[q] = psi[q];
+                }
+                if constexpr (MODE == 1) {
+#pragma unroll
+                    for (int q = 0; q < AB; ++q) a.psi[((size_t)g * a.A + nb + q) * V + v] = psi[q];
+                }
+                if constexpr (MODE == 2) {
+                    float pacc = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < AB; ++q)
+                        pacc = fmaf(dt.w[q] * psi[q], __ldg(a.psi + ((size_t)g * a.A + nb + q) * V + v), pacc);
+                    atomicAdd(a.prod + gV + v, pacc);
+                }
+                // outgoing face records of plane kr
+                if (xout || yout) {
+                    float4 rec[ABP / 4];
+#pragma unroll
+                    for (int c4 = 0; c4 < ABP / 4; ++c4)
+                        rec[c4] = make_float4(4 * c4 < AB ? psi[4 * c4 < AB ? 4 * c4 : 0] : 0.0f,
+                                              4 * c4 + 1 < AB ? psi[4 * c4 + 1 < AB ? 4 * c4 + 1 : 0] : 0.0f,
+                                              4 * c4 + 2 < AB ? psi[4 * c4 + 2 < AB ? 4 * c4 + 2 : 0] : 0.0f,
+                                              4 * c4 + 3 < AB ? psi[4 * c4 + 3 < AB ? 4 * c4 + 3 : 0] : 0.0f);
+                    if (xout) {
+                        float4* dst = reinterpret_cast<float4*>(xo + (size_t)kr * ABP);
+#pragma unroll
+                        for (int c4 = 0; c4 < ABP / 4; ++c4) dst[c4] = rec[c4];
+                    }
+                    if (yout) {
+                        float4* dst = reinterpret_cast<float4*>(yo + (size_t)kr * ABP);
+#pragma unroll
+                        for (int c4 = 0; c4 < ABP / 4; ++c4) dst[c4] = rec[c4];
+                    }
+                }
+                if (xleak || yleak || last) {
+#pragma unroll
+                    for (int q = 0; q < AB; ++q) {
+                        float f = 0.0f;
+                        if (xleak) f += dt.lx[q];
+                        if (yleak) f += dt.ly[q];
+                        if (last) f += dt.lz[q];
+                        lk = fmaf(f, psi[q], lk);
+                    }
+                }
+                // directions -> moments (Eq. 3 for lm = 00): table rows hold w R_lm
+                float acc[M];
+#pragma unroll
+                for (int m = 0; m < M; ++m) acc[m] = 0.0f;
+#pragma unroll
+                for (int q = 0; q < AB; ++q) {
+#pragma unroll
+                    for (int m = 0; m < M; ++m) acc[m] = fmaf(c_Dop1[rb + q * 16 + lm_of_pos(m, M)], psi[q], acc[m]);
+                }
+#pragma unroll
+                for (int m = 0; m < M; ++m) acc[m] *= octant_sign<M>(m, fx, fy, fz);
+                add_moments<M>(a.mom + mo, acc);
+                if (last && lk != 0.0f) {
+                    atomicAdd(leak_s + gi, (double)lk);
+                    lk = 0.0f;
+                }
+            }
+            // incoming records of plane kf: wait until the producer has
+            // written every flux (no NaN left), move them into the halo and
+            // hand the records back to the next sweep as NaN
+            if (kf >= 0 && ((xedge && xi) || (yedge && yi))) {
+                cp_async_wait_all();
+                float* hb = buf + cb * P * RS;
+                for (int side = 0; side < 2; ++side) {
+                    float* src = side == 0 ? (xedge ? xi : nullptr) : (yedge ? yi : nullptr);
+                    if (!src) continue;
+                    float4* land = side == 0 ? myland_x : myland_y;
+                    const float* lf = reinterpret_cast<const float*>(land);
+                    src += (size_t)kf * ABP;
+                    bool ok = false;
+                    for (int it = 0; it < kFlowSpinLimit; ++it) {
+                        ok = true;
+#pragma unroll
+                        for (int q = 0; q < AB; ++q) ok = ok && !isnan(lf[q]);
+                        if (ok) break;
+                        __nanosleep(100);
+#pragma unroll
+                        for (int c4 = 0; c4 < ABP / 4; ++c4) cp_async_cg16(land + c4, src + 4 * c4);
+                        cp_async_wait_all();
+                    }
+                    if (!ok) atomicExch(a.flow + 2, 1);
+                    const int hs = side == 0 ? xs : ys;
+#pragma unroll
+                    for (int q = 0; q < AB; ++q) hb[hs + q] = ok ? lf[q] : 0.0f;
+                    float4* back = reinterpret_cast<float4*>(src);
+#pragma unroll
+                    for (int c4 = 0; c4 < ABP / 4; ++c4) back[c4] = make_float4(qnan, qnan, qnan, qnan);
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int e = threadIdx.x; e < a.gcount; e += blockDim.x)
+        if (leak_s[e] != 0.0) atomicAdd(a.leak + a.g0 + e, leak_s[e]);
+    // the last CTA out resets the queue for the next sweep
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(a.flow + 1, 1) == (int)gridDim.x - 1) {
+            a.flow[0] = 0;
+            a.flow[1] = 0;
+        }
+    }
+}
+
+template <int M>
+int sweep_flow_blocks_per_sm(int ab, int threads, size_t smem) {
+    int b = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    auto query = [&](auto kern) {
+        e = smem > 48 * 1024 ? cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                             : cudaSuccess;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, smem);
+    };
+    switch (ab) {
+        case 1: query(k_sweep_flow<1, M, 0>); break;
+        case 3: query(k_sweep_flow<3, M, 0>); break;
+        case 6: query(k_sweep_flow<6, M, 0>); break;
+        case 10: query(k_sweep_flow<10, M, 0>); break;
+        default: break;
+    }
+    return e == cudaSuccess ? b : 0;
+}
+
+template <int M, int MODE>
+cudaError_t launch_sweep_flow_m(const SweepArgs& a, cudaStream_t s) {
+    if (a.gcount <= 0) return cudaSuccess;
+    if (a.dir_table == nullptr || a.flow == nullptr || a.nab != 1) return cudaErrorInvalidValue;
+    int ntasks = 0;
+    for (int st = 0; st < a.ntx + a.nty - 1; ++st) {
+        const int lo = st - (a.nty - 1) > 0 ? st - (a.nty - 1) : 0;
+        const int hi = st < a.ntx - 1 ? st : a.ntx - 1;
+        ntasks += (hi - lo + 1) * 8 * a.gcount;
+    }
+    const int grid = ntasks < a.chain_slots ? ntasks : a.chain_slots;
+    const int T = a.tx * a.ty;
+    const size_t smem = sweep_flow_smem_bytes(a.ab, a.tx, a.ty, a.gcount, a.nmat);
+    cudaError_t e = cudaSuccess;
+    auto launch = [&](auto kern) {
+        if (smem > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) kern<<<grid, T, smem, s>>>(a, *a.dir_table);
+    };
+    switch (a.ab) {
+        case 1: launch(k_sweep_flow<1, M, MODE>); break;
+        case 3: launch(k_sweep_flow<3, M, MODE>); break;
+        case 6: launch(k_sweep_flow<6, M, MODE>); break;
+        case 10: launch(k_sweep_flow<10, M, MODE>); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+}  // namespace doctors

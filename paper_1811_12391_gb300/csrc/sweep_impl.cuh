@@ -51,16 +51,19 @@ __device__ __forceinline__ void load_moments(const float* p, float (&s)[M]) {
     }
 }
 
+// moments added with reductions that return nothing (red, not atom): the
+// thread never waits for them
 template <int M>
 __device__ __forceinline__ void add_moments(float* p, const float (&a)[M]) {
     if constexpr (M % 4 == 0) {
-        float4* p4 = reinterpret_cast<float4*>(p);
 #pragma unroll
         for (int q = 0; q < M / 4; ++q)
-            atomicAdd(p4 + q, make_float4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]));
+            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(p + 4 * q), "f"(a[4 * q]),
+                         "f"(a[4 * q + 1]), "f"(a[4 * q + 2]), "f"(a[4 * q + 3])
+                         : "memory");
     } else {
 #pragma unroll
-        for (int q = 0; q < M; ++q) atomicAdd(p + q, a[q]);
+        for (int q = 0; q < M; ++q) asm volatile("red.global.add.f32 [%0], %1;\n" ::"l"(p + q), "f"(a[q]) : "memory");
     }
 }
 

@@ -1,6 +1,7 @@
 // Instantiations of the octant wavefront sweep for 4 flux moment(s) per cell:
-// the tile-stage kernel (k_sweep) and the chained kernel (k_sweep_chain).
-#include "sweep_chain.cuh"
+// the tile-stage kernel (k_sweep), the chained kernel (k_sweep_chain) and
+// the dataflow kernel (k_sweep_flow).
+#include "sweep_flow.cuh"
 
 namespace doctors {
 cudaError_t launch_sweep_m4_entry(const SweepArgs& a, int mode, cudaStream_t s) {
@@ -19,6 +20,15 @@ cudaError_t launch_sweep_m4_entry(const SweepArgs& a, int mode, cudaStream_t s) 
         default: return cudaErrorInvalidValue;
     }
 }
+cudaError_t launch_sweep_flow_m4_entry(const SweepArgs& a, int mode, cudaStream_t s) {
+    switch (mode) {
+        case 0: return launch_sweep_flow_m<4, 0>(a, s);
+        case 1: return launch_sweep_flow_m<4, 1>(a, s);
+        case 2: return launch_sweep_flow_m<4, 2>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+int sweep_flow_blocks_m4(int ab, int threads, size_t smem) { return sweep_flow_blocks_per_sm<4>(ab, threads, smem); }
 int sweep_chain_blocks_m4(int ab, bool ct, int threads, size_t smem) { return sweep_chain_blocks_per_sm<4>(ab, ct, threads, smem); }
 cudaError_t upload_tables_m4(const float* R, const float* w) {
     cudaError_t e = upload_direction_tables(R, w);
