@@ -48,6 +48,7 @@ SWEEP_TRAFFIC = {
     (16, 16, 5, 1): (1687.6e6, "sweep_impl.cuh", "592eff4d10129e1bde8b55aecdf9fbf52f768e8c"),
     (16, 16, 10, 2): (2121.9e6, "sweep_tc.cu", "79ec5703826b205c1bdc9d4f7ff57c205fec428a"),
     (16, 8, 10, 3): (2534.9e6, "sweep_chain.cuh", "3502773d12d37fb58b50dbc1187553785b1df685"),
+    (8, 8, 10, 4): (2975.9e6, "sweep_flow.cuh", "8c584040bcbd9a4f099aabcdc4d03555e0c21724"),
 }
 
 # sweep kernel by the library's sweep_kernel code
@@ -341,7 +342,7 @@ def main():
                    "directions": p.n_angles, "groups": p.G, "moments": M,
                    "sweeps_per_step": sweeps / args.steps, "l2": "inputs larger than L2 (4 x 160 MB moment arrays)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "roofline": {"bound": "alu", "kernel": f"{SWEEP_KERNELS.get(tuning['sweep_kernel'], '?')} (the stage launches of one sweep)",
+        "roofline": {"bound": "alu", "kernel": f"{SWEEP_KERNELS.get(tuning['sweep_kernel'], '?')} (the launches of one sweep)",
                      "achieved": achieved_tflops, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": achieved_tflops / alu_peak,
                      "peak_kind": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_mhz:.0f} MHz",

@@ -83,9 +83,11 @@ typedef struct doctors_options {
     double tol;              /* stop when, in every group, ||phi00_new - phi00_old||_2 / ||phi00_new||_2 < tol;
                                 values below 1e-6 are raised to 1e-6 (FP32 sweep) */
     int max_iters;           /* source-iteration cap, >= 1 */
-    int tile_x, tile_y;      /* sweep tile in voxels (0 = default 16 x 16); tile_x*tile_y <= 256 */
+    int tile_x, tile_y;      /* sweep tile in voxels (0 = default: 8 x 8 for the dataflow sweep, else
+                                16 x 16); tile_x*tile_y <= 256 */
     int angles_per_block;    /* directions per sweep block (0 = default); must divide N(N+2)/8 */
-    int sweep_kernel;        /* 0 = default (the chained CUDA-core sweep, the fastest measured),
+    int sweep_kernel;        /* 0 = default (the fastest measured: dataflow where it applies, else
+                                chained),
                                 1 = CUDA-core transforms, one task (tile, octant, direction block,
                                 group) per CTA, 2 = tensor-core (3xTF32 mma) moment transforms
                                 (P3 only), 3 = CUDA-core transforms, each CTA running a chain of
@@ -212,6 +214,14 @@ int doctors_dose_noalloc(doctors_problem *p, const double *k, double *dose);
  * `info` (may be NULL) reports the adjoint iteration. */
 int doctors_adjoint_solve(doctors_problem *p, const double *response, int mem, double *d_weights,
                           double *d_spectrum, double *d_density, doctors_result *info);
+
+/* Test hook for the dataflow sweep's bounded waits (sweep_kernel 4): from the
+ * next sweep on, the sweep task numbered `task` (stage-major order) does not
+ * write the face fluxes it owes its downstream tiles, so their waits run out;
+ * the solve then returns DOCTORS_ERR_TIMEOUT and resets the sweep's queue and
+ * face buffers.  task < 0 clears the hook.  DOCTORS_ERR_STATE if the problem's
+ * sweep is not the dataflow kernel.  The paper has no counterpart. */
+int doctors_debug_withhold_faces(doctors_problem *p, int task);
 
 /* Test hook: the voxel index list and segment lengths of the ray from
  * source `src` to the centre of voxel `voxel`, as walked by the ray-trace

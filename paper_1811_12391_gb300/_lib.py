@@ -92,6 +92,7 @@ SIGNATURES = [
     ("doctors_dose", _int, [_vp, _P(ctypes.c_double), _vp, _int]),
     ("doctors_dose_noalloc", _int, [_vp, _P(ctypes.c_double), _vp]),
     ("doctors_adjoint_solve", _int, [_vp, _vp, _int, _vp, _vp, _vp, _P(doctors_result)]),
+    ("doctors_debug_withhold_faces", _int, [_vp, _int]),
     ("doctors_debug_ray_indices", _int, [_vp, _int, _int, _P(ctypes.c_int32), _P(ctypes.c_float), _int,
                                          _P(_int)]),
     ("doctors_quadrature", _int, [_int, _int, _P(ctypes.c_double), _P(ctypes.c_double),
@@ -155,6 +156,7 @@ doctors_dose = _fwd("doctors_dose")
 doctors_dose_noalloc = _fwd("doctors_dose_noalloc")
 doctors_adjoint_solve = _fwd("doctors_adjoint_solve")
 doctors_debug_ray_indices = _fwd("doctors_debug_ray_indices")
+doctors_debug_withhold_faces = _fwd("doctors_debug_withhold_faces")
 doctors_quadrature = _fwd("doctors_quadrature")
 doctors_solve_batch = _fwd("doctors_solve_batch")
 doctors_autotune = _fwd("doctors_autotune")

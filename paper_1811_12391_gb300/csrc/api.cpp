@@ -50,7 +50,7 @@ namespace {
 // default choice of the moment-transform path of the sweep for P3 problems
 constexpr bool kDefaultTensorCoreSweep = false;
 constexpr bool kDefaultChainedSweep = true;
-constexpr bool kDefaultDataflowSweep = false;
+constexpr bool kDefaultDataflowSweep = true;
 
 int dalloc(void** p, size_t bytes, const char* what) {
     if (bytes == 0) bytes = 16;
@@ -228,7 +228,7 @@ int check_flow(doctors_problem* p) {
     CU(cudaMemcpyAsync(h, p->d_flow, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
     CU(cudaStreamSynchronize(p->stream));
     if (h[2] == 0) return DOCTORS_OK;
-    CU(cudaMemsetAsync(p->d_flow, 0, 4 * sizeof(int), p->stream));
+    CU(cudaMemsetAsync(p->d_flow, 0, 3 * sizeof(int), p->stream));
     CU(cudaMemsetAsync(p->d_xface, 0xff, p->xface_bytes, p->stream));
     CU(cudaMemsetAsync(p->d_yface, 0xff, p->yface_bytes, p->stream));
     CU(cudaStreamSynchronize(p->stream));
@@ -638,9 +638,15 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     p->A = (int)w.size(); p->A8 = p->A / 8;
     p->dirs = dirs; p->w = w;
     p->stream = (cudaStream_t)cuda_stream;
-    p->tx = opt->tile_x > 0 ? opt->tile_x : std::min(16, p->nx);
-    p->ty = opt->tile_y > 0 ? opt->tile_y : std::min(16, p->ny);
     p->ab = opt->angles_per_block > 0 ? opt->angles_per_block : default_ab(p->A8);
+    // default tile: 8 x 8 for the dataflow sweep (whole octants of S2..S8),
+    // 16 x 16 for the stage kernels (the fastest measured shapes)
+    const bool flow_default = opt->sweep_kernel == 4 ||
+                              (opt->sweep_kernel == 0 && kDefaultDataflowSweep && p->A8 == p->ab &&
+                               chain_const_table_ab(p->ab));
+    const int tdef = flow_default ? 8 : 16;
+    p->tx = opt->tile_x > 0 ? opt->tile_x : std::min(tdef, p->nx);
+    p->ty = opt->tile_y > 0 ? opt->tile_y : std::min(tdef, p->ny);
     auto fail = [&](int code, const std::string& msg) {
         if (!msg.empty()) set_error(msg);
         free_problem(p);
@@ -934,6 +940,19 @@ int doctors_dose(doctors_problem* p, const double* k, double* dose, int mem) {
         set_error(std::string("dose: ") + cudaGetErrorString(e));
         return DOCTORS_ERR_CUDA;
     }
+    return DOCTORS_OK;
+}
+
+int doctors_debug_withhold_faces(doctors_problem* p, int task) {
+    int rc = check_problem(p);
+    if (rc) return rc;
+    if (!p->use_flow || !p->d_flow) {
+        set_error("the problem's sweep is not the dataflow kernel");
+        return DOCTORS_ERR_STATE;
+    }
+    const int v = task < 0 ? 0 : task + 1;
+    CU(cudaMemcpyAsync(p->d_flow + 3, &v, sizeof(int), cudaMemcpyHostToDevice, p->stream));
+    CU(cudaStreamSynchronize(p->stream));
     return DOCTORS_OK;
 }
 

@@ -181,7 +181,8 @@ struct SweepArgs {
     const int* skip;                   // if non-null and *skip != 0 the kernel does nothing
     int chain_slots;                   // > 0: chained kernel, at most this many CTAs per stage launch
     const struct ChainDirTable* dir_table;   // host copy of the first-octant direction table (chained kernel)
-    int* flow;                         // non-null: dataflow kernel; [0] task queue, [1] CTAs done, [2] wait timed out
+    int* flow;                         // non-null: dataflow kernel; [0] task queue, [1] CTAs done, [2] wait timed out,
+                                       // [3] test hook: task + 1 that writes no faces (0: none)
 };
 
 // Per-problem direction data of the first octant for the chained sweep,

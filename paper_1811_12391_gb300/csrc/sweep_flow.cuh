@@ -18,8 +18,9 @@
 // waits only on tasks with smaller numbers, which are held by running CTAs
 // (a task is taken only by a running CTA) and themselves wait only on smaller
 // numbers.  A wait that exceeds kFlowSpinLimit polls records the failure in
-// the problem's flag word, uses zero fluxes and goes on; the host turns the
-// flag into DOCTORS_ERR_TIMEOUT and resets the buffers.
+// the problem's flag word, uses zero fluxes and goes on (later waits of the
+// sweep then give up at once); the host turns the flag into
+// DOCTORS_ERR_TIMEOUT and resets the buffers.
 #pragma once
 
 #include "sweep_chain.cuh"
@@ -107,6 +108,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
         __syncthreads();
         const int t = *task_s;
         if (t >= ntasks) break;
+        const bool withhold = a.flow[3] == t + 1;   // test hook: this task owes no faces
         // task t: stage, then tile fastest, octant, group
         int s = 0, r = t, ntiles = 1;
         for (; s < nst; ++s) {
@@ -129,8 +131,8 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
         const int j = sy > 0 ? jr : a.ny - 1 - jr;
         const size_t vcol = (size_t)j * a.nx + i;
         const size_t gV = (size_t)g * V;
-        const bool xout = li == a.tx - 1 && at < a.ntx - 1;
-        const bool yout = lj == a.ty - 1 && bt < a.nty - 1;
+        const bool xout = li == a.tx - 1 && at < a.ntx - 1 && !withhold;
+        const bool yout = lj == a.ty - 1 && bt < a.nty - 1 && !withhold;
         const bool xleak = ir == a.nx - 1, yleak = jr == a.ny - 1;
         const size_t og = (size_t)o * a.G + g;
         float* const xo = a.xface + (og * ntxf + at) * xslab + (size_t)jr * a.nz * ABP;
@@ -294,6 +296,8 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
 #pragma unroll
                         for (int q = 0; q < AB; ++q) ok = ok && !isnan(lf[q]);
                         if (ok) break;
+                        // once any wait of this sweep has given up, give up at once
+                        if ((it & 63) == 63 && *reinterpret_cast<volatile int*>(a.flow + 2)) break;
                         __nanosleep(100);
 #pragma unroll
                         for (int c4 = 0; c4 < ABP / 4; ++c4) cp_async_cg16(land + c4, src + 4 * c4);

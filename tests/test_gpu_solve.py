@@ -191,6 +191,40 @@ def test_iteration_cap_reports_not_converged(dp):
         d.close()
 
 
+def test_dataflow_wait_times_out_and_recovers(dp):
+    """The dataflow sweep's waits are bounded: with one task withholding the
+    faces it owes (test hook), the downstream waits give up, the solve
+    returns DOCTORS_ERR_TIMEOUT, and after the hook is cleared the same
+    problem solves to the oracle again."""
+    import time
+    from paper_1811_12391_gb300 import _lib as C
+    p = ph.tiny_cube(n=8)
+    ref = osv.solve(p, tol=1e-11)
+    d = dp(p, tol=1e-6, max_iters=3, tile=(4, 4), sweep_kernel=4, angles_per_block=3)
+    C.check(C.doctors_debug_withhold_faces(d.h, 0))
+    t0 = time.time()
+    with pytest.raises(C.DoctorsError) as e:
+        d.solve(allow_not_converged=True)
+    assert e.value.code == C.DOCTORS_ERR_TIMEOUT
+    assert time.time() - t0 < 30.0
+    C.check(C.doctors_debug_withhold_faces(d.h, -1))
+    d.close()
+    d = dp(p, tol=1e-6, max_iters=300, tile=(4, 4), sweep_kernel=4, angles_per_block=3)
+    C.check(C.doctors_debug_withhold_faces(d.h, 5))
+    with pytest.raises(C.DoctorsError):
+        d.solve(allow_not_converged=True)
+    C.check(C.doctors_debug_withhold_faces(d.h, -1))
+    r = d.solve()
+    assert r["converged"] == 1
+    assert max_rel(d.fluence_host(2), ref.phi) <= REL_TOL
+    d.close()
+    q = dp(p, tol=1e-6, max_iters=10, sweep_kernel=3, angles_per_block=3)
+    with pytest.raises(C.DoctorsError) as e:
+        C.check(C.doctors_debug_withhold_faces(q.h, 0))
+    assert e.value.code == C.DOCTORS_ERR_STATE
+    q.close()
+
+
 def test_water_cylinder_full_size_properties(dp):
     """The 64x64x32 S8 P3 19-group cylinder at full size: converged,
     particle balance, and mirror symmetry in x and z of the collided and
