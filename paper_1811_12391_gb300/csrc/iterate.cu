@@ -150,7 +150,7 @@ size_t scatter_table_bytes(const ScatterArgs& a) {
 }
 
 template <int GMAX>
-__global__ void __launch_bounds__(kScatterThreads, 4) k_scatter(const ScatterArgs a, int table_in_smem) {
+__global__ void __launch_bounds__(kScatterThreads, 3) k_scatter(const ScatterArgs a, int table_in_smem) {
     extern __shared__ float tab_s[];
     if (a.skip && *a.skip) return;
     const int G = a.G;
@@ -183,12 +183,16 @@ __global__ void __launch_bounds__(kScatterThreads, 4) k_scatter(const ScatterArg
                 ph[gp] = need ? __ldg(a.phi + gp * VM + t) : 0.0f;
             }
         }
+        // the fixed source of every destination group, also loaded up front
+        float qb[GMAX];
+#pragma unroll
+        for (int g = 0; g < GMAX; ++g) qb[g] = (a.base && g >= g_beg && g < g_end) ? __ldg(a.base + g * VM + t) : 0.0f;
         const float* ts = tab_s + (size_t)mb * scatter_block_pitch<GMAX>();
         const float* tg = a.sigs + (size_t)mb * G * G;
 #pragma unroll
         for (int g = 0; g < GMAX; ++g) {
             if (g < g_beg || g >= g_end) continue;
-            float out = a.base ? __ldg(a.base + g * VM + t) : 0.0f;
+            float out = qb[g];
             if (lm == 0) {
                 if (a.iso) out += __ldg(a.iso + g);
                 if (a.iso_field) out += a.iso_field_scale * __ldg(a.iso_field + (size_t)g * a.V + v);
@@ -357,6 +361,7 @@ cudaError_t launch_scatter_g(const ScatterArgs& a, cudaStream_t s) {
 cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s) {
     if (a.G <= 8) return launch_scatter_g<8>(a, s);
     if (a.G <= 16) return launch_scatter_g<16>(a, s);
+    if (a.G <= 20) return launch_scatter_g<20>(a, s);
     if (a.G <= 24) return launch_scatter_g<24>(a, s);
     if (a.G <= 32) return launch_scatter_g<32>(a, s);
     if (a.G <= 64) return launch_scatter_g<64>(a, s);
