@@ -256,13 +256,15 @@ __global__ void __launch_bounds__(256, 2)
     float sn[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) sn[m] = 0.0f;
-    float sig_n = 0.0f;
+    float rho_n = 0.0f;       // density and material of the prefetched cell: the cross
+    int mat_n = 0;            // section is looked up when the cell is swept, not at the load
     auto prefetch = [&](int kn) {
         if (col) {
             const int k = sz > 0 ? kn : a.nz - 1 - kn;
             const size_t v = (size_t)k * nxy + vcol;
             load_moments<M>(a.src + (gV + v) * M, sn);
-            sig_n = __ldg(a.rho + v) * sigt_s[gi * a.nmat + __ldg(a.mat + v)];
+            rho_n = __ldg(a.rho + v);
+            mat_n = __ldg(a.mat + v);
         }
     };
 
@@ -291,7 +293,7 @@ __global__ void __launch_bounds__(256, 2)
                 for (int m = 0; m < M; ++m)
                     s[m] = CT ? sn[m] * octant_sign<M>(m, fx, fy, fz)
                               : sn[m] * ((2 * degree_of_lm(lm_of_pos(m, M)) + 1) * 0.07957747154594767f);
-                const float sig = sig_n;
+                const float sig = rho_n * sigt_s[gi * a.nmat + mat_n];
                 const int k = sz > 0 ? kr : a.nz - 1 - kr;
                 const size_t v = (size_t)k * nxy + vcol;
                 const size_t mo = (gV + v) * M;

@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
     float sn[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) sn[m] = 0.0f;
-    float sig_n = 0.0f;
+    float rho_n = 0.0f;       // density and material of the prefetched cell: the cross
+    int mat_n = 0;            // section is looked up when the cell is swept, not at the load
     float zc[AB];
     float lk = 0.0f;
 
@@ -146,7 +147,8 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
             const int k = sz > 0 ? kn : a.nz - 1 - kn;
             const size_t v = (size_t)k * nxy + vcol;
             load_moments<M>(a.src + (gV + v) * M, sn);
-            sig_n = __ldg(a.rho + v) * sigt_s[gi * a.nmat + __ldg(a.mat + v)];
+            rho_n = __ldg(a.rho + v);
+            mat_n = __ldg(a.mat + v);
         };
         if (col) prefetch(0);
 #pragma unroll
@@ -185,7 +187,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
                 const bool last = kr == a.nz - 1;
 #pragma unroll
                 for (int m = 0; m < M; ++m) sn[m] *= octant_sign<M>(m, fx, fy, fz);
-                const float sig = sig_n;
+                const float sig = rho_n * sigt_s[gi * a.nmat + mat_n];
                 const int k = sz > 0 ? kr : a.nz - 1 - kr;
                 const size_t v = (size_t)k * nxy + vcol;
                 const size_t mo = (gV + v) * M;

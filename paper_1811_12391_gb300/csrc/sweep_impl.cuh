@@ -191,13 +191,15 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs a) {
     // software pipeline: the source moments and material of the next cell
     // are loaded one hyperplane step ahead
     float sn[M];
-    float sig_n = 0.0f;
+    float rho_n = 0.0f;       // density and material of the prefetched cell: the cross
+    int mat_n = 0;            // section is looked up when the cell is swept, not at the load
     auto prefetch = [&](int kr) {
         if (col && kr >= 0 && kr < a.nz) {
             const int k = sz > 0 ? kr : a.nz - 1 - kr;
             const size_t v = (size_t)k * plane + vcol;
             load_moments<M>(a.src + (gV + v) * M, sn);
-            sig_n = __ldg(a.rho + v) * sigt_s[__ldg(a.mat + v)];
+            rho_n = __ldg(a.rho + v);
+            mat_n = __ldg(a.mat + v);
         }
     };
     prefetch(0);      // first cell of this column
@@ -213,7 +215,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs a) {
 #pragma unroll
             for (int m = 0; m < M; ++m)
                 s[m] = sn[m] * ((2 * degree_of_lm(lm_of_pos(m, M)) + 1) * 0.07957747154594767f);
-            const float sig = sig_n;
+            const float sig = rho_n * sigt_s[mat_n];
             prefetch(kr + 1);
             const int k = sz > 0 ? kr : a.nz - 1 - kr;
             const size_t v = (size_t)k * plane + vcol;
