@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(256, 2)
                                                        dt_at<CT>(dt, 5, q))
                                          : coef_s[tab + q];
                     const float num = fmaf(cq.z, zc[q], fmaf(cq.y, py, fmaf(cq.x, px, psi[q])));
-                    psi[q] = __fdividef(num, sig + cq.w);
+                    psi[q] = num * rcp_approx(sig + cq.w);
                     cv[os + q] = psi[q];
                     zc[q] = psi[q];
                 }

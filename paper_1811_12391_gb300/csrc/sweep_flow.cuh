@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
                     const float px = pv[xs + q];
                     const float py = pv[ys + q];
                     const float num = fmaf(dt.cz[q], zc[q], fmaf(dt.cy[q], py, fmaf(dt.cx[q], px, psi[q])));
-                    psi[q] = __fdividef(num, sig + dt.csum[q]);
+                    psi[q] = num * rcp_approx(sig + dt.csum[q]);
                     cv[os + q] = psi[q];
                     zc[q] = psi[q];
                 }

@@ -36,6 +36,15 @@
 
 namespace doctors {
 
+// 1 / x by the hardware's approximate reciprocal (relative error about one
+// unit in the last place; x here is a positive total cross section plus the
+// step coefficients, far from the denormal and overflow ranges)
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 template <int M>
 __device__ __forceinline__ void load_moments(const float* p, float (&s)[M]) {
     if constexpr (M % 4 == 0) {
