@@ -188,6 +188,65 @@ def bench_batched(torch, DoctorsProblem, ph, stream):
             "converged": all(r["converged"] for r in res)}
 
 
+def bench_configs(torch, DoctorsProblem, ph, stream):
+    """The other full-size workloads, each autotuned and timed on one solve
+    after a warm-up: the S16 abdomen (one cone-beam projection), the 64-view
+    axial scan superposed into one solve, and the differentiable abdomen
+    (S8, 32 views) whose adjoint solve gives the gradients of the liver-ROI
+    mean dose with respect to the view weights, the spectrum and every voxel
+    density."""
+    import numpy as np
+    out = {}
+    for name in ("abdomen", "axial_scan", "differentiable_abdomen"):
+        p = ph.config_problem(name)
+        d = DoctorsProblem(p, stream=stream, tol=1e-6, max_iters=500)
+        tune = d.autotune()
+        d.solve()
+        r = d.solve()
+        rec = {"voxels": p.V, "directions": p.n_angles, "groups": p.G, "sources": len(p.sources),
+               "ms_per_solve": r["ms_total"], "cell_updates_per_s": r["cell_updates"] / (r["ms_total"] / 1e3),
+               "iterations": r["iterations"], "converged": bool(r["converged"]),
+               "schedule": {k: tune[k] for k in ("tile_x", "tile_y", "angles_per_block", "sweep_kernel")}}
+        if name == "differentiable_abdomen":
+            roi = p.roi / p.roi.sum()
+            resp = torch.as_tensor(p.k_dep[p.mat].T * (p.density.astype(np.float64) * roi)[None, :], device="cuda")
+            d.adjoint(resp)
+            g = d.adjoint(resp)
+            rec["adjoint_ms"] = g["result"]["ms_total"]
+            rec["adjoint_iterations"] = g["result"]["iterations"]
+            rec["gradients"] = {"view_weights": int(g["weights"].numel()), "spectrum": int(g["spectrum"].numel()),
+                                "densities": int(g["density"].numel())}
+        d.close()
+        out[name] = rec
+    return out
+
+
+# the paper's GPU runtimes for its water phantom, S6 P0, 7 groups (Table 6;
+# one GK110 die of a GTX Titan Z, the paper's phantom and cross sections):
+# context for the same-shaped synthetic runs, not a target
+PAPER_TABLE6_GPU_S = {"paper_water_coarse_sp": 2.8, "paper_water_coarse_ct": 3.2,
+                      "paper_water_fine_sp": 66.8, "paper_water_fine_ct": 364.4}
+
+
+def bench_paper_workloads(torch, DoctorsProblem, ph, stream):
+    """The paper's own water-phantom runs at its mesh sizes and settings
+    (64x64x16 and 256x256x64, S6 P0, 7 groups; one point source or 16 cone
+    beams), each autotuned and timed on one solve after a warm-up."""
+    out = {}
+    for name, paper_s in PAPER_TABLE6_GPU_S.items():
+        p = ph.config_problem(name)
+        d = DoctorsProblem(p, stream=stream, tol=1e-6, max_iters=500)
+        tune = d.autotune()
+        d.solve()
+        r = d.solve()
+        out[name] = {"voxels": p.V, "directions": p.n_angles, "groups": p.G, "sources": len(p.sources),
+                     "ms_per_solve": r["ms_total"], "cell_updates_per_s": r["cell_updates"] / (r["ms_total"] / 1e3),
+                     "iterations": r["iterations"], "converged": bool(r["converged"]),
+                     "sweep_kernel": tune["sweep_kernel"], "paper_gpu_s_context": paper_s}
+        d.close()
+    return out
+
+
 def run_reference(args, rank, world):
     from synth import phantoms as ph
     if rank != 0:
@@ -223,7 +282,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extra", action="store_true",
-                    help="omit the adjoint and batched-scan measurements (the headline line is unchanged)")
+                    help="omit the adjoint, batched-scan and other-workload measurements (the headline line is unchanged)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -305,6 +364,8 @@ def main():
                        "gradients": "view weights, spectrum, densities"}
         d.close()
         batched = None if (args.no_extra or world > 1) else bench_batched(torch, DoctorsProblem, ph, stream)
+        others = None if (args.no_extra or world > 1) else bench_configs(torch, DoctorsProblem, ph, stream)
+        paper = None if (args.no_extra or world > 1) else bench_paper_workloads(torch, DoctorsProblem, ph, stream)
 
     if world > 1:
         dist.destroy_process_group()
@@ -361,6 +422,8 @@ def main():
         "autotune": tuning,
         "adjoint": adjoint,
         "batched_axial_scan": batched,
+        "other_workloads": others,
+        "paper_workloads": paper,
     }
     print(json.dumps(line), flush=True)
 

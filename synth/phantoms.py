@@ -43,6 +43,10 @@ CONFIG_NAMES = (
     "abdomen",                 # 128x128x48 abdomen, S16 P3, 19 groups
     "axial_scan",              # 64 views on the cylinder + 16 extra cylinders
     "differentiable_abdomen",  # abdomen, S8 P3, 32 views, liver ROI
+    "paper_water_coarse_sp",   # the paper's 64x64x16 water runs, S6 P0, 7 groups: one point source
+    "paper_water_coarse_ct",   # ... 16 cone beams
+    "paper_water_fine_sp",     # the paper's 256x256x64 water runs
+    "paper_water_fine_ct",
 )
 
 
@@ -295,6 +299,45 @@ def abdomen(seed: int = 2, nx: int = 128, ny: int = 128, nz: int = 48, d: float 
     return p
 
 
+# the paper's seven group edges (keV, high to low; Sec. II.D)
+PAPER_EDGES = np.array([100.0, 75.0, 70.0, 60.0, 45.0, 30.0, 20.0, 10.0])
+
+
+def paper_water(seed: int = 6, fine: bool = False, ct: bool = False, sn: int = 6, L: int = 0,
+                sid: float = 54.0) -> Problem:
+    """The paper's water-phantom runs (Sec. II.D, III.D, Table 6): a 35 cm
+    water cylinder in a 50 x 50 x 12.5 cm volume, on the fine 256 x 256 x 64
+    mesh (1.95 mm voxels) or the coarse 64 x 64 x 16 mesh (7.81 mm), seven
+    groups with the paper's edges 10-100 keV, S6 P0.  Single projection: an
+    isotropic point source; CT scan: 16 cone beams with a 30 degree cone angle
+    placed uniformly on the gantry circle.  The source distance is not given
+    in the paper; the sources sit at sid cm from the isocentre."""
+    rng = np.random.default_rng(seed)
+    n, nzz = (256, 64) if fine else (64, 16)
+    d = 50.0 / n
+    e_mid = 0.5 * (PAPER_EDGES[:-1] + PAPER_EDGES[1:])
+    sigt, sigs = _material_tables(e_mid, [0.9, 1.0], rng, L)
+    rho_mat = np.array([0.0012, 1.0]) * (1.0 + 0.05 * rng.uniform(-1.0, 1.0, size=2))
+    origin = _centred_origin(n, n, nzz, d, d, d)
+    V = n * n * nzz
+    name = f"paper_water_{'fine' if fine else 'coarse'}_{'ct' if ct else 'sp'}"
+    p = Problem(name=name, seed=seed, nx=n, ny=n, nz=nzz, dx=d, dy=d, dz=d, origin=origin,
+                mat=np.zeros(V, np.uint8), density=np.zeros(V, np.float32), sigma_t=sigt, sigma_s=sigs,
+                sn=sn, legendre=L, sources=[], k_dep=deposition_weights(sigt, sigs, e_mid),
+                e_mid=e_mid, tol=1e-8)
+    X, Y, _ = p.centres()
+    p.mat[:] = np.where(X * X + Y * Y <= 17.5 ** 2, 1, 0).astype(np.uint8)
+    p.density[:] = rho_mat[p.mat].astype(np.float32)
+    spec = kramers_spectrum(e_mid, rng, kvp=100.0)
+    if ct:
+        z_half = sid * math.tan(math.radians(15.0))
+        p.sources = [_ring_source(2.0 * math.pi * k / 16, sid, spec, 30.0, z_half) for k in range(16)]
+    else:
+        p.sources = [Source(kind=SRC_POINT, pos=np.array([0.0, -sid, 0.0]), axis=np.array([0.0, 1.0, 0.0]),
+                            spectrum=spec, iso_dist=sid)]
+    return p
+
+
 def liver_roi(p: Problem, size_cm: float = 4.0, centre=(-6.0, 0.0, 0.0)) -> np.ndarray:
     """Cubic region of interest (bool [V]) of about size_cm centred at centre."""
     X, Y, Z = p.centres()
@@ -358,6 +401,9 @@ def config_problem(name: str) -> Problem:
     if name == "axial_scan":
         p = water_cylinder()
         return p.with_sources(axial_scan_sources(p, 64), name="axial_scan")
+    if name.startswith("paper_water_"):
+        _, _, mesh, mode = name.split("_")
+        return paper_water(fine=mesh == "fine", ct=mode == "ct")
     if name == "differentiable_abdomen":
         p = abdomen(sn=8, n_views=32)
         p.name = "differentiable_abdomen"

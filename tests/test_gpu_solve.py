@@ -225,6 +225,34 @@ def test_dataflow_wait_times_out_and_recovers(dp):
     q.close()
 
 
+@pytest.mark.parametrize("name", ["paper_water_coarse_sp", "paper_water_coarse_ct"])
+def test_paper_coarse_water_runs(dp, name):
+    """The paper's coarse 64x64x16 water runs (S6 P0, 7 groups; one isotropic
+    point source, or 16 cone beams of 30 degrees) against the FP64 oracle."""
+    p = ph.config_problem(name)
+    sol = osv.solve(p, tol=1e-10)
+    d = dp(p, tol=1e-6, max_iters=500)
+    _compare(d, p, sol, name)
+    d.close()
+
+
+def test_air_dose_zeroing(dp):
+    """Setting the air row of the conversion table to zero (the paper's remedy
+    for ray effects in air, Sec. IV) zeroes the dose in air voxels and leaves
+    every other voxel's dose unchanged."""
+    p = ph.water_cylinder(nx=24, ny=24, nz=8, dx=1.5, dy=1.5, dz=2.0, diameter=30.0, G=4, sn=4, L=1)
+    d = dp(p, tol=1e-6, max_iters=300)
+    d.solve()
+    full = d.dose_host(p.k_dep)
+    k = p.k_dep.copy()
+    k[0] = 0.0                                   # material 0 is air
+    zeroed = d.dose_host(k)
+    air = p.mat == 0
+    assert np.all(zeroed[air] == 0.0) and np.any(full[air] > 0.0)
+    assert np.array_equal(zeroed[~air], full[~air])
+    d.close()
+
+
 def test_water_cylinder_full_size_properties(dp):
     """The 64x64x32 S8 P3 19-group cylinder at full size: converged,
     particle balance, and mirror symmetry in x and z of the collided and
