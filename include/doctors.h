@@ -95,7 +95,12 @@ typedef struct doctors_options {
                                 4 = dataflow: one launch per sweep, CTAs take tasks from a queue and
                                 wait (bounded) on their upstream tiles' face fluxes plane by plane;
                                 needs angles_per_block = N(N+2)/8 and N <= 8.  A wait that gives up
-                                makes the solve return DOCTORS_ERR_TIMEOUT */
+                                makes the solve return DOCTORS_ERR_TIMEOUT,
+                                5 = dataflow with the transforms split out: a pass turns the source
+                                moments into angular sources of all directions, the sweep reads and
+                                writes one angular record per cell, a pass turns the angular fluence
+                                back into moments (same conditions as 4; two more arrays of
+                                G x N(N+2) x V floats, padded) */
     int device_loop;         /* 1 = run the source iteration as one CUDA graph whose while loop is
                                 decided on the device (no host round trip per iteration) */
     int reserved[6];         /* must be zero */
@@ -215,7 +220,7 @@ int doctors_dose_noalloc(doctors_problem *p, const double *k, double *dose);
 int doctors_adjoint_solve(doctors_problem *p, const double *response, int mem, double *d_weights,
                           double *d_spectrum, double *d_density, doctors_result *info);
 
-/* Test hook for the dataflow sweep's bounded waits (sweep_kernel 4): from the
+/* Test hook for the dataflow sweep's bounded waits (sweep_kernel 4 or 5): from the
  * next sweep on, the sweep task numbered `task` (stage-major order) does not
  * write the face fluxes it owes its downstream tiles, so their waits run out;
  * the solve then returns DOCTORS_ERR_TIMEOUT and resets the sweep's queue and
@@ -254,7 +259,8 @@ int doctors_solve_batch(doctors_problem **problems, int n, doctors_result *resul
 typedef struct doctors_tuning {
     int tile_x, tile_y;      /* tile of columns */
     int angles_per_block;    /* directions per CTA */
-    int sweep_kernel;        /* 1 CUDA-core, 2 tensor-core, 3 chained, 4 dataflow (as doctors_options) */
+    int sweep_kernel;        /* 1 CUDA-core, 2 tensor-core, 3 chained, 4 dataflow, 5 dataflow with split
+                                transforms (as doctors_options) */
     double ms_per_sweep;     /* measured time of one full sweep of this problem */
     int candidates;          /* schedules timed (0 if taken from the cache) */
 } doctors_tuning;

@@ -51,6 +51,7 @@ namespace {
 constexpr bool kDefaultTensorCoreSweep = false;
 constexpr bool kDefaultChainedSweep = true;
 constexpr bool kDefaultDataflowSweep = true;
+constexpr bool kDefaultSplitSweep = false;
 
 int dalloc(void** p, size_t bytes, const char* what) {
     if (bytes == 0) bytes = 16;
@@ -81,7 +82,7 @@ void free_problem(doctors_problem* p) {
                     p->d_phiu_src, p->d_phiu, p->d_U, p->d_Q, p->d_mom, p->d_src, p->d_prev,
                     p->d_emit, p->d_iso, p->d_xface, p->d_yface, p->d_red,
                     p->d_Z, p->d_Qa, p->d_T, p->d_rf, p->d_r, p->d_acc, p->d_grad, p->d_H,
-                    p->d_ones, p->d_psi, p->d_prod, p->d_flow};
+                    p->d_ones, p->d_psi, p->d_prod, p->d_flow, p->d_qang, p->d_pang};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (p->h_red) cudaFreeHost(p->h_red);
@@ -199,14 +200,19 @@ SweepArgs sweep_args(const doctors_problem* p, int reverse, const float* src, fl
     a.gcount = p->G;
     a.chain_slots = p->use_tc ? 0 : p->chain_slots;
     a.dir_table = &p->dir_table;
-    a.flow = p->use_flow ? p->d_flow : nullptr;
+    a.flow = (p->use_flow || p->use_split) ? p->d_flow : nullptr;
+    a.qang = p->d_qang;
+    a.pang = p->d_pang;
     return a;
 }
 
 // One full sweep with the problem's chosen kernel: one launch per tile stage,
 // or one dataflow launch.  Returns the kernels launched in *count.
 cudaError_t launch_sweep(const doctors_problem* p, SweepArgs sw, int mode, cudaStream_t s, int* count) {
-    if (p->use_flow) {
+    if (p->use_split && mode == 0) return launch_split_sweep(sw, p->M, s, count);
+    if (p->use_flow || p->use_split) {
+        // the split path's modes 1 and 2 (stored / paired angular fluence) use the plain dataflow kernel
+        if (p->use_split) sw.chain_slots = p->flow_slots;
         *count = 1;
         return launch_sweep_flow(sw, p->M, mode, s);
     }
@@ -223,7 +229,7 @@ cudaError_t launch_sweep(const doctors_problem* p, SweepArgs sw, int mode, cudaS
 // After a dataflow sweep: a face wait that timed out leaves the queue and the
 // face records in an unknown state; reset them and report the failure.
 int check_flow(doctors_problem* p) {
-    if (!p->use_flow || !p->d_flow) return DOCTORS_OK;
+    if (!(p->use_flow || p->use_split) || !p->d_flow) return DOCTORS_OK;
     int h[4] = {0, 0, 0, 0};
     CU(cudaMemcpyAsync(h, p->d_flow, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
     CU(cudaStreamSynchronize(p->stream));
@@ -273,7 +279,8 @@ int iterate(doctors_problem* p, int reverse, const float* Q, float* mom, doctors
             CU(launch_scatter(sa, p->stream));
             ++p->launches;
         }
-        CU(cudaMemsetAsync(mom + (size_t)g0 * VM, 0, (size_t)gc * VM * sizeof(float), p->stream));
+        if (!p->use_split)   // the split path's d2m pass writes the window's moments
+            CU(cudaMemsetAsync(mom + (size_t)g0 * VM, 0, (size_t)gc * VM * sizeof(float), p->stream));
         CU(cudaMemsetAsync(p->d_red + g0, 0, (size_t)gc * sizeof(double), p->stream));
         CU(cudaMemsetAsync(d_res + 2 * g0, 0, 2 * (size_t)gc * sizeof(double), p->stream));
         CU(cudaEventRecord(p->ev[3], p->stream));
@@ -412,7 +419,7 @@ int graph_iterate(doctors_problem** ps, int n, int reverse, const float* const* 
             sa.mat = p->d_mat; sa.rho = p->d_rho; sa.sigs = p->d_sigs;
             sa.base = Qs[q]; sa.phi = moms[q]; sa.out = p->d_src; sa.skip = skip;
             e = launch_scatter(sa, cs);
-            if (e == cudaSuccess) e = launch_zero(moms[q], (size_t)p->G * p->V * p->M, skip, cs);
+            if (e == cudaSuccess && !p->use_split) e = launch_zero(moms[q], (size_t)p->G * p->V * p->M, skip, cs);
             if (e == cudaSuccess) e = launch_zero(p->d_red, 5 * (size_t)p->G, skip, cs);
             SweepArgs sw = sweep_args(p, reverse, p->d_src, moms[q]);
             sw.skip = skip;
@@ -497,11 +504,11 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
         set_error("angles_per_block must divide N(N+2)/8 and be one of 1,2,3,4,5,6,7,9,10,12");
         return DOCTORS_ERR_INVALID_ARG;
     }
-    if (kernel < 0 || kernel > 4) {
-        set_error("sweep_kernel must be 0, 1, 2, 3 or 4");
+    if (kernel < 0 || kernel > 5) {
+        set_error("sweep_kernel must be 0, 1, 2, 3, 4 or 5");
         return DOCTORS_ERR_INVALID_ARG;
     }
-    if (kernel == 4 && !(p->A8 == ab && chain_const_table_ab(ab))) {
+    if ((kernel == 4 || kernel == 5) && !(p->A8 == ab && chain_const_table_ab(ab))) {
         set_error("dataflow sweep needs whole octants per CTA (angles_per_block = N(N+2)/8) of S2, S4, S6 or S8");
         return DOCTORS_ERR_INVALID_ARG;
     }
@@ -512,24 +519,27 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
     }
     const bool use_tc = kernel == 2 || (kernel == 0 && tc_ok && kDefaultTensorCoreSweep);
     const bool flow_ok = p->A8 == ab && chain_const_table_ab(ab);
-    const bool use_flow = kernel == 4 || (kernel == 0 && !use_tc && flow_ok && kDefaultDataflowSweep);
-    const bool use_chain = !use_tc && !use_flow && (kernel == 3 || (kernel == 0 && kDefaultChainedSweep));
+    const bool use_split = kernel == 5 || (kernel == 0 && !use_tc && flow_ok && kDefaultSplitSweep);
+    const bool use_flow = !use_split && (kernel == 4 || (kernel == 0 && !use_tc && flow_ok && kDefaultDataflowSweep));
+    const bool use_chain = !use_tc && !use_flow && !use_split && (kernel == 3 || (kernel == 0 && kDefaultChainedSweep));
     const int ntx = (p->nx + tx - 1) / tx, nty = (p->ny + ty - 1) / ty;
-    int chain_slots = 0;
+    int chain_slots = 0, flow_slots = 0;
     size_t smem = 0;
     if (use_tc) {
         smem = sweep_tc_smem_bytes(ab, tx, ty, p->nz, kMaxMat);
-    } else if (use_flow) {
+    } else if (use_flow || use_split) {
         int sms = 0;
         CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
         smem = sweep_flow_smem_bytes(ab, tx, ty, p->G, kMaxMat);
         if (smem <= 227 * 1024) {
-            const int per_sm = sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem);
-            if (per_sm < 1) {
+            const int per_sm = sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem, false);
+            const int per_sm_split = use_split ? sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem, true) : per_sm;
+            if (per_sm < 1 || per_sm_split < 1) {
                 set_error("dataflow sweep cannot be resident with this tile");
                 return DOCTORS_ERR_INVALID_ARG;
             }
-            chain_slots = sms * per_sm;
+            chain_slots = sms * per_sm_split;
+            flow_slots = sms * per_sm;
         }
     } else if (use_chain) {
         // CTA slots from the occupancy at the largest chain a stage can need
@@ -579,7 +589,21 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
         p->d_yface = nb;
         p->yface_bytes = yf * sizeof(float);
     }
-    if (use_flow) {
+    if (use_split) {
+        // angular source and fluence records of every direction, group and voxel
+        const size_t nang = (size_t)p->G * 8 * p->V * flow_abp_host(p->A8);
+        if (p->ang_floats < nang) {
+            if (p->d_qang) cudaFree(p->d_qang);
+            if (p->d_pang) cudaFree(p->d_pang);
+            p->d_qang = p->d_pang = nullptr;
+            p->ang_floats = 0;
+            int rc = dalloc_t(&p->d_qang, nang, "angular source");
+            if (!rc) rc = dalloc_t(&p->d_pang, nang, "angular fluence");
+            if (rc) return rc;
+            p->ang_floats = nang;
+        }
+    }
+    if (use_flow || use_split) {
         // every face record starts as NaN (not yet written); the queue at zero
         if (!p->d_flow) {
             int rc = dalloc_t(&p->d_flow, 4, "dataflow queue");
@@ -591,7 +615,9 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
     }
     p->tx = tx; p->ty = ty; p->ab = ab; p->nab = p->A8 / ab; p->ntx = ntx; p->nty = nty; p->use_tc = use_tc;
     p->use_flow = use_flow;
+    p->use_split = use_split;
     p->chain_slots = chain_slots;
+    p->flow_slots = flow_slots;
     return DOCTORS_OK;
 }
 
@@ -641,7 +667,7 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     p->ab = opt->angles_per_block > 0 ? opt->angles_per_block : default_ab(p->A8);
     // default tile: 8 x 8 for the dataflow sweep (whole octants of S2..S8),
     // 16 x 16 for the stage kernels (the fastest measured shapes)
-    const bool flow_default = opt->sweep_kernel == 4 ||
+    const bool flow_default = opt->sweep_kernel == 4 || opt->sweep_kernel == 5 ||
                               (opt->sweep_kernel == 0 && kDefaultDataflowSweep && p->A8 == p->ab &&
                                chain_const_table_ab(p->ab));
     const int tdef = flow_default ? 8 : 16;
@@ -659,7 +685,7 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     p->nab = p->A8 / p->ab;
     p->ntx = (p->nx + p->tx - 1) / p->tx;
     p->nty = (p->ny + p->ty - 1) / p->ty;
-    if (opt->sweep_kernel < 0 || opt->sweep_kernel > 4) return fail(DOCTORS_ERR_INVALID_ARG, "sweep_kernel must be 0, 1, 2, 3 or 4");
+    if (opt->sweep_kernel < 0 || opt->sweep_kernel > 5) return fail(DOCTORS_ERR_INVALID_ARG, "sweep_kernel must be 0, 1, 2, 3, 4 or 5");
     if (opt->sweep_kernel == 2 && !sweep_tc_supported(p->ab, p->M, p->tx, p->ty))
         return fail(DOCTORS_ERR_INVALID_ARG, "tensor-core sweep needs P3, <= 16 directions per block and a 16x16, 32x8, 16x8, 8x16, 8x8 or 8x4 tile");
     cudaError_t e = cudaGetDevice(&p->device);
@@ -946,7 +972,7 @@ int doctors_dose(doctors_problem* p, const double* k, double* dose, int mem) {
 int doctors_debug_withhold_faces(doctors_problem* p, int task) {
     int rc = check_problem(p);
     if (rc) return rc;
-    if (!p->use_flow || !p->d_flow) {
+    if (!(p->use_flow || p->use_split) || !p->d_flow) {
         set_error("the problem's sweep is not the dataflow kernel");
         return DOCTORS_ERR_STATE;
     }
@@ -1085,12 +1111,13 @@ int doctors_autotune(doctors_problem* p, doctors_tuning* out) {
     doctors_tuning best{};
     best.ms_per_sweep = 1e30;
     int count = 0;
-    const int saved[4] = {p->tx, p->ty, p->ab, p->use_tc ? 2 : p->use_flow ? 4 : (p->chain_slots > 0 ? 3 : 1)};
+    const int saved[4] = {p->tx, p->ty, p->ab,
+                          p->use_tc ? 2 : p->use_split ? 5 : p->use_flow ? 4 : (p->chain_slots > 0 ? 3 : 1)};
     for (const auto& t : tiles) {
         for (int ab : abs_ok) {
-            for (int kernel = 1; kernel <= 4; ++kernel) {
+            for (int kernel = 1; kernel <= 5; ++kernel) {
                 if (kernel == 2 && !sweep_tc_supported(ab, p->M, t[0], t[1])) continue;
-                if (kernel == 4 && !(p->A8 == ab && chain_const_table_ab(ab))) continue;
+                if (kernel >= 4 && !(p->A8 == ab && chain_const_table_ab(ab))) continue;
                 if (configure_sweep(p, t[0], t[1], ab, kernel) != DOCTORS_OK) continue;
                 SweepArgs sw = sweep_args(p, 0, p->d_Q, p->d_mom);
                 float total = 0.0f;

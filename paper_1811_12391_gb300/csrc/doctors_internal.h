@@ -181,6 +181,8 @@ struct SweepArgs {
     const int* skip;                   // if non-null and *skip != 0 the kernel does nothing
     int chain_slots;                   // > 0: chained kernel, at most this many CTAs per stage launch
     const struct ChainDirTable* dir_table;   // host copy of the first-octant direction table (chained kernel)
+    const float* qang;                 // split transforms: angular source [G][8][V][ABP] (direction octant)
+    float* pang;                       // split transforms: angular fluence [G][8][V][ABP]
     int* flow;                         // non-null: dataflow kernel; [0] task queue, [1] CTAs done, [2] wait timed out,
                                        // [3] test hook: task + 1 that writes no faces (0: none)
 };
@@ -231,8 +233,12 @@ inline size_t sweep_flow_smem_bytes(int ab, int tx, int ty, int gcount, int nmat
     return 4 * (size_t)(tx + ty) * flow_abp_host(ab) + 8 * (size_t)gcount +
            4 * ((size_t)2 * chain_rs(ab) * chain_px(tx) * (ty + 1) + (size_t)gcount * nmat) + 16;
 }
-int sweep_flow_blocks_per_sm(int ab, int M, int threads, size_t smem);
+int sweep_flow_blocks_per_sm(int ab, int M, int threads, size_t smem, bool split = false);
 cudaError_t launch_sweep_flow(const SweepArgs& a, int M, int mode, cudaStream_t s);
+// split transforms (whole octants of S2..S8): moments -> angular source for
+// all 8 octants, the dataflow sweep on angular records (a.qang -> a.pang),
+// angular fluence -> moments (plain stores into a.mom)
+cudaError_t launch_split_sweep(const SweepArgs& a, int M, cudaStream_t s, int* count);
 // Upload the shared direction tables (all S_N sets) to the current device,
 // once per device; returns the first table row of order N in *base.
 cudaError_t ensure_direction_tables(int device, int N, int* base);
@@ -263,6 +269,11 @@ struct doctors_problem {
     bool use_tc = false;            // tensor-core transforms in the sweep
     int chain_slots = 0;            // > 0: chained or dataflow sweep with this many CTA slots
     bool use_flow = false;          // dataflow sweep (one launch per sweep, task queue)
+    bool use_split = false;         // dataflow sweep with the transforms in separate passes
+    int flow_slots = 0;             // CTA slots of the plain dataflow kernel (modes 1, 2 under split)
+    float* d_qang = nullptr;        // [G][8][V][ABP] angular source (split)
+    float* d_pang = nullptr;        // [G][8][V][ABP] angular fluence (split)
+    size_t ang_floats = 0;
     int* d_flow = nullptr;          // [4] dataflow queue, done count, timeout flag
     doctors::ChainDirTable dir_table{};   // first-octant direction table of the chained sweep
     // device tables

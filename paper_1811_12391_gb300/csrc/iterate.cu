@@ -30,10 +30,14 @@ cudaError_t launch_sweep_flow_m1_entry(const SweepArgs& a, int mode, cudaStream_
 cudaError_t launch_sweep_flow_m4_entry(const SweepArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_sweep_flow_m9_entry(const SweepArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_sweep_flow_m16_entry(const SweepArgs& a, int mode, cudaStream_t s);
-int sweep_flow_blocks_m1(int ab, int threads, size_t smem);
-int sweep_flow_blocks_m4(int ab, int threads, size_t smem);
-int sweep_flow_blocks_m9(int ab, int threads, size_t smem);
-int sweep_flow_blocks_m16(int ab, int threads, size_t smem);
+int sweep_flow_blocks_m1(int ab, int threads, size_t smem, bool split);
+cudaError_t launch_split_sweep_m1_entry(const SweepArgs& a, cudaStream_t s, int* count);
+int sweep_flow_blocks_m4(int ab, int threads, size_t smem, bool split);
+cudaError_t launch_split_sweep_m4_entry(const SweepArgs& a, cudaStream_t s, int* count);
+int sweep_flow_blocks_m9(int ab, int threads, size_t smem, bool split);
+cudaError_t launch_split_sweep_m9_entry(const SweepArgs& a, cudaStream_t s, int* count);
+int sweep_flow_blocks_m16(int ab, int threads, size_t smem, bool split);
+cudaError_t launch_split_sweep_m16_entry(const SweepArgs& a, cudaStream_t s, int* count);
 
 cudaError_t upload_tables_m1(const float* R, const float* w);
 cudaError_t upload_tables_m4(const float* R, const float* w);
@@ -96,13 +100,23 @@ int sweep_chain_blocks_per_sm(int ab, bool ct, int M, int threads, size_t smem) 
     }
 }
 
-int sweep_flow_blocks_per_sm(int ab, int M, int threads, size_t smem) {
+int sweep_flow_blocks_per_sm(int ab, int M, int threads, size_t smem, bool split) {
     switch (M) {
-        case 1: return sweep_flow_blocks_m1(ab, threads, smem);
-        case 4: return sweep_flow_blocks_m4(ab, threads, smem);
-        case 9: return sweep_flow_blocks_m9(ab, threads, smem);
-        case 16: return sweep_flow_blocks_m16(ab, threads, smem);
+        case 1: return sweep_flow_blocks_m1(ab, threads, smem, split);
+        case 4: return sweep_flow_blocks_m4(ab, threads, smem, split);
+        case 9: return sweep_flow_blocks_m9(ab, threads, smem, split);
+        case 16: return sweep_flow_blocks_m16(ab, threads, smem, split);
         default: return 0;
+    }
+}
+
+cudaError_t launch_split_sweep(const SweepArgs& a, int M, cudaStream_t s, int* count) {
+    switch (M) {
+        case 1: return launch_split_sweep_m1_entry(a, s, count);
+        case 4: return launch_split_sweep_m4_entry(a, s, count);
+        case 9: return launch_split_sweep_m9_entry(a, s, count);
+        case 16: return launch_split_sweep_m16_entry(a, s, count);
+        default: return cudaErrorInvalidValue;
     }
 }
 

@@ -23,6 +23,8 @@
 // DOCTORS_ERR_TIMEOUT and resets the buffers.
 #pragma once
 
+#include <algorithm>
+
 #include "sweep_chain.cuh"
 
 namespace doctors {
@@ -44,8 +46,13 @@ __device__ __forceinline__ int flow_stage_tiles(int s, int ntx, int nty) {
     return hi - lo + 1;
 }
 
-template <int AB, int M, int MODE>
+// SPLIT = true: the transforms run in separate passes (k_split_m2d before,
+// k_split_d2m after); the sweep reads each cell's angular-source record
+// a.qang and writes its angular-fluence record a.pang, with no moments and
+// no reductions (mode 0 only).
+template <int AB, int M, int MODE, bool SPLIT = false>
 __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const ChainDirTable dt) {
+    static_assert(!SPLIT || MODE == 0, "split transforms sweep in mode 0 only");
     constexpr int ABP = flow_abp(AB);
     constexpr int RS = AB | 1;
     extern __shared__ float4 sm4[];
@@ -95,9 +102,10 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
     float4* const myland_y = landy + li * (ABP / 4);
     const float qnan = __int_as_float(0x7fffffff);
 
-    float sn[M];
+    constexpr int NS = SPLIT ? ABP : M;       // prefetched source values per cell
+    float sn[NS];
 #pragma unroll
-    for (int m = 0; m < M; ++m) sn[m] = 0.0f;
+    for (int m = 0; m < NS; ++m) sn[m] = 0.0f;
     float rho_n = 0.0f;       // density and material of the prefetched cell: the cross
     int mat_n = 0;            // section is looked up when the cell is swept, not at the load
     float zc[AB];
@@ -143,10 +151,20 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
         float* const yi = (lj == 0 && bt > 0) ? a.yface + (og * ntyf + bt - 1) * yslab + (size_t)ir * a.nz * ABP : nullptr;
         const bool xedge = col && li == 0, yedge = col && lj == 0;
 
+        const size_t ang0 = ((size_t)g * 8 + oe) * V;       // angular records of (group, direction octant)
         auto prefetch = [&](int kn) {
             const int k = sz > 0 ? kn : a.nz - 1 - kn;
             const size_t v = (size_t)k * nxy + vcol;
-            load_moments<M>(a.src + (gV + v) * M, sn);
+            if constexpr (SPLIT) {
+                const float4* r4 = reinterpret_cast<const float4*>(a.qang + (ang0 + v) * ABP);
+#pragma unroll
+                for (int c4 = 0; c4 < ABP / 4; ++c4) {
+                    const float4 t4 = __ldg(r4 + c4);
+                    sn[4 * c4] = t4.x; sn[4 * c4 + 1] = t4.y; sn[4 * c4 + 2] = t4.z; sn[4 * c4 + 3] = t4.w;
+                }
+            } else {
+                load_moments<M>(a.src + (gV + v) * M, sn);
+            }
             rho_n = __ldg(a.rho + v);
             mat_n = __ldg(a.mat + v);
         };
@@ -185,21 +203,26 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
             }
             if (act) {
                 const bool last = kr == a.nz - 1;
+                if constexpr (!SPLIT) {
 #pragma unroll
-                for (int m = 0; m < M; ++m) sn[m] *= octant_sign<M>(m, fx, fy, fz);
+                    for (int m = 0; m < NS; ++m) sn[m] *= octant_sign<M>(m, fx, fy, fz);
+                }
                 const float sig = rho_n * sigt_s[gi * a.nmat + mat_n];
                 const int k = sz > 0 ? kr : a.nz - 1 - kr;
                 const size_t v = (size_t)k * nxy + vcol;
                 const size_t mo = (gV + v) * M;
-                float s[M];
+                float s[NS];
 #pragma unroll
-                for (int m = 0; m < M; ++m) s[m] = sn[m];
+                for (int m = 0; m < NS; ++m) s[m] = sn[m];
                 if (!last) prefetch(kr + 1);
                 constexpr int rb = chain_row_base(AB) * 16;
-                // moments -> directions
+                // moments -> directions (split: the record already holds them)
                 float psi[AB];
 #pragma unroll
                 for (int q = 0; q < AB; ++q) {
+                  if constexpr (SPLIT) {
+                    psi[q] = s[q];
+                  } else {
                     float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f, t3 = 0.0f;
 #pragma unroll
                     for (int m = 0; m < M; m += 4) {
@@ -209,6 +232,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
                         if (m + 3 < M) t3 = fmaf(c_Mop1[rb + q * 16 + lm_of_pos(m + 3, M)], s[m + 3], t3);
                     }
                     psi[q] = (t0 + t1) + (t2 + t3);
+                  }
                 }
                 // step-differenced cell solve
                 const float* pv = buf + pb * P * RS;
@@ -263,18 +287,30 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
                         lk = fmaf(f, psi[q], lk);
                     }
                 }
-                // directions -> moments (Eq. 3 for lm = 00): table rows hold w R_lm
-                float acc[M];
+                if constexpr (SPLIT) {
+                    // the cell's angular fluence record, for k_split_d2m
+                    float4* w4 = reinterpret_cast<float4*>(a.pang + (ang0 + v) * ABP);
 #pragma unroll
-                for (int m = 0; m < M; ++m) acc[m] = 0.0f;
+                    for (int c4 = 0; c4 < ABP / 4; ++c4)
+                        w4[c4] = make_float4(4 * c4 < AB ? psi[4 * c4 < AB ? 4 * c4 : 0] : 0.0f,
+                                             4 * c4 + 1 < AB ? psi[4 * c4 + 1 < AB ? 4 * c4 + 1 : 0] : 0.0f,
+                                             4 * c4 + 2 < AB ? psi[4 * c4 + 2 < AB ? 4 * c4 + 2 : 0] : 0.0f,
+                                             4 * c4 + 3 < AB ? psi[4 * c4 + 3 < AB ? 4 * c4 + 3 : 0] : 0.0f);
+                    (void)mo;
+                } else {
+                    // directions -> moments (Eq. 3 for lm = 00): table rows hold w R_lm
+                    float acc[M];
 #pragma unroll
-                for (int q = 0; q < AB; ++q) {
+                    for (int m = 0; m < M; ++m) acc[m] = 0.0f;
 #pragma unroll
-                    for (int m = 0; m < M; ++m) acc[m] = fmaf(c_Dop1[rb + q * 16 + lm_of_pos(m, M)], psi[q], acc[m]);
+                    for (int q = 0; q < AB; ++q) {
+#pragma unroll
+                        for (int m = 0; m < M; ++m) acc[m] = fmaf(c_Dop1[rb + q * 16 + lm_of_pos(m, M)], psi[q], acc[m]);
+                    }
+#pragma unroll
+                    for (int m = 0; m < M; ++m) acc[m] *= octant_sign<M>(m, fx, fy, fz);
+                    add_moments<M>(a.mom + mo, acc);
                 }
-#pragma unroll
-                for (int m = 0; m < M; ++m) acc[m] *= octant_sign<M>(m, fx, fy, fz);
-                add_moments<M>(a.mom + mo, acc);
                 if (last && lk != 0.0f) {
                     atomicAdd(leak_s + gi, (double)lk);
                     lk = 0.0f;
@@ -329,8 +365,94 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
     }
 }
 
+// Moments -> angular source of every direction of every octant (the
+// transform taken out of the split sweep): q[g][o][v][j] =
+// sum_lm (2l+1)/(4 pi) R_lm(Omega_{o,j}) s_lm[g][v], with R of octant o the
+// first octant's times the reflection signs.  One thread per (group, voxel),
+// records written as 16-byte vectors; HBM-bound.
+template <int M, int AB>
+__global__ void __launch_bounds__(256) k_split_m2d(const float* src, float* qang, size_t V, int g0, int gcount,
+                                                  const int* skip) {
+    constexpr int ABP = flow_abp(AB);
+    constexpr int rb = chain_row_base(AB) * 16;
+    if (skip && *skip) return;
+    const size_t n = (size_t)gcount * V;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const int g = g0 + (int)(e / V);
+        const size_t v = e % V;
+        float s[M];
+        load_moments<M>(src + ((size_t)g * V + v) * M, s);
+#pragma unroll 1
+        for (int o = 0; o < 8; ++o) {
+            const float fx = (o & 1) ? -1.0f : 1.0f, fy = (o & 2) ? -1.0f : 1.0f, fz = (o & 4) ? -1.0f : 1.0f;
+            float so[M];
+#pragma unroll
+            for (int m = 0; m < M; ++m) so[m] = s[m] * octant_sign<M>(m, fx, fy, fz);
+            float q[ABP];
+#pragma unroll
+            for (int j = 0; j < ABP; ++j) {
+                float t = 0.0f;
+                if (j < AB) {
+#pragma unroll
+                    for (int m = 0; m < M; ++m) t = fmaf(c_Mop1[rb + j * 16 + lm_of_pos(m, M)], so[m], t);
+                }
+                q[j] = t;
+            }
+            float4* out = reinterpret_cast<float4*>(qang + (((size_t)g * 8 + o) * V + v) * ABP);
+#pragma unroll
+            for (int c4 = 0; c4 < ABP / 4; ++c4) out[c4] = make_float4(q[4 * c4], q[4 * c4 + 1], q[4 * c4 + 2], q[4 * c4 + 3]);
+        }
+    }
+}
+
+// Angular fluence of every direction -> moments (Eq. 3 for lm = 00):
+// mom[g][v][lm] = sum_o sum_j w_j R_lm(Omega_{o,j}) psi[g][o][v][j], written
+// with plain stores (one thread per (group, voxel), no reductions).
+template <int M, int AB>
+__global__ void __launch_bounds__(256) k_split_d2m(const float* pang, float* mom, size_t V, int g0, int gcount,
+                                                  const int* skip) {
+    constexpr int ABP = flow_abp(AB);
+    constexpr int rb = chain_row_base(AB) * 16;
+    if (skip && *skip) return;
+    const size_t n = (size_t)gcount * V;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const int g = g0 + (int)(e / V);
+        const size_t v = e % V;
+        float acc[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) acc[m] = 0.0f;
+#pragma unroll 1
+        for (int o = 0; o < 8; ++o) {
+            const float fx = (o & 1) ? -1.0f : 1.0f, fy = (o & 2) ? -1.0f : 1.0f, fz = (o & 4) ? -1.0f : 1.0f;
+            const float4* in = reinterpret_cast<const float4*>(pang + (((size_t)g * 8 + o) * V + v) * ABP);
+            float ps[ABP];
+#pragma unroll
+            for (int c4 = 0; c4 < ABP / 4; ++c4) {
+                const float4 t4 = __ldg(in + c4);
+                ps[4 * c4] = t4.x; ps[4 * c4 + 1] = t4.y; ps[4 * c4 + 2] = t4.z; ps[4 * c4 + 3] = t4.w;
+            }
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                float b = 0.0f;
+#pragma unroll
+                for (int j = 0; j < AB; ++j) b = fmaf(c_Dop1[rb + j * 16 + lm_of_pos(m, M)], ps[j], b);
+                acc[m] = fmaf(octant_sign<M>(m, fx, fy, fz), b, acc[m]);
+            }
+        }
+        float* out = mom + ((size_t)g * V + v) * M;
+        if constexpr (M % 4 == 0) {
+            float4* o4 = reinterpret_cast<float4*>(out);
+#pragma unroll
+            for (int c4 = 0; c4 < M / 4; ++c4) o4[c4] = make_float4(acc[4 * c4], acc[4 * c4 + 1], acc[4 * c4 + 2], acc[4 * c4 + 3]);
+        } else {
+#pragma unroll
+            for (int m = 0; m < M; ++m) out[m] = acc[m];
+        }
+    }
+}
+
 template <int M>
-int sweep_flow_blocks_per_sm(int ab, int threads, size_t smem) {
+int sweep_flow_blocks_per_sm(int ab, int threads, size_t smem, bool split) {
     int b = 0;
     cudaError_t e = cudaErrorInvalidValue;
     auto query = [&](auto kern) {
@@ -339,13 +461,57 @@ int sweep_flow_blocks_per_sm(int ab, int threads, size_t smem) {
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, smem);
     };
     switch (ab) {
-        case 1: query(k_sweep_flow<1, M, 0>); break;
-        case 3: query(k_sweep_flow<3, M, 0>); break;
-        case 6: query(k_sweep_flow<6, M, 0>); break;
-        case 10: query(k_sweep_flow<10, M, 0>); break;
+        case 1: split ? query(k_sweep_flow<1, M, 0, true>) : query(k_sweep_flow<1, M, 0>); break;
+        case 3: split ? query(k_sweep_flow<3, M, 0, true>) : query(k_sweep_flow<3, M, 0>); break;
+        case 6: split ? query(k_sweep_flow<6, M, 0, true>) : query(k_sweep_flow<6, M, 0>); break;
+        case 10: split ? query(k_sweep_flow<10, M, 0, true>) : query(k_sweep_flow<10, M, 0>); break;
         default: break;
     }
     return e == cudaSuccess ? b : 0;
+}
+
+// m2d, split sweep, d2m: one full sweep with the transforms taken out
+template <int M>
+cudaError_t launch_split_sweep_m(const SweepArgs& a, cudaStream_t s, int* count) {
+    *count = 0;
+    if (a.gcount <= 0) return cudaSuccess;
+    if (a.dir_table == nullptr || a.flow == nullptr || a.nab != 1 || !a.qang || !a.pang) return cudaErrorInvalidValue;
+    const size_t V = (size_t)a.nx * a.ny * a.nz;
+    const size_t n = (size_t)a.gcount * V;
+    const unsigned tgrid = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 8);
+    int ntasks = 0;
+    for (int st = 0; st < a.ntx + a.nty - 1; ++st) {
+        const int lo = st - (a.nty - 1) > 0 ? st - (a.nty - 1) : 0;
+        const int hi = st < a.ntx - 1 ? st : a.ntx - 1;
+        ntasks += (hi - lo + 1) * 8 * a.gcount;
+    }
+    const int grid = ntasks < a.chain_slots ? ntasks : a.chain_slots;
+    const int T = a.tx * a.ty;
+    const size_t smem = sweep_flow_smem_bytes(a.ab, a.tx, a.ty, a.gcount, a.nmat);
+    cudaError_t e = cudaSuccess;
+    auto run = [&](auto m2d, auto sweep, auto d2m) {
+        m2d<<<tgrid, 256, 0, s>>>(a.src, const_cast<float*>(a.qang), V, a.g0, a.gcount, a.skip);
+        e = cudaGetLastError();
+        if (e == cudaSuccess && smem > 48 * 1024)
+            e = cudaFuncSetAttribute(sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) {
+            sweep<<<grid, T, smem, s>>>(a, *a.dir_table);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
+            d2m<<<tgrid, 256, 0, s>>>(a.pang, a.mom, V, a.g0, a.gcount, a.skip);
+            e = cudaGetLastError();
+        }
+    };
+    switch (a.ab) {
+        case 1: run(k_split_m2d<M, 1>, k_sweep_flow<1, M, 0, true>, k_split_d2m<M, 1>); break;
+        case 3: run(k_split_m2d<M, 3>, k_sweep_flow<3, M, 0, true>, k_split_d2m<M, 3>); break;
+        case 6: run(k_split_m2d<M, 6>, k_sweep_flow<6, M, 0, true>, k_split_d2m<M, 6>); break;
+        case 10: run(k_split_m2d<M, 10>, k_sweep_flow<10, M, 0, true>, k_split_d2m<M, 10>); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (e == cudaSuccess) *count = 3;
+    return e;
 }
 
 template <int M, int MODE>

@@ -28,7 +28,12 @@ cudaError_t launch_sweep_flow_m1_entry(const SweepArgs& a, int mode, cudaStream_
         default: return cudaErrorInvalidValue;
     }
 }
-int sweep_flow_blocks_m1(int ab, int threads, size_t smem) { return sweep_flow_blocks_per_sm<1>(ab, threads, smem); }
+int sweep_flow_blocks_m1(int ab, int threads, size_t smem, bool split) {
+    return sweep_flow_blocks_per_sm<1>(ab, threads, smem, split);
+}
+cudaError_t launch_split_sweep_m1_entry(const SweepArgs& a, cudaStream_t s, int* count) {
+    return launch_split_sweep_m<1>(a, s, count);
+}
 int sweep_chain_blocks_m1(int ab, bool ct, int threads, size_t smem) { return sweep_chain_blocks_per_sm<1>(ab, ct, threads, smem); }
 cudaError_t upload_tables_m1(const float* R, const float* w) {
     cudaError_t e = upload_direction_tables(R, w);

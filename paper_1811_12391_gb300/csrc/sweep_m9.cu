@@ -28,7 +28,12 @@ cudaError_t launch_sweep_flow_m9_entry(const SweepArgs& a, int mode, cudaStream_
         default: return cudaErrorInvalidValue;
     }
 }
-int sweep_flow_blocks_m9(int ab, int threads, size_t smem) { return sweep_flow_blocks_per_sm<9>(ab, threads, smem); }
+int sweep_flow_blocks_m9(int ab, int threads, size_t smem, bool split) {
+    return sweep_flow_blocks_per_sm<9>(ab, threads, smem, split);
+}
+cudaError_t launch_split_sweep_m9_entry(const SweepArgs& a, cudaStream_t s, int* count) {
+    return launch_split_sweep_m<9>(a, s, count);
+}
 int sweep_chain_blocks_m9(int ab, bool ct, int threads, size_t smem) { return sweep_chain_blocks_per_sm<9>(ab, ct, threads, smem); }
 cudaError_t upload_tables_m9(const float* R, const float* w) {
     cudaError_t e = upload_direction_tables(R, w);
