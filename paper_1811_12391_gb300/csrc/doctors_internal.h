@@ -230,7 +230,8 @@ inline size_t sweep_chain_smem_bytes(int ab, int tx, int ty, int cmax, int gcoun
 // hyperplanes, sigma_t of the swept groups and the task slot
 inline int flow_abp_host(int ab) { return (ab + 3) & ~3; }
 inline size_t sweep_flow_smem_bytes(int ab, int tx, int ty, int gcount, int nmat) {
-    return 4 * (size_t)(tx + ty) * flow_abp_host(ab) + 8 * (size_t)gcount +
+    // two landing slots per edge column (pipeline depth 2 of the split sweep)
+    return 2 * 4 * (size_t)(tx + ty) * flow_abp_host(ab) + 8 * (size_t)gcount +
            4 * ((size_t)2 * chain_rs(ab) * chain_px(tx) * (ty + 1) + (size_t)gcount * nmat) + 16;
 }
 int sweep_flow_blocks_per_sm(int ab, int M, int threads, size_t smem, bool split = false);

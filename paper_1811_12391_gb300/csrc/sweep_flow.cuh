@@ -55,13 +55,17 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
     static_assert(!SPLIT || MODE == 0, "split transforms sweep in mode 0 only");
     constexpr int ABP = flow_abp(AB);
     constexpr int RS = AB | 1;
+    // pipeline depth: face records and source values are fetched PD steps
+    // before the step that uses them (the split sweep's steps are short, so
+    // one step does not cover the L2 latency)
+    constexpr int PD = SPLIT ? 2 : 1;
     extern __shared__ float4 sm4[];
     if (a.skip && *a.skip) return;          // retired instance of a batched loop
     const int PX = chain_px(a.tx);
     const int P = PX * (a.ty + 1);
-    float4* landx = sm4;                                      // [ty][ABP/4] fetched x-face records
-    float4* landy = landx + a.ty * (ABP / 4);                 // [tx][ABP/4] fetched y-face records
-    double* leak_s = reinterpret_cast<double*>(landy + a.tx * (ABP / 4));   // [gcount]
+    float4* landx = sm4;                                      // [PD][ty][ABP/4] fetched x-face records
+    float4* landy = landx + PD * a.ty * (ABP / 4);            // [PD][tx][ABP/4] fetched y-face records
+    double* leak_s = reinterpret_cast<double*>(landy + PD * a.tx * (ABP / 4));   // [gcount]
     float* buf = reinterpret_cast<float*>(leak_s + a.gcount);              // [2][P][RS]
     float* sigt_s = buf + 2 * P * RS;                         // [gcount][nmat]
     int* task_s = reinterpret_cast<int*>(sigt_s + a.gcount * a.nmat);
@@ -98,16 +102,17 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
     const size_t xslab = (size_t)a.ny * a.nz * ABP, yslab = (size_t)a.nx * a.nz * ABP;
     int ntasks = 0;
     for (int s = 0; s < nst; ++s) ntasks += flow_stage_tiles(s, a.ntx, a.nty) * 8 * a.gcount;
-    float4* const myland_x = landx + lj * (ABP / 4);
-    float4* const myland_y = landy + li * (ABP / 4);
+    // this thread's landing slot for the record used at step st
+    auto land_x = [&](int st) { return landx + ((st & (PD - 1)) * a.ty + lj) * (ABP / 4); };
+    auto land_y = [&](int st) { return landy + ((st & (PD - 1)) * a.tx + li) * (ABP / 4); };
     const float qnan = __int_as_float(0x7fffffff);
 
     constexpr int NS = SPLIT ? ABP : M;       // prefetched source values per cell
-    float sn[NS];
+    float sn[NS], sn2[PD == 2 ? NS : 1];      // next cell; the cell after (depth 2)
 #pragma unroll
     for (int m = 0; m < NS; ++m) sn[m] = 0.0f;
-    float rho_n = 0.0f;       // density and material of the prefetched cell: the cross
-    int mat_n = 0;            // section is looked up when the cell is swept, not at the load
+    float rho_n = 0.0f, rho_n2 = 0.0f;        // density and material of the prefetched cells: the cross
+    int mat_n = 0, mat_n2 = 0;                // section is looked up when the cell is swept, not at the load
     float zc[AB];
     float lk = 0.0f;
 
@@ -152,7 +157,8 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
         const bool xedge = col && li == 0, yedge = col && lj == 0;
 
         const size_t ang0 = ((size_t)g * 8 + oe) * V;       // angular records of (group, direction octant)
-        auto prefetch = [&](int kn) {
+        // source values, density and material of plane kn into (dst, rho, mat)
+        auto fetch = [&](int kn, float* dst, float& rho, int& mt) {
             const int k = sz > 0 ? kn : a.nz - 1 - kn;
             const size_t v = (size_t)k * nxy + vcol;
             if constexpr (SPLIT) {
@@ -160,47 +166,64 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
 #pragma unroll
                 for (int c4 = 0; c4 < ABP / 4; ++c4) {
                     const float4 t4 = __ldg(r4 + c4);
-                    sn[4 * c4] = t4.x; sn[4 * c4 + 1] = t4.y; sn[4 * c4 + 2] = t4.z; sn[4 * c4 + 3] = t4.w;
+                    dst[4 * c4] = t4.x; dst[4 * c4 + 1] = t4.y; dst[4 * c4 + 2] = t4.z; dst[4 * c4 + 3] = t4.w;
                 }
             } else {
-                load_moments<M>(a.src + (gV + v) * M, sn);
+                float tmp[M];
+                load_moments<M>(a.src + (gV + v) * M, tmp);
+#pragma unroll
+                for (int m = 0; m < M; ++m) dst[m] = tmp[m];
             }
-            rho_n = __ldg(a.rho + v);
-            mat_n = __ldg(a.mat + v);
+            rho = __ldg(a.rho + v);
+            mt = __ldg(a.mat + v);
         };
-        if (col) prefetch(0);
+        // the cell after the one in (sn, rho_n, mat_n) moves up, plane kn is fetched behind it
+        auto prefetch = [&](int kn) {
+            if constexpr (PD == 2) {
+#pragma unroll
+                for (int m = 0; m < NS; ++m) sn[m] = sn2[m];
+                rho_n = rho_n2;
+                mat_n = mat_n2;
+                if (kn < a.nz) fetch(kn, sn2, rho_n2, mat_n2);
+            } else {
+                if (kn < a.nz) fetch(kn, sn, rho_n, mat_n);
+            }
+        };
+        if (col) {
+            fetch(0, sn, rho_n, mat_n);
+            if constexpr (PD == 2) {
+                if (a.nz > 1) fetch(1, sn2, rho_n2, mat_n2);
+            }
+        }
 #pragma unroll
         for (int q = 0; q < AB; ++q) zc[q] = 0.0f;
 
-        // step h = -1 only fetches the first halo of column (0, 0)
+        // issue the fetch of the face records this thread uses at step st
+        // (plane st - d): one commit group per step for every thread
+        auto issue_faces = [&](int st) {
+            const int kt = st - d;
+            if (col && kt >= 0 && kt < a.nz) {
+                if (xedge && xi) {
+#pragma unroll
+                    for (int c4 = 0; c4 < ABP / 4; ++c4) cp_async_cg16(land_x(st) + c4, xi + (size_t)kt * ABP + 4 * c4);
+                }
+                if (yedge && yi) {
+#pragma unroll
+                    for (int c4 = 0; c4 < ABP / 4; ++c4) cp_async_cg16(land_y(st) + c4, yi + (size_t)kt * ABP + 4 * c4);
+                }
+            }
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+        };
+        // steps -PD .. -1 only fetch the first records
+        for (int st = 0; st < PD - 1; ++st) issue_faces(st);
         const int hend = a.nz + a.tx + a.ty - 2;
         for (int h = -1; h < hend; ++h) {
             const int cb = h & 1, pb = cb ^ 1;
             const int kr = h - d;
             const bool act = col && kr >= 0 && kr < a.nz;
+            issue_faces(h + PD);
             // plane whose incoming faces this thread needs next step
-            const int kf = (h + 1 == d) ? 0 : (act && kr + 1 < a.nz ? kr + 1 : -1);
-            if (kf >= 0) {
-                float* hb = buf + cb * P * RS;
-                if (xedge) {
-                    if (xi) {
-#pragma unroll
-                        for (int c4 = 0; c4 < ABP / 4; ++c4) cp_async_cg16(myland_x + c4, xi + (size_t)kf * ABP + 4 * c4);
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < AB; ++q) hb[xs + q] = 0.0f;
-                    }
-                }
-                if (yedge) {
-                    if (yi) {
-#pragma unroll
-                        for (int c4 = 0; c4 < ABP / 4; ++c4) cp_async_cg16(myland_y + c4, yi + (size_t)kf * ABP + 4 * c4);
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < AB; ++q) hb[ys + q] = 0.0f;
-                    }
-                }
-            }
+            const int kf = (h + 1 - d >= 0 && h + 1 - d < a.nz) ? h + 1 - d : -1;
             if (act) {
                 const bool last = kr == a.nz - 1;
                 if constexpr (!SPLIT) {
@@ -214,7 +237,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
                 float s[NS];
 #pragma unroll
                 for (int m = 0; m < NS; ++m) s[m] = sn[m];
-                if (!last) prefetch(kr + 1);
+                if (!last) prefetch(kr + PD);
                 constexpr int rb = chain_row_base(AB) * 16;
                 // moments -> directions (split: the record already holds them)
                 float psi[AB];
@@ -316,16 +339,28 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
                     lk = 0.0f;
                 }
             }
-            // incoming records of plane kf: wait until the producer has
-            // written every flux (no NaN left), move them into the halo and
-            // hand the records back to the next sweep as NaN
-            if (kf >= 0 && ((xedge && xi) || (yedge && yi))) {
-                cp_async_wait_all();
+            // incoming records of plane kf (fetched PD steps ago): wait until
+            // the producer has written every flux (no NaN left), move them into
+            // the halo read next step and hand the records back to the next
+            // sweep as NaN; zero inflow on the mesh boundary
+            if (col && kf >= 0 && (xedge || yedge)) {
+                if constexpr (PD == 2) {
+                    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+                } else {
+                    cp_async_wait_all();
+                }
                 float* hb = buf + cb * P * RS;
                 for (int side = 0; side < 2; ++side) {
-                    float* src = side == 0 ? (xedge ? xi : nullptr) : (yedge ? yi : nullptr);
-                    if (!src) continue;
-                    float4* land = side == 0 ? myland_x : myland_y;
+                    const bool edge = side == 0 ? xedge : yedge;
+                    if (!edge) continue;
+                    const int hs = side == 0 ? xs : ys;
+                    float* src = side == 0 ? xi : yi;
+                    if (!src) {
+#pragma unroll
+                        for (int q = 0; q < AB; ++q) hb[hs + q] = 0.0f;
+                        continue;
+                    }
+                    float4* land = side == 0 ? land_x(h + 1) : land_y(h + 1);
                     const float* lf = reinterpret_cast<const float*>(land);
                     src += (size_t)kf * ABP;
                     bool ok = false;
@@ -342,7 +377,6 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
                         cp_async_wait_all();
                     }
                     if (!ok) atomicExch(a.flow + 2, 1);
-                    const int hs = side == 0 ? xs : ys;
 #pragma unroll
                     for (int q = 0; q < AB; ++q) hb[hs + q] = ok ? lf[q] : 0.0f;
                     float4* back = reinterpret_cast<float4*>(src);

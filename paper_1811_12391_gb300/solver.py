@@ -123,8 +123,12 @@ class DoctorsProblem:
         C.check(C.doctors_get_fluence(self.h, which, ctypes.c_void_p(out.data_ptr()), C.DOCTORS_MEM_DEVICE))
         return out
 
-    def fluence_host(self, which: int = C.DOCTORS_FLUENCE_TOTAL) -> np.ndarray:
-        out = np.zeros((self.G, self.V), np.float32)
+    def fluence_host(self, which: int = C.DOCTORS_FLUENCE_TOTAL, out: Optional[np.ndarray] = None) -> np.ndarray:
+        """[G][V] float32 on the host (into `out` if given, e.g. a pinned buffer)."""
+        if out is None:
+            out = np.zeros((self.G, self.V), np.float32)
+        elif out.dtype != np.float32 or out.size != self.G * self.V or not out.flags.c_contiguous:
+            raise ValueError("out must be a contiguous float32 array of G*V values")
         C.check(C.doctors_get_fluence(self.h, which, out.ctypes.data_as(ctypes.c_void_p), C.DOCTORS_MEM_HOST))
         return out
 
@@ -138,9 +142,13 @@ class DoctorsProblem:
                                C.DOCTORS_MEM_DEVICE))
         return out
 
-    def dose_host(self, k) -> np.ndarray:
+    def dose_host(self, k, out: Optional[np.ndarray] = None) -> np.ndarray:
+        """[V] float64 on the host (into `out` if given)."""
         kk = np.ascontiguousarray(k, np.float64)
-        out = np.zeros(self.V, np.float64)
+        if out is None:
+            out = np.zeros(self.V, np.float64)
+        elif out.dtype != np.float64 or out.size != self.V or not out.flags.c_contiguous:
+            raise ValueError("out must be a contiguous float64 array of V values")
         C.check(C.doctors_dose(self.h, _dptr(kk, ctypes.c_double), out.ctypes.data_as(ctypes.c_void_p),
                                C.DOCTORS_MEM_HOST))
         return out
