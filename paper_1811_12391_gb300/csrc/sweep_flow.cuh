@@ -55,10 +55,11 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
     static_assert(!SPLIT || MODE == 0, "split transforms sweep in mode 0 only");
     constexpr int ABP = flow_abp(AB);
     constexpr int RS = AB | 1;
-    // pipeline depth: face records and source values are fetched PD steps
-    // before the step that uses them (the split sweep's steps are short, so
-    // one step does not cover the L2 latency)
-    constexpr int PD = SPLIT ? 2 : 1;
+    // pipeline depths: face records are fetched PD steps before the step
+    // that uses them, source values PDS steps (the split sweep's steps are
+    // short, so one step does not cover the memory latency)
+    constexpr int PD = 2;                     // face records
+    constexpr int PDS = SPLIT ? 2 : 1;        // source values (registers)
     extern __shared__ float4 sm4[];
     if (a.skip && *a.skip) return;          // retired instance of a batched loop
     const int PX = chain_px(a.tx);
@@ -108,7 +109,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
     const float qnan = __int_as_float(0x7fffffff);
 
     constexpr int NS = SPLIT ? ABP : M;       // prefetched source values per cell
-    float sn[NS], sn2[PD == 2 ? NS : 1];      // next cell; the cell after (depth 2)
+    float sn[NS], sn2[PDS == 2 ? NS : 1];     // next cell; the cell after (depth 2)
 #pragma unroll
     for (int m = 0; m < NS; ++m) sn[m] = 0.0f;
     float rho_n = 0.0f, rho_n2 = 0.0f;        // density and material of the prefetched cells: the cross
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
         };
         // the cell after the one in (sn, rho_n, mat_n) moves up, plane kn is fetched behind it
         auto prefetch = [&](int kn) {
-            if constexpr (PD == 2) {
+            if constexpr (PDS == 2) {
 #pragma unroll
                 for (int m = 0; m < NS; ++m) sn[m] = sn2[m];
                 rho_n = rho_n2;
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
         };
         if (col) {
             fetch(0, sn, rho_n, mat_n);
-            if constexpr (PD == 2) {
+            if constexpr (PDS == 2) {
                 if (a.nz > 1) fetch(1, sn2, rho_n2, mat_n2);
             }
         }
@@ -237,7 +238,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
                 float s[NS];
 #pragma unroll
                 for (int m = 0; m < NS; ++m) s[m] = sn[m];
-                if (!last) prefetch(kr + PD);
+                if (!last) prefetch(kr + PDS);
                 constexpr int rb = chain_row_base(AB) * 16;
                 // moments -> directions (split: the record already holds them)
                 float psi[AB];
