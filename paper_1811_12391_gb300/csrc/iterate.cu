@@ -270,13 +270,26 @@ __global__ void __launch_bounds__(256) k_residual(size_t V, int M, const float* 
     if (skip && *skip) return;
     const int g = g0 + blockIdx.y;
     double x[2] = {0.0, 0.0};
-    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (size_t)gridDim.x * blockDim.x) {
-        const float cur = mom[((size_t)g * V + v) * M];
-        const float old = prev[(size_t)g * V + v];
-        const double d = (double)cur - (double)old;
-        x[0] += d * d;
-        x[1] += (double)cur * (double)cur;
-        prev[(size_t)g * V + v] = cur;
+    // four voxels per thread and pass, their loads issued together
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t v0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v0 < V; v0 += 4 * stride) {
+        float cur[4], old[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const size_t v = v0 + u * stride;
+            cur[u] = v < V ? mom[((size_t)g * V + v) * M] : 0.0f;
+            old[u] = v < V ? prev[(size_t)g * V + v] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const size_t v = v0 + u * stride;
+            if (v < V) {
+                const double d = (double)cur[u] - (double)old[u];
+                x[0] += d * d;
+                x[1] += (double)cur[u] * (double)cur[u];
+                prev[(size_t)g * V + v] = cur[u];
+            }
+        }
     }
     block_reduce_add<2>(x, res + 2 * g);
 }
@@ -384,7 +397,7 @@ cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s) {
 
 cudaError_t launch_residual(size_t V, int G, int M, const float* mom, float* prev, double* res,
                             cudaStream_t s, const int* skip, int g0, int gcount) {
-    dim3 grid(blocks_for(V, 256, 296), gcount < 0 ? G : gcount);
+    dim3 grid(blocks_for((V + 3) / 4, 256, 152), gcount < 0 ? G : gcount);
     k_residual<<<grid, 256, 0, s>>>(V, M, mom, prev, res, skip, g0);
     return cudaGetLastError();
 }
