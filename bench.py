@@ -48,7 +48,8 @@ SWEEP_TRAFFIC = {
     (16, 16, 5, 1): (1687.6e6, "sweep_impl.cuh", "592eff4d10129e1bde8b55aecdf9fbf52f768e8c"),
     (16, 16, 10, 2): (2121.9e6, "sweep_tc.cu", "79ec5703826b205c1bdc9d4f7ff57c205fec428a"),
     (16, 8, 10, 3): (2534.9e6, "sweep_chain.cuh", "3502773d12d37fb58b50dbc1187553785b1df685"),
-    (8, 8, 10, 4): (2975.9e6, "sweep_flow.cuh", "8c584040bcbd9a4f099aabcdc4d03555e0c21724"),
+    (8, 8, 10, 4): (2963.0e6, "sweep_flow.cuh", "936b4ea6dba4536cc7dbc8e72dcee44bc5a75b02"),
+    (8, 8, 10, 5): (4668.5e6, "sweep_flow.cuh", "936b4ea6dba4536cc7dbc8e72dcee44bc5a75b02"),
 }
 
 # sweep kernel by the library's sweep_kernel code
