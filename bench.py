@@ -54,7 +54,7 @@ SWEEP_TRAFFIC = {
 
 # sweep kernel by the library's sweep_kernel code
 SWEEP_KERNELS = {1: "k_sweep", 2: "k_sweep_tc", 3: "k_sweep_chain", 4: "k_sweep_flow",
-                 5: "k_split_m2d + k_sweep_flow<split> + k_split_d2m"}
+                 5: "k_split_m2d + k_sweep_flow<split> + k_split_d2m", 6: "k_sweep_flow<two planes per step>"}
 
 # FP32 lanes per SM and SMs of a GB300 (the ALU roofline of the CUDA-core sweep)
 FP32_LANES_PER_SM = 128

@@ -100,7 +100,9 @@ typedef struct doctors_options {
                                 moments into angular sources of all directions, the sweep reads and
                                 writes one angular record per cell, a pass turns the angular fluence
                                 back into moments (same conditions as 4; two more arrays of
-                                G x N(N+2) x V floats, padded) */
+                                G x N(N+2) x V floats, padded),
+                                6 = dataflow sweeping two z planes of a column per hyperplane step
+                                (same conditions as 4) */
     int device_loop;         /* 1 = run the source iteration as one CUDA graph whose while loop is
                                 decided on the device (no host round trip per iteration) */
     int reserved[6];         /* must be zero */
@@ -260,7 +262,7 @@ typedef struct doctors_tuning {
     int tile_x, tile_y;      /* tile of columns */
     int angles_per_block;    /* directions per CTA */
     int sweep_kernel;        /* 1 CUDA-core, 2 tensor-core, 3 chained, 4 dataflow, 5 dataflow with split
-                                transforms (as doctors_options) */
+                                transforms, 6 dataflow with two planes per step (as doctors_options) */
     double ms_per_sweep;     /* measured time of one full sweep of this problem */
     int candidates;          /* schedules timed (0 if taken from the cache) */
 } doctors_tuning;

@@ -52,6 +52,7 @@ constexpr bool kDefaultTensorCoreSweep = false;
 constexpr bool kDefaultChainedSweep = true;
 constexpr bool kDefaultDataflowSweep = true;
 constexpr bool kDefaultSplitSweep = false;
+constexpr bool kDefaultTwoPlaneSweep = false;
 
 int dalloc(void** p, size_t bytes, const char* what) {
     if (bytes == 0) bytes = 16;
@@ -203,6 +204,7 @@ SweepArgs sweep_args(const doctors_problem* p, int reverse, const float* src, fl
     a.flow = (p->use_flow || p->use_split) ? p->d_flow : nullptr;
     a.qang = p->d_qang;
     a.pang = p->d_pang;
+    a.zp = p->flow_zp;
     return a;
 }
 
@@ -211,8 +213,9 @@ SweepArgs sweep_args(const doctors_problem* p, int reverse, const float* src, fl
 cudaError_t launch_sweep(const doctors_problem* p, SweepArgs sw, int mode, cudaStream_t s, int* count) {
     if (p->use_split && mode == 0) return launch_split_sweep(sw, p->M, s, count);
     if (p->use_flow || p->use_split) {
-        // the split path's modes 1 and 2 (stored / paired angular fluence) use the plain dataflow kernel
-        if (p->use_split) sw.chain_slots = p->flow_slots;
+        // modes 1 and 2 (stored / paired angular fluence) of the split and two-plane
+        // paths use the plain dataflow kernel
+        if (p->use_split || (mode != 0 && p->flow_zp != 1)) sw.chain_slots = p->flow_slots;
         *count = 1;
         return launch_sweep_flow(sw, p->M, mode, s);
     }
@@ -504,11 +507,11 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
         set_error("angles_per_block must divide N(N+2)/8 and be one of 1,2,3,4,5,6,7,9,10,12");
         return DOCTORS_ERR_INVALID_ARG;
     }
-    if (kernel < 0 || kernel > 5) {
-        set_error("sweep_kernel must be 0, 1, 2, 3, 4 or 5");
+    if (kernel < 0 || kernel > 6) {
+        set_error("sweep_kernel must be 0 .. 6");
         return DOCTORS_ERR_INVALID_ARG;
     }
-    if ((kernel == 4 || kernel == 5) && !(p->A8 == ab && chain_const_table_ab(ab))) {
+    if (kernel >= 4 && !(p->A8 == ab && chain_const_table_ab(ab))) {
         set_error("dataflow sweep needs whole octants per CTA (angles_per_block = N(N+2)/8) of S2, S4, S6 or S8");
         return DOCTORS_ERR_INVALID_ARG;
     }
@@ -520,7 +523,9 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
     const bool use_tc = kernel == 2 || (kernel == 0 && tc_ok && kDefaultTensorCoreSweep);
     const bool flow_ok = p->A8 == ab && chain_const_table_ab(ab);
     const bool use_split = kernel == 5 || (kernel == 0 && !use_tc && flow_ok && kDefaultSplitSweep);
-    const bool use_flow = !use_split && (kernel == 4 || (kernel == 0 && !use_tc && flow_ok && kDefaultDataflowSweep));
+    const bool use_flow = !use_split && (kernel == 4 || kernel == 6 ||
+                                         (kernel == 0 && !use_tc && flow_ok && kDefaultDataflowSweep));
+    const int zp = kernel == 6 || (kernel == 0 && use_flow && kDefaultTwoPlaneSweep) ? 2 : 1;
     const bool use_chain = !use_tc && !use_flow && !use_split && (kernel == 3 || (kernel == 0 && kDefaultChainedSweep));
     const int ntx = (p->nx + tx - 1) / tx, nty = (p->ny + ty - 1) / ty;
     int chain_slots = 0, flow_slots = 0;
@@ -530,15 +535,17 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
     } else if (use_flow || use_split) {
         int sms = 0;
         CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-        smem = sweep_flow_smem_bytes(ab, tx, ty, p->G, kMaxMat);
+        smem = sweep_flow_smem_bytes(ab, tx, ty, p->G, kMaxMat, zp);
         if (smem <= 227 * 1024) {
-            const int per_sm = sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem, false);
-            const int per_sm_split = use_split ? sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem, true) : per_sm;
-            if (per_sm < 1 || per_sm_split < 1) {
+            const size_t smem1 = sweep_flow_smem_bytes(ab, tx, ty, p->G, kMaxMat, 1);
+            const int per_sm = sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem1, false, 1);
+            const int per_sm_main = use_split ? sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem, true, 1)
+                                  : zp == 2 ? sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem, false, 2) : per_sm;
+            if (per_sm < 1 || per_sm_main < 1) {
                 set_error("dataflow sweep cannot be resident with this tile");
                 return DOCTORS_ERR_INVALID_ARG;
             }
-            chain_slots = sms * per_sm_split;
+            chain_slots = sms * per_sm_main;
             flow_slots = sms * per_sm;
         }
     } else if (use_chain) {
@@ -616,6 +623,7 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
     p->tx = tx; p->ty = ty; p->ab = ab; p->nab = p->A8 / ab; p->ntx = ntx; p->nty = nty; p->use_tc = use_tc;
     p->use_flow = use_flow;
     p->use_split = use_split;
+    p->flow_zp = use_flow ? zp : 1;
     p->chain_slots = chain_slots;
     p->flow_slots = flow_slots;
     return DOCTORS_OK;
@@ -667,7 +675,7 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     p->ab = opt->angles_per_block > 0 ? opt->angles_per_block : default_ab(p->A8);
     // default tile: 8 x 8 for the dataflow sweep (whole octants of S2..S8),
     // 16 x 16 for the stage kernels (the fastest measured shapes)
-    const bool flow_default = opt->sweep_kernel == 4 || opt->sweep_kernel == 5 ||
+    const bool flow_default = opt->sweep_kernel >= 4 ||
                               (opt->sweep_kernel == 0 && kDefaultDataflowSweep && p->A8 == p->ab &&
                                chain_const_table_ab(p->ab));
     const int tdef = flow_default ? 8 : 16;
@@ -685,7 +693,7 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     p->nab = p->A8 / p->ab;
     p->ntx = (p->nx + p->tx - 1) / p->tx;
     p->nty = (p->ny + p->ty - 1) / p->ty;
-    if (opt->sweep_kernel < 0 || opt->sweep_kernel > 5) return fail(DOCTORS_ERR_INVALID_ARG, "sweep_kernel must be 0, 1, 2, 3, 4 or 5");
+    if (opt->sweep_kernel < 0 || opt->sweep_kernel > 6) return fail(DOCTORS_ERR_INVALID_ARG, "sweep_kernel must be 0 .. 6");
     if (opt->sweep_kernel == 2 && !sweep_tc_supported(p->ab, p->M, p->tx, p->ty))
         return fail(DOCTORS_ERR_INVALID_ARG, "tensor-core sweep needs P3, <= 16 directions per block and a 16x16, 32x8, 16x8, 8x16, 8x8 or 8x4 tile");
     cudaError_t e = cudaGetDevice(&p->device);
@@ -1112,10 +1120,11 @@ int doctors_autotune(doctors_problem* p, doctors_tuning* out) {
     best.ms_per_sweep = 1e30;
     int count = 0;
     const int saved[4] = {p->tx, p->ty, p->ab,
-                          p->use_tc ? 2 : p->use_split ? 5 : p->use_flow ? 4 : (p->chain_slots > 0 ? 3 : 1)};
+                          p->use_tc ? 2 : p->use_split ? 5 : p->use_flow ? (p->flow_zp == 2 ? 6 : 4)
+                                                                          : (p->chain_slots > 0 ? 3 : 1)};
     for (const auto& t : tiles) {
         for (int ab : abs_ok) {
-            for (int kernel = 1; kernel <= 5; ++kernel) {
+            for (int kernel = 1; kernel <= 6; ++kernel) {
                 if (kernel == 2 && !sweep_tc_supported(ab, p->M, t[0], t[1])) continue;
                 if (kernel >= 4 && !(p->A8 == ab && chain_const_table_ab(ab))) continue;
                 if (configure_sweep(p, t[0], t[1], ab, kernel) != DOCTORS_OK) continue;

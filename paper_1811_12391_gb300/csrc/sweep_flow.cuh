@@ -50,23 +50,29 @@ __device__ __forceinline__ int flow_stage_tiles(int s, int ntx, int nty) {
 // k_split_d2m after); the sweep reads each cell's angular-source record
 // a.qang and writes its angular-fluence record a.pang, with no moments and
 // no reductions (mode 0 only).
-template <int AB, int M, int MODE, bool SPLIT = false>
+//
+// ZP = 2: each hyperplane step sweeps two consecutive z planes of a column
+// (the second takes the first's fluence as its z inflow), so a task takes
+// ceil(nz / 2) + tx + ty - 2 steps instead of nz + tx + ty - 2; the planes
+// hold both cells' fluxes per column and two face records per edge and step.
+template <int AB, int M, int MODE, bool SPLIT = false, int ZP = 1>
 __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const ChainDirTable dt) {
     static_assert(!SPLIT || MODE == 0, "split transforms sweep in mode 0 only");
+    static_assert(ZP == 1 || (ZP == 2 && !SPLIT), "two planes per step in the fused kernel only");
     constexpr int ABP = flow_abp(AB);
-    constexpr int RS = AB | 1;
+    constexpr int RS = (ZP * AB) | 1;         // a column's record: ZP cells' fluxes (odd length)
     // pipeline depths: face records are fetched PD steps before the step
     // that uses them, source values PDS steps (the split sweep's steps are
     // short, so one step does not cover the memory latency)
     constexpr int PD = 2;                     // face records
-    constexpr int PDS = SPLIT ? 2 : 1;        // source values (registers)
+    constexpr int PDS = (SPLIT || ZP == 2) ? 2 : 1;   // source values (registers)
     extern __shared__ float4 sm4[];
     if (a.skip && *a.skip) return;          // retired instance of a batched loop
     const int PX = chain_px(a.tx);
     const int P = PX * (a.ty + 1);
-    float4* landx = sm4;                                      // [PD][ty][ABP/4] fetched x-face records
-    float4* landy = landx + PD * a.ty * (ABP / 4);            // [PD][tx][ABP/4] fetched y-face records
-    double* leak_s = reinterpret_cast<double*>(landy + PD * a.tx * (ABP / 4));   // [gcount]
+    float4* landx = sm4;                                      // [PD][ZP][ty][ABP/4] fetched x-face records
+    float4* landy = landx + PD * ZP * a.ty * (ABP / 4);       // [PD][ZP][tx][ABP/4] fetched y-face records
+    double* leak_s = reinterpret_cast<double*>(landy + PD * ZP * a.tx * (ABP / 4));   // [gcount]
     float* buf = reinterpret_cast<float*>(leak_s + a.gcount);              // [2][P][RS]
     float* sigt_s = buf + 2 * P * RS;                         // [gcount][nmat]
     int* task_s = reinterpret_cast<int*>(sigt_s + a.gcount * a.nmat);
@@ -104,8 +110,8 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
     int ntasks = 0;
     for (int s = 0; s < nst; ++s) ntasks += flow_stage_tiles(s, a.ntx, a.nty) * 8 * a.gcount;
     // this thread's landing slot for the record used at step st
-    auto land_x = [&](int st) { return landx + ((st & (PD - 1)) * a.ty + lj) * (ABP / 4); };
-    auto land_y = [&](int st) { return landy + ((st & (PD - 1)) * a.tx + li) * (ABP / 4); };
+    auto land_x = [&](int st, int zz) { return landx + (((st & (PD - 1)) * ZP + zz) * a.ty + lj) * (ABP / 4); };
+    auto land_y = [&](int st, int zz) { return landy + (((st & (PD - 1)) * ZP + zz) * a.tx + li) * (ABP / 4); };
     const float qnan = __int_as_float(0x7fffffff);
 
     constexpr int NS = SPLIT ? ABP : M;       // prefetched source values per cell
@@ -202,29 +208,35 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
         // issue the fetch of the face records this thread uses at step st
         // (plane st - d): one commit group per step for every thread
         auto issue_faces = [&](int st) {
-            const int kt = st - d;
-            if (col && kt >= 0 && kt < a.nz) {
-                if (xedge && xi) {
+            const int pt = st - d;
 #pragma unroll
-                    for (int c4 = 0; c4 < ABP / 4; ++c4) cp_async_cg16(land_x(st) + c4, xi + (size_t)kt * ABP + 4 * c4);
-                }
-                if (yedge && yi) {
+            for (int zz = 0; zz < ZP; ++zz) {
+                const int kt = ZP * pt + zz;
+                if (col && pt >= 0 && kt < a.nz) {
+                    if (xedge && xi) {
 #pragma unroll
-                    for (int c4 = 0; c4 < ABP / 4; ++c4) cp_async_cg16(land_y(st) + c4, yi + (size_t)kt * ABP + 4 * c4);
+                        for (int c4 = 0; c4 < ABP / 4; ++c4)
+                            cp_async_cg16(land_x(st, zz) + c4, xi + (size_t)kt * ABP + 4 * c4);
+                    }
+                    if (yedge && yi) {
+#pragma unroll
+                        for (int c4 = 0; c4 < ABP / 4; ++c4)
+                            cp_async_cg16(land_y(st, zz) + c4, yi + (size_t)kt * ABP + 4 * c4);
+                    }
                 }
             }
             asm volatile("cp.async.commit_group;\n" ::: "memory");
         };
         // steps -PD .. -1 only fetch the first records
         for (int st = 0; st < PD - 1; ++st) issue_faces(st);
-        const int hend = a.nz + a.tx + a.ty - 2;
+        const int hend = (a.nz + ZP - 1) / ZP + a.tx + a.ty - 2;
         for (int h = -1; h < hend; ++h) {
             const int cb = h & 1, pb = cb ^ 1;
-            const int kr = h - d;
-            const bool act = col && kr >= 0 && kr < a.nz;
             issue_faces(h + PD);
-            // plane whose incoming faces this thread needs next step
-            const int kf = (h + 1 - d >= 0 && h + 1 - d < a.nz) ? h + 1 - d : -1;
+#pragma unroll
+          for (int zz = 0; zz < ZP; ++zz) {
+            const int kr = ZP * (h - d) + zz;
+            const bool act = col && h >= d && kr < a.nz;
             if (act) {
                 const bool last = kr == a.nz - 1;
                 if constexpr (!SPLIT) {
@@ -239,6 +251,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
 #pragma unroll
                 for (int m = 0; m < NS; ++m) s[m] = sn[m];
                 if (!last) prefetch(kr + PDS);
+                const int zo = zz * AB;               // this cell's fluxes within the column record
                 constexpr int rb = chain_row_base(AB) * 16;
                 // moments -> directions (split: the record already holds them)
                 float psi[AB];
@@ -263,11 +276,11 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
                 float* cv = buf + cb * P * RS;
 #pragma unroll
                 for (int q = 0; q < AB; ++q) {
-                    const float px = pv[xs + q];
-                    const float py = pv[ys + q];
+                    const float px = pv[xs + zo + q];
+                    const float py = pv[ys + zo + q];
                     const float num = fmaf(dt.cz[q], zc[q], fmaf(dt.cy[q], py, fmaf(dt.cx[q], px, psi[q])));
                     psi[q] = num * rcp_approx(sig + dt.csum[q]);
-                    cv[os + q] = psi[q];
+                    cv[os + zo + q] = psi[q];
                     zc[q] = psi[q];
                 }
                 if constexpr (MODE == 1) {
@@ -340,28 +353,34 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
                     lk = 0.0f;
                 }
             }
-            // incoming records of plane kf (fetched PD steps ago): wait until
-            // the producer has written every flux (no NaN left), move them into
-            // the halo read next step and hand the records back to the next
-            // sweep as NaN; zero inflow on the mesh boundary
-            if (col && kf >= 0 && (xedge || yedge)) {
+          }
+            // incoming records of the planes swept next step (fetched PD steps
+            // ago): wait until the producer has written every flux (no NaN
+            // left), move them into the halo and hand the records back to the
+            // next sweep as NaN; zero inflow on the mesh boundary
+            const int pf = h + 1 - d;
+            if (col && pf >= 0 && ZP * pf < a.nz && (xedge || yedge)) {
                 if constexpr (PD == 2) {
                     asm volatile("cp.async.wait_group 1;\n" ::: "memory");
                 } else {
                     cp_async_wait_all();
                 }
                 float* hb = buf + cb * P * RS;
-                for (int side = 0; side < 2; ++side) {
+#pragma unroll
+                for (int zz = 0; zz < ZP; ++zz) {
+                  const int kf = ZP * pf + zz;
+                  if (kf >= a.nz) break;
+                  for (int side = 0; side < 2; ++side) {
                     const bool edge = side == 0 ? xedge : yedge;
                     if (!edge) continue;
-                    const int hs = side == 0 ? xs : ys;
+                    const int hs = (side == 0 ? xs : ys) + zz * AB;
                     float* src = side == 0 ? xi : yi;
                     if (!src) {
 #pragma unroll
                         for (int q = 0; q < AB; ++q) hb[hs + q] = 0.0f;
                         continue;
                     }
-                    float4* land = side == 0 ? land_x(h + 1) : land_y(h + 1);
+                    float4* land = side == 0 ? land_x(h + 1, zz) : land_y(h + 1, zz);
                     const float* lf = reinterpret_cast<const float*>(land);
                     src += (size_t)kf * ABP;
                     bool ok = false;
@@ -383,6 +402,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
                     float4* back = reinterpret_cast<float4*>(src);
 #pragma unroll
                     for (int c4 = 0; c4 < ABP / 4; ++c4) back[c4] = make_float4(qnan, qnan, qnan, qnan);
+                  }
                 }
             }
             __syncthreads();
@@ -487,7 +507,7 @@ __global__ void __launch_bounds__(256) k_split_d2m(const float* pang, float* mom
 }
 
 template <int M>
-int sweep_flow_blocks_per_sm(int ab, int threads, size_t smem, bool split) {
+int sweep_flow_blocks_per_sm(int ab, int threads, size_t smem, bool split, int zp) {
     int b = 0;
     cudaError_t e = cudaErrorInvalidValue;
     auto query = [&](auto kern) {
@@ -495,13 +515,20 @@ int sweep_flow_blocks_per_sm(int ab, int threads, size_t smem, bool split) {
                              : cudaSuccess;
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, smem);
     };
+#define DOCTORS_FLOW_OCC(AB)                                                            \
+    case AB:                                                                            \
+        if (split) query(k_sweep_flow<AB, M, 0, true>);                                  \
+        else if (zp == 2) query(k_sweep_flow<AB, M, 0, false, 2>);                       \
+        else query(k_sweep_flow<AB, M, 0>);                                              \
+        break;
     switch (ab) {
-        case 1: split ? query(k_sweep_flow<1, M, 0, true>) : query(k_sweep_flow<1, M, 0>); break;
-        case 3: split ? query(k_sweep_flow<3, M, 0, true>) : query(k_sweep_flow<3, M, 0>); break;
-        case 6: split ? query(k_sweep_flow<6, M, 0, true>) : query(k_sweep_flow<6, M, 0>); break;
-        case 10: split ? query(k_sweep_flow<10, M, 0, true>) : query(k_sweep_flow<10, M, 0>); break;
+        DOCTORS_FLOW_OCC(1)
+        DOCTORS_FLOW_OCC(3)
+        DOCTORS_FLOW_OCC(6)
+        DOCTORS_FLOW_OCC(10)
         default: break;
     }
+#undef DOCTORS_FLOW_OCC
     return e == cudaSuccess ? b : 0;
 }
 
@@ -561,19 +588,31 @@ cudaError_t launch_sweep_flow_m(const SweepArgs& a, cudaStream_t s) {
     }
     const int grid = ntasks < a.chain_slots ? ntasks : a.chain_slots;
     const int T = a.tx * a.ty;
-    const size_t smem = sweep_flow_smem_bytes(a.ab, a.tx, a.ty, a.gcount, a.nmat);
+    const int zp = (MODE == 0 && a.zp == 2) ? 2 : 1;
+    const size_t smem = sweep_flow_smem_bytes(a.ab, a.tx, a.ty, a.gcount, a.nmat, zp);
     cudaError_t e = cudaSuccess;
     auto launch = [&](auto kern) {
         if (smem > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess) kern<<<grid, T, smem, s>>>(a, *a.dir_table);
     };
+#define DOCTORS_FLOW_CASE(AB)                                                           \
+    case AB:                                                                            \
+        if constexpr (MODE == 0) {                                                      \
+            if (zp == 2) {                                                              \
+                launch(k_sweep_flow<AB, M, 0, false, 2>);                                \
+                break;                                                                  \
+            }                                                                           \
+        }                                                                               \
+        launch(k_sweep_flow<AB, M, MODE>);                                               \
+        break;
     switch (a.ab) {
-        case 1: launch(k_sweep_flow<1, M, MODE>); break;
-        case 3: launch(k_sweep_flow<3, M, MODE>); break;
-        case 6: launch(k_sweep_flow<6, M, MODE>); break;
-        case 10: launch(k_sweep_flow<10, M, MODE>); break;
+        DOCTORS_FLOW_CASE(1)
+        DOCTORS_FLOW_CASE(3)
+        DOCTORS_FLOW_CASE(6)
+        DOCTORS_FLOW_CASE(10)
         default: return cudaErrorInvalidValue;
     }
+#undef DOCTORS_FLOW_CASE
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

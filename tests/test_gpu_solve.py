@@ -58,11 +58,13 @@ def cylinder_ref():
                                             ((8, 4), 5, 2), ((8, 4), 5, 3), ((5, 7), 2, 1), ((5, 7), 2, 3),
                                             ((32, 8), 10, 2), ((32, 8), 10, 3), ((8, 16), 10, 2), ((16, 2), 1, 3),
                                             ((16, 16), 10, 4), ((16, 8), 10, 4), ((5, 7), 10, 4), ((8, 4), 10, 4),
-                                            ((8, 8), 10, 5), ((16, 8), 10, 5), ((5, 7), 10, 5)])
+                                            ((8, 8), 10, 5), ((16, 8), 10, 5), ((5, 7), 10, 5),
+                                            ((8, 8), 10, 6), ((16, 8), 10, 6), ((5, 7), 10, 6)])
 def test_ragged_multitile_cylinder(dp, cylinder_ref, tile, ab, kernel):
     """Several sweep tiles with ragged tails in x and y, S8 P3, with the
-    CUDA-core (1), tensor-core (2), chained (3), dataflow (4) and dataflow
-    with split transforms (5) sweeps."""
+    CUDA-core (1), tensor-core (2), chained (3), dataflow (4), dataflow
+    with split transforms (5) and dataflow with two z planes per step (6;
+    odd plane counts are in test_degenerate_meshes) sweeps."""
     p, sol = cylinder_ref
     d = dp(p, tol=1e-6, max_iters=400, tile=tile, angles_per_block=ab, sweep_kernel=kernel)
     _compare(d, p, sol, f"cylinder tile={tile} ab={ab} kernel={kernel}")
@@ -85,12 +87,12 @@ def test_sweep_kernels_agree(dp):
     cylinder (one sweep from the first-collision source)."""
     p = ph.water_cylinder()
     outs = []
-    for kernel in (1, 2, 3, 4, 5):
+    for kernel in (1, 2, 3, 4, 5, 6):
         d = dp(p, tol=1e-6, max_iters=1, sweep_kernel=kernel, angles_per_block=10)
         d.solve(allow_not_converged=True)
         outs.append(d.fluence_host(1))
         d.close()
-    for k in (1, 2, 3, 4):
+    for k in (1, 2, 3, 4, 5):
         assert max_rel(outs[k], outs[0]) <= 2e-5
 
 
@@ -118,7 +120,7 @@ def test_infinite_medium_volume_source(dp):
     d.close()
 
 
-@pytest.mark.parametrize("kernel", [1, 3, 4, 5])
+@pytest.mark.parametrize("kernel", [1, 3, 4, 5, 6])
 def test_degenerate_meshes(dp, kernel):
     """Single voxel, single column and single plane meshes."""
     for dims in ((1, 1, 1), (1, 1, 7), (5, 1, 1), (4, 6, 1)):
@@ -176,7 +178,7 @@ def test_iteration_cap_reports_not_converged(dp):
     from paper_1811_12391_gb300 import _lib as C
     p = ph.tiny_cube(n=8)
     ref = osv.solve(p, tol=1e-11)
-    for device_loop, kernel in ((0, 0), (1, 0), (1, 4), (0, 5), (1, 5)):
+    for device_loop, kernel in ((0, 0), (1, 0), (1, 4), (0, 5), (1, 5), (0, 6), (1, 6)):
         d = dp(p, tol=1e-6, max_iters=3, device_loop=device_loop, sweep_kernel=kernel, angles_per_block=3)
         with pytest.raises(C.DoctorsError) as e:
             d.solve()
