@@ -231,8 +231,9 @@ inline size_t sweep_chain_smem_bytes(int ab, int tx, int ty, int cmax, int gcoun
 // hyperplanes, sigma_t of the swept groups and the task slot
 inline int flow_abp_host(int ab) { return (ab + 3) & ~3; }
 inline size_t sweep_flow_smem_bytes(int ab, int tx, int ty, int gcount, int nmat, int zp = 1) {
-    // two landing slots (pipeline depth 2) of zp records per edge column
-    return 2 * (size_t)zp * 4 * (tx + ty) * flow_abp_host(ab) + 8 * (size_t)gcount +
+    // prefetched source moments (2 slots of 16 floats per thread), two landing
+    // slots (pipeline depth 2) of zp records per edge column, ...
+    return 2 * 16 * 4 * (size_t)tx * ty + 2 * (size_t)zp * 4 * (tx + ty) * flow_abp_host(ab) + 8 * (size_t)gcount +
            4 * ((size_t)2 * chain_rs(zp * ab) * chain_px(tx) * (ty + 1) + (size_t)gcount * nmat) + 16;
 }
 int sweep_flow_blocks_per_sm(int ab, int M, int threads, size_t smem, bool split = false, int zp = 1);

@@ -56,7 +56,8 @@ __device__ __forceinline__ int flow_stage_tiles(int s, int ntx, int nty) {
 // ceil(nz / 2) + tx + ty - 2 steps instead of nz + tx + ty - 2; the planes
 // hold both cells' fluxes per column and two face records per edge and step.
 template <int AB, int M, int MODE, bool SPLIT = false, int ZP = 1>
-__global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const ChainDirTable dt) {
+__global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2)
+    k_sweep_flow(const SweepArgs a, const ChainDirTable dt) {
     static_assert(!SPLIT || MODE == 0, "split transforms sweep in mode 0 only");
     static_assert(ZP == 1 || (ZP == 2 && !SPLIT), "two planes per step in the fused kernel only");
     constexpr int ABP = flow_abp(AB);
@@ -66,11 +67,15 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
     // short, so one step does not cover the memory latency)
     constexpr int PD = 2;                     // face records
     constexpr int PDS = (SPLIT || ZP == 2) ? 2 : 1;   // source values (registers)
+    // fused one-plane kernel: the next cell's source moments go to shared
+    // memory by cp.async (no registers held for them across the step)
+    constexpr bool SMEMPF = !SPLIT && ZP == 1 && M % 4 == 0;
     extern __shared__ float4 sm4[];
     if (a.skip && *a.skip) return;          // retired instance of a batched loop
     const int PX = chain_px(a.tx);
     const int P = PX * (a.ty + 1);
-    float4* landx = sm4;                                      // [PD][ZP][ty][ABP/4] fetched x-face records
+    float4* momst = sm4;                                      // [2][blockDim][16] prefetched source moments
+    float4* landx = momst + 2 * blockDim.x * 4;               // [PD][ZP][ty][ABP/4] fetched x-face records
     float4* landy = landx + PD * ZP * a.ty * (ABP / 4);       // [PD][ZP][tx][ABP/4] fetched y-face records
     double* leak_s = reinterpret_cast<double*>(landy + PD * ZP * a.tx * (ABP / 4));   // [gcount]
     float* buf = reinterpret_cast<float*>(leak_s + a.gcount);              // [2][P][RS]
@@ -175,6 +180,12 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
                     const float4 t4 = __ldg(r4 + c4);
                     dst[4 * c4] = t4.x; dst[4 * c4 + 1] = t4.y; dst[4 * c4 + 2] = t4.z; dst[4 * c4 + 3] = t4.w;
                 }
+            } else if constexpr (SMEMPF) {
+                float4* slot = momst + ((kn & 1) * blockDim.x + threadIdx.x) * 4;
+                const float* srcm = a.src + (gV + v) * M;
+#pragma unroll
+                for (int c4 = 0; c4 < M / 4; ++c4) cp_async_cg16(slot + c4, srcm + 4 * c4);
+                (void)dst;
             } else {
                 float tmp[M];
                 load_moments<M>(a.src + (gV + v) * M, tmp);
@@ -202,6 +213,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
                 if (a.nz > 1) fetch(1, sn2, rho_n2, mat_n2);
             }
         }
+        if constexpr (SMEMPF) asm volatile("cp.async.commit_group;\n" ::: "memory");
 #pragma unroll
         for (int q = 0; q < AB; ++q) zc[q] = 0.0f;
 
@@ -232,6 +244,17 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
         const int hend = (a.nz + ZP - 1) / ZP + a.tx + a.ty - 2;
         for (int h = -1; h < hend; ++h) {
             const int cb = h & 1, pb = cb ^ 1;
+            float sig_cur = 0.0f;
+            if constexpr (SMEMPF) {
+                // this step's cross section, then the next cell's moments (their own
+                // commit group, ahead of the face records of this step)
+                const int kr0 = h - d;
+                if (col && kr0 >= 0 && kr0 < a.nz) {
+                    sig_cur = rho_n * sigt_s[gi * a.nmat + mat_n];
+                    if (kr0 + 1 < a.nz) fetch(kr0 + 1, sn, rho_n, mat_n);
+                }
+                asm volatile("cp.async.commit_group;\n" ::: "memory");
+            }
             issue_faces(h + PD);
 #pragma unroll
           for (int zz = 0; zz < ZP; ++zz) {
@@ -239,18 +262,31 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
             const bool act = col && h >= d && kr < a.nz;
             if (act) {
                 const bool last = kr == a.nz - 1;
-                if constexpr (!SPLIT) {
-#pragma unroll
-                    for (int m = 0; m < NS; ++m) sn[m] *= octant_sign<M>(m, fx, fy, fz);
-                }
-                const float sig = rho_n * sigt_s[gi * a.nmat + mat_n];
                 const int k = sz > 0 ? kr : a.nz - 1 - kr;
                 const size_t v = (size_t)k * nxy + vcol;
                 const size_t mo = (gV + v) * M;
                 float s[NS];
+                float sig;
+                if constexpr (SMEMPF) {
+                    sig = sig_cur;
+                    const float4* slot = momst + ((kr & 1) * blockDim.x + threadIdx.x) * 4;
 #pragma unroll
-                for (int m = 0; m < NS; ++m) s[m] = sn[m];
-                if (!last) prefetch(kr + PDS);
+                    for (int c4 = 0; c4 < M / 4; ++c4) {
+                        const float4 t4 = slot[c4];
+                        s[4 * c4] = t4.x; s[4 * c4 + 1] = t4.y; s[4 * c4 + 2] = t4.z; s[4 * c4 + 3] = t4.w;
+                    }
+#pragma unroll
+                    for (int m = 0; m < NS; ++m) s[m] *= octant_sign<M>(m, fx, fy, fz);
+                } else {
+                    if constexpr (!SPLIT) {
+#pragma unroll
+                        for (int m = 0; m < NS; ++m) sn[m] *= octant_sign<M>(m, fx, fy, fz);
+                    }
+                    sig = rho_n * sigt_s[gi * a.nmat + mat_n];
+#pragma unroll
+                    for (int m = 0; m < NS; ++m) s[m] = sn[m];
+                    if (!last) prefetch(kr + PDS);
+                }
                 const int zo = zz * AB;               // this cell's fluxes within the column record
                 constexpr int rb = chain_row_base(AB) * 16;
                 // moments -> directions (split: the record already holds them)
@@ -359,6 +395,10 @@ __global__ void __launch_bounds__(256, 2) k_sweep_flow(const SweepArgs a, const 
             // left), move them into the halo and hand the records back to the
             // next sweep as NaN; zero inflow on the mesh boundary
             const int pf = h + 1 - d;
+            if constexpr (SMEMPF) {
+                // the next cell's moments (and the faces fetched a step ago) have landed
+                asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+            }
             if (col && pf >= 0 && ZP * pf < a.nz && (xedge || yedge)) {
                 if constexpr (PD == 2) {
                     asm volatile("cp.async.wait_group 1;\n" ::: "memory");
