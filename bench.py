@@ -48,8 +48,7 @@ SWEEP_TRAFFIC = {
     (16, 16, 5, 1): (1687.6e6, "sweep_impl.cuh", "592eff4d10129e1bde8b55aecdf9fbf52f768e8c"),
     (16, 16, 10, 2): (2121.9e6, "sweep_tc.cu", "79ec5703826b205c1bdc9d4f7ff57c205fec428a"),
     (16, 8, 10, 3): (2534.9e6, "sweep_chain.cuh", "3502773d12d37fb58b50dbc1187553785b1df685"),
-    (8, 8, 10, 4): (2963.0e6, "sweep_flow.cuh", "936b4ea6dba4536cc7dbc8e72dcee44bc5a75b02"),
-    (8, 8, 10, 5): (4668.5e6, "sweep_flow.cuh", "936b4ea6dba4536cc7dbc8e72dcee44bc5a75b02"),
+    (8, 8, 10, 4): (3143.6e6, "sweep_flow.cuh", "e12ca326980e8536d967d4f9ac393409447e53dc"),
 }
 
 # sweep kernel by the library's sweep_kernel code
@@ -371,6 +370,16 @@ def main():
             adjoint = {"ms_per_solve": g["result"]["ms_total"], "iterations": g["result"]["iterations"],
                        "gradients": "view weights, spectrum, densities"}
         d.close()
+        plain = None
+        if not args.no_extra:
+            # the plain single-instance solve: tile-stage kernel, default schedule, no autotuning
+            q = DoctorsProblem(p, stream=stream, tol=1e-6, max_iters=500, sweep_kernel=1)
+            q.solve()
+            rp = q.solve()
+            q.close()
+            plain = {"kernel": "k_sweep (tile stages, default 16x16 tiles, whole octants per CTA)",
+                     "ms_per_solve": rp["ms_total"], "ms_per_sweep": rp["ms_sweep"] / rp["iterations"],
+                     "speedup_of_the_timed_solve": rp["ms_total"] / (ms_max / args.steps)}
         batched = None if (args.no_extra or world > 1) else bench_batched(torch, DoctorsProblem, ph, stream)
         others = None if (args.no_extra or world > 1) else bench_configs(torch, DoctorsProblem, ph, stream)
         paper = None if (args.no_extra or world > 1) else bench_paper_workloads(torch, DoctorsProblem, ph, stream)
@@ -429,6 +438,7 @@ def main():
         "clocks": clocks,
         "autotune": tuning,
         "adjoint": adjoint,
+        "plain_single_instance_solve": plain,
         "batched_axial_scan": batched,
         "other_workloads": others,
         "paper_workloads": paper,
