@@ -240,6 +240,74 @@ __global__ void __launch_bounds__(kScatterThreads, 3) k_scatter(const ScatterArg
     }
 }
 
+// The iteration's form of the same map (a scattering term, no isotropic
+// terms, fewer than 2^31 entries) with no branch in its group loops: the
+// direction of the sum (downscatter or its transpose) and the presence of a
+// fixed source are template parameters, the group window only predicates the
+// loads of the fixed source and the stores, and entry indices are 32-bit.  The
+// inner sums are those of k_scatter term by term, so the two kernels give
+// identical results.  Every source group below G is needed by some group of
+// the window (the forward window only retires leading groups, the adjoint
+// window trailing ones), so all G source moments are loaded; padding groups up
+// to GMAX read group G-1's row again and are zeroed.
+__device__ __forceinline__ float ldg_if(const float* p, bool pred) {
+    float x = 0.0f;
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.nc.f32 %0, [%1];\n\t}"
+        : "+f"(x)
+        : "l"(p), "r"((unsigned)pred));
+    return x;
+}
+
+template <int GMAX, bool TR, bool HAS_BASE>
+__global__ void __launch_bounds__(kScatterThreads, GMAX <= 24 ? 3 : GMAX <= 32 ? 2 : 1) k_scatter_fast(const ScatterArgs a) {
+    extern __shared__ float tab_s[];
+    if (a.skip && *a.skip) return;
+    const int G = a.G;
+    constexpr int BP = scatter_block_pitch<GMAX>();
+    const int nblk = a.nmat * (a.L + 1);
+    for (int e = threadIdx.x; e < nblk * BP; e += blockDim.x) {
+        const int blk = e / BP, r = e % BP, i = r / GMAX, j = r % GMAX;
+        tab_s[e] = (r < GMAX * GMAX && i < G && j < G) ? __ldg(a.sigs + ((size_t)blk * G + i) * G + j) : 0.0f;
+    }
+    __syncthreads();
+    const unsigned VM = (unsigned)(a.V * a.M), M = (unsigned)a.M;
+    const int g_beg = a.g0, g_end = a.g1 > 0 ? a.g1 : G;
+    const int L1 = a.L + 1;
+    // no barrier below: threads leave the grid-stride loop independently
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < VM; t += gridDim.x * blockDim.x) {
+        const unsigned v = t / M;
+        const int lm = (int)(t - v * M);
+        const int mb = __ldg(a.mat + v) * L1 + degree_of_lm(lm_of_pos(lm, (int)M));
+        const float r = __ldg(a.rho + v);
+        float ph[GMAX];
+        const float* pp = a.phi + t;
+#pragma unroll
+        for (int gp = 0; gp < GMAX; ++gp) {
+            const float x = __ldg(pp + (size_t)(gp < G ? gp : G - 1) * VM);
+            ph[gp] = gp < G ? x : 0.0f;
+        }
+        float qb[GMAX];
+        const float* pb = a.base + t;
+#pragma unroll
+        for (int g = 0; g < GMAX; ++g) qb[g] = HAS_BASE ? ldg_if(pb + (size_t)g * VM, g >= g_beg && g < g_end) : 0.0f;
+        const float* ts = tab_s + mb * BP;
+        float* po = a.out + t;
+#pragma unroll
+        for (int g = 0; g < GMAX; ++g) {
+            float acc = 0.0f;
+            if (!TR) {
+#pragma unroll
+                for (int gp = 0; gp <= g; ++gp) acc = fmaf(ts[gp * GMAX + g], ph[gp], acc);
+            } else {
+#pragma unroll
+                for (int gp = g; gp < GMAX; ++gp) acc = fmaf(ts[g * GMAX + gp], ph[gp], acc);
+            }
+            const float out = fmaf(r, acc, qb[g]);
+            if (g >= g_beg && g < g_end) po[(size_t)g * VM] = out;
+        }
+    }
+}
+
 template <int NV>
 __device__ __forceinline__ void block_reduce_add(double (&x)[NV], double* dst) {
     __shared__ double red[NV][32];
@@ -372,11 +440,36 @@ unsigned blocks_for(size_t n, int bs, unsigned cap = 0) {
 
 }  // namespace
 
+// one resident wave of k_scatter_fast
+template <int GMAX, bool TR, bool HAS_BASE>
+cudaError_t launch_scatter_fast(const ScatterArgs& a, size_t smem, cudaStream_t s) {
+    auto kern = k_scatter_fast<GMAX, TR, HAS_BASE>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int nb = 0, dev = 0, nsm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kScatterThreads, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = blocks_for(a.V * a.M, kScatterThreads, (unsigned)(nsm * (nb > 0 ? nb : 1)));
+    kern<<<grid, kScatterThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int GMAX>
 cudaError_t launch_scatter_g(const ScatterArgs& a, cudaStream_t s) {
     const size_t tab_bytes = scatter_table_bytes<GMAX>(a);
     const int staged = tab_bytes <= kScatterTableSmem ? 1 : 0;
     const size_t smem = staged ? tab_bytes : 0;
+    if (staged && a.phi && !a.iso && !a.iso_field && a.V * a.M < ((size_t)1 << 31)) {
+        if (a.transpose)
+            return a.base ? launch_scatter_fast<GMAX, true, true>(a, smem, s)
+                          : launch_scatter_fast<GMAX, true, false>(a, smem, s);
+        return a.base ? launch_scatter_fast<GMAX, false, true>(a, smem, s)
+                      : launch_scatter_fast<GMAX, false, false>(a, smem, s);
+    }
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_scatter<GMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
