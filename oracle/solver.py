@@ -15,7 +15,9 @@ steps in order:
    scattering kernel as a Legendre expansion: the moment source
    s_lm[g](v) = rho(v) sum_{g' <= g} sigma_s,l(g' -> g) (phi_c + phi_u)_lm[g'](v)
    is mapped to directions with (2l+1)/(4 pi) R_lm(Omega_n) and swept with
-   step differencing; moments are summed with w_n R_lm(Omega_n) (Eq. 3).
+   step differencing (or, when the problem asks for it, diamond differencing
+   without a negative-flux fixup); moments are summed with w_n R_lm(Omega_n)
+   (Eq. 3).
    Reading of the unstated iteration: groups are solved from high to low
    energy (Gauss-Seidel); within a group, unaccelerated source iteration until
    the relative L2 change of the scalar fluence is below tol.
@@ -124,6 +126,11 @@ class Solution:
         return self.phi_u + self.phi_c[:, 0, :]
 
 
+def diamond(p) -> bool:
+    """Whether the problem asks for diamond differencing (differencing = 1)."""
+    return bool(getattr(p, "differencing", 0))
+
+
 def external_moments(p) -> np.ndarray:
     """Moment source of volumetric sources: s_00[g] = weight * chi_g per cm^3."""
     E = np.zeros((p.G, quad.n_moments(p.legendre), p.V))
@@ -143,7 +150,7 @@ def _iterate(p, fixed: np.ndarray, self_op, dirs, w, Mop, Dop, sigt_v, tol, max_
     it = 0
     while True:
         s = fixed + self_op(phi)
-        new, leak, psi = tr.sweep(dims, sp, dirs, w, Mop, Dop, sigt_v, s, store_psi)
+        new, leak, psi = tr.sweep(dims, sp, dirs, w, Mop, Dop, sigt_v, s, store_psi, diamond(p))
         it += 1
         nrm = np.linalg.norm(new[0])
         eps = 0.0 if nrm == 0.0 else np.linalg.norm(new[0] - phi[0]) / nrm
@@ -192,7 +199,7 @@ def solve(p, tol: float = 1e-10, max_iters: int = 100000, store_psi: bool = Fals
         if store_psi:
             # one more sweep with the converged source to store the angular fluence
             _, _, psi = tr.sweep((p.nx, p.ny, p.nz), (p.dx, p.dy, p.dz), dirs, w, Mop, Dop,
-                                 sigt_v, fixed + scatter(p, phi, g, g), True)
+                                 sigt_v, fixed + scatter(p, phi, g, g), True, diamond(p))
             psi_all[g] = psi
     return Solution(phi_u=phi_u, U=U, phi_c=phi_c, iters=iters, leak=leaks, balance=bals,
                     source=srcs, per_source_phi_u=per, psi=psi_all)
@@ -215,8 +222,9 @@ class AdjointSolution:
 def adjoint_solve(p, r: np.ndarray, tol: float = 1e-10, max_iters: int = 100000,
                   store_psi: bool = False) -> AdjointSolution:
     """Adjoint of the collided problem for the response r[g][v] on the scalar
-    fluence.  The discrete adjoint of the step-differenced sweep of direction
-    n is the same sweep along -Omega_n; the adjoint moment equation is
+    fluence.  The discrete adjoint of the sweep of direction n (step or
+    diamond differenced, on a uniform mesh) is the same sweep along -Omega_n;
+    the adjoint moment equation is
       Z = D L^-T M (4 pi r delta_{lm,00} + S^T Z),
     solved from low to high energy (S^T couples each group to lower-energy
     groups)."""
@@ -240,7 +248,8 @@ def adjoint_solve(p, r: np.ndarray, tol: float = 1e-10, max_iters: int = 100000,
         iters.append(it)
         if store_psi:
             _, _, psi = tr.sweep((p.nx, p.ny, p.nz), (p.dx, p.dy, p.dz), rdirs, w, Mop, Dop,
-                                 sigt_v, fixed + scatter(p, phi, g, g, transpose=True), True)
+                                 sigt_v, fixed + scatter(p, phi, g, g, transpose=True), True,
+                                 diamond(p))
             psi_all[g] = psi
     T = np.zeros_like(Z)
     for g in range(G):

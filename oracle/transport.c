@@ -198,22 +198,34 @@ void oracle_collimator_mask(int nx, int ny, int nz, const float *o, const float 
 /* One transport sweep of one group (Eq. 2) for a given moment source.       */
 /* For every direction n:                                                    */
 /*   q_n(v) = sum_lm Mop[n][lm] src[lm][v]      (Legendre scattering source) */
-/*   step differencing, vacuum inflow: with c_q = |Omega_q| / d_q,           */
-/*   psi(v) = (q_n(v) + sum_q c_q psi_in,q) / (sigt(v) + sum_q c_q),          */
-/*   where psi_in,q is psi of the upwind neighbour along q (0 outside)        */
+/*   with c_q = |Omega_q| / d_q and psi_in,q the flux entering through the   */
+/*   upwind face along q (0 on the mesh boundary: vacuum inflow):           */
+/*   diamond = 0, step differencing: every outgoing face flux equals the     */
+/*     cell flux,  psi(v) = (q_n(v) + sum_q c_q psi_in,q) / (sigt(v) + sum_q c_q);   */
+/*   diamond = 1, diamond difference (no negative-flux fixup): the cell      */
+/*     balance  sum_q c_q (psi_out,q - psi_in,q) + sigt(v) psi(v) = q_n(v)    */
+/*     with the cell flux the mean of each face pair, psi(v) =                */
+/*     (psi_in,q + psi_out,q) / 2, so                                         */
+/*     psi(v) = (q_n(v) + 2 sum_q c_q psi_in,q) / (sigt(v) + 2 sum_q c_q),    */
+/*     psi_out,q = 2 psi(v) - psi_in,q;                                       */
 /*   phi[lm][v] += Dop[n][lm] psi(v)            (Eq. 3 for lm = 00)          */
 /* The outgoing current through the mesh boundary is summed into *leak:     */
-/*   w_n |Omega_q| psi(v) A_q over boundary faces (A_q the face area).        */
+/*   w_n |Omega_q| psi_out,q(v) A_q over boundary faces (A_q the face area).  */
 /* If psi_out is given, psi of every direction is stored there [A][V].      */
 /* ------------------------------------------------------------------------ */
 void oracle_sweep(int nx, int ny, int nz, double dx, double dy, double dz,
                   int A, const double *dirs /* [A][3] */, const double *w /* [A] */,
                   int M, const double *Mop /* [A][M] */, const double *Dop /* [A][M] */,
                   const double *sigt /* [V] */, const double *src /* [M][V] */,
-                  double *phi /* [M][V] */, double *leak, double *psi_out /* [A][V] or NULL */)
+                  double *phi /* [M][V] */, double *leak, double *psi_out /* [A][V] or NULL */,
+                  int diamond)
 {
     size_t V = (size_t)nx * ny * nz;
     double *psi = (double *)malloc(sizeof(double) * V);
+    /* outgoing face fluxes along x, y, z of every cell of the current direction */
+    double *fx = (double *)malloc(sizeof(double) * V);
+    double *fy = (double *)malloc(sizeof(double) * V);
+    double *fz = (double *)malloc(sizeof(double) * V);
     memset(phi, 0, sizeof(double) * V * (size_t)M);
     double lk = 0.0;
     for (int n = 0; n < A; ++n) {
@@ -231,14 +243,23 @@ void oracle_sweep(int nx, int ny, int nz, double dx, double dy, double dz,
                     size_t v = IDX(i, j, k);
                     double q = 0.0;
                     for (int lm = 0; lm < M; ++lm) q += Mop[(size_t)n * M + lm] * src[(size_t)lm * V + v];
-                    double px = ii > 0 ? psi[IDX(i - di, j, k)] : 0.0;
-                    double py = jj > 0 ? psi[IDX(i, j - dj, k)] : 0.0;
-                    double pz = kk > 0 ? psi[IDX(i, j, k - dk)] : 0.0;
-                    double p = (q + cx * px + cy * py + cz * pz) / (sigt[v] + cx + cy + cz);
+                    double px = ii > 0 ? fx[IDX(i - di, j, k)] : 0.0;
+                    double py = jj > 0 ? fy[IDX(i, j - dj, k)] : 0.0;
+                    double pz = kk > 0 ? fz[IDX(i, j, k - dk)] : 0.0;
+                    double p;
+                    if (diamond) {
+                        p = (q + 2.0 * (cx * px + cy * py + cz * pz)) / (sigt[v] + 2.0 * (cx + cy + cz));
+                        fx[v] = 2.0 * p - px;
+                        fy[v] = 2.0 * p - py;
+                        fz[v] = 2.0 * p - pz;
+                    } else {
+                        p = (q + cx * px + cy * py + cz * pz) / (sigt[v] + cx + cy + cz);
+                        fx[v] = fy[v] = fz[v] = p;
+                    }
                     psi[v] = p;
-                    if (ii == nx - 1) lk += w[n] * fabs(ox) * p * dy * dz;
-                    if (jj == ny - 1) lk += w[n] * fabs(oy) * p * dx * dz;
-                    if (kk == nz - 1) lk += w[n] * fabs(oz) * p * dx * dy;
+                    if (ii == nx - 1) lk += w[n] * fabs(ox) * fx[v] * dy * dz;
+                    if (jj == ny - 1) lk += w[n] * fabs(oy) * fy[v] * dx * dz;
+                    if (kk == nz - 1) lk += w[n] * fabs(oz) * fz[v] * dx * dy;
                 }
             }
         }
@@ -251,6 +272,9 @@ void oracle_sweep(int nx, int ny, int nz, double dx, double dy, double dz,
     }
     *leak = lk;
     free(psi);
+    free(fx);
+    free(fy);
+    free(fz);
 }
 
 /* Back-projection along the rays for the density gradient of the

@@ -54,7 +54,7 @@ def lib():
             L.oracle_collimator_mask.restype = None
             L.oracle_sweep.argtypes = [_int, _int, _int, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, _int, _d, _d, _int, _d, _d, _d, _d, _d,
-                                       _d, _d]
+                                       _d, _d, _int]
             L.oracle_sweep.restype = None
             L.oracle_backproject.argtypes = [_int, _int, _int, _d, _d, _u8, _int, _d, _d, _d]
             L.oracle_backproject.restype = _int
@@ -127,8 +127,9 @@ def collimator_mask(dims, origin, spacing, S, axis, perp, up, tan_half, z_slope)
     return W
 
 
-def sweep(dims, spacing, dirs, w, Mop, Dop, sigt, src, store_psi=False):
-    """One sweep of one group; returns (phi [M][V], leakage, psi [A][V] or None)."""
+def sweep(dims, spacing, dirs, w, Mop, Dop, sigt, src, store_psi=False, diamond=False):
+    """One sweep of one group; returns (phi [M][V], leakage, psi [A][V] or None).
+    diamond selects diamond differencing instead of step differencing."""
     nx, ny, nz = dims
     V = nx * ny * nz
     A = dirs.shape[0]
@@ -145,7 +146,7 @@ def sweep(dims, spacing, dirs, w, Mop, Dop, sigt, src, store_psi=False):
     lib().oracle_sweep(nx, ny, nz, float(spacing[0]), float(spacing[1]), float(spacing[2]), A,
                        _p(dirs, _d), _p(w, _d), M, _p(Mop, _d), _p(Dop, _d), _p(sigt, _d),
                        _p(src, _d), _p(phi, _d), _p(leak, _d),
-                       _p(psi, _d) if psi is not None else None)
+                       _p(psi, _d) if psi is not None else None, int(bool(diamond)))
     return phi, float(leak[0]), psi
 
 

@@ -85,6 +85,7 @@ class Problem:
     tol: float = 1e-8
     max_iters: int = 500
     roi: Optional[np.ndarray] = None  # bool [V]
+    differencing: int = 0            # spatial scheme of the sweep: 0 step, 1 diamond
 
     @property
     def G(self) -> int:

@@ -28,9 +28,12 @@ def _roi(p):
     return roi
 
 
-def test_reciprocity_collided_response():
-    """<r, phi_c,00> = sum_{g,lm,v} (2l+1)/(4 pi) (S^T Z)[g][lm][v] U[g][lm][v]."""
+@pytest.mark.parametrize("differencing", [0, 1])
+def test_reciprocity_collided_response(differencing):
+    """<r, phi_c,00> = sum_{g,lm,v} (2l+1)/(4 pi) (S^T Z)[g][lm][v] U[g][lm][v],
+    for step and diamond differencing."""
     p = _small()
+    p.differencing = differencing
     roi = _roi(p)
     sol = osv.solve(p, tol=1e-13)
     r = osv.response_from_roi(p, roi)
@@ -61,8 +64,13 @@ def _J(p, roi):
     return osv.roi_dose(p, roi, tol=1e-13)
 
 
-def test_gradients_match_central_differences():
+@pytest.mark.parametrize("differencing", [0, 1])
+def test_gradients_match_central_differences(differencing):
+    """View-weight, spectrum and density gradients by the adjoint against
+    central differences of the forward solve (step and diamond differencing:
+    the density enters both schemes' cell balance only through sigma_t psi)."""
     p = _small()
+    p.differencing = differencing
     roi = _roi(p)
     gr = osv.gradients(p, roi, tol=1e-13)
     assert abs(gr["J"] - _J(p, roi)) < 1e-12 * abs(gr["J"])
