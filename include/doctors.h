@@ -68,6 +68,10 @@ extern "C" {
 #define DOCTORS_FLUENCE_TOTAL       2
 #define DOCTORS_FLUENCE_ADJOINT     3   /* adjoint scalar fluence (importance) of the last adjoint solve */
 
+/* spatial differencing of the sweep (doctors_options.differencing) */
+#define DOCTORS_DIFF_STEP     0
+#define DOCTORS_DIFF_DIAMOND  1
+
 /* Voxel mesh (Sec. II.D: Cartesian voxel phantoms). */
 typedef struct doctors_mesh {
     int nx, ny, nz;          /* voxels per axis, each >= 1 */
@@ -105,7 +109,15 @@ typedef struct doctors_options {
                                 (same conditions as 4) */
     int device_loop;         /* 1 = run the source iteration as one CUDA graph whose while loop is
                                 decided on the device (no host round trip per iteration) */
-    int reserved[6];         /* must be zero */
+    int differencing;        /* spatial scheme of the sweep (the paper does not state one):
+                                DOCTORS_DIFF_STEP (0, default): every outgoing face flux is the cell
+                                flux, psi = (q + sum_d c_d psi_in,d) / (sigma_t + sum_d c_d);
+                                DOCTORS_DIFF_DIAMOND (1): the cell flux is the mean of each face pair,
+                                psi = (q + 2 sum_d c_d psi_in,d) / (sigma_t + 2 sum_d c_d) and
+                                psi_out,d = 2 psi - psi_in,d, with no negative-flux fixup
+                                (c_d = |Omega_d| / delta_d).  Diamond differencing runs on the dataflow
+                                sweep only: sweep_kernel 0 or 4, angles_per_block = N(N+2)/8, N <= 8 */
+    int reserved[5];         /* must be zero */
 } doctors_options;
 
 /* One source (Sec. II.B: position, energy distribution, azimuthal and polar

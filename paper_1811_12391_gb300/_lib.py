@@ -32,6 +32,8 @@ DOCTORS_FLUENCE_UNCOLLIDED = 0
 DOCTORS_FLUENCE_COLLIDED = 1
 DOCTORS_FLUENCE_TOTAL = 2
 DOCTORS_FLUENCE_ADJOINT = 3
+DOCTORS_DIFF_STEP = 0
+DOCTORS_DIFF_DIAMOND = 1
 
 ERROR_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "TIMEOUT",
                6: "STATE"}
@@ -48,7 +50,7 @@ class doctors_options(ctypes.Structure):
                 ("tol", ctypes.c_double), ("max_iters", ctypes.c_int), ("tile_x", ctypes.c_int),
                 ("tile_y", ctypes.c_int), ("angles_per_block", ctypes.c_int),
                 ("sweep_kernel", ctypes.c_int), ("device_loop", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("differencing", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class doctors_source(ctypes.Structure):

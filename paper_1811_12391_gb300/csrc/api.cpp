@@ -205,6 +205,7 @@ SweepArgs sweep_args(const doctors_problem* p, int reverse, const float* src, fl
     a.qang = p->d_qang;
     a.pang = p->d_pang;
     a.zp = p->flow_zp;
+    a.dd = p->differencing == DOCTORS_DIFF_DIAMOND ? 1 : 0;
     return a;
 }
 
@@ -515,6 +516,20 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
         set_error("dataflow sweep needs whole octants per CTA (angles_per_block = N(N+2)/8) of S2, S4, S6 or S8");
         return DOCTORS_ERR_INVALID_ARG;
     }
+    const bool dd = p->differencing == DOCTORS_DIFF_DIAMOND;
+    if (dd) {
+        // diamond differencing is built into the one-plane dataflow kernel only
+        if (kernel != 0 && kernel != 4) {
+            set_error("diamond differencing runs on the dataflow sweep (sweep_kernel 0 or 4)");
+            return DOCTORS_ERR_INVALID_ARG;
+        }
+        if (!(p->A8 == ab && chain_const_table_ab(ab))) {
+            set_error("diamond differencing needs the dataflow sweep: whole octants per CTA "
+                      "(angles_per_block = N(N+2)/8) of S2, S4, S6 or S8");
+            return DOCTORS_ERR_INVALID_ARG;
+        }
+        kernel = 4;
+    }
     const bool tc_ok = sweep_tc_supported(ab, p->M, tx, ty);
     if (kernel == 2 && !tc_ok) {
         set_error("tensor-core sweep needs P3, <= 16 directions per block and a 16x16, 32x8, 16x8, 8x16, 8x8 or 8x4 tile");
@@ -535,10 +550,10 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
     } else if (use_flow || use_split) {
         int sms = 0;
         CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-        smem = sweep_flow_smem_bytes(ab, tx, ty, p->G, kMaxMat, zp);
+        smem = sweep_flow_smem_bytes(ab, tx, ty, p->G, kMaxMat, zp, dd);
         if (smem <= 227 * 1024) {
-            const size_t smem1 = sweep_flow_smem_bytes(ab, tx, ty, p->G, kMaxMat, 1);
-            const int per_sm = sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem1, false, 1);
+            const size_t smem1 = sweep_flow_smem_bytes(ab, tx, ty, p->G, kMaxMat, 1, dd);
+            const int per_sm = sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem1, false, 1, dd);
             const int per_sm_main = use_split ? sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem, true, 1)
                                   : zp == 2 ? sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem, false, 2) : per_sm;
             if (per_sm < 1 || per_sm_main < 1) {
@@ -630,9 +645,9 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
 }
 
 struct TuneKey {
-    int nx, ny, nz, N, L, G;
+    int nx, ny, nz, N, L, G, differencing;
     bool operator<(const TuneKey& o) const {
-        return std::tie(nx, ny, nz, N, L, G) < std::tie(o.nx, o.ny, o.nz, o.N, o.L, o.G);
+        return std::tie(nx, ny, nz, N, L, G, differencing) < std::tie(o.nx, o.ny, o.nz, o.N, o.L, o.G, o.differencing);
     }
 };
 std::mutex g_tune_mu;
@@ -656,6 +671,8 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     CHECK_ARG(opt->legendre >= 0 && opt->legendre <= 3, "legendre must be 0..3");
     CHECK_ARG(opt->tol > 0 && std::isfinite(opt->tol), "tol must be > 0");
     CHECK_ARG(opt->max_iters >= 1, "max_iters must be >= 1");
+    CHECK_ARG(opt->differencing == DOCTORS_DIFF_STEP || opt->differencing == DOCTORS_DIFF_DIAMOND,
+              "differencing must be DOCTORS_DIFF_STEP or DOCTORS_DIFF_DIAMOND");
     for (int r : opt->reserved) CHECK_ARG(r == 0, "reserved option fields must be zero");
     std::vector<double> dirs, w;
     std::string err;
@@ -672,10 +689,11 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     p->A = (int)w.size(); p->A8 = p->A / 8;
     p->dirs = dirs; p->w = w;
     p->stream = (cudaStream_t)cuda_stream;
+    p->differencing = opt->differencing;
     p->ab = opt->angles_per_block > 0 ? opt->angles_per_block : default_ab(p->A8);
     // default tile: 8 x 8 for the dataflow sweep (whole octants of S2..S8),
     // 16 x 16 for the stage kernels (the fastest measured shapes)
-    const bool flow_default = opt->sweep_kernel >= 4 ||
+    const bool flow_default = opt->sweep_kernel >= 4 || p->differencing == DOCTORS_DIFF_DIAMOND ||
                               (opt->sweep_kernel == 0 && kDefaultDataflowSweep && p->A8 == p->ab &&
                                chain_const_table_ab(p->ab));
     const int tdef = flow_default ? 8 : 16;
@@ -730,11 +748,13 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
                     return fail(DOCTORS_ERR_INVALID_ARG, "quadrature octants are not reflections of the first");
             }
         }
+        // diamond differencing: the dataflow kernel's cell solve takes 2 c
+        const float cf = p->differencing == DOCTORS_DIFF_DIAMOND ? 2.0f : 1.0f;
         for (int j = 0; j < p->A8; ++j) {
-            t.cx[j] = coef[j * 8 + 0];
-            t.cy[j] = coef[j * 8 + 1];
-            t.cz[j] = coef[j * 8 + 2];
-            t.csum[j] = coef[j * 8 + 3];
+            t.cx[j] = cf * coef[j * 8 + 0];
+            t.cy[j] = cf * coef[j * 8 + 1];
+            t.cz[j] = cf * coef[j * 8 + 2];
+            t.csum[j] = cf * coef[j * 8 + 3];
             t.lx[j] = coef[j * 8 + 4];
             t.ly[j] = coef[j * 8 + 5];
             t.lz[j] = coef[j * 8 + 6];
@@ -1093,7 +1113,7 @@ int doctors_autotune(doctors_problem* p, doctors_tuning* out) {
         set_error("set materials and sources before autotuning");
         return DOCTORS_ERR_STATE;
     }
-    const TuneKey key{p->nx, p->ny, p->nz, p->N, p->L, p->G};
+    const TuneKey key{p->nx, p->ny, p->nz, p->N, p->L, p->G, p->differencing};
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -1125,6 +1145,7 @@ int doctors_autotune(doctors_problem* p, doctors_tuning* out) {
     for (const auto& t : tiles) {
         for (int ab : abs_ok) {
             for (int kernel = 1; kernel <= 6; ++kernel) {
+                if (p->differencing == DOCTORS_DIFF_DIAMOND && kernel != 4) continue;
                 if (kernel == 2 && !sweep_tc_supported(ab, p->M, t[0], t[1])) continue;
                 if (kernel >= 4 && !(p->A8 == ab && chain_const_table_ab(ab))) continue;
                 if (configure_sweep(p, t[0], t[1], ab, kernel) != DOCTORS_OK) continue;

@@ -55,11 +55,19 @@ __device__ __forceinline__ int flow_stage_tiles(int s, int ntx, int nty) {
 // (the second takes the first's fluence as its z inflow), so a task takes
 // ceil(nz / 2) + tx + ty - 2 steps instead of nz + tx + ty - 2; the planes
 // hold both cells' fluxes per column and two face records per edge and step.
-template <int AB, int M, int MODE, bool SPLIT = false, int ZP = 1>
+//
+// DD = true: diamond differencing (no negative-flux fixup).  The direction
+// table then holds 2 c_x, 2 c_y, 2 c_z and their sum, so the cell solve
+// (q + sum 2 c psi_in) / (sigma + 2 sum c) is the step formula's; each face
+// leaves with 2 psi - psi_in.  The x-going and y-going face fluxes of a cell
+// differ, so they are kept in two planes (x: buf, y: bufy), and the face
+// records and the leakage carry the face fluxes, not the cell flux.
+template <int AB, int M, int MODE, bool SPLIT = false, int ZP = 1, bool DD = false>
 __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2)
     k_sweep_flow(const SweepArgs a, const ChainDirTable dt) {
     static_assert(!SPLIT || MODE == 0, "split transforms sweep in mode 0 only");
     static_assert(ZP == 1 || (ZP == 2 && !SPLIT), "two planes per step in the fused kernel only");
+    static_assert(!DD || (!SPLIT && ZP == 1), "diamond differencing in the fused one-plane kernel only");
     constexpr int ABP = flow_abp(AB);
     constexpr int RS = (ZP * AB) | 1;         // a column's record: ZP cells' fluxes (odd length)
     // pipeline depths: face records are fetched PD steps before the step
@@ -79,13 +87,14 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
     float4* landy = landx + PD * ZP * a.ty * (ABP / 4);       // [PD][ZP][tx][ABP/4] fetched y-face records
     double* leak_s = reinterpret_cast<double*>(landy + PD * ZP * a.tx * (ABP / 4));   // [gcount]
     float* buf = reinterpret_cast<float*>(leak_s + a.gcount);              // [2][P][RS]
-    float* sigt_s = buf + 2 * P * RS;                         // [gcount][nmat]
+    float* bufy = DD ? buf + 2 * P * RS : buf;                // [2][P][RS] y-going faces (diamond)
+    float* sigt_s = buf + (DD ? 4 : 2) * P * RS;              // [gcount][nmat]
     int* task_s = reinterpret_cast<int*>(sigt_s + a.gcount * a.nmat);
 
     for (int e = threadIdx.x; e < a.gcount * a.nmat; e += blockDim.x)
         sigt_s[e] = a.sigt[(e % a.nmat) * a.G + a.g0 + e / a.nmat];
     for (int e = threadIdx.x; e < a.gcount; e += blockDim.x) leak_s[e] = 0.0;
-    for (int e = threadIdx.x; e < 2 * P * RS; e += blockDim.x) buf[e] = 0.0f;
+    for (int e = threadIdx.x; e < (DD ? 4 : 2) * P * RS; e += blockDim.x) buf[e] = 0.0f;
 
     // threads own the tile's columns in diagonal order (li + lj ascending)
     const int tid = threadIdx.x;
@@ -310,14 +319,22 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                 // step-differenced cell solve
                 const float* pv = buf + pb * P * RS;
                 float* cv = buf + cb * P * RS;
+                const float* pvy = bufy + pb * P * RS;    // step: the same plane
+                float* cvy = bufy + cb * P * RS;
 #pragma unroll
                 for (int q = 0; q < AB; ++q) {
                     const float px = pv[xs + zo + q];
-                    const float py = pv[ys + zo + q];
+                    const float py = pvy[ys + zo + q];
                     const float num = fmaf(dt.cz[q], zc[q], fmaf(dt.cy[q], py, fmaf(dt.cx[q], px, psi[q])));
                     psi[q] = num * rcp_approx(sig + dt.csum[q]);
-                    cv[os + zo + q] = psi[q];
-                    zc[q] = psi[q];
+                    if constexpr (DD) {
+                        cv[os + zo + q] = fmaf(2.0f, psi[q], -px);
+                        cvy[os + zo + q] = fmaf(2.0f, psi[q], -py);
+                        zc[q] = fmaf(2.0f, psi[q], -zc[q]);
+                    } else {
+                        cv[os + zo + q] = psi[q];
+                        zc[q] = psi[q];
+                    }
                 }
                 if constexpr (MODE == 1) {
 #pragma unroll
@@ -331,6 +348,35 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                     atomicAdd(a.prod + gV + v, pacc);
                 }
                 // outgoing face records of plane kr
+                if constexpr (DD) {
+                    // the x and y face fluxes, read back from this thread's plane entries
+                    const float* fxo = cv + os + zo;
+                    const float* fyo = cvy + os + zo;
+                    if (xout) {
+                        float4* dst = reinterpret_cast<float4*>(xo + (size_t)kr * ABP);
+#pragma unroll
+                        for (int c4 = 0; c4 < ABP / 4; ++c4)
+                            dst[c4] = make_float4(4 * c4 < AB ? fxo[4 * c4] : 0.0f, 4 * c4 + 1 < AB ? fxo[4 * c4 + 1] : 0.0f,
+                                                  4 * c4 + 2 < AB ? fxo[4 * c4 + 2] : 0.0f,
+                                                  4 * c4 + 3 < AB ? fxo[4 * c4 + 3] : 0.0f);
+                    }
+                    if (yout) {
+                        float4* dst = reinterpret_cast<float4*>(yo + (size_t)kr * ABP);
+#pragma unroll
+                        for (int c4 = 0; c4 < ABP / 4; ++c4)
+                            dst[c4] = make_float4(4 * c4 < AB ? fyo[4 * c4] : 0.0f, 4 * c4 + 1 < AB ? fyo[4 * c4 + 1] : 0.0f,
+                                                  4 * c4 + 2 < AB ? fyo[4 * c4 + 2] : 0.0f,
+                                                  4 * c4 + 3 < AB ? fyo[4 * c4 + 3] : 0.0f);
+                    }
+                    if (xleak || yleak || last) {
+#pragma unroll
+                        for (int q = 0; q < AB; ++q) {
+                            if (xleak) lk = fmaf(dt.lx[q], fxo[q], lk);
+                            if (yleak) lk = fmaf(dt.ly[q], fyo[q], lk);
+                            if (last) lk = fmaf(dt.lz[q], zc[q], lk);
+                        }
+                    }
+                } else {
                 if (xout || yout) {
                     float4 rec[ABP / 4];
 #pragma unroll
@@ -359,6 +405,7 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                         if (last) f += dt.lz[q];
                         lk = fmaf(f, psi[q], lk);
                     }
+                }
                 }
                 if constexpr (SPLIT) {
                     // the cell's angular fluence record, for k_split_d2m
@@ -405,7 +452,8 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                 } else {
                     cp_async_wait_all();
                 }
-                float* hb = buf + cb * P * RS;
+                float* hbx = buf + cb * P * RS;
+                float* hby = bufy + cb * P * RS;
 #pragma unroll
                 for (int zz = 0; zz < ZP; ++zz) {
                   const int kf = ZP * pf + zz;
@@ -414,6 +462,7 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                     const bool edge = side == 0 ? xedge : yedge;
                     if (!edge) continue;
                     const int hs = (side == 0 ? xs : ys) + zz * AB;
+                    float* hb = side == 0 ? hbx : hby;
                     float* src = side == 0 ? xi : yi;
                     if (!src) {
 #pragma unroll
@@ -547,7 +596,7 @@ __global__ void __launch_bounds__(256) k_split_d2m(const float* pang, float* mom
 }
 
 template <int M>
-int sweep_flow_blocks_per_sm(int ab, int threads, size_t smem, bool split, int zp) {
+int sweep_flow_blocks_per_sm(int ab, int threads, size_t smem, bool split, int zp, bool dd) {
     int b = 0;
     cudaError_t e = cudaErrorInvalidValue;
     auto query = [&](auto kern) {
@@ -559,6 +608,7 @@ int sweep_flow_blocks_per_sm(int ab, int threads, size_t smem, bool split, int z
     case AB:                                                                            \
         if (split) query(k_sweep_flow<AB, M, 0, true>);                                  \
         else if (zp == 2) query(k_sweep_flow<AB, M, 0, false, 2>);                       \
+        else if (dd) query(k_sweep_flow<AB, M, 0, false, 1, true>);                      \
         else query(k_sweep_flow<AB, M, 0>);                                              \
         break;
     switch (ab) {
@@ -628,8 +678,9 @@ cudaError_t launch_sweep_flow_m(const SweepArgs& a, cudaStream_t s) {
     }
     const int grid = ntasks < a.chain_slots ? ntasks : a.chain_slots;
     const int T = a.tx * a.ty;
-    const int zp = (MODE == 0 && a.zp == 2) ? 2 : 1;
-    const size_t smem = sweep_flow_smem_bytes(a.ab, a.tx, a.ty, a.gcount, a.nmat, zp);
+    const bool dd = a.dd != 0;
+    const int zp = (MODE == 0 && a.zp == 2 && !dd) ? 2 : 1;
+    const size_t smem = sweep_flow_smem_bytes(a.ab, a.tx, a.ty, a.gcount, a.nmat, zp, dd);
     cudaError_t e = cudaSuccess;
     auto launch = [&](auto kern) {
         if (smem > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -637,6 +688,10 @@ cudaError_t launch_sweep_flow_m(const SweepArgs& a, cudaStream_t s) {
     };
 #define DOCTORS_FLOW_CASE(AB)                                                           \
     case AB:                                                                            \
+        if (dd) {                                                                       \
+            launch(k_sweep_flow<AB, M, MODE, false, 1, true>);                           \
+            break;                                                                      \
+        }                                                                               \
         if constexpr (MODE == 0) {                                                      \
             if (zp == 2) {                                                              \
                 launch(k_sweep_flow<AB, M, 0, false, 2>);                                \

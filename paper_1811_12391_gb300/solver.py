@@ -73,6 +73,7 @@ class DoctorsProblem:
         opt.angles_per_block = int(angles_per_block)
         opt.sweep_kernel = int(sweep_kernel)
         opt.device_loop = int(device_loop)
+        opt.differencing = int(getattr(prob, "differencing", 0))
         h = ctypes.c_void_p()
         C.check(C.doctors_create_problem(ctypes.byref(mesh), ctypes.byref(opt),
                                          ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))

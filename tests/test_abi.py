@@ -85,6 +85,11 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib):
     assert C.doctors_create_problem(ctypes.byref(mesh), ctypes.byref(opt), None, ctypes.byref(h)) == \
         C.DOCTORS_ERR_INVALID_ARG
     opt.legendre = 1
+    opt.differencing = 2
+    assert C.doctors_create_problem(ctypes.byref(mesh), ctypes.byref(opt), None, ctypes.byref(h)) == \
+        C.DOCTORS_ERR_INVALID_ARG
+    assert "differencing" in C.last_error()
+    opt.differencing = C.DOCTORS_DIFF_DIAMOND
     opt.reserved[0] = 1
     assert C.doctors_create_problem(ctypes.byref(mesh), ctypes.byref(opt), None, ctypes.byref(h)) == \
         C.DOCTORS_ERR_INVALID_ARG
