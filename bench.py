@@ -248,6 +248,35 @@ def bench_paper_workloads(torch, DoctorsProblem, ph, stream):
     return out
 
 
+def bench_diamond(torch, DoctorsProblem, ph, stream):
+    """Diamond against step differencing on the 16^3 cube (S4 P1, 4 groups)
+    and the full-size water cylinder: each scheme autotuned (diamond runs on
+    the dataflow kernel only) and timed on one solve after a warm-up, with
+    the largest relative difference of the two schemes' per-group collided
+    fluence integrals."""
+    out = {}
+    for name in ("tiny_cube", "water_cylinder"):
+        rec = {}
+        sums = {}
+        for diff, label in ((0, "step"), (1, "diamond")):
+            p = ph.config_problem(name)
+            p.differencing = diff
+            d = DoctorsProblem(p, stream=stream, tol=1e-6, max_iters=500)
+            tune = d.autotune()
+            d.solve()
+            r = d.solve()
+            sums[diff] = d.fluence_host(1).astype("float64").sum(axis=1)
+            rec[label] = {"ms_per_solve": r["ms_total"], "ms_per_sweep": r["ms_sweep"] / max(1, r["iterations"]),
+                          "iterations": r["iterations"], "converged": bool(r["converged"]),
+                          "balance_rel": r["balance_rel"],
+                          "cell_updates_per_s": r["cell_updates"] / (r["ms_total"] / 1e3),
+                          "schedule": {k: tune[k] for k in ("tile_x", "tile_y", "angles_per_block", "sweep_kernel")}}
+            d.close()
+        rec["max_rel_group_integral_diff"] = float(abs(sums[1] / sums[0] - 1).max())
+        out[name] = rec
+    return out
+
+
 def run_reference(args, rank, world):
     from synth import phantoms as ph
     if rank != 0:
@@ -383,6 +412,7 @@ def main():
         batched = None if (args.no_extra or world > 1) else bench_batched(torch, DoctorsProblem, ph, stream)
         others = None if (args.no_extra or world > 1) else bench_configs(torch, DoctorsProblem, ph, stream)
         paper = None if (args.no_extra or world > 1) else bench_paper_workloads(torch, DoctorsProblem, ph, stream)
+        diamond = None if (args.no_extra or world > 1) else bench_diamond(torch, DoctorsProblem, ph, stream)
 
     if world > 1:
         dist.destroy_process_group()
@@ -442,6 +472,7 @@ def main():
         "batched_axial_scan": batched,
         "other_workloads": others,
         "paper_workloads": paper,
+        "diamond_difference": diamond,
     }
     print(json.dumps(line), flush=True)
 
