@@ -300,6 +300,40 @@ def abdomen(seed: int = 2, nx: int = 128, ny: int = 128, nz: int = 48, d: float 
     return p
 
 
+# ----------------------------------------------------------------------------
+# synthetic CT calibration (the paper's stoichiometric calibration is cited,
+# not printed; Sec. II.B)
+# ----------------------------------------------------------------------------
+
+def ct_calibration() -> dict:
+    """A synthetic CT-number calibration for the abdomen's five materials
+    (0 air, 1 fat, 2 soft tissue, 3 liver, 4 bone): bin thresholds in HU and
+    a piecewise-linear HU -> density curve (g/cm^3)."""
+    return {
+        "thresholds": np.array([-500.0, -30.0, 45.0, 150.0], np.float32),
+        "bin_material": np.array([0, 1, 2, 3, 4], np.uint8),
+        "hu_knots": np.array([-1000.0, -100.0, 20.0, 60.0, 1000.0], np.float32),
+        "rho_knots": np.array([0.0012, 0.93, 1.03, 1.06, 1.85], np.float32),
+    }
+
+
+# per material: centre and half-width of the synthetic CT numbers (inside the
+# material's bin of ct_calibration)
+_CT_HU = {0: (-1000.0, 20.0), 1: (-100.0, 30.0), 2: (10.0, 25.0), 3: (60.0, 10.0), 4: (700.0, 200.0)}
+
+
+def synthetic_ct(p: Problem, seed: int = 9) -> np.ndarray:
+    """A seeded CT image (HU, float32 [V]) of a phantom with the abdomen's
+    materials: each voxel's number drawn uniformly around its material's
+    centre, inside that material's calibration bin."""
+    rng = np.random.default_rng(seed)
+    hu = np.zeros(p.V, np.float32)
+    for m, (c, w) in _CT_HU.items():
+        sel = p.mat == m
+        hu[sel] = (c + w * rng.uniform(-1.0, 1.0, size=int(sel.sum()))).astype(np.float32)
+    return hu
+
+
 # the paper's seven group edges (keV, high to low; Sec. II.D)
 PAPER_EDGES = np.array([100.0, 75.0, 70.0, 60.0, 45.0, 30.0, 20.0, 10.0])
 
