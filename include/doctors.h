@@ -38,6 +38,7 @@
 #ifndef DOCTORS_H
 #define DOCTORS_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -249,6 +250,35 @@ int doctors_debug_withhold_faces(doctors_problem *p, int task);
  * DOCTORS_ERR_INVALID_ARG if cap is too small or src is not a point source. */
 int doctors_debug_ray_indices(doctors_problem *p, int src, int voxel, int32_t *idx, float *len,
                               int cap, int *n);
+
+/* CT numbers -> materials and densities (Sec. II.B: the reconstructed CT
+ * image is converted into dosimetrically equivalent materials through a
+ * calibration; the paper cites a stoichiometric calibration it does not
+ * print).  Applies any piecewise calibration, voxel by voxel:
+ *   material: bin b = the number of thresholds t_i with t_i <= hu (so a CT
+ *     number equal to a threshold falls in the upper bin),
+ *     mat_out = bin_material[b]; thresholds [n_thresholds] strictly
+ *     ascending, finite, 0..31 of them; bin_material [n_thresholds + 1];
+ *   density: piecewise linear through the knots (hu_knots[k], rho_knots[k]),
+ *     k = 0..n_knots-1 (1..32 knots, CT numbers strictly ascending, densities
+ *     finite and >= 0), constant rho_knots[0] below the first knot and
+ *     rho_knots[n_knots-1] at or above the last; within hu_knots[k] <= hu <
+ *     hu_knots[k+1]:  t = (hu - hu_knots[k]) / (hu_knots[k+1] - hu_knots[k]),
+ *     rho = rho_knots[k] + t * (rho_knots[k+1] - rho_knots[k]), each operation
+ *     an FP32 operation rounded to nearest, in that order (no fused
+ *     multiply-add).
+ * A NaN CT number gives bin 0 and rho_knots[0].
+ * hu [n] float32, mat_out [n] uint8, rho_out [n] float32: all host or all
+ * device memory per `mem` (device: on the current device); the tables are
+ * host memory.  Device memory: stream-ordered on `cuda_stream` (NULL: the
+ * legacy default stream), does not synchronise; host memory: staged
+ * through temporary device buffers, synchronises.  The outputs feed
+ * doctors_set_materials.  DOCTORS_ERR_INVALID_ARG for bad tables or null
+ * arrays (checked before any device work). */
+int doctors_ct_to_materials(const float *hu, size_t n, int n_thresholds, const float *thresholds,
+                            const uint8_t *bin_material, int n_knots, const float *hu_knots,
+                            const float *rho_knots, uint8_t *mat_out, float *rho_out, int mem,
+                            void *cuda_stream);
 
 /* Level-symmetric quadrature and real spherical harmonics as used by the
  * sweep (Sec. II.D, Eq. 3).  Host only, needs no GPU.  dirs [A][3], w [A],

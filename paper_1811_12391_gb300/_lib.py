@@ -100,6 +100,8 @@ SIGNATURES = [
     ("doctors_quadrature", _int, [_int, _int, _P(ctypes.c_double), _P(ctypes.c_double),
                                   _P(ctypes.c_double), _P(_int)]),
     ("doctors_solve_batch", _int, [_P(_vp), _int, _P(doctors_result)]),
+    ("doctors_ct_to_materials", _int, [_vp, ctypes.c_size_t, _int, _P(ctypes.c_float), _P(ctypes.c_uint8), _int,
+                                       _P(ctypes.c_float), _P(ctypes.c_float), _vp, _vp, _int, _vp]),
     ("doctors_autotune", _int, [_vp, _P(doctors_tuning)]),
     ("doctors_destroy", None, [_vp]),
     ("doctors_last_error", ctypes.c_char_p, []),
@@ -161,6 +163,7 @@ doctors_debug_ray_indices = _fwd("doctors_debug_ray_indices")
 doctors_debug_withhold_faces = _fwd("doctors_debug_withhold_faces")
 doctors_quadrature = _fwd("doctors_quadrature")
 doctors_solve_batch = _fwd("doctors_solve_batch")
+doctors_ct_to_materials = _fwd("doctors_ct_to_materials")
 doctors_autotune = _fwd("doctors_autotune")
 doctors_destroy = _fwd("doctors_destroy")
 doctors_last_error = _fwd("doctors_last_error")

@@ -220,3 +220,38 @@ def quadrature(sn_order: int, legendre: int):
     C.check(C.doctors_quadrature(sn_order, legendre, _dptr(dirs, ctypes.c_double), _dptr(w, ctypes.c_double),
                                  _dptr(R, ctypes.c_double), ctypes.byref(n)))
     return dirs, w, R
+
+
+def ct_to_materials(hu, thresholds, bin_material, hu_knots, rho_knots, stream=None):
+    """CT numbers -> (material ids uint8, densities float32) by the library's
+    kernel (doctors_ct_to_materials).  `hu` is a float32 numpy array (host;
+    numpy arrays are returned) or a float32 CUDA tensor (device; CUDA tensors
+    are returned, stream-ordered on `stream` or the current torch stream)."""
+    t = np.ascontiguousarray(thresholds, np.float32).ravel()
+    bm = np.ascontiguousarray(bin_material, np.uint8).ravel()
+    hk = np.ascontiguousarray(hu_knots, np.float32).ravel()
+    rk = np.ascontiguousarray(rho_knots, np.float32).ravel()
+    tp = _dptr(t, ctypes.c_float) if t.size else None
+    if isinstance(hu, np.ndarray):
+        h = np.ascontiguousarray(hu, np.float32).ravel()
+        mat = np.zeros(h.size, np.uint8)
+        rho = np.zeros(h.size, np.float32)
+        C.check(C.doctors_ct_to_materials(h.ctypes.data_as(ctypes.c_void_p), h.size, t.size, tp,
+                                          _dptr(bm, ctypes.c_uint8), hk.size, _dptr(hk, ctypes.c_float),
+                                          _dptr(rk, ctypes.c_float), mat.ctypes.data_as(ctypes.c_void_p),
+                                          rho.ctypes.data_as(ctypes.c_void_p), C.DOCTORS_MEM_HOST, None))
+        return mat, rho
+    torch = _require_torch_cuda()
+    if hu.dtype != torch.float32 or not hu.is_cuda:
+        raise ValueError("hu must be a float32 numpy array or a float32 CUDA tensor")
+    h = hu.contiguous().view(-1)
+    mat = torch.empty(h.numel(), dtype=torch.uint8, device=h.device)
+    rho = torch.empty(h.numel(), dtype=torch.float32, device=h.device)
+    s = stream if stream is not None else torch.cuda.current_stream(h.device)
+    with torch.cuda.device(h.device):
+        C.check(C.doctors_ct_to_materials(ctypes.c_void_p(h.data_ptr()), h.numel(), t.size, tp,
+                                          _dptr(bm, ctypes.c_uint8), hk.size, _dptr(hk, ctypes.c_float),
+                                          _dptr(rk, ctypes.c_float), ctypes.c_void_p(mat.data_ptr()),
+                                          ctypes.c_void_p(rho.data_ptr()), C.DOCTORS_MEM_DEVICE,
+                                          ctypes.c_void_p(s.cuda_stream)))
+    return mat, rho

@@ -96,3 +96,30 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib):
     assert h.value is None
     assert C.doctors_solve(None, None) == C.DOCTORS_ERR_INVALID_ARG
     C.doctors_destroy(None)
+
+
+def test_ct_conversion_checks_tables_before_touching_the_device(lib):
+    """doctors_ct_to_materials validates its calibration on the host and
+    returns at once for an empty image (no device needed for either)."""
+    import numpy as np
+    from paper_1811_12391_gb300 import solver as S
+    C = lib
+    hu = np.zeros(4, np.float32)
+    bad = [
+        ([0.0, 0.0], [0, 1, 2], [0.0, 1.0], [1.0, 1.0], "ascending"),
+        ([np.nan], [0, 1], [0.0, 1.0], [1.0, 1.0], "finite"),
+        ([0.0], [0, 1], [1.0, 0.0], [1.0, 1.0], "ascending"),
+        ([0.0], [0, 1], [0.0, 1.0], [1.0, -1.0], ">= 0"),
+        ([0.0], [0, 1], [], [], "n_knots"),
+        (list(range(32)), list(range(33)), [0.0], [1.0], "n_thresholds"),
+    ]
+    for t, b, hk, rk, word in bad:
+        try:
+            S.ct_to_materials(hu, t, b, hk, rk)
+        except C.DoctorsError as e:
+            assert e.code == C.DOCTORS_ERR_INVALID_ARG
+            assert word in str(e)
+        else:
+            raise AssertionError(f"accepted {t} {hk} {rk}")
+    m0, r0 = S.ct_to_materials(np.zeros(0, np.float32), [], [4], [0.0], [1.25])
+    assert m0.size == 0 and r0.size == 0
