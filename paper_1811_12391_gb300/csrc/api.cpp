@@ -750,6 +750,13 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
         }
         // diamond differencing: the dataflow kernel's cell solve takes 2 c
         const float cf = p->differencing == DOCTORS_DIFF_DIAMOND ? 2.0f : 1.0f;
+        for (int j = 0; j < p->A8 && j < kFlowMaxAB; ++j) {
+            real_harmonics(3, dirs[3 * j], dirs[3 * j + 1], dirs[3 * j + 2], Rb);
+            for (int lm = 0; lm < 16; ++lm) {
+                t.mop[j * 16 + lm] = (float)((2 * degree_of_lm(lm) + 1) / (4.0 * M_PI) * Rb[lm]);
+                t.dop[j * 16 + lm] = (float)(w[j] * Rb[lm]);
+            }
+        }
         for (int j = 0; j < p->A8; ++j) {
             t.cx[j] = cf * coef[j * 8 + 0];
             t.cy[j] = cf * coef[j * 8 + 1];

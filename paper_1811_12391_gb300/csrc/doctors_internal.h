@@ -196,10 +196,15 @@ struct SweepArgs {
 // builds them that way), and R_lm of a reflected direction is R_lm of the
 // original times (-1) to the number of reflected axes in which R_lm is odd.
 constexpr int kMaxA8 = 36;             // S16
+constexpr int kFlowMaxAB = 10;         // whole octants of S2..S8
 struct ChainDirTable {
     float cx[kMaxA8], cy[kMaxA8], cz[kMaxA8], csum[kMaxA8];   // |Omega_q| / d_q and their sum
     float lx[kMaxA8], ly[kMaxA8], lz[kMaxA8];                  // boundary current per face (w |Omega_q| area)
     float w[kMaxA8];
+    // the dataflow kernel's moment <-> direction rows of the first octant, in
+    // lm order: mop = (2l+1)/(4 pi) R_lm(Omega_q), dop = w_q R_lm(Omega_q)
+    // (kernel-parameter operands of the FMAs)
+    float mop[kFlowMaxAB * 16], dop[kFlowMaxAB * 16];
 };
 // R_lm odd in x, y, z (bit lm)
 constexpr unsigned kOddX = (1u << 3) | (1u << 4) | (1u << 7) | (1u << 10) | (1u << 13) | (1u << 15);

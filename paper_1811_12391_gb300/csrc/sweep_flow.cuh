@@ -297,7 +297,6 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                     if (!last) prefetch(kr + PDS);
                 }
                 const int zo = zz * AB;               // this cell's fluxes within the column record
-                constexpr int rb = chain_row_base(AB) * 16;
                 // moments -> directions (split: the record already holds them)
                 float psi[AB];
 #pragma unroll
@@ -305,15 +304,13 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                   if constexpr (SPLIT) {
                     psi[q] = s[q];
                   } else {
-                    float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f, t3 = 0.0f;
+                    float t0 = 0.0f, t1 = 0.0f;
 #pragma unroll
-                    for (int m = 0; m < M; m += 4) {
-                        t0 = fmaf(c_Mop1[rb + q * 16 + lm_of_pos(m, M)], s[m], t0);
-                        if (m + 1 < M) t1 = fmaf(c_Mop1[rb + q * 16 + lm_of_pos(m + 1, M)], s[m + 1], t1);
-                        if (m + 2 < M) t2 = fmaf(c_Mop1[rb + q * 16 + lm_of_pos(m + 2, M)], s[m + 2], t2);
-                        if (m + 3 < M) t3 = fmaf(c_Mop1[rb + q * 16 + lm_of_pos(m + 3, M)], s[m + 3], t3);
+                    for (int m = 0; m < M; m += 2) {
+                        t0 = fmaf(dt.mop[q * 16 + lm_of_pos(m, M)], s[m], t0);
+                        if (m + 1 < M) t1 = fmaf(dt.mop[q * 16 + lm_of_pos(m + 1, M)], s[m + 1], t1);
                     }
-                    psi[q] = (t0 + t1) + (t2 + t3);
+                    psi[q] = t0 + t1;
                   }
                 }
                 // step-differenced cell solve
@@ -425,7 +422,7 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
 #pragma unroll
                     for (int q = 0; q < AB; ++q) {
 #pragma unroll
-                        for (int m = 0; m < M; ++m) acc[m] = fmaf(c_Dop1[rb + q * 16 + lm_of_pos(m, M)], psi[q], acc[m]);
+                        for (int m = 0; m < M; ++m) acc[m] = fmaf(dt.dop[q * 16 + lm_of_pos(m, M)], psi[q], acc[m]);
                     }
 #pragma unroll
                     for (int m = 0; m < M; ++m) acc[m] *= octant_sign<M>(m, fx, fy, fz);
