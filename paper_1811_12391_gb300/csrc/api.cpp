@@ -80,7 +80,7 @@ int default_ab(int A8) {
 
 void free_problem(doctors_problem* p) {
     void* ptrs[] = {p->d_coef, p->d_mat, p->d_rho, p->d_sigt, p->d_sigs,
-                    p->d_phiu_src, p->d_phiu, p->d_U, p->d_Q, p->d_mom, p->d_src, p->d_prev,
+                    p->d_phiu_src, p->d_phiu, p->d_U, p->d_Q, p->d_mom, p->d_src, p->d_src2, p->d_prev,
                     p->d_emit, p->d_iso, p->d_xface, p->d_yface, p->d_red,
                     p->d_Z, p->d_Qa, p->d_T, p->d_rf, p->d_r, p->d_acc, p->d_grad, p->d_H,
                     p->d_ones, p->d_psi, p->d_prod, p->d_flow, p->d_qang, p->d_pang};
@@ -268,26 +268,28 @@ int iterate(doctors_problem* p, int reverse, const float* Q, float* mom, doctors
     // (transposed scattering, upward in energy) its trailing groups.
     int g0 = 0, g1 = p->G;
     std::vector<double> eps(p->G, 0.0);
-    SweepArgs sw = sweep_args(p, reverse, p->d_src, mom);
+    // The next iteration's scattering source is formed while the host reads
+    // this iteration's residuals: it is launched right after the residual
+    // copy, for the current window (a superset of the next one), into the
+    // other source buffer; the host waits only for the copy.  After the last
+    // iteration that launch is wasted, and the source of the last sweep stays
+    // in its own buffer for the balance.
+    float* srcs[2] = {p->d_src, p->d_src2};
+    int cur = 0;
+    SweepArgs sw = sweep_args(p, reverse, srcs[cur], mom);
     ScatterArgs sa{};
     sa.V = p->V; sa.G = p->G; sa.M = p->M; sa.L = p->L; sa.nmat = p->nmat; sa.transpose = reverse;
     sa.mat = p->d_mat; sa.rho = p->d_rho; sa.sigs = p->d_sigs;
-    sa.base = Q; sa.phi = mom; sa.out = p->d_src;
+    sa.base = Q; sa.phi = mom;
+    CU(cudaMemcpyAsync(srcs[cur], Q, GVM * sizeof(float), cudaMemcpyDeviceToDevice, p->stream));
     while (it < p->opt.max_iters) {
         const int gc = g1 - g0;
-        if (it == 0) {
-            CU(cudaMemcpyAsync(p->d_src, Q, GVM * sizeof(float), cudaMemcpyDeviceToDevice, p->stream));
-        } else {
-            sa.g0 = g0;
-            sa.g1 = g1;
-            CU(launch_scatter(sa, p->stream));
-            ++p->launches;
-        }
         if (!p->use_split)   // the split path's d2m pass writes the window's moments
             CU(cudaMemsetAsync(mom + (size_t)g0 * VM, 0, (size_t)gc * VM * sizeof(float), p->stream));
         CU(cudaMemsetAsync(p->d_red + g0, 0, (size_t)gc * sizeof(double), p->stream));
         CU(cudaMemsetAsync(d_res + 2 * g0, 0, 2 * (size_t)gc * sizeof(double), p->stream));
         CU(cudaEventRecord(p->ev[3], p->stream));
+        sw.src = srcs[cur];
         sw.g0 = g0;
         sw.gcount = gc;
         int nl = 0;
@@ -298,7 +300,16 @@ int iterate(doctors_problem* p, int reverse, const float* Q, float* mom, doctors
         ++p->launches;
         CU(cudaMemcpyAsync(p->h_red, p->d_red, 3 * (size_t)p->G * sizeof(double), cudaMemcpyDeviceToHost,
                            p->stream));
-        CU(cudaStreamSynchronize(p->stream));
+        CU(cudaEventRecord(p->ev[5], p->stream));
+        const bool ahead = it + 1 < p->opt.max_iters;
+        if (ahead) {
+            sa.g0 = g0;
+            sa.g1 = g1;
+            sa.out = srcs[cur ^ 1];
+            CU(launch_scatter(sa, p->stream));
+            ++p->launches;
+        }
+        CU(cudaEventSynchronize(p->ev[5]));
         float ms = 0.0f;
         CU(cudaEventElapsedTime(&ms, p->ev[3], p->ev[4]));
         ms_sweep += ms;
@@ -309,6 +320,7 @@ int iterate(doctors_problem* p, int reverse, const float* Q, float* mom, doctors
             const double num = p->h_red[p->G + 2 * g], den = p->h_red[p->G + 2 * g + 1];
             eps[g] = den > 0.0 ? std::sqrt(num / den) : 0.0;
             if (!std::isfinite(eps[g])) {
+                CU(cudaStreamSynchronize(p->stream));
                 set_error("source iteration produced a non-finite fluence");
                 return DOCTORS_ERR_INVALID_ARG;
             }
@@ -318,14 +330,16 @@ int iterate(doctors_problem* p, int reverse, const float* Q, float* mom, doctors
             conv = true;
             break;
         }
+        if (!ahead) break;
         if (!reverse)
             while (g0 < g1 - 1 && eps[g0] < tol) ++g0;
         else
             while (g1 - 1 > g0 && eps[g1 - 1] < tol) --g1;
+        cur ^= 1;
     }
     // particle balance of the last sweep (FP64)
     const double vol = p->mesh.dx * p->mesh.dy * p->mesh.dz;
-    CU(launch_balance(p->V, p->G, p->M, p->d_mat, p->d_rho, p->d_sigt, p->d_src, mom, vol, d_bal,
+    CU(launch_balance(p->V, p->G, p->M, p->d_mat, p->d_rho, p->d_sigt, srcs[cur], mom, vol, d_bal,
                       p->stream));
     ++p->launches;
     CU(cudaMemcpyAsync(p->h_red, p->d_red, 5 * (size_t)p->G * sizeof(double), cudaMemcpyDeviceToHost,
@@ -781,6 +795,7 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     rc = rc ? rc : dalloc_t(&p->d_Q, GVM, "first-collision source");
     rc = rc ? rc : dalloc_t(&p->d_mom, GVM, "moments");
     rc = rc ? rc : dalloc_t(&p->d_src, GVM, "sweep source");
+    rc = rc ? rc : dalloc_t(&p->d_src2, GVM, "sweep source (next iteration)");
     rc = rc ? rc : dalloc_t(&p->d_prev, GV, "previous scalar fluence");
     rc = rc ? rc : dalloc_t(&p->d_iso, (size_t)p->G, "volume source");
     rc = rc ? rc : configure_sweep(p, p->tx, p->ty, p->ab, opt->sweep_kernel);

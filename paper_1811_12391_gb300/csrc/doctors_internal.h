@@ -311,6 +311,7 @@ struct doctors_problem {
     float* d_Q = nullptr;          // [G][V][M]
     float* d_mom = nullptr;        // [G][V][M]
     float* d_src = nullptr;        // [G][V][M]
+    float* d_src2 = nullptr;       // [G][V][M] the next iteration's source (formed ahead)
     float* d_prev = nullptr;       // [G][V]
     float* d_emit = nullptr;       // [G]
     float* d_iso = nullptr;        // [G]

@@ -1,6 +1,8 @@
 // Dataflow octant wavefront sweep: the step-differenced cell update of
-// k_sweep_chain (whole octants per CTA, first-octant tables in the constant
-// bank) with the tile stages replaced by a task queue in one launch.
+// k_sweep_chain (whole octants per CTA; the first octant's direction rows,
+// coefficients and moment tables are kernel parameters, read through the
+// constant bank at compile-time offsets) with the tile stages replaced by a
+// task queue in one launch.
 //
 // The tasks (tile, octant, group) are numbered stage by stage (the tile
 // diagonal of the octant's reflected tile grid).  Each CTA takes the next
