@@ -1,7 +1,7 @@
 """Command line: solve a named synthetic workload and print the report.
 
   python -m paper_1811_12391_gb300 <workload> [--iters N] [--tol T] [--tile X Y] [--ab K] [--kernel 1..6]
-                                   [--device-loop] [--autotune] [--repeat R]
+                                   [--device-loop] [--diamond] [--autotune] [--repeat R]
 
 Workloads: tiny_cube, water_cylinder, abdomen, axial_scan, differentiable_abdomen
 (see synth/phantoms.py).  Used as the profiled command in profiles/.
@@ -26,6 +26,7 @@ def main():
     ap.add_argument("--kernel", type=int, default=0, help="sweep kernel: 0 default, 1 CUDA-core, 2 tensor-core, 3 chained CUDA-core, 4 dataflow, 5 dataflow with split transforms, 6 dataflow with two planes per step")
     ap.add_argument("--device-loop", action="store_true",
                     help="run the source iteration as one CUDA graph with a device-side while loop")
+    ap.add_argument("--diamond", action="store_true", help="diamond differencing (dataflow sweep)")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--repeat", type=int, default=1)
     args = ap.parse_args()
@@ -35,6 +36,8 @@ def main():
     from synth import phantoms as ph
 
     p = ph.config_problem(args.workload)
+    if args.diamond:
+        p.differencing = 1
     d = DoctorsProblem(p, tol=args.tol, max_iters=args.iters, tile=tuple(args.tile), angles_per_block=args.ab,
                        sweep_kernel=args.kernel, device_loop=int(args.device_loop))
     if args.autotune:

@@ -181,3 +181,25 @@ def test_diamond_option_checks(env):
     with pytest.raises(C.DoctorsError) as ei:
         DoctorsProblem(p, tol=1e-6, max_iters=10)
     assert ei.value.code == C.DOCTORS_ERR_INVALID_ARG
+
+
+def test_diamond_device_loop_and_batch(env):
+    """Diamond differencing through the graph-captured device loop and in a
+    batch with a step-differenced problem: each matches its own oracle."""
+    torch, C, DoctorsProblem = env
+    from paper_1811_12391_gb300.solver import solve_batch
+    a = ph.water_cylinder(nx=20, ny=16, nz=6, dx=1.5, dy=1.8, dz=1.5, diameter=22.0, G=3, sn=6, L=2)
+    a.differencing = 1
+    b = ph.tiny_cube(n=8)
+    refs = [osv.solve(a, tol=1e-11), osv.solve(b, tol=1e-11)]
+    d = DoctorsProblem(a, tol=1e-6, max_iters=400, device_loop=1)
+    r = d.solve()
+    assert r["converged"] == 1 and r["balance_rel"] < 1e-5
+    assert max_rel(d.fluence_host(2), refs[0].phi) <= REL_TOL
+    d.close()
+    ds = [DoctorsProblem(a, tol=1e-6, max_iters=400), DoctorsProblem(b, tol=1e-6, max_iters=400)]
+    res = solve_batch(ds)
+    for p, dd, rr, ref in zip((a, b), ds, res, refs):
+        assert rr["converged"] == 1, rr
+        assert max_rel(dd.fluence_host(2), ref.phi) <= REL_TOL
+        dd.close()
