@@ -139,7 +139,12 @@ int check_problem(doctors_problem* p) {
 int first_collision(doctors_problem* p) {
     const size_t GV = (size_t)p->G * p->V;
     CU(cudaMemsetAsync(p->d_phiu, 0, GV * sizeof(float), p->stream));
-    CU(cudaMemsetAsync(p->d_U, 0, GV * p->M * sizeof(float), p->stream));
+    // the first point source stores the uncollided moments, later ones add;
+    // with volume sources only they stay zero
+    bool any_point = false;
+    for (const doctors_source& src : p->srcs) any_point = any_point || src.kind != DOCTORS_SRC_VOLUME;
+    if (!any_point) CU(cudaMemsetAsync(p->d_U, 0, GV * p->M * sizeof(float), p->stream));
+    bool first_point = true;
     std::vector<float> iso(p->G, 0.0f);
     std::vector<float> emit_all((size_t)p->srcs.size() * p->G);
     for (size_t s = 0; s < p->srcs.size(); ++s)
@@ -165,6 +170,8 @@ int first_collision(doctors_problem* p) {
         m.sx = r.sx; m.sy = r.sy; m.sz = r.sz;
         m.phi_src = p->d_phiu_src;
         m.U = p->d_U;
+        m.accumulate = first_point ? 0 : 1;
+        first_point = false;
         e = launch_uncollided_moments(m, p->stream);
         ++p->launches;
     }

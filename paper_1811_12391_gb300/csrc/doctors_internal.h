@@ -99,6 +99,7 @@ struct MomentArgs {
     float ox, oy, oz, dx, dy, dz, sx, sy, sz;
     const float* phi_src;              // [G][V]
     float* U;                          // [G][V][M]
+    int accumulate;                    // 0: U = phi R (first source), 1: U += phi R
 };
 cudaError_t launch_uncollided_moments(const MomentArgs& a, cudaStream_t s);
 

@@ -240,8 +240,10 @@ __global__ void __launch_bounds__(kScatterThreads, 3) k_scatter(const ScatterArg
     }
 }
 
-// The iteration's form of the same map (a scattering term, no isotropic
-// terms, fewer than 2^31 entries) with no branch in its group loops: the
+// The iteration's form of the same map (a scattering term, no per-voxel
+// isotropic field, fewer than 2^31 entries) with no branch in its group
+// loops (ISO: the first-collision form, with the volume sources' isotropic
+// term and no fixed source, added to the l = 0 entries): the
 // direction of the sum (downscatter or its transpose) and the presence of a
 // fixed source are template parameters, the group window only predicates the
 // loads of the fixed source and the stores, and entry indices are 32-bit.  The
@@ -258,7 +260,7 @@ __device__ __forceinline__ float ldg_if(const float* p, bool pred) {
     return x;
 }
 
-template <int GMAX, bool TR, bool HAS_BASE>
+template <int GMAX, bool TR, bool HAS_BASE, bool ISO = false>
 __global__ void __launch_bounds__(kScatterThreads, GMAX <= 24 ? 3 : GMAX <= 32 ? 2 : 1) k_scatter_fast(const ScatterArgs a) {
     extern __shared__ float tab_s[];
     if (a.skip && *a.skip) return;
@@ -290,6 +292,11 @@ __global__ void __launch_bounds__(kScatterThreads, GMAX <= 24 ? 3 : GMAX <= 32 ?
         const float* pb = a.base + t;
 #pragma unroll
         for (int g = 0; g < GMAX; ++g) qb[g] = HAS_BASE ? ldg_if(pb + (size_t)g * VM, g >= g_beg && g < g_end) : 0.0f;
+        if (ISO && lm == 0) {
+#pragma unroll
+            for (int g = 0; g < GMAX; ++g)
+                if (g < G) qb[g] += __ldg(a.iso + g);
+        }
         const float* ts = tab_s + mb * BP;
         float* po = a.out + t;
 #pragma unroll
@@ -448,9 +455,9 @@ unsigned blocks_for(size_t n, int bs, unsigned cap = 0) {
 }  // namespace
 
 // one resident wave of k_scatter_fast
-template <int GMAX, bool TR, bool HAS_BASE>
+template <int GMAX, bool TR, bool HAS_BASE, bool ISO = false>
 cudaError_t launch_scatter_fast(const ScatterArgs& a, size_t smem, cudaStream_t s) {
-    auto kern = k_scatter_fast<GMAX, TR, HAS_BASE>;
+    auto kern = k_scatter_fast<GMAX, TR, HAS_BASE, ISO>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -470,6 +477,8 @@ cudaError_t launch_scatter_g(const ScatterArgs& a, cudaStream_t s) {
     const size_t tab_bytes = scatter_table_bytes<GMAX>(a);
     const int staged = tab_bytes <= kScatterTableSmem ? 1 : 0;
     const size_t smem = staged ? tab_bytes : 0;
+    if (staged && a.phi && a.iso && !a.iso_field && !a.transpose && !a.base && a.V * a.M < ((size_t)1 << 31))
+        return launch_scatter_fast<GMAX, false, false, true>(a, smem, s);
     if (staged && a.phi && !a.iso && !a.iso_field && a.V * a.M < ((size_t)1 << 31)) {
         if (a.transpose)
             return a.base ? launch_scatter_fast<GMAX, true, true>(a, smem, s)

@@ -179,8 +179,12 @@ __global__ void k_debug_ray(const RayArgs r, int voxel, int32_t* idx, float* len
 }
 
 // Uncollided angular fluence is a delta in the direction source -> voxel, so
-// its moments are phi_u * R_lm(that direction) (first-collision source).
-template <int M>
+// its moments are phi_u * R_lm(that direction) (first-collision source).  One
+// thread per voxel; a voxel's moments of a group are one record of M floats,
+// written as 16-byte vectors when M is a multiple of 4 (the first source
+// stores, later sources of a superposed scan add).  HBM-bound: the record is
+// written (and, when adding, read) once per group.
+template <int M, bool ACC>
 __global__ void __launch_bounds__(256) k_uncollided_moments(const MomentArgs a) {
     const size_t V = (size_t)a.nx * a.ny * a.nz;
     const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -210,10 +214,23 @@ __global__ void __launch_bounds__(256) k_uncollided_moments(const MomentArgs a) 
     }
     for (int g = 0; g < a.G; ++g) {
         const float p = a.phi_src[(size_t)g * V + v];
-        if (p == 0.0f) continue;
         float* u = a.U + ((size_t)g * V + v) * M;
+        if constexpr (M % 4 == 0) {
+            float4* u4 = reinterpret_cast<float4*>(u);
 #pragma unroll
-        for (int m = 0; m < M; ++m) u[m] += p * R[lm_of_pos(m, M)];
+            for (int c = 0; c < M / 4; ++c) {
+                float4 w = make_float4(p * R[lm_of_pos(4 * c, M)], p * R[lm_of_pos(4 * c + 1, M)],
+                                       p * R[lm_of_pos(4 * c + 2, M)], p * R[lm_of_pos(4 * c + 3, M)]);
+                if (ACC) {
+                    const float4 o = u4[c];
+                    w.x += o.x; w.y += o.y; w.z += o.z; w.w += o.w;
+                }
+                u4[c] = w;
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < M; ++m) u[m] = ACC ? u[m] + p * R[lm_of_pos(m, M)] : p * R[lm_of_pos(m, M)];
+        }
     }
 }
 
@@ -244,11 +261,12 @@ cudaError_t launch_uncollided_moments(const MomentArgs& a, cudaStream_t s) {
     const size_t V = (size_t)a.nx * a.ny * a.nz;
     const int bs = 256;
     const unsigned grid = (unsigned)((V + bs - 1) / bs);
+    const bool acc = a.accumulate != 0;
     switch (a.M) {
-        case 1: k_uncollided_moments<1><<<grid, bs, 0, s>>>(a); break;
-        case 4: k_uncollided_moments<4><<<grid, bs, 0, s>>>(a); break;
-        case 9: k_uncollided_moments<9><<<grid, bs, 0, s>>>(a); break;
-        case 16: k_uncollided_moments<16><<<grid, bs, 0, s>>>(a); break;
+        case 1: acc ? k_uncollided_moments<1, true><<<grid, bs, 0, s>>>(a) : k_uncollided_moments<1, false><<<grid, bs, 0, s>>>(a); break;
+        case 4: acc ? k_uncollided_moments<4, true><<<grid, bs, 0, s>>>(a) : k_uncollided_moments<4, false><<<grid, bs, 0, s>>>(a); break;
+        case 9: acc ? k_uncollided_moments<9, true><<<grid, bs, 0, s>>>(a) : k_uncollided_moments<9, false><<<grid, bs, 0, s>>>(a); break;
+        case 16: acc ? k_uncollided_moments<16, true><<<grid, bs, 0, s>>>(a) : k_uncollided_moments<16, false><<<grid, bs, 0, s>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
