@@ -189,6 +189,30 @@ def bench_batched(torch, DoctorsProblem, ph, stream):
             "converged": all(r["converged"] for r in res)}
 
 
+def ray_visits(p, src):
+    """Voxel visits of the uncollided ray trace of one point source (the work
+    of the ray-trace kernel): for each voxel centre, 1 + the grid planes its
+    ray crosses between the mesh entry and the centre (a tie where the ray
+    crosses two planes at once counts twice, so this slightly over-counts)."""
+    import numpy as np
+    X, Y, Z = p.centres()
+    T = np.stack([X, Y, Z], axis=1)
+    S = np.asarray(src.pos, np.float64)
+    o = np.asarray(p.origin, np.float64)
+    sp = np.array([p.dx, p.dy, p.dz])
+    n = np.array([p.nx, p.ny, p.nz])
+    d = T - S
+    lo, hi = o, o + n * sp
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t1 = (lo - S) / d
+        t2 = (hi - S) / d
+    tmin = np.where(d != 0, np.minimum(t1, t2), -np.inf).max(axis=1)
+    E = S + (tmin[:, None] + 1e-9) * d
+    iE = np.clip(np.floor((E - o) / sp), 0, n - 1)
+    iT = np.clip(np.floor((T - o) / sp), 0, n - 1)
+    return int((1 + np.abs(iT - iE).sum(axis=1)).sum())
+
+
 def bench_configs(torch, DoctorsProblem, ph, stream):
     """The other full-size workloads, each autotuned and timed on one solve
     after a warm-up: the S16 abdomen (one cone-beam projection), the 64-view
@@ -208,6 +232,9 @@ def bench_configs(torch, DoctorsProblem, ph, stream):
                "ms_per_solve": r["ms_total"], "cell_updates_per_s": r["cell_updates"] / (r["ms_total"] / 1e3),
                "iterations": r["iterations"], "converged": bool(r["converged"]),
                "schedule": {k: tune[k] for k in ("tile_x", "tile_y", "angles_per_block", "sweep_kernel")}}
+        if name == "abdomen":
+            rec["raytrace"] = {"rays_per_source": p.V, "voxel_visits_per_source": ray_visits(p, p.sources[0]),
+                               "ms_first_collision": r["ms_raytrace"]}
         if name == "differentiable_abdomen":
             roi = p.roi / p.roi.sum()
             resp = torch.as_tensor(p.k_dep[p.mat].T * (p.density.astype(np.float64) * roi)[None, :], device="cuda")
@@ -384,6 +411,28 @@ def main():
         e2e_s = time.perf_counter() - t0
         h2d = p.V * 1 + p.V * 4
         d2h = phi.nbytes + dose.nbytes
+        parity = None
+        gold = os.path.join(ROOT, "tests", "golden", f"{WORKLOAD}_samples.npz")
+        if world == 1 and os.path.exists(gold):
+            # the last end-to-end solve against FP64 oracle values stored for 600
+            # seeded voxels (largest relative error over groups, on values above
+            # 1e-6 of the group's maximum) and the per-group fluence totals
+            ref = np.load(gold)
+            idx = ref["voxels"]
+
+            def max_rel(a, b):
+                a, b = np.atleast_2d(a).astype(np.float64), np.atleast_2d(b).astype(np.float64)
+                worst = 0.0
+                for x, y in zip(a, b):
+                    sel = np.abs(y) > 1e-6 * np.abs(y).max()
+                    worst = max(worst, float((np.abs(x[sel] - y[sel]) / np.abs(y[sel])).max()))
+                return worst
+
+            parity = {"reference": "FP64 oracle, tests/golden/" + os.path.basename(gold), "voxels": int(idx.size),
+                      "max_rel_phi": max_rel(phi[:, idx], ref["phi"]), "max_rel_dose": max_rel(dose[idx], ref["dose"]),
+                      "max_rel_group_totals": float(np.abs(phi.astype(np.float64).sum(axis=1) / ref["phi_total"]
+                                                          - 1.0).max()),
+                      "tolerance": 1e-4}
 
         # adjoint (backward) solve of the mean dose in a central region
         adjoint = None
@@ -464,6 +513,7 @@ def main():
             "sample": f"{cpu_n} whole-mesh FP64 sweeps of group 0 of the same workload in {cpu_s:.1f} s"},
         "e2e": {"value": world * e2e_cells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
+        "parity": parity,
         "gpu_launches": launches,
         "clocks": clocks,
         "autotune": tuning,
