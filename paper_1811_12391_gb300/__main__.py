@@ -1,7 +1,7 @@
 """Command line: solve a named synthetic workload and print the report.
 
   python -m paper_1811_12391_gb300 <workload> [--iters N] [--tol T] [--tile X Y] [--ab K] [--kernel 1..6]
-                                   [--device-loop] [--diamond] [--autotune] [--repeat R]
+                                   [--device-loop] [--diamond] [--adjoint] [--autotune] [--repeat R]
 
 Workloads: tiny_cube, water_cylinder, abdomen, axial_scan, differentiable_abdomen
 (see synth/phantoms.py).  Used as the profiled command in profiles/.
@@ -27,6 +27,8 @@ def main():
     ap.add_argument("--device-loop", action="store_true",
                     help="run the source iteration as one CUDA graph with a device-side while loop")
     ap.add_argument("--diamond", action="store_true", help="diamond differencing (dataflow sweep)")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="after each solve, the adjoint solve and all gradients of the mean dose in a central box")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--repeat", type=int, default=1)
     args = ap.parse_args()
@@ -42,9 +44,21 @@ def main():
                        sweep_kernel=args.kernel, device_loop=int(args.device_loop))
     if args.autotune:
         print(json.dumps({"autotune": d.autotune()}), flush=True)
+    resp = None
+    if args.adjoint:
+        import numpy as np
+        import torch
+        roi = np.zeros(p.V)
+        roi.reshape(p.nz, p.ny, p.nx)[p.nz // 2 - 2:p.nz // 2 + 2, p.ny // 2 - 4:p.ny // 2 + 4,
+                                      p.nx // 2 - 4:p.nx // 2 + 4] = 1.0
+        roi /= roi.sum()
+        resp = torch.as_tensor(p.k_dep[p.mat].T * (p.density.astype(np.float64) * roi)[None, :], device="cuda")
     for _ in range(args.repeat):
         r = d.solve(allow_not_converged=True)
         print(json.dumps(r), flush=True)
+        if resp is not None:
+            g = d.adjoint(resp)
+            print(json.dumps({"adjoint": g["result"]}), flush=True)
     d.close()
 
 

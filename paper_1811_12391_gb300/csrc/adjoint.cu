@@ -105,6 +105,100 @@ __global__ void __launch_bounds__(256) k_density_grad(const DensityGradArgs a) {
     a.grad[v] += acc;
 }
 
+// The same density gradient with the scattering term laid out like the
+// scattering source: one (voxel, moment) entry per thread in a resident grid,
+// coalesced loads of every group's X = phi_c + U and Z at the entry, the
+// (material, degree) blocks of sigma_s staged in shared memory (odd block
+// pitch), the triangular sum over source groups in registers, and the
+// voxel's M entries summed by a shuffle within their M-lane segment (M = 1, 4
+// or 16 divides the warp); the collision term is added by the voxel's first
+// lane.  Per entry: (2l+1)/(4 pi) sum_g Z_g sum_{g' <= g} sigma_s,l(g' -> g) X_g'.
+constexpr int kGradThreads = 256;
+constexpr size_t kGradTableSmem = 100 * 1024;
+template <int GMAX>
+__host__ __device__ constexpr int grad_block_pitch() { return GMAX * GMAX + 1; }
+
+template <int GMAX, int M>
+__global__ void __launch_bounds__(kGradThreads, GMAX <= 24 ? 3 : 1) k_density_grad_fast(const DensityGradArgs a) {
+    extern __shared__ float tab_s[];
+    const int G = a.G;
+    constexpr int BP = grad_block_pitch<GMAX>();
+    const int nblk = a.nmat * (a.L + 1);
+    for (int e = threadIdx.x; e < nblk * BP; e += blockDim.x) {
+        const int blk = e / BP, r = e % BP, i = r / GMAX, j = r % GMAX;
+        tab_s[e] = (r < GMAX * GMAX && i < G && j < G) ? __ldg(a.sigs + ((size_t)blk * G + i) * G + j) : 0.0f;
+    }
+    __syncthreads();
+    const unsigned V = (unsigned)a.V, VM = (unsigned)(a.V * M);
+    const unsigned stride = gridDim.x * blockDim.x;               // a multiple of 32
+    const unsigned tend = (VM + 31u) & ~31u;                      // whole warps iterate together
+    const int L1 = a.L + 1;
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < tend; t += stride) {
+        const bool ok = t < VM;
+        const unsigned tt = ok ? t : 0u;
+        const unsigned v = tt / M;
+        const int lm = (int)(tt - v * M);
+        const int l = degree_of_lm(lm_of_pos(lm, M));
+        const int m = __ldg(a.mat + v);
+        float x[GMAX], z[GMAX];
+#pragma unroll
+        for (int g = 0; g < GMAX; ++g) {
+            const size_t o = (size_t)(g < G ? g : G - 1) * VM + tt;
+            const float xp = __ldg(a.phic + o) + __ldg(a.U + o);
+            const float zz = __ldg(a.Z + o);
+            x[g] = g < G ? xp : 0.0f;
+            z[g] = g < G ? zz : 0.0f;
+        }
+        const float* ts = tab_s + (m * L1 + l) * BP;
+        float acc = 0.0f;
+#pragma unroll
+        for (int g = 0; g < GMAX; ++g) {
+            float sg = 0.0f;
+#pragma unroll
+            for (int gp = 0; gp <= g; ++gp) sg = fmaf(ts[gp * GMAX + g], x[gp], sg);
+            acc = fmaf(z[g], sg, acc);
+        }
+        double part = ok ? (double)(acc * (float)(2 * l + 1) * 0.07957747154594767f) : 0.0;
+#pragma unroll
+        for (int off = M / 2; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off, M);
+        if (ok && lm == 0) {
+            if (a.prod)
+                for (int g = 0; g < G; ++g)
+                    part -= (double)__ldg(a.sigt + m * G + g) * (double)a.prod[(size_t)g * V + v];
+            a.grad[v] += part;
+        }
+    }
+}
+
+template <int GMAX, int M>
+cudaError_t launch_density_grad_fast(const DensityGradArgs& a, size_t smem, cudaStream_t s) {
+    auto kern = k_density_grad_fast<GMAX, M>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int nb = 0, dev = 0, nsm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kGradThreads, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    size_t want = (a.V * M + kGradThreads - 1) / kGradThreads, cap = (size_t)nsm * (nb > 0 ? nb : 1);
+    kern<<<(unsigned)(want < cap ? want : cap), kGradThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int GMAX>
+cudaError_t launch_density_grad_g(const DensityGradArgs& a, cudaStream_t s) {
+    const size_t smem = (size_t)a.nmat * (a.L + 1) * grad_block_pitch<GMAX>() * sizeof(float);
+    if (smem > kGradTableSmem || a.V * a.M >= ((size_t)1 << 31)) return cudaErrorNotSupported;
+    switch (a.M) {
+        case 1: return launch_density_grad_fast<GMAX, 1>(a, smem, s);
+        case 4: return launch_density_grad_fast<GMAX, 4>(a, smem, s);
+        case 16: return launch_density_grad_fast<GMAX, 16>(a, smem, s);
+        default: return cudaErrorNotSupported;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_sum00(size_t V, int M, const float* mom, double* out) {
     const int g = blockIdx.y;
     double x = 0.0;
@@ -145,6 +239,13 @@ cudaError_t launch_source_grad(const SourceGradArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_density_grad(const DensityGradArgs& a, cudaStream_t s) {
+    cudaError_t e = cudaErrorNotSupported;
+    if (a.G <= 8) e = launch_density_grad_g<8>(a, s);
+    else if (a.G <= 16) e = launch_density_grad_g<16>(a, s);
+    else if (a.G <= 20) e = launch_density_grad_g<20>(a, s);
+    else if (a.G <= 24) e = launch_density_grad_g<24>(a, s);
+    if (e != cudaErrorNotSupported) return e;
+    // M = 9, more groups or larger tables: the voxel-per-thread form
     k_density_grad<<<nblocks(a.V, 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -177,7 +177,7 @@ struct SweepArgs {
     float* yface;                      // [8][A8][G][nty-1][nx][nz]
     double* leak;                      // [G]
     int A;                             // directions (psi indexing)
-    float* psi;                        // [G][A][V]: written (mode 1) or read (mode 2)
+    float* psi;                        // written (mode 1) or read (mode 2): [G][A][V], dataflow kernel [G][V][8][ABP]
     float* prod;                       // [G][V]: mode 2 accumulator
     const int* skip;                   // if non-null and *skip != 0 the kernel does nothing
     int chain_slots;                   // > 0: chained kernel, at most this many CTAs per stage launch

@@ -335,16 +335,30 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                         zc[q] = psi[q];
                     }
                 }
+                // stored angular fluence, laid out for this kernel as one 16-byte
+                // aligned record of ABP floats per (group, voxel, direction octant):
+                // [G][V][8][ABP] (the stage kernels use [G][A][V])
                 if constexpr (MODE == 1) {
+                    float4* rec = reinterpret_cast<float4*>(a.psi + (((size_t)g * V + v) * 8 + oe) * ABP);
 #pragma unroll
-                    for (int q = 0; q < AB; ++q) a.psi[((size_t)g * a.A + nb + q) * V + v] = psi[q];
+                    for (int c4 = 0; c4 < ABP / 4; ++c4)
+                        rec[c4] = make_float4(4 * c4 < AB ? psi[4 * c4 < AB ? 4 * c4 : 0] : 0.0f,
+                                              4 * c4 + 1 < AB ? psi[4 * c4 + 1 < AB ? 4 * c4 + 1 : 0] : 0.0f,
+                                              4 * c4 + 2 < AB ? psi[4 * c4 + 2 < AB ? 4 * c4 + 2 : 0] : 0.0f,
+                                              4 * c4 + 3 < AB ? psi[4 * c4 + 3 < AB ? 4 * c4 + 3 : 0] : 0.0f);
                 }
                 if constexpr (MODE == 2) {
+                    const float4* rec = reinterpret_cast<const float4*>(a.psi + (((size_t)g * V + v) * 8 + oe) * ABP);
                     float pacc = 0.0f;
 #pragma unroll
-                    for (int q = 0; q < AB; ++q)
-                        pacc = fmaf(dt.w[q] * psi[q], __ldg(a.psi + ((size_t)g * a.A + nb + q) * V + v), pacc);
-                    atomicAdd(a.prod + gV + v, pacc);
+                    for (int c4 = 0; c4 < ABP / 4; ++c4) {
+                        const float4 t4 = __ldg(rec + c4);
+                        const float st4[4] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (4 * c4 + e < AB) pacc = fmaf(dt.w[4 * c4 + e] * psi[4 * c4 + e < AB ? 4 * c4 + e : 0], st4[e], pacc);
+                    }
+                    red_add_f32(a.prod + gV + v, pacc);
                 }
                 // outgoing face records of plane kr
                 if constexpr (DD) {

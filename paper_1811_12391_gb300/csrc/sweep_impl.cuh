@@ -60,6 +60,11 @@ __device__ __forceinline__ void load_moments(const float* p, float (&s)[M]) {
     }
 }
 
+// one float added with a reduction that returns nothing
+__device__ __forceinline__ void red_add_f32(float* p, float x) {
+    asm volatile("red.global.add.f32 [%0], %1;\n" ::"l"(p), "f"(x) : "memory");
+}
+
 // moments added with reductions that return nothing (red, not atom): the
 // thread never waits for them
 template <int M>
