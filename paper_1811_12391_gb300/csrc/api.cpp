@@ -1262,7 +1262,7 @@ int ensure_adjoint_buffers(doctors_problem* p, bool density) {
     if (!p->d_grad) rc = rc ? rc : dalloc_t(&p->d_grad, p->V, "density gradient");
     if (density) {
         if (!p->d_H) rc = rc ? rc : dalloc_t(&p->d_H, (size_t)kMaxMat * p->V, "ray importance");
-        // [G][A][V] for the stage kernels, [G][V][8][A/8 padded to 4] for the dataflow kernel
+        // [G][V][A] for the stage kernels, [G][V][8][A/8 padded to 4] for the dataflow kernel
         if (!p->d_psi)
             rc = rc ? rc : dalloc_t(&p->d_psi, GV * std::max((size_t)p->A, (size_t)8 * flow_abp_host(p->A8)),
                                     "stored angular fluence");

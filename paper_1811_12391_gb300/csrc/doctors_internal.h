@@ -177,7 +177,7 @@ struct SweepArgs {
     float* yface;                      // [8][A8][G][nty-1][nx][nz]
     double* leak;                      // [G]
     int A;                             // directions (psi indexing)
-    float* psi;                        // written (mode 1) or read (mode 2): [G][A][V], dataflow kernel [G][V][8][ABP]
+    float* psi;                        // written (mode 1) or read (mode 2): [G][V][A], dataflow kernel [G][V][8][ABP]
     float* prod;                       // [G][V]: mode 2 accumulator
     const int* skip;                   // if non-null and *skip != 0 the kernel does nothing
     int chain_slots;                   // > 0: chained kernel, at most this many CTAs per stage launch
@@ -331,7 +331,7 @@ struct doctors_problem {
     double* d_grad = nullptr;      // [V] density gradient
     float* d_H = nullptr;          // [kMaxMat][V]
     float* d_ones = nullptr;       // [G]
-    float* d_psi = nullptr;        // [G][A][V] stored forward angular fluence
+    float* d_psi = nullptr;        // stored forward angular fluence ([G][V][A], or the dataflow layout)
     float* d_prod = nullptr;       // [G][V] angular product
     double* h_acc = nullptr;       // pinned [2G]
     bool solved = false;

@@ -337,17 +337,13 @@ __global__ void __launch_bounds__(256, 2)
                     cv[os + q] = psi[q];
                     zc[q] = psi[q];
                 }
-                if constexpr (MODE == 1) {
-#pragma unroll
-                    for (int q = 0; q < AB; ++q) a.psi[((size_t)(a.g0 + gi) * a.A + nb + q) * V + v] = psi[q];
-                }
+                if constexpr (MODE == 1) psi_store_run<AB>(a.psi + ((size_t)(a.g0 + gi) * V + v) * a.A + nb, psi);
                 if constexpr (MODE == 2) {
-                    float pacc = 0.0f;
+                    float wpsi[AB];
 #pragma unroll
-                    for (int q = 0; q < AB; ++q)
-                        pacc = fmaf((CT ? dt_at<CT>(dt, 9, q) : w_s[tab + q]) * psi[q],
-                                    __ldg(a.psi + ((size_t)(a.g0 + gi) * a.A + nb + q) * V + v), pacc);
-                    atomicAdd(a.prod + gV + v, pacc);
+                    for (int q = 0; q < AB; ++q) wpsi[q] = (CT ? dt_at<CT>(dt, 9, q) : w_s[tab + q]) * psi[q];
+                    red_add_f32(a.prod + gV + v,
+                                psi_product_run<AB>(a.psi + ((size_t)(a.g0 + gi) * V + v) * a.A + nb, wpsi));
                 }
                 // faces leaving the tile and current leaving the mesh
                 if (xout) {

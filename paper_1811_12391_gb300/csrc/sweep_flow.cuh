@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                 }
                 // stored angular fluence, laid out for this kernel as one 16-byte
                 // aligned record of ABP floats per (group, voxel, direction octant):
-                // [G][V][8][ABP] (the stage kernels use [G][A][V])
+                // [G][V][8][ABP] (the stage kernels use [G][V][A])
                 if constexpr (MODE == 1) {
                     float4* rec = reinterpret_cast<float4*>(a.psi + (((size_t)g * V + v) * 8 + oe) * ABP);
 #pragma unroll

@@ -60,6 +60,42 @@ __device__ __forceinline__ void load_moments(const float* p, float (&s)[M]) {
     }
 }
 
+// The stored angular fluence of the stage, chained and tensor-core kernels
+// (modes 1 and 2) is [G][V][A]: a voxel's directions are contiguous, so the
+// thread that sweeps a cell writes, and later reads, one contiguous run of
+// its block's directions (16-byte vectors when the block is a multiple of 4
+// directions, which then also starts on a 16-byte boundary).
+template <int AB>
+__device__ __forceinline__ void psi_store_run(float* rec, const float (&psi)[AB]) {
+    if constexpr (AB % 4 == 0) {
+#pragma unroll
+        for (int c4 = 0; c4 < AB / 4; ++c4)
+            reinterpret_cast<float4*>(rec)[c4] = make_float4(psi[4 * c4], psi[4 * c4 + 1], psi[4 * c4 + 2], psi[4 * c4 + 3]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < AB; ++q) rec[q] = psi[q];
+    }
+}
+// sum_q w_q psi_q stored_q over the run
+template <int AB>
+__device__ __forceinline__ float psi_product_run(const float* rec, const float (&wpsi)[AB]) {
+    float pacc = 0.0f;
+    if constexpr (AB % 4 == 0) {
+#pragma unroll
+        for (int c4 = 0; c4 < AB / 4; ++c4) {
+            const float4 t4 = __ldg(reinterpret_cast<const float4*>(rec) + c4);
+            pacc = fmaf(wpsi[4 * c4], t4.x, pacc);
+            pacc = fmaf(wpsi[4 * c4 + 1], t4.y, pacc);
+            pacc = fmaf(wpsi[4 * c4 + 2], t4.z, pacc);
+            pacc = fmaf(wpsi[4 * c4 + 3], t4.w, pacc);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < AB; ++q) pacc = fmaf(wpsi[q], __ldg(rec + q), pacc);
+    }
+    return pacc;
+}
+
 // one float added with a reduction that returns nothing
 __device__ __forceinline__ void red_add_f32(float* p, float x) {
     asm volatile("red.global.add.f32 [%0], %1;\n" ::"l"(p), "f"(x) : "memory");
@@ -259,16 +295,12 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs a) {
                 buf[(cb * AB + q) * T + col_id] = psi[q];
                 zc[q] = psi[q];
             }
-            if constexpr (MODE == 1) {
-#pragma unroll
-                for (int q = 0; q < AB; ++q) a.psi[((size_t)g * a.A + nbase + q) * V + v] = psi[q];
-            }
+            if constexpr (MODE == 1) psi_store_run<AB>(a.psi + ((size_t)g * V + v) * a.A + nbase, psi);
             if constexpr (MODE == 2) {
-                float pacc = 0.0f;
+                float wpsi[AB];
 #pragma unroll
-                for (int q = 0; q < AB; ++q)
-                    pacc = fmaf(w_s[q] * psi[q], __ldg(a.psi + ((size_t)g * a.A + nbase + q) * V + v), pacc);
-                atomicAdd(a.prod + gV + v, pacc);
+                for (int q = 0; q < AB; ++q) wpsi[q] = w_s[q] * psi[q];
+                red_add_f32(a.prod + gV + v, psi_product_run<AB>(a.psi + ((size_t)g * V + v) * a.A + nbase, wpsi));
             }
             // faces leaving the tile and current leaving the mesh
             if (xout) {

@@ -330,13 +330,15 @@ __global__ void __launch_bounds__(TX * TY, 2) k_sweep_tc(const SweepArgs a) {
                         lk = fmaf(f, my[s], lk);
                     }
                 }
+                // stored angular fluence [G][V][A] (the stage kernels' layout)
                 if constexpr (MODE == 1) {
-                    for (int s = 0; s < AB; ++s) a.psi[((size_t)g * a.A + nbase + s) * V + vme] = my[s];
+                    float* rec = a.psi + ((size_t)g * V + vme) * a.A + nbase;
+                    for (int s = 0; s < AB; ++s) rec[s] = my[s];
                 }
                 if constexpr (MODE == 2) {
+                    const float* rec = a.psi + ((size_t)g * V + vme) * a.A + nbase;
                     float pacc = 0.0f;
-                    for (int s = 0; s < AB; ++s)
-                        pacc = fmaf(leakc[s].w * my[s], __ldg(a.psi + ((size_t)g * a.A + nbase + s) * V + vme), pacc);
+                    for (int s = 0; s < AB; ++s) pacc = fmaf(leakc[s].w * my[s], __ldg(rec + s), pacc);
                     atomicAdd(a.prod + gV + vme, pacc);
                 }
             } else {

@@ -165,3 +165,31 @@ def test_gradients_satisfy_euler_identity(env, kernel):
     assert abs(float(w @ g["weights"].cpu().numpy()) - J) <= 2 * REL_TOL * abs(J)
     assert abs(float(chi @ g["spectrum"].cpu().numpy()) - J) <= 2 * REL_TOL * abs(J)
     d.close()
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_adjoint_gradients_s16_direction_blocks(env, kernel):
+    """S16 (three blocks of 12 directions per octant): the chained (default)
+    and tile-stage kernels store and pair the angular fluence in 16-byte runs
+    of a voxel's directions; adjoint fluence and all gradients against the
+    oracle."""
+    torch, C, DoctorsProblem = env
+    p = ph.abdomen(nx=16, ny=14, nz=4, d=2.0, dz=2.0, G=2, sn=16, L=1)
+    rng = np.random.default_rng(7)
+    p.density[:] = (p.density * rng.uniform(0.9, 1.1, size=p.V)).astype(np.float32)
+    roi = np.zeros(p.V)
+    roi.reshape(p.nz, p.ny, p.nx)[1:3, 5:9, 5:9] = 1.0 / 32.0
+    ref = osv.gradients(p, roi, tol=1e-12)
+    d = DoctorsProblem(p, tol=1e-6, max_iters=400, sweep_kernel=kernel, angles_per_block=12)
+    d.solve()
+    r = osv.response_from_roi(p, roi)
+    g = d.adjoint(torch.as_tensor(r, device="cuda"))
+    assert g["result"]["converged"] == 1
+    assert max_rel(d.fluence_host(C.DOCTORS_FLUENCE_ADJOINT), ref["adjoint"].Z[:, 0, :]) <= REL_TOL
+    np.testing.assert_allclose(g["weights"].cpu().numpy(), ref["d_weights"], rtol=REL_TOL)
+    np.testing.assert_allclose(g["spectrum"].cpu().numpy(), ref["d_spectrum"], rtol=REL_TOL)
+    explicit = (roi[None, :] * p.k_dep[p.mat].T * ref["forward"].phi).sum(axis=0)
+    gd = g["density"].cpu().numpy() + explicit
+    rd = ref["d_density"]
+    assert np.abs(gd - rd).max() <= REL_TOL * np.abs(rd).max()
+    d.close()
