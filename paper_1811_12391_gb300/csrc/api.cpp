@@ -773,9 +773,10 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
         const float cf = p->differencing == DOCTORS_DIFF_DIAMOND ? 2.0f : 1.0f;
         for (int j = 0; j < p->A8 && j < kFlowMaxAB; ++j) {
             real_harmonics(3, dirs[3 * j], dirs[3 * j + 1], dirs[3 * j + 2], Rb);
-            for (int lm = 0; lm < 16; ++lm) {
-                t.mop[j * 16 + lm] = (float)((2 * degree_of_lm(lm) + 1) / (4.0 * M_PI) * Rb[lm]);
-                t.dop[j * 16 + lm] = (float)(w[j] * Rb[lm]);
+            for (int m = 0; m < p->M; ++m) {
+                const int lm = lm_of_pos(m, p->M);
+                t.mop[j * 16 + m] = (float)((2 * degree_of_lm(lm) + 1) / (4.0 * M_PI) * Rb[lm]);
+                t.dop[m * kFlowMaxAB + j] = (float)(w[j] * Rb[lm]);
             }
         }
         for (int j = 0; j < p->A8; ++j) {

@@ -202,10 +202,13 @@ struct ChainDirTable {
     float cx[kMaxA8], cy[kMaxA8], cz[kMaxA8], csum[kMaxA8];   // |Omega_q| / d_q and their sum
     float lx[kMaxA8], ly[kMaxA8], lz[kMaxA8];                  // boundary current per face (w |Omega_q| area)
     float w[kMaxA8];
-    // the dataflow kernel's moment <-> direction rows of the first octant, in
-    // lm order: mop = (2l+1)/(4 pi) R_lm(Omega_q), dop = w_q R_lm(Omega_q)
-    // (kernel-parameter operands of the FMAs)
-    float mop[kFlowMaxAB * 16], dop[kFlowMaxAB * 16];
+    // the dataflow kernel's moment <-> direction tables of the first octant,
+    // indexed by the moment's storage position m (lm = lm_of_pos(m, M)):
+    // mop[q * 16 + m] = (2l+1)/(4 pi) R_lm(Omega_q) and, transposed,
+    // dop[m * kFlowMaxAB + q] = w_q R_lm(Omega_q), so that the operands of a
+    // packed two-lane FMA (two moments of one direction, two directions of one
+    // moment) are adjacent kernel-parameter words
+    float mop[kFlowMaxAB * 16], dop[16 * kFlowMaxAB];
 };
 // R_lm odd in x, y, z (bit lm)
 constexpr unsigned kOddX = (1u << 3) | (1u << 4) | (1u << 7) | (1u << 10) | (1u << 13) | (1u << 15);

@@ -306,13 +306,14 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                   if constexpr (SPLIT) {
                     psi[q] = s[q];
                   } else {
-                    float t0 = 0.0f, t1 = 0.0f;
+                    // even and odd moments in the two lanes of packed FMAs
+                    float2 t2 = make_float2(0.0f, 0.0f);
 #pragma unroll
-                    for (int m = 0; m < M; m += 2) {
-                        t0 = fmaf(dt.mop[q * 16 + lm_of_pos(m, M)], s[m], t0);
-                        if (m + 1 < M) t1 = fmaf(dt.mop[q * 16 + lm_of_pos(m + 1, M)], s[m + 1], t1);
-                    }
-                    psi[q] = t0 + t1;
+                    for (int m = 0; m + 1 < M; m += 2)
+                        t2 = __ffma2_rn(make_float2(dt.mop[q * 16 + m], dt.mop[q * 16 + m + 1]),
+                                        make_float2(s[m], s[m + 1]), t2);
+                    if constexpr (M % 2 == 1) t2.x = fmaf(dt.mop[q * 16 + M - 1], s[M - 1], t2.x);
+                    psi[q] = t2.x + t2.y;
                   }
                 }
                 // step-differenced cell solve
@@ -432,16 +433,18 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                     (void)mo;
                 } else {
                     // directions -> moments (Eq. 3 for lm = 00): table rows hold w R_lm
+                    // even and odd directions in the two lanes of packed FMAs
                     float acc[M];
 #pragma unroll
-                    for (int m = 0; m < M; ++m) acc[m] = 0.0f;
+                    for (int m = 0; m < M; ++m) {
+                        float2 t2 = make_float2(0.0f, 0.0f);
 #pragma unroll
-                    for (int q = 0; q < AB; ++q) {
-#pragma unroll
-                        for (int m = 0; m < M; ++m) acc[m] = fmaf(dt.dop[q * 16 + lm_of_pos(m, M)], psi[q], acc[m]);
+                        for (int q = 0; q + 1 < AB; q += 2)
+                            t2 = __ffma2_rn(make_float2(dt.dop[m * kFlowMaxAB + q], dt.dop[m * kFlowMaxAB + q + 1]),
+                                            make_float2(psi[q], psi[q + 1]), t2);
+                        if constexpr (AB % 2 == 1) t2.x = fmaf(dt.dop[m * kFlowMaxAB + AB - 1], psi[AB - 1], t2.x);
+                        acc[m] = (t2.x + t2.y) * octant_sign<M>(m, fx, fy, fz);
                     }
-#pragma unroll
-                    for (int m = 0; m < M; ++m) acc[m] *= octant_sign<M>(m, fx, fy, fz);
                     add_moments<M>(a.mom + mo, acc);
                 }
                 if (last && lk != 0.0f) {
