@@ -287,7 +287,14 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                         s[4 * c4] = t4.x; s[4 * c4 + 1] = t4.y; s[4 * c4 + 2] = t4.z; s[4 * c4 + 3] = t4.w;
                     }
 #pragma unroll
-                    for (int m = 0; m < NS; ++m) s[m] *= octant_sign<M>(m, fx, fy, fz);
+                    for (int m = 0; m + 1 < NS; m += 2) {
+                        const float2 r2 = __fmul2_rn(make_float2(s[m], s[m + 1]),
+                                                     make_float2(octant_sign<M>(m, fx, fy, fz),
+                                                                 octant_sign<M>(m + 1, fx, fy, fz)));
+                        s[m] = r2.x;
+                        s[m + 1] = r2.y;
+                    }
+                    if constexpr (NS % 2 == 1) s[NS - 1] *= octant_sign<M>(NS - 1, fx, fy, fz);
                 } else {
                     if constexpr (!SPLIT) {
 #pragma unroll
@@ -301,28 +308,59 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                 const int zo = zz * AB;               // this cell's fluxes within the column record
                 // moments -> directions (split: the record already holds them)
                 float psi[AB];
+                if constexpr (SPLIT) {
 #pragma unroll
-                for (int q = 0; q < AB; ++q) {
-                  if constexpr (SPLIT) {
-                    psi[q] = s[q];
-                  } else {
-                    // even and odd moments in the two lanes of packed FMAs
-                    float2 t2 = make_float2(0.0f, 0.0f);
+                    for (int q = 0; q < AB; ++q) psi[q] = s[q];
+                } else {
+                    // even and odd moments in the two lanes of packed FMAs; the lane
+                    // sums of directions q, q+1 in one packed add
+                    auto msum = [&](int q) {
+                        float2 t2 = make_float2(0.0f, 0.0f);
 #pragma unroll
-                    for (int m = 0; m + 1 < M; m += 2)
-                        t2 = __ffma2_rn(make_float2(dt.mop[q * 16 + m], dt.mop[q * 16 + m + 1]),
-                                        make_float2(s[m], s[m + 1]), t2);
-                    if constexpr (M % 2 == 1) t2.x = fmaf(dt.mop[q * 16 + M - 1], s[M - 1], t2.x);
-                    psi[q] = t2.x + t2.y;
-                  }
+                        for (int m = 0; m + 1 < M; m += 2)
+                            t2 = __ffma2_rn(make_float2(dt.mop[q * 16 + m], dt.mop[q * 16 + m + 1]),
+                                            make_float2(s[m], s[m + 1]), t2);
+                        if constexpr (M % 2 == 1) t2.x = fmaf(dt.mop[q * 16 + M - 1], s[M - 1], t2.x);
+                        return t2;
+                    };
+#pragma unroll
+                    for (int q = 0; q + 1 < AB; q += 2) {
+                        const float2 ta = msum(q), tb = msum(q + 1);
+                        const float2 p2 = __fadd2_rn(make_float2(ta.x, tb.x), make_float2(ta.y, tb.y));
+                        psi[q] = p2.x;
+                        psi[q + 1] = p2.y;
+                    }
+                    if constexpr (AB % 2 == 1) {
+                        const float2 ta = msum(AB - 1);
+                        psi[AB - 1] = ta.x + ta.y;
+                    }
                 }
                 // step-differenced cell solve
                 const float* pv = buf + pb * P * RS;
                 float* cv = buf + cb * P * RS;
                 const float* pvy = bufy + pb * P * RS;    // step: the same plane
                 float* cvy = bufy + cb * P * RS;
+                if constexpr (!DD) {
+                    // two directions per packed operation
 #pragma unroll
-                for (int q = 0; q < AB; ++q) {
+                    for (int q = 0; q + 1 < AB; q += 2) {
+                        const float2 px2 = make_float2(pv[xs + zo + q], pv[xs + zo + q + 1]);
+                        const float2 py2 = make_float2(pvy[ys + zo + q], pvy[ys + zo + q + 1]);
+                        float2 n2 = __ffma2_rn(make_float2(dt.cx[q], dt.cx[q + 1]), px2, make_float2(psi[q], psi[q + 1]));
+                        n2 = __ffma2_rn(make_float2(dt.cy[q], dt.cy[q + 1]), py2, n2);
+                        n2 = __ffma2_rn(make_float2(dt.cz[q], dt.cz[q + 1]), make_float2(zc[q], zc[q + 1]), n2);
+                        const float2 d2 = __fadd2_rn(make_float2(sig, sig), make_float2(dt.csum[q], dt.csum[q + 1]));
+                        const float2 p2 = make_float2(n2.x * rcp_approx(d2.x), n2.y * rcp_approx(d2.y));
+                        psi[q] = p2.x;
+                        psi[q + 1] = p2.y;
+                        cv[os + zo + q] = p2.x;
+                        cv[os + zo + q + 1] = p2.y;
+                        zc[q] = p2.x;
+                        zc[q + 1] = p2.y;
+                    }
+                }
+#pragma unroll
+                for (int q = DD ? 0 : (AB & ~1); q < AB; ++q) {
                     const float px = pv[xs + zo + q];
                     const float py = pvy[ys + zo + q];
                     const float num = fmaf(dt.cz[q], zc[q], fmaf(dt.cy[q], py, fmaf(dt.cx[q], px, psi[q])));
@@ -435,15 +473,29 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                     // directions -> moments (Eq. 3 for lm = 00): table rows hold w R_lm
                     // even and odd directions in the two lanes of packed FMAs
                     float acc[M];
-#pragma unroll
-                    for (int m = 0; m < M; ++m) {
+                    // sum over directions of moment m, even and odd directions in the two lanes
+                    auto dsum = [&](int m) {
                         float2 t2 = make_float2(0.0f, 0.0f);
 #pragma unroll
                         for (int q = 0; q + 1 < AB; q += 2)
                             t2 = __ffma2_rn(make_float2(dt.dop[m * kFlowMaxAB + q], dt.dop[m * kFlowMaxAB + q + 1]),
                                             make_float2(psi[q], psi[q + 1]), t2);
                         if constexpr (AB % 2 == 1) t2.x = fmaf(dt.dop[m * kFlowMaxAB + AB - 1], psi[AB - 1], t2.x);
-                        acc[m] = (t2.x + t2.y) * octant_sign<M>(m, fx, fy, fz);
+                        return t2;
+                    };
+#pragma unroll
+                    for (int m = 0; m + 1 < M; m += 2) {
+                        // lane sums and octant signs of moments m, m+1 in one packed add and multiply
+                        const float2 ta = dsum(m), tb = dsum(m + 1);
+                        const float2 r2 = __fmul2_rn(__fadd2_rn(make_float2(ta.x, tb.x), make_float2(ta.y, tb.y)),
+                                                     make_float2(octant_sign<M>(m, fx, fy, fz),
+                                                                 octant_sign<M>(m + 1, fx, fy, fz)));
+                        acc[m] = r2.x;
+                        acc[m + 1] = r2.y;
+                    }
+                    if constexpr (M % 2 == 1) {
+                        const float2 ta = dsum(M - 1);
+                        acc[M - 1] = (ta.x + ta.y) * octant_sign<M>(M - 1, fx, fy, fz);
                     }
                     add_moments<M>(a.mom + mo, acc);
                 }
