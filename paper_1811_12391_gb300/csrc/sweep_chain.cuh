@@ -305,8 +305,7 @@ __global__ void __launch_bounds__(256, 2)
                 float psi[AB];
 #pragma unroll
                 for (int q = 0; q < AB; ++q) {
-                    // four partial sums (moments m mod 4) in two packed two-lane FMAs
-                    float2 t01 = make_float2(0.0f, 0.0f), t23 = make_float2(0.0f, 0.0f);
+                    float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f, t3 = 0.0f;
 #pragma unroll
                     for (int m = 0; m < M; m += 4) {
                         constexpr int rb = chain_row_base(AB) * 16;
@@ -315,12 +314,12 @@ __global__ void __launch_bounds__(256, 2)
                                                           c_Mop1[rb + q * 16 + lm_of_pos(m + 2, M)],
                                                           c_Mop1[rb + q * 16 + lm_of_pos(m + 3, M)])
                                             : R_s[4 * (tab + q) + m / 4];
-                        if (m + 1 < M) t01 = __ffma2_rn(make_float2(R.x, R.y), make_float2(s[m], s[m + 1]), t01);
-                        else t01.x = fmaf(R.x, s[m], t01.x);
-                        if (m + 3 < M) t23 = __ffma2_rn(make_float2(R.z, R.w), make_float2(s[m + 2], s[m + 3]), t23);
-                        else if (m + 2 < M) t23.x = fmaf(R.z, s[m + 2], t23.x);
+                        t0 = fmaf(R.x, s[m], t0);
+                        if (m + 1 < M) t1 = fmaf(R.y, s[m + 1], t1);
+                        if (m + 2 < M) t2 = fmaf(R.z, s[m + 2], t2);
+                        if (m + 3 < M) t3 = fmaf(R.w, s[m + 3], t3);
                     }
-                    psi[q] = (t01.x + t01.y) + (t23.x + t23.y);
+                    psi[q] = (t0 + t1) + (t2 + t3);
                 }
                 // step-differenced cell solve per direction (branch-free
                 // upwind reads: the halo holds the incoming face values)
@@ -380,7 +379,6 @@ __global__ void __launch_bounds__(256, 2)
                 for (int q = 0; q < AB; ++q) {
                     // CT: the table holds w R_lm
                     const float wp = CT ? psi[q] : w_s[tab + q] * psi[q];
-                    const float2 w2 = make_float2(wp, wp);
 #pragma unroll
                     for (int m = 0; m < M; m += 4) {
                         constexpr int rb = chain_row_base(AB) * 16;
@@ -389,21 +387,10 @@ __global__ void __launch_bounds__(256, 2)
                                                           c_Dop1[rb + q * 16 + lm_of_pos(m + 2, M)],
                                                           c_Dop1[rb + q * 16 + lm_of_pos(m + 3, M)])
                                             : R_s[4 * (tab + q) + m / 4];
-                        // moment pairs in packed two-lane FMAs
-                        if (m + 1 < M) {
-                            const float2 r2 = __ffma2_rn(make_float2(R.x, R.y), w2, make_float2(acc[m], acc[m + 1]));
-                            acc[m] = r2.x;
-                            acc[m + 1] = r2.y;
-                        } else {
-                            acc[m] = fmaf(R.x, wp, acc[m]);
-                        }
-                        if (m + 3 < M) {
-                            const float2 r2 = __ffma2_rn(make_float2(R.z, R.w), w2, make_float2(acc[m + 2], acc[m + 3]));
-                            acc[m + 2] = r2.x;
-                            acc[m + 3] = r2.y;
-                        } else if (m + 2 < M) {
-                            acc[m + 2] = fmaf(R.z, wp, acc[m + 2]);
-                        }
+                        acc[m] = fmaf(R.x, wp, acc[m]);
+                        if (m + 1 < M) acc[m + 1] = fmaf(R.y, wp, acc[m + 1]);
+                        if (m + 2 < M) acc[m + 2] = fmaf(R.z, wp, acc[m + 2]);
+                        if (m + 3 < M) acc[m + 3] = fmaf(R.w, wp, acc[m + 3]);
                     }
                 }
                 if constexpr (CT) {
