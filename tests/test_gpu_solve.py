@@ -58,6 +58,7 @@ def cylinder_ref():
                                             ((8, 4), 5, 2), ((8, 4), 5, 3), ((5, 7), 2, 1), ((5, 7), 2, 3),
                                             ((32, 8), 10, 2), ((32, 8), 10, 3), ((8, 16), 10, 2), ((16, 2), 1, 3),
                                             ((16, 16), 10, 4), ((16, 8), 10, 4), ((5, 7), 10, 4), ((8, 4), 10, 4),
+                                            ((8, 8), 10, 4), ((8, 8), 10, 0),
                                             ((8, 8), 10, 5), ((16, 8), 10, 5), ((5, 7), 10, 5),
                                             ((8, 8), 10, 6), ((16, 8), 10, 6), ((5, 7), 10, 6)])
 def test_ragged_multitile_cylinder(dp, cylinder_ref, tile, ab, kernel):
