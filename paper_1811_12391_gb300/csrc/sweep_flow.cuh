@@ -161,7 +161,6 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
         const int sx = (o & 1) ? -1 : 1, sy = (o & 2) ? -1 : 1, sz = (o & 4) ? -1 : 1;
         const int oe = a.reverse ? (o ^ 7) : o;     // octant of the directions
         const float fx = (oe & 1) ? -1.0f : 1.0f, fy = (oe & 2) ? -1.0f : 1.0f, fz = (oe & 4) ? -1.0f : 1.0f;
-        const int nb = oe * a.A8;
         const int ir = at * a.tx + li, jr = bt * a.ty + lj;
         const bool col = ir < a.nx && jr < a.ny;
         const int i = sx > 0 ? ir : a.nx - 1 - ir;
