@@ -123,3 +123,40 @@ def test_ct_conversion_checks_tables_before_touching_the_device(lib):
             raise AssertionError(f"accepted {t} {hk} {rk}")
     m0, r0 = S.ct_to_materials(np.zeros(0, np.float32), [], [4], [0.0], [1.25])
     assert m0.size == 0 and r0.size == 0
+
+
+def _c_struct_fields(header: str, name: str):
+    """(field name, array length) in declaration order of `typedef struct name {...}`
+    in the public header (comments stripped)."""
+    import re
+    m = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), header, re.S)
+    assert m, name
+    body = re.sub(r"/\*.*?\*/", "", m.group(1), flags=re.S)
+    out = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        # "type a, b[3], c": the first part ends with the first declarator
+        for part in decl.split(","):
+            mm = re.search(r"\**\s*(\w+)\s*(?:\[(\d+)\])?\s*$", part.strip())
+            assert mm, (name, part)
+            out.append((mm.group(1), int(mm.group(2) or 1)))
+    return out
+
+
+def test_ctypes_structs_mirror_the_header():
+    """Every struct of include/doctors.h and its ctypes mirror in the binding
+    have the same fields in the same order with the same array lengths (an
+    inserted option field must move in both)."""
+    import ctypes
+    import os
+    from paper_1811_12391_gb300 import _lib as C
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "doctors.h")).read()
+    for name in ("doctors_mesh", "doctors_options", "doctors_source", "doctors_result", "doctors_tuning"):
+        want = _c_struct_fields(hdr, name)
+        got = []
+        for fname, ftype in getattr(C, name)._fields_:
+            n = getattr(ftype, "_length_", 1) if issubclass(ftype, ctypes.Array) else 1
+            got.append((fname, n))
+        assert got == want, (name, got, want)
