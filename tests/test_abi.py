@@ -138,10 +138,13 @@ def _c_struct_fields(header: str, name: str):
         if not decl:
             continue
         # "type a, b[3], c": the first part ends with the first declarator
-        for part in decl.split(","):
+        parts = decl.split(",")
+        tm = re.match(r"((?:const\s+)?(?:unsigned\s+)?(?:long\s+long|\w+))\s*(\**)", parts[0].strip())
+        ctype = tm.group(1).replace("const ", "").strip() + ("*" if tm.group(2) else "")
+        for part in parts:
             mm = re.search(r"\**\s*(\w+)\s*(?:\[(\d+)\])?\s*$", part.strip())
             assert mm, (name, part)
-            out.append((mm.group(1), int(mm.group(2) or 1)))
+            out.append((mm.group(1), int(mm.group(2) or 1), ctype))
     return out
 
 
@@ -153,10 +156,17 @@ def test_ctypes_structs_mirror_the_header():
     import os
     from paper_1811_12391_gb300 import _lib as C
     hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "doctors.h")).read()
+    ctypes_of = {"int": ctypes.c_int, "double": ctypes.c_double, "long long": ctypes.c_longlong,
+                 "float": ctypes.c_float, "double*": ctypes.POINTER(ctypes.c_double)}
     for name in ("doctors_mesh", "doctors_options", "doctors_source", "doctors_result", "doctors_tuning"):
         want = _c_struct_fields(hdr, name)
         got = []
         for fname, ftype in getattr(C, name)._fields_:
             n = getattr(ftype, "_length_", 1) if issubclass(ftype, ctypes.Array) else 1
-            got.append((fname, n))
-        assert got == want, (name, got, want)
+            got.append((fname, n, ftype._type_ if n > 1 else ftype))
+        assert [(f, n) for f, n, _ in got] == [(f, n) for f, n, _ in want], (name, got, want)
+        for (f, n, t), (_, _, ct) in zip(got, want):
+            assert ct in ctypes_of, (name, f, ct)
+            assert ctypes.sizeof(t) == ctypes.sizeof(ctypes_of[ct]) and \
+                (t is ctypes_of[ct] or getattr(t, "_type_", None) == getattr(ctypes_of[ct], "_type_", None)), (name, f, t, ct)
+        assert ctypes.sizeof(getattr(C, name)) >= 1
