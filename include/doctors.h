@@ -184,8 +184,9 @@ int doctors_set_source(doctors_problem *p, int n_src, const doctors_source *src)
 
 /* Solve: Siddon ray trace of the uncollided fluence of every point source
  * and its first-collision source (Sec. II.A), then source iteration of the
- * collided problem (Eq. 2, vacuum boundaries) with step-differenced octant
- * wavefront sweeps, all groups per sweep.  Synchronises the stream.  Returns
+ * collided problem (Eq. 2, vacuum boundaries) with step-differenced (or, per
+ * options.differencing, diamond-differenced) octant wavefront sweeps, all
+ * active groups per sweep.  Synchronises the stream.  Returns
  * DOCTORS_ERR_NOT_CONVERGED (results kept) if max_iters is reached.  `info`
  * may be NULL. */
 int doctors_solve(doctors_problem *p, doctors_result *info);
