@@ -733,6 +733,11 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     p->ntx = (p->nx + p->tx - 1) / p->tx;
     p->nty = (p->ny + p->ty - 1) / p->ty;
     if (opt->sweep_kernel < 0 || opt->sweep_kernel > 6) return fail(DOCTORS_ERR_INVALID_ARG, "sweep_kernel must be 0 .. 6");
+    if (p->differencing == DOCTORS_DIFF_DIAMOND &&
+        !((opt->sweep_kernel == 0 || opt->sweep_kernel == 4) && p->A8 == p->ab && chain_const_table_ab(p->ab)))
+        return fail(DOCTORS_ERR_INVALID_ARG,
+                    "diamond differencing runs on the dataflow sweep: sweep_kernel 0 or 4, angles_per_block = "
+                    "N(N+2)/8 and N <= 8");
     if (opt->sweep_kernel == 2 && !sweep_tc_supported(p->ab, p->M, p->tx, p->ty))
         return fail(DOCTORS_ERR_INVALID_ARG, "tensor-core sweep needs P3, <= 16 directions per block and a 16x16, 32x8, 16x8, 8x16, 8x8 or 8x4 tile");
     cudaError_t e = cudaGetDevice(&p->device);

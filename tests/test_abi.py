@@ -90,6 +90,12 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib):
         C.DOCTORS_ERR_INVALID_ARG
     assert "differencing" in C.last_error()
     opt.differencing = C.DOCTORS_DIFF_DIAMOND
+    for kernel, sn in ((1, 4), (3, 4), (5, 4), (0, 16)):
+        opt.sweep_kernel, opt.sn_order = kernel, sn
+        assert C.doctors_create_problem(ctypes.byref(mesh), ctypes.byref(opt), None, ctypes.byref(h)) == \
+            C.DOCTORS_ERR_INVALID_ARG
+        assert "diamond" in C.last_error()
+    opt.sweep_kernel, opt.sn_order = 0, 4
     opt.reserved[0] = 1
     assert C.doctors_create_problem(ctypes.byref(mesh), ctypes.byref(opt), None, ctypes.byref(h)) == \
         C.DOCTORS_ERR_INVALID_ARG
