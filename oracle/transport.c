@@ -14,6 +14,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define IDX(i, j, k) (((size_t)(k) * (size_t)ny + (size_t)(j)) * (size_t)nx + (size_t)(i))
 
@@ -143,15 +146,18 @@ int oracle_optical_depth(int nx, int ny, int nz, const double *o, const double *
 {
     size_t V = (size_t)nx * ny * nz;
     int cap = 4 * (nx + ny + nz) + 8;
-    int32_t *idx = (int32_t *)malloc(sizeof(int32_t) * cap);
-    double *len = (double *)malloc(sizeof(double) * cap);
     int rc = 0;
-    for (int k = 0; k < nz && rc == 0; ++k)
-        for (int j = 0; j < ny && rc == 0; ++j)
+    /* every voxel's ray is independent: one z plane per OpenMP iteration */
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int k = 0; k < nz; ++k) {
+        int32_t *idx = (int32_t *)malloc(sizeof(int32_t) * cap);
+        double *len = (double *)malloc(sizeof(double) * cap);
+        int err = !idx || !len;
+        for (int j = 0; j < ny && !err; ++j)
             for (int i = 0; i < nx; ++i) {
                 size_t v = IDX(i, j, k);
                 int cnt = oracle_siddon_f64(S, i, j, k, nx, ny, nz, o, d, idx, len, cap);
-                if (cnt < 0) { rc = -1; break; }
+                if (cnt < 0) { err = 1; break; }
                 for (int g = 0; g < G; ++g) tau[(size_t)g * V + v] = 0.0;
                 for (int s = 0; s < cnt; ++s) {
                     size_t u = (size_t)idx[s];
@@ -163,8 +169,13 @@ int oracle_optical_depth(int nx, int ny, int nz, const double *o, const double *
                 double t2 = o[2] + ((double)k + 0.5) * d[2] - S[2];
                 r2[v] = t0 * t0 + t1 * t1 + t2 * t2;
             }
-    free(idx);
-    free(len);
+        free(idx);
+        free(len);
+        if (err) {
+#pragma omp atomic write
+            rc = -1;
+        }
+    }
     return rc;
 }
 
@@ -213,68 +224,126 @@ void oracle_collimator_mask(int nx, int ny, int nz, const float *o, const float 
 /*   w_n |Omega_q| psi_out,q(v) A_q over boundary faces (A_q the face area).  */
 /* If psi_out is given, psi of every direction is stored there [A][V].      */
 /* ------------------------------------------------------------------------ */
-void oracle_sweep(int nx, int ny, int nz, double dx, double dy, double dz,
-                  int A, const double *dirs /* [A][3] */, const double *w /* [A] */,
-                  int M, const double *Mop /* [A][M] */, const double *Dop /* [A][M] */,
-                  const double *sigt /* [V] */, const double *src /* [M][V] */,
-                  double *phi /* [M][V] */, double *leak, double *psi_out /* [A][V] or NULL */,
-                  int diamond)
+/* The directions are taken in ORACLE_DIRECTION_BLOCKS fixed contiguous     */
+/* blocks; each block sums its directions' contributions to phi and to the   */
+/* leakage in direction order, and the blocks are then added in block order  */
+/* (Eq. 3's quadrature sum, in an order that does not depend on how many     */
+/* host threads run the blocks: with OpenMP the blocks run in parallel).     */
+#define ORACLE_DIRECTION_BLOCKS 8
+
+static void sweep_direction(int nx, int ny, int nz, double dx, double dy, double dz, int n,
+                            const double *dirs, const double *w, int M, const double *Mop,
+                            const double *Dop, const double *sigt, const double *src,
+                            double *phi, double *lk_out, double *psi_out, int diamond,
+                            double *psi, double *fx, double *fy, double *fz)
 {
     size_t V = (size_t)nx * ny * nz;
-    double *psi = (double *)malloc(sizeof(double) * V);
-    /* outgoing face fluxes along x, y, z of every cell of the current direction */
-    double *fx = (double *)malloc(sizeof(double) * V);
-    double *fy = (double *)malloc(sizeof(double) * V);
-    double *fz = (double *)malloc(sizeof(double) * V);
-    memset(phi, 0, sizeof(double) * V * (size_t)M);
     double lk = 0.0;
-    for (int n = 0; n < A; ++n) {
-        double ox = dirs[3 * n + 0], oy = dirs[3 * n + 1], oz = dirs[3 * n + 2];
-        double cx = fabs(ox) / dx, cy = fabs(oy) / dy, cz = fabs(oz) / dz;
-        int i0 = ox > 0 ? 0 : nx - 1, di = ox > 0 ? 1 : -1;
-        int j0 = oy > 0 ? 0 : ny - 1, dj = oy > 0 ? 1 : -1;
-        int k0 = oz > 0 ? 0 : nz - 1, dk = oz > 0 ? 1 : -1;
-        for (int kk = 0; kk < nz; ++kk) {
-            int k = k0 + dk * kk;
-            for (int jj = 0; jj < ny; ++jj) {
-                int j = j0 + dj * jj;
-                for (int ii = 0; ii < nx; ++ii) {
-                    int i = i0 + di * ii;
-                    size_t v = IDX(i, j, k);
-                    double q = 0.0;
-                    for (int lm = 0; lm < M; ++lm) q += Mop[(size_t)n * M + lm] * src[(size_t)lm * V + v];
-                    double px = ii > 0 ? fx[IDX(i - di, j, k)] : 0.0;
-                    double py = jj > 0 ? fy[IDX(i, j - dj, k)] : 0.0;
-                    double pz = kk > 0 ? fz[IDX(i, j, k - dk)] : 0.0;
-                    double p;
-                    if (diamond) {
-                        p = (q + 2.0 * (cx * px + cy * py + cz * pz)) / (sigt[v] + 2.0 * (cx + cy + cz));
-                        fx[v] = 2.0 * p - px;
-                        fy[v] = 2.0 * p - py;
-                        fz[v] = 2.0 * p - pz;
-                    } else {
-                        p = (q + cx * px + cy * py + cz * pz) / (sigt[v] + cx + cy + cz);
-                        fx[v] = fy[v] = fz[v] = p;
-                    }
-                    psi[v] = p;
-                    if (ii == nx - 1) lk += w[n] * fabs(ox) * fx[v] * dy * dz;
-                    if (jj == ny - 1) lk += w[n] * fabs(oy) * fy[v] * dx * dz;
-                    if (kk == nz - 1) lk += w[n] * fabs(oz) * fz[v] * dx * dy;
+    double ox = dirs[3 * n + 0], oy = dirs[3 * n + 1], oz = dirs[3 * n + 2];
+    double cx = fabs(ox) / dx, cy = fabs(oy) / dy, cz = fabs(oz) / dz;
+    int i0 = ox > 0 ? 0 : nx - 1, di = ox > 0 ? 1 : -1;
+    int j0 = oy > 0 ? 0 : ny - 1, dj = oy > 0 ? 1 : -1;
+    int k0 = oz > 0 ? 0 : nz - 1, dk = oz > 0 ? 1 : -1;
+    for (int kk = 0; kk < nz; ++kk) {
+        int k = k0 + dk * kk;
+        for (int jj = 0; jj < ny; ++jj) {
+            int j = j0 + dj * jj;
+            for (int ii = 0; ii < nx; ++ii) {
+                int i = i0 + di * ii;
+                size_t v = IDX(i, j, k);
+                double q = 0.0;
+                for (int lm = 0; lm < M; ++lm) q += Mop[(size_t)n * M + lm] * src[(size_t)lm * V + v];
+                double px = ii > 0 ? fx[IDX(i - di, j, k)] : 0.0;
+                double py = jj > 0 ? fy[IDX(i, j - dj, k)] : 0.0;
+                double pz = kk > 0 ? fz[IDX(i, j, k - dk)] : 0.0;
+                double p;
+                if (diamond) {
+                    p = (q + 2.0 * (cx * px + cy * py + cz * pz)) / (sigt[v] + 2.0 * (cx + cy + cz));
+                    fx[v] = 2.0 * p - px;
+                    fy[v] = 2.0 * p - py;
+                    fz[v] = 2.0 * p - pz;
+                } else {
+                    p = (q + cx * px + cy * py + cz * pz) / (sigt[v] + cx + cy + cz);
+                    fx[v] = fy[v] = fz[v] = p;
                 }
+                psi[v] = p;
+                if (ii == nx - 1) lk += w[n] * fabs(ox) * fx[v] * dy * dz;
+                if (jj == ny - 1) lk += w[n] * fabs(oy) * fy[v] * dx * dz;
+                if (kk == nz - 1) lk += w[n] * fabs(oz) * fz[v] * dx * dy;
             }
         }
-        for (int lm = 0; lm < M; ++lm) {
-            double c = Dop[(size_t)n * M + lm];
-            double *ph = phi + (size_t)lm * V;
-            for (size_t v = 0; v < V; ++v) ph[v] += c * psi[v];
-        }
-        if (psi_out) memcpy(psi_out + (size_t)n * V, psi, sizeof(double) * V);
+    }
+    for (int lm = 0; lm < M; ++lm) {
+        double c = Dop[(size_t)n * M + lm];
+        double *ph = phi + (size_t)lm * V;
+        for (size_t v = 0; v < V; ++v) ph[v] += c * psi[v];
+    }
+    if (psi_out) memcpy(psi_out + (size_t)n * V, psi, sizeof(double) * V);
+    *lk_out += lk;
+}
+
+/* Returns 0, or -1 if scratch memory could not be allocated. */
+int oracle_sweep(int nx, int ny, int nz, double dx, double dy, double dz,
+                 int A, const double *dirs /* [A][3] */, const double *w /* [A] */,
+                 int M, const double *Mop /* [A][M] */, const double *Dop /* [A][M] */,
+                 const double *sigt /* [V] */, const double *src /* [M][V] */,
+                 double *phi /* [M][V] */, double *leak, double *psi_out /* [A][V] or NULL */,
+                 int diamond)
+{
+    size_t V = (size_t)nx * ny * nz;
+    const int NB = ORACLE_DIRECTION_BLOCKS;
+    double lkb[ORACLE_DIRECTION_BLOCKS];
+    /* block 0 accumulates into phi, blocks 1.. into their own arrays */
+    double *part = (double *)calloc((size_t)(NB - 1) * M * V, sizeof(double));
+    double *scratch = (double *)malloc(sizeof(double) * 4 * V * (size_t)NB);
+    if (!part || !scratch) {
+        free(part);
+        free(scratch);
+        return -1;
+    }
+    memset(phi, 0, sizeof(double) * V * (size_t)M);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int b = 0; b < NB; ++b) {
+        double *acc = b == 0 ? phi : part + (size_t)(b - 1) * M * V;
+        double *sc = scratch + (size_t)b * 4 * V;
+        lkb[b] = 0.0;
+        int n0 = (int)(((long)A * b) / NB), n1 = (int)(((long)A * (b + 1)) / NB);
+        for (int n = n0; n < n1; ++n)
+            sweep_direction(nx, ny, nz, dx, dy, dz, n, dirs, w, M, Mop, Dop, sigt, src, acc, &lkb[b],
+                            psi_out, diamond, sc, sc + V, sc + 2 * V, sc + 3 * V);
+    }
+    double lk = lkb[0];
+    for (int b = 1; b < NB; ++b) {
+        const double *pb = part + (size_t)(b - 1) * M * V;
+        for (size_t e = 0; e < (size_t)M * V; ++e) phi[e] += pb[e];
+        lk += lkb[b];
     }
     *leak = lk;
-    free(psi);
-    free(fx);
-    free(fy);
-    free(fz);
+    free(part);
+    free(scratch);
+    return 0;
+}
+
+/* Host threads used by the OpenMP loops (1 when built without OpenMP). */
+int oracle_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Sets the number of host threads of the OpenMP loops; returns the number
+ * in effect. */
+int oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+    return oracle_threads();
 }
 
 /* Back-projection along the rays for the density gradient of the

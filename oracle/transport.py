@@ -28,14 +28,30 @@ _int = ctypes.c_int
 
 
 def build(force: bool = False) -> str:
-    """Compile transport.c (no FMA contraction, IEEE operations as written)."""
+    """Compile transport.c (no FMA contraction, IEEE operations as written),
+    with OpenMP when the compiler offers it (the sweep's direction blocks and
+    the ray trace's planes then run on all host cores; results do not depend
+    on the thread count)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=gnu99", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
+        try:
+            subprocess.check_call(base + ["-fopenmp", "-o", tmp, _SRC, "-lm"], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base + ["-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
     return _SO
+
+
+def threads() -> int:
+    """Host threads of the oracle's OpenMP loops (1 without OpenMP)."""
+    return int(lib().oracle_threads())
+
+
+def set_threads(n: int) -> int:
+    """Sets the oracle's host threads; returns the number in effect."""
+    return int(lib().oracle_set_threads(int(n)))
 
 
 def lib():
@@ -55,7 +71,11 @@ def lib():
             L.oracle_sweep.argtypes = [_int, _int, _int, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, _int, _d, _d, _int, _d, _d, _d, _d, _d,
                                        _d, _d, _int]
-            L.oracle_sweep.restype = None
+            L.oracle_sweep.restype = _int
+            L.oracle_threads.argtypes = []
+            L.oracle_threads.restype = _int
+            L.oracle_set_threads.argtypes = [_int]
+            L.oracle_set_threads.restype = _int
             L.oracle_backproject.argtypes = [_int, _int, _int, _d, _d, _u8, _int, _d, _d, _d]
             L.oracle_backproject.restype = _int
             _lib = L
@@ -143,10 +163,12 @@ def sweep(dims, spacing, dirs, w, Mop, Dop, sigt, src, store_psi=False, diamond=
     phi = np.zeros((M, V))
     leak = np.zeros(1)
     psi = np.zeros((A, V)) if store_psi else None
-    lib().oracle_sweep(nx, ny, nz, float(spacing[0]), float(spacing[1]), float(spacing[2]), A,
-                       _p(dirs, _d), _p(w, _d), M, _p(Mop, _d), _p(Dop, _d), _p(sigt, _d),
-                       _p(src, _d), _p(phi, _d), _p(leak, _d),
-                       _p(psi, _d) if psi is not None else None, int(bool(diamond)))
+    rc = lib().oracle_sweep(nx, ny, nz, float(spacing[0]), float(spacing[1]), float(spacing[2]), A,
+                            _p(dirs, _d), _p(w, _d), M, _p(Mop, _d), _p(Dop, _d), _p(sigt, _d),
+                            _p(src, _d), _p(phi, _d), _p(leak, _d),
+                            _p(psi, _d) if psi is not None else None, int(bool(diamond)))
+    if rc != 0:
+        raise MemoryError("oracle sweep: scratch allocation failed")
     return phi, float(leak[0]), psi
 
 
