@@ -236,10 +236,9 @@ def bench_configs(torch, DoctorsProblem, ph, stream):
             rec["raytrace"] = {"rays_per_source": p.V, "voxel_visits_per_source": ray_visits(p, p.sources[0]),
                                "ms_first_collision": r["ms_raytrace"]}
         if name == "differentiable_abdomen":
-            roi = p.roi / p.roi.sum()
-            resp = torch.as_tensor(p.k_dep[p.mat].T * (p.density.astype(np.float64) * roi)[None, :], device="cuda")
-            d.adjoint(resp)
-            g = d.adjoint(resp)
+            roi = torch.as_tensor(p.roi / p.roi.sum(), device="cuda")
+            d.roi_gradients(p.k_dep, roi)
+            g = d.roi_gradients(p.k_dep, roi)
             rec["adjoint_ms"] = g["result"]["ms_total"]
             rec["adjoint_iterations"] = g["result"]["iterations"]
             rec["gradients"] = {"view_weights": int(g["weights"].numel()), "spectrum": int(g["spectrum"].numel()),
@@ -440,11 +439,10 @@ def main():
             roi = np.zeros(p.V)
             roi.reshape(p.nz, p.ny, p.nx)[p.nz // 2 - 2:p.nz // 2 + 2, p.ny // 2 - 4:p.ny // 2 + 4,
                                           p.nx // 2 - 4:p.nx // 2 + 4] = 1.0 / 256.0
-            resp = torch.as_tensor(p.k_dep[p.mat].T * (p.density.astype(np.float64) * roi)[None, :],
-                                   device="cuda")
+            roi = torch.as_tensor(roi, device="cuda")
             d.solve()
-            g = d.adjoint(resp)
-            g = d.adjoint(resp)
+            g = d.roi_gradients(p.k_dep, roi)
+            g = d.roi_gradients(p.k_dep, roi)
             adjoint = {"ms_per_solve": g["result"]["ms_total"], "iterations": g["result"]["iterations"],
                        "gradients": "view weights, spectrum, densities"}
         d.close()

@@ -236,6 +236,31 @@ int doctors_dose_noalloc(doctors_problem *p, const double *k, double *dose);
 int doctors_adjoint_solve(doctors_problem *p, const double *response, int mem, double *d_weights,
                           double *d_spectrum, double *d_density, doctors_result *info);
 
+/* Region-of-interest dose (Sec. II.A, III.A: the dose tally, summed over a
+ * region with voxel weights).  J = sum_v roi[v] * dose[v], dose as in
+ * doctors_dose, summed in FP64 on the device in a fixed order (the same
+ * inputs give the same bits).  k [n_mat][G] host doubles, finite; roi [V]
+ * float64 in `mem` (finite); *J is host memory; dose [V] float64 in `mem`
+ * or NULL.  Host inputs are copied before the call returns.  DOCTORS_ERR_STATE
+ * before a successful solve; DOCTORS_ERR_INVALID_ARG for null or non-finite
+ * inputs, with no output written.  Synchronises. */
+int doctors_roi_dose(doctors_problem *p, const double *k, const double *roi, int mem, double *J,
+                     double *dose);
+
+/* Gradients of the region-of-interest dose J above (no counterpart in the
+ * paper; the discrete adjoint of Eq. 2 and the chain rule through the ray
+ * trace and the tally).  Forms the adjoint response
+ * r[g][v] = roi[v] * k[mat v][g] * density[v] on the device, solves the
+ * adjoint as doctors_adjoint_solve does, and writes *J (host) and every
+ * non-NULL output (float64, in `mem`): d_weights [n_src], d_spectrum [G] as
+ * doctors_adjoint_solve, and d_density [V] = the full dJ/d density[v]: the
+ * transport part plus the dose's own density factor
+ * roi[v] * sum_g k[mat v][g] * (phi_u + phi_c)[g][v].  Argument rules as
+ * doctors_roi_dose; `info` (may be NULL) reports the adjoint iteration;
+ * DOCTORS_ERR_NOT_CONVERGED keeps the outputs.  Synchronises. */
+int doctors_roi_gradients(doctors_problem *p, const double *k, const double *roi, int mem, double *J,
+                          double *d_weights, double *d_spectrum, double *d_density, doctors_result *info);
+
 /* Test hook for the dataflow sweep's bounded waits (sweep_kernel 4 or 5): from the
  * next sweep on, the sweep task numbered `task` (stage-major order) does not
  * write the face fluxes it owes its downstream tiles, so their waits run out;

@@ -94,6 +94,9 @@ SIGNATURES = [
     ("doctors_dose", _int, [_vp, _P(ctypes.c_double), _vp, _int]),
     ("doctors_dose_noalloc", _int, [_vp, _P(ctypes.c_double), _vp]),
     ("doctors_adjoint_solve", _int, [_vp, _vp, _int, _vp, _vp, _vp, _P(doctors_result)]),
+    ("doctors_roi_dose", _int, [_vp, _P(ctypes.c_double), _vp, _int, _P(ctypes.c_double), _vp]),
+    ("doctors_roi_gradients", _int, [_vp, _P(ctypes.c_double), _vp, _int, _P(ctypes.c_double), _vp, _vp, _vp,
+                                     _P(doctors_result)]),
     ("doctors_debug_withhold_faces", _int, [_vp, _int]),
     ("doctors_debug_ray_indices", _int, [_vp, _int, _int, _P(ctypes.c_int32), _P(ctypes.c_float), _int,
                                          _P(_int)]),
@@ -159,6 +162,8 @@ doctors_get_fluence = _fwd("doctors_get_fluence")
 doctors_dose = _fwd("doctors_dose")
 doctors_dose_noalloc = _fwd("doctors_dose_noalloc")
 doctors_adjoint_solve = _fwd("doctors_adjoint_solve")
+doctors_roi_dose = _fwd("doctors_roi_dose")
+doctors_roi_gradients = _fwd("doctors_roi_gradients")
 doctors_debug_ray_indices = _fwd("doctors_debug_ray_indices")
 doctors_debug_withhold_faces = _fwd("doctors_debug_withhold_faces")
 doctors_quadrature = _fwd("doctors_quadrature")

@@ -1,19 +1,17 @@
 """Differentiable region-of-interest dose.
 
 RoiDose.apply(weights [S], spectrum [G], density [V]) -> J = sum_v roi(v) D(v)
-with D the dose tally of the forward solve.  The forward pass and the
-gradients run in libdoctors: doctors_solve + doctors_dose forward, and
-doctors_adjoint_solve (adjoint sweeps, ray back-projection) backward.  The
-only torch arithmetic is the explicit density factor of the dose itself,
-d D(v)/d rho(v) at fixed fluence = sum_g k[mat v][g] phi[g](v), and the
-response r[g][v] = roi(v) k[mat v][g] rho(v) handed to the adjoint.
+with D the dose tally of the forward solve.  Every step runs in libdoctors:
+doctors_solve + doctors_roi_dose forward (J summed in FP64 on the device), and
+doctors_roi_gradients backward (the adjoint response, adjoint sweeps, ray
+back-projection and the dose's own density factor, all on the device).  This
+module only moves the inputs into the problem and scales the returned
+gradients by the incoming gradient of J.
 """
 from __future__ import annotations
 
 import numpy as np
 import torch
-
-from . import _lib as C
 
 
 class DoseProblem:
@@ -24,8 +22,7 @@ class DoseProblem:
         self.prob = prob
         self.solver = DoctorsProblem(prob, tol=tol, max_iters=max_iters)
         self.k = np.ascontiguousarray(prob.k_dep if k is None else k, np.float64)
-        self.mat = torch.as_tensor(prob.mat.astype(np.int64), device="cuda")
-        self.k_t = torch.as_tensor(self.k, device="cuda")                     # [nmat][G]
+        self.mat = torch.as_tensor(prob.mat.astype(np.uint8), device="cuda")
         self.roi = torch.as_tensor(np.asarray(roi, np.float64), device="cuda")  # [V]
 
     def set_inputs(self, weights, spectrum, density):
@@ -39,7 +36,7 @@ class DoseProblem:
             srcs.append(q)
         self.solver.set_sources(srcs)
         rho = density.detach().float().contiguous()
-        self.solver.set_materials(self.mat.to(torch.uint8), rho, self.prob.sigma_t, self.prob.sigma_s)
+        self.solver.set_materials(self.mat, rho, self.prob.sigma_t, self.prob.sigma_s)
 
 
 class RoiDose(torch.autograd.Function):
@@ -47,23 +44,16 @@ class RoiDose(torch.autograd.Function):
     def forward(ctx, weights, spectrum, density, dp: DoseProblem):
         dp.set_inputs(weights, spectrum, density)
         dp.solver.solve()
-        dose = dp.solver.dose(dp.k)
+        J = dp.solver.roi_dose(dp.k, dp.roi)
         ctx.dp = dp
-        ctx.devices = (weights.device, spectrum.device)
-        ctx.save_for_backward(density)
-        return (dp.roi * dose).sum().to(weights.device)
+        ctx.meta = (weights.device, spectrum.device, density.dtype)
+        return torch.tensor(J, dtype=torch.float64, device=weights.device)
 
     @staticmethod
     def backward(ctx, gJ):
         dp = ctx.dp
-        (density,) = ctx.saved_tensors
-        kv = dp.k_t[dp.mat].T                                      # [G][V]
-        rho = density.detach().double()
-        response = (kv * (dp.roi * rho)[None, :]).contiguous()
-        g = dp.solver.adjoint(response)
-        phi = dp.solver.fluence(C.DOCTORS_FLUENCE_TOTAL).double()
-        explicit = dp.roi * (kv * phi).sum(dim=0)
-        d_rho = g["density"] + explicit
+        dev_w, dev_s, dtype_rho = ctx.meta
+        g = dp.solver.roi_gradients(dp.k, dp.roi)
         gJ = gJ.to(torch.float64)
-        return (gJ * g["weights"]).to(ctx.devices[0]), (gJ * g["spectrum"]).to(ctx.devices[1]), \
-            (gJ * d_rho).to(density.dtype), None
+        return (gJ * g["weights"]).to(dev_w), (gJ * g["spectrum"]).to(dev_s), \
+            (gJ * g["density"]).to(dtype_rho), None

@@ -83,7 +83,8 @@ void free_problem(doctors_problem* p) {
                     p->d_phiu_src, p->d_phiu, p->d_U, p->d_Q, p->d_mom, p->d_src, p->d_src2, p->d_prev,
                     p->d_emit, p->d_iso, p->d_xface, p->d_yface, p->d_red,
                     p->d_Z, p->d_Qa, p->d_T, p->d_rf, p->d_r, p->d_acc, p->d_grad, p->d_H,
-                    p->d_ones, p->d_psi, p->d_prod, p->d_flow, p->d_qang, p->d_pang};
+                    p->d_ones, p->d_psi, p->d_prod, p->d_flow, p->d_qang, p->d_pang,
+                    p->d_k, p->d_roi, p->d_part};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (p->h_red) cudaFreeHost(p->h_red);
@@ -1295,25 +1296,35 @@ int copy_out(doctors_problem* p, double* dst, const double* src_host_or_dev, siz
 
 }  // namespace
 
-extern "C" int doctors_adjoint_solve(doctors_problem* p, const double* response, int mem, double* d_weights,
-                                     double* d_spectrum, double* d_density, doctors_result* info) {
-    int rc = check_problem(p);
-    if (rc) return rc;
-    CHECK_ARG(response != nullptr, "null response");
-    CHECK_ARG(mem == DOCTORS_MEM_HOST || mem == DOCTORS_MEM_DEVICE, "bad mem");
-    if (!p->solved) {
-        set_error("no forward solution: call doctors_solve first");
-        return DOCTORS_ERR_STATE;
-    }
+namespace {
+
+// The ROI form of the adjoint: the response is formed on the device from the
+// staged dose factors and ROI weights, and the explicit density term of the
+// dose is added to the density gradient.
+struct RoiTerms {
+    const double* k;     // device [n_mat][G]
+    const double* roi;   // device [V]
+};
+
+// The adjoint solve and gradients behind doctors_adjoint_solve (response
+// given, roi null) and doctors_roi_gradients (response null, roi given).
+// Arguments are checked by the callers.
+int adjoint_impl(doctors_problem* p, const double* response, int mem, const RoiTerms* roi, double* d_weights,
+                 double* d_spectrum, double* d_density, doctors_result* info) {
     const bool density = d_density != nullptr;
-    rc = ensure_adjoint_buffers(p, density);
+    int rc = ensure_adjoint_buffers(p, density);
     if (rc) return rc;
     const size_t GV = (size_t)p->G * p->V, GVM = GV * p->M;
     p->launches = 0;
     CU(cudaEventRecord(p->ev[0], p->stream));
-    CU(cudaMemcpyAsync(p->d_r, response, GV * sizeof(double),
-                       mem == DOCTORS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
-    CU(launch_to_float(GV, p->d_r, p->d_rf, p->stream));
+    if (roi) {
+        CU(launch_roi_response(p->V, p->G, p->d_mat, p->d_rho, roi->k, roi->roi, p->d_r, p->d_rf, p->stream));
+    } else {
+        CU(cudaMemcpyAsync(p->d_r, response, GV * sizeof(double),
+                           mem == DOCTORS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           p->stream));
+        CU(launch_to_float(GV, p->d_r, p->d_rf, p->stream));
+    }
     ++p->launches;
     {
         std::vector<float> ones(p->G, 1.0f);
@@ -1415,6 +1426,12 @@ extern "C" int doctors_adjoint_solve(doctors_problem* p, const double* response,
         da.Z = p->d_Z; da.phic = p->d_mom; da.U = p->d_U; da.prod = p->d_prod; da.grad = p->d_grad;
         CU(launch_density_grad(da, p->stream));
         ++p->launches;
+        if (roi) {
+            // the dose's own density factor, at fixed fluence
+            CU(launch_roi_explicit(p->V, p->G, p->M, p->d_mat, roi->k, roi->roi, p->d_phiu, p->d_mom, p->d_grad,
+                                   p->stream));
+            ++p->launches;
+        }
     }
     // 8. outputs
     if (d_weights) {
@@ -1446,4 +1463,97 @@ extern "C" int doctors_adjoint_solve(doctors_problem* p, const double* response,
     p->adjoint_done = true;
     if (irc == DOCTORS_ERR_NOT_CONVERGED) set_error("adjoint iteration cap reached before convergence");
     return irc;
+}
+
+}  // namespace
+
+extern "C" int doctors_adjoint_solve(doctors_problem* p, const double* response, int mem, double* d_weights,
+                                     double* d_spectrum, double* d_density, doctors_result* info) {
+    int rc = check_problem(p);
+    if (rc) return rc;
+    CHECK_ARG(response != nullptr, "null response");
+    CHECK_ARG(mem == DOCTORS_MEM_HOST || mem == DOCTORS_MEM_DEVICE, "bad mem");
+    if (!p->solved) {
+        set_error("no forward solution: call doctors_solve first");
+        return DOCTORS_ERR_STATE;
+    }
+    return adjoint_impl(p, response, mem, nullptr, d_weights, d_spectrum, d_density, info);
+}
+
+namespace {
+
+// Stages the dose factors (host, [n_mat][G]) and the ROI weights ([V] in
+// `mem`) in the problem's ROI buffers, allocated on first use.
+int stage_roi(doctors_problem* p, const double* k, const double* roi, int mem, RoiTerms* out) {
+    int rc = 0;
+    if (!p->d_k) rc = dalloc_t(&p->d_k, (size_t)kMaxMat * p->G, "dose factors");
+    if (!rc && !p->d_part) rc = dalloc_t(&p->d_part, (size_t)kRoiPartials + 1, "ROI partial sums");
+    if (!rc && mem == DOCTORS_MEM_HOST && !p->d_roi) rc = dalloc_t(&p->d_roi, p->V, "ROI weights");
+    if (rc) return rc;
+    // copies from pageable host memory are staged before the call returns, so
+    // the caller may change k (and a host roi) as soon as this returns
+    CU(cudaMemcpyAsync(p->d_k, k, (size_t)p->nmat * p->G * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    if (mem == DOCTORS_MEM_HOST) {
+        CU(cudaMemcpyAsync(p->d_roi, roi, p->V * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+        out->roi = p->d_roi;
+    } else {
+        out->roi = roi;
+    }
+    out->k = p->d_k;
+    return DOCTORS_OK;
+}
+
+int check_roi_args(doctors_problem* p, const double* k, const double* roi, int mem, const double* J) {
+    int rc = check_problem(p);
+    if (rc) return rc;
+    CHECK_ARG(k && roi && J, "null argument");
+    CHECK_ARG(mem == DOCTORS_MEM_HOST || mem == DOCTORS_MEM_DEVICE, "bad mem");
+    if (!p->solved) {
+        set_error("no forward solution: call doctors_solve first");
+        return DOCTORS_ERR_STATE;
+    }
+    for (int q = 0; q < p->nmat * p->G; ++q) CHECK_ARG(std::isfinite(k[q]), "k must be finite");
+    if (mem == DOCTORS_MEM_HOST)
+        for (size_t v = 0; v < p->V; ++v) CHECK_ARG(std::isfinite(roi[v]), "roi must be finite");
+    return DOCTORS_OK;
+}
+
+}  // namespace
+
+extern "C" int doctors_roi_dose(doctors_problem* p, const double* k, const double* roi, int mem, double* J,
+                                double* dose) {
+    int rc = check_roi_args(p, k, roi, mem, J);
+    if (rc) return rc;
+    RoiTerms t{};
+    rc = stage_roi(p, k, roi, mem, &t);
+    if (rc) return rc;
+    double* dose_dev = mem == DOCTORS_MEM_DEVICE ? dose : nullptr;
+    // host output: the dose is staged through the FP64 response buffer
+    if (dose && mem == DOCTORS_MEM_HOST) {
+        rc = ensure_adjoint_buffers(p, false);
+        if (rc) return rc;
+        dose_dev = p->d_r;
+    }
+    CU(launch_roi_dose(p->V, p->G, p->M, p->d_mat, p->d_rho, t.k, t.roi, p->d_phiu, p->d_mom, dose_dev, p->d_part,
+                       p->d_part + kRoiPartials, p->stream));
+    if (dose && mem == DOCTORS_MEM_HOST)
+        CU(cudaMemcpyAsync(dose, dose_dev, p->V * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    CU(cudaMemcpyAsync(J, p->d_part + kRoiPartials, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    CU(cudaStreamSynchronize(p->stream));
+    return DOCTORS_OK;
+}
+
+extern "C" int doctors_roi_gradients(doctors_problem* p, const double* k, const double* roi, int mem, double* J,
+                                     double* d_weights, double* d_spectrum, double* d_density,
+                                     doctors_result* info) {
+    int rc = check_roi_args(p, k, roi, mem, J);
+    if (rc) return rc;
+    RoiTerms t{};
+    rc = stage_roi(p, k, roi, mem, &t);
+    if (rc) return rc;
+    CU(launch_roi_dose(p->V, p->G, p->M, p->d_mat, p->d_rho, t.k, t.roi, p->d_phiu, p->d_mom, nullptr, p->d_part,
+                       p->d_part + kRoiPartials, p->stream));
+    CU(cudaMemcpyAsync(J, p->d_part + kRoiPartials, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    CU(cudaStreamSynchronize(p->stream));
+    return adjoint_impl(p, nullptr, mem, &t, d_weights, d_spectrum, d_density, info);
 }

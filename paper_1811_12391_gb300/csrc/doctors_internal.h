@@ -264,6 +264,23 @@ size_t sweep_tc_smem_bytes(int ab, int tx, int ty, int nz, int nmat);
 cudaError_t launch_sweep_tc(const SweepArgs& a, int mode, cudaStream_t s);
 cudaError_t upload_tables_tc(const float* R, const float* w);
 
+// ---------------------------------------------------------------------------
+// region-of-interest dose and its gradient terms (roi.cu)
+// ---------------------------------------------------------------------------
+constexpr int kRoiPartials = 1024;   // per-block partial sums of J (fixed grid)
+
+// J = sum_v roi(v) D(v) into the device scalar *J (and dose [V], if non-null);
+// partial holds kRoiPartials doubles.
+cudaError_t launch_roi_dose(size_t V, int G, int M, const uint8_t* mat, const float* rho, const double* k,
+                            const double* roi, const float* phi_u, const float* mom, double* dose,
+                            double* partial, double* J, cudaStream_t s);
+// r[g][v] = roi(v) k[mat v][g] rho(v) in FP64 (r) and FP32 (rf)
+cudaError_t launch_roi_response(size_t V, int G, const uint8_t* mat, const float* rho, const double* k,
+                                const double* roi, double* r, float* rf, cudaStream_t s);
+// grad[v] += roi(v) sum_g k[mat v][g] (phi_u + phi_c)[g](v)
+cudaError_t launch_roi_explicit(size_t V, int G, int M, const uint8_t* mat, const double* k, const double* roi,
+                                const float* phi_u, const float* mom, double* grad, cudaStream_t s);
+
 }  // namespace doctors
 
 // ---------------------------------------------------------------------------
@@ -337,6 +354,10 @@ struct doctors_problem {
     float* d_psi = nullptr;        // stored forward angular fluence ([G][V][A], or the dataflow layout)
     float* d_prod = nullptr;       // [G][V] angular product
     double* h_acc = nullptr;       // pinned [2G]
+    // region-of-interest dose (allocated on first use)
+    double* d_k = nullptr;         // [kMaxMat][G] dose factors
+    double* d_roi = nullptr;       // [V] ROI weights (staged from host memory)
+    double* d_part = nullptr;      // [kRoiPartials + 1] partial sums of J, then J
     bool solved = false;
     bool adjoint_done = false;
     cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};

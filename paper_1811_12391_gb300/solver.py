@@ -172,6 +172,42 @@ class DoctorsProblem:
         outs["result"] = res.as_dict()
         return outs
 
+    def roi_dose(self, k, roi, want_dose: bool = False):
+        """J = sum_v roi(v) D(v) (float) and, if want_dose, the dose [V]
+        (float64 device tensor).  roi: [V] float64 device tensor."""
+        torch = self.torch
+        kk = np.ascontiguousarray(k, np.float64)
+        r = roi.contiguous().to(torch.float64)
+        J = ctypes.c_double()
+        dose = torch.empty(self.V, dtype=torch.float64, device="cuda") if want_dose else None
+        C.check(C.doctors_roi_dose(self.h, _dptr(kk, ctypes.c_double), ctypes.c_void_p(r.data_ptr()),
+                                   C.DOCTORS_MEM_DEVICE, ctypes.byref(J),
+                                   ctypes.c_void_p(dose.data_ptr()) if dose is not None else None))
+        return (J.value, dose) if want_dose else J.value
+
+    def roi_gradients(self, k, roi, want=("weights", "spectrum", "density")) -> dict:
+        """J and its gradients with respect to the source weights, the shared
+        spectrum and the densities (the density gradient includes the dose's
+        own density factor).  roi: [V] float64 device tensor.  Returns device
+        tensors and J (float)."""
+        torch = self.torch
+        kk = np.ascontiguousarray(k, np.float64)
+        r = roi.contiguous().to(torch.float64)
+        outs = {
+            "weights": torch.zeros(self.n_src, dtype=torch.float64, device="cuda") if "weights" in want else None,
+            "spectrum": torch.zeros(self.G, dtype=torch.float64, device="cuda") if "spectrum" in want else None,
+            "density": torch.zeros(self.V, dtype=torch.float64, device="cuda") if "density" in want else None,
+        }
+        J = ctypes.c_double()
+        res = C.doctors_result()
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+        C.check(C.doctors_roi_gradients(self.h, _dptr(kk, ctypes.c_double), ctypes.c_void_p(r.data_ptr()),
+                                        C.DOCTORS_MEM_DEVICE, ctypes.byref(J), ptr(outs["weights"]),
+                                        ptr(outs["spectrum"]), ptr(outs["density"]), ctypes.byref(res)))
+        outs["J"] = J.value
+        outs["result"] = res.as_dict()
+        return outs
+
     def autotune(self) -> dict:
         t = C.doctors_tuning()
         C.check(C.doctors_autotune(self.h, ctypes.byref(t)))
