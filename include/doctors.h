@@ -106,8 +106,9 @@ typedef struct doctors_options {
                                 writes one angular record per cell, a pass turns the angular fluence
                                 back into moments (same conditions as 4; two more arrays of
                                 G x N(N+2) x V floats, padded),
-                                6 = dataflow sweeping two z planes of a column per hyperplane step
-                                (same conditions as 4) */
+                                6 = dataflow with two groups per task: each thread updates its
+                                cell in two groups at every hyperplane step (same conditions as 4,
+                                and P1 or P3) */
     int device_loop;         /* 1 = run the source iteration as one CUDA graph whose while loop is
                                 decided on the device (no host round trip per iteration) */
     int differencing;        /* spatial scheme of the sweep (the paper does not state one):
@@ -214,9 +215,17 @@ int doctors_dose(doctors_problem *p, const double *k, double *dose, int mem);
  * DOCTORS_ERR_INVALID_ARG), held by every GPU that loads the library until
  * the process exits.  All calls share that array: calls that overlap on the
  * GPU race on it.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress, once per device); make that first call
- * before any stream capture.  Stream-ordered, does not synchronise.
- * DOCTORS_ERR_STATE before a successful solve. */
+ * address (cudaGetSymbolAddress, once per device, cached for the life of the
+ * process: the cache assumes one context per device, so do not use it across
+ * cudaDeviceReset); make that first call before any stream capture.
+ * Stream-ordered, does not synchronise: k is copied with cudaMemcpyAsync on
+ * the problem's stream.  From pageable host memory the copy is staged before
+ * the call returns, so k may change at once; from pinned host memory the copy
+ * runs when the stream reaches it, so k must stay unchanged until then (and,
+ * under stream capture, for the life of the captured graph, which reads k on
+ * every replay).  DOCTORS_ERR_STATE before a successful solve;
+ * DOCTORS_ERR_INVALID_ARG for null or non-finite arguments; on either error
+ * nothing is written. */
 int doctors_dose_noalloc(doctors_problem *p, const double *k, double *dose);
 
 /* Adjoint solve and gradients (no counterpart in the paper; the discrete
@@ -330,7 +339,7 @@ typedef struct doctors_tuning {
     int tile_x, tile_y;      /* tile of columns */
     int angles_per_block;    /* directions per CTA */
     int sweep_kernel;        /* 1 CUDA-core, 2 tensor-core, 3 chained, 4 dataflow, 5 dataflow with split
-                                transforms, 6 dataflow with two planes per step (as doctors_options) */
+                                transforms, 6 dataflow with two groups per task (as doctors_options) */
     double ms_per_sweep;     /* measured time of one full sweep of this problem */
     int candidates;          /* schedules timed (0 if taken from the cache) */
 } doctors_tuning;

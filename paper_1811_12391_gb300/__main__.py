@@ -23,7 +23,7 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--tile", type=int, nargs=2, default=(0, 0))
     ap.add_argument("--ab", type=int, default=0)
-    ap.add_argument("--kernel", type=int, default=0, help="sweep kernel: 0 default, 1 CUDA-core, 2 tensor-core, 3 chained CUDA-core, 4 dataflow, 5 dataflow with split transforms, 6 dataflow with two planes per step")
+    ap.add_argument("--kernel", type=int, default=0, help="sweep kernel: 0 default, 1 CUDA-core, 2 tensor-core, 3 chained CUDA-core, 4 dataflow, 5 dataflow with split transforms, 6 dataflow with two groups per task")
     ap.add_argument("--device-loop", action="store_true",
                     help="run the source iteration as one CUDA graph with a device-side while loop")
     ap.add_argument("--diamond", action="store_true", help="diamond differencing (dataflow sweep)")
@@ -44,21 +44,20 @@ def main():
                        sweep_kernel=args.kernel, device_loop=int(args.device_loop))
     if args.autotune:
         print(json.dumps({"autotune": d.autotune()}), flush=True)
-    resp = None
+    roi = None
     if args.adjoint:
         import numpy as np
         import torch
-        roi = np.zeros(p.V)
-        roi.reshape(p.nz, p.ny, p.nx)[p.nz // 2 - 2:p.nz // 2 + 2, p.ny // 2 - 4:p.ny // 2 + 4,
+        box = np.zeros(p.V)
+        box.reshape(p.nz, p.ny, p.nx)[p.nz // 2 - 2:p.nz // 2 + 2, p.ny // 2 - 4:p.ny // 2 + 4,
                                       p.nx // 2 - 4:p.nx // 2 + 4] = 1.0
-        roi /= roi.sum()
-        resp = torch.as_tensor(p.k_dep[p.mat].T * (p.density.astype(np.float64) * roi)[None, :], device="cuda")
+        roi = torch.as_tensor(box / box.sum(), device="cuda")
     for _ in range(args.repeat):
         r = d.solve(allow_not_converged=True)
         print(json.dumps(r), flush=True)
-        if resp is not None:
-            g = d.adjoint(resp)
-            print(json.dumps({"adjoint": g["result"]}), flush=True)
+        if roi is not None:
+            g = d.roi_gradients(p.k_dep, roi)
+            print(json.dumps({"adjoint": g["result"], "J": g["J"]}), flush=True)
     d.close()
 
 

@@ -52,7 +52,7 @@ constexpr bool kDefaultTensorCoreSweep = false;
 constexpr bool kDefaultChainedSweep = true;
 constexpr bool kDefaultDataflowSweep = true;
 constexpr bool kDefaultSplitSweep = false;
-constexpr bool kDefaultTwoPlaneSweep = false;
+constexpr bool kDefaultTwoGroupSweep = false;
 
 int dalloc(void** p, size_t bytes, const char* what) {
     if (bytes == 0) bytes = 16;
@@ -212,7 +212,7 @@ SweepArgs sweep_args(const doctors_problem* p, int reverse, const float* src, fl
     a.flow = (p->use_flow || p->use_split) ? p->d_flow : nullptr;
     a.qang = p->d_qang;
     a.pang = p->d_pang;
-    a.zp = p->flow_zp;
+    a.gp = p->flow_gp;
     a.dd = p->differencing == DOCTORS_DIFF_DIAMOND ? 1 : 0;
     return a;
 }
@@ -222,9 +222,9 @@ SweepArgs sweep_args(const doctors_problem* p, int reverse, const float* src, fl
 cudaError_t launch_sweep(const doctors_problem* p, SweepArgs sw, int mode, cudaStream_t s, int* count) {
     if (p->use_split && mode == 0) return launch_split_sweep(sw, p->M, s, count);
     if (p->use_flow || p->use_split) {
-        // modes 1 and 2 (stored / paired angular fluence) of the split and two-plane
+        // modes 1 and 2 (stored / paired angular fluence) of the split and two-group
         // paths use the plain dataflow kernel
-        if (p->use_split || (mode != 0 && p->flow_zp != 1)) sw.chain_slots = p->flow_slots;
+        if (p->use_split || (mode != 0 && p->flow_gp != 1)) sw.chain_slots = p->flow_slots;
         *count = 1;
         return launch_sweep_flow(sw, p->M, mode, s);
     }
@@ -538,9 +538,13 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
         set_error("dataflow sweep needs whole octants per CTA (angles_per_block = N(N+2)/8) of S2, S4, S6 or S8");
         return DOCTORS_ERR_INVALID_ARG;
     }
+    if (kernel == 6 && p->M % 4 != 0) {
+        set_error("the two-group dataflow sweep (sweep_kernel 6) needs P1 or P3 (legendre 1 or 3)");
+        return DOCTORS_ERR_INVALID_ARG;
+    }
     const bool dd = p->differencing == DOCTORS_DIFF_DIAMOND;
     if (dd) {
-        // diamond differencing is built into the one-plane dataflow kernel only
+        // diamond differencing is built into the one-group dataflow kernel only
         if (kernel != 0 && kernel != 4) {
             set_error("diamond differencing runs on the dataflow sweep (sweep_kernel 0 or 4)");
             return DOCTORS_ERR_INVALID_ARG;
@@ -562,7 +566,7 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
     const bool use_split = kernel == 5 || (kernel == 0 && !use_tc && flow_ok && kDefaultSplitSweep);
     const bool use_flow = !use_split && (kernel == 4 || kernel == 6 ||
                                          (kernel == 0 && !use_tc && flow_ok && kDefaultDataflowSweep));
-    const int zp = kernel == 6 || (kernel == 0 && use_flow && kDefaultTwoPlaneSweep) ? 2 : 1;
+    const int gp = kernel == 6 || (kernel == 0 && use_flow && kDefaultTwoGroupSweep && p->M % 4 == 0) ? 2 : 1;
     const bool use_chain = !use_tc && !use_flow && !use_split && (kernel == 3 || (kernel == 0 && kDefaultChainedSweep));
     const int ntx = (p->nx + tx - 1) / tx, nty = (p->ny + ty - 1) / ty;
     int chain_slots = 0, flow_slots = 0;
@@ -572,12 +576,12 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
     } else if (use_flow || use_split) {
         int sms = 0;
         CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-        smem = sweep_flow_smem_bytes(ab, tx, ty, p->G, kMaxMat, zp, dd);
+        smem = sweep_flow_smem_bytes(ab, tx, ty, p->G, kMaxMat, gp, dd);
         if (smem <= 227 * 1024) {
             const size_t smem1 = sweep_flow_smem_bytes(ab, tx, ty, p->G, kMaxMat, 1, dd);
             const int per_sm = sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem1, false, 1, dd);
             const int per_sm_main = use_split ? sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem, true, 1)
-                                  : zp == 2 ? sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem, false, 2) : per_sm;
+                                  : gp == 2 ? sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem, false, 2) : per_sm;
             if (per_sm < 1 || per_sm_main < 1) {
                 set_error("dataflow sweep cannot be resident with this tile");
                 return DOCTORS_ERR_INVALID_ARG;
@@ -660,7 +664,7 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
     p->tx = tx; p->ty = ty; p->ab = ab; p->nab = p->A8 / ab; p->ntx = ntx; p->nty = nty; p->use_tc = use_tc;
     p->use_flow = use_flow;
     p->use_split = use_split;
-    p->flow_zp = use_flow ? zp : 1;
+    p->flow_gp = use_flow ? gp : 1;
     p->chain_slots = chain_slots;
     p->flow_slots = flow_slots;
     return DOCTORS_OK;
@@ -1176,7 +1180,7 @@ int doctors_autotune(doctors_problem* p, doctors_tuning* out) {
     best.ms_per_sweep = 1e30;
     int count = 0;
     const int saved[4] = {p->tx, p->ty, p->ab,
-                          p->use_tc ? 2 : p->use_split ? 5 : p->use_flow ? (p->flow_zp == 2 ? 6 : 4)
+                          p->use_tc ? 2 : p->use_split ? 5 : p->use_flow ? (p->flow_gp == 2 ? 6 : 4)
                                                                           : (p->chain_slots > 0 ? 3 : 1)};
     for (const auto& t : tiles) {
         for (int ab : abs_ok) {

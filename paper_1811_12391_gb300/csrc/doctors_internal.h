@@ -184,7 +184,7 @@ struct SweepArgs {
     const struct ChainDirTable* dir_table;   // host copy of the first-octant direction table (chained kernel)
     const float* qang;                 // split transforms: angular source [G][8][V][ABP] (direction octant)
     float* pang;                       // split transforms: angular fluence [G][8][V][ABP]
-    int zp;                            // dataflow kernel: z planes per hyperplane step (1 or 2)
+    int gp;                            // dataflow kernel: groups per task (1 or 2)
     int dd;                            // dataflow kernel: 1 = diamond differencing (dir_table holds 2c), 0 = step
     int* flow;                         // non-null: dataflow kernel; [0] task queue, [1] CTAs done, [2] wait timed out,
                                        // [3] test hook: task + 1 that writes no faces (0: none)
@@ -240,15 +240,17 @@ inline size_t sweep_chain_smem_bytes(int ab, int tx, int ty, int cmax, int gcoun
 // tile's first row and column, per-group leakage, the two halo-padded
 // hyperplanes, sigma_t of the swept groups and the task slot
 inline int flow_abp_host(int ab) { return (ab + 3) & ~3; }
-inline size_t sweep_flow_smem_bytes(int ab, int tx, int ty, int gcount, int nmat, int zp = 1, bool dd = false) {
-    // prefetched source moments (2 slots of 16 floats per thread), two landing
-    // slots (pipeline depth 2) of zp records per edge column, the leakage per
+inline size_t sweep_flow_smem_bytes(int ab, int tx, int ty, int gcount, int nmat, int gp = 1, bool dd = false) {
+    // prefetched source moments (2 slots of 16 floats per thread and group of
+    // the task), two landing slots (pipeline depth 2) of gp records per edge
+    // column (one per group of the task), the leakage per
     // group, two planes of column records (diamond differencing: x-going and
     // y-going face fluxes in separate planes), the cross sections and the task slot
-    return 2 * 16 * 4 * (size_t)tx * ty + 2 * (size_t)zp * 4 * (tx + ty) * flow_abp_host(ab) + 8 * (size_t)gcount +
-           4 * ((size_t)(dd ? 4 : 2) * chain_rs(zp * ab) * chain_px(tx) * (ty + 1) + (size_t)gcount * nmat) + 16;
+    return 2 * (size_t)gp * 16 * 4 * (size_t)tx * ty + 2 * (size_t)gp * 4 * (tx + ty) * flow_abp_host(ab) +
+           8 * (size_t)gcount +
+           4 * ((size_t)(dd ? 4 : 2) * chain_rs(gp * ab) * chain_px(tx) * (ty + 1) + (size_t)gcount * nmat) + 16;
 }
-int sweep_flow_blocks_per_sm(int ab, int M, int threads, size_t smem, bool split = false, int zp = 1, bool dd = false);
+int sweep_flow_blocks_per_sm(int ab, int M, int threads, size_t smem, bool split = false, int gp = 1, bool dd = false);
 cudaError_t launch_sweep_flow(const SweepArgs& a, int M, int mode, cudaStream_t s);
 // split transforms (whole octants of S2..S8): moments -> angular source for
 // all 8 octants, the dataflow sweep on angular records (a.qang -> a.pang),
@@ -302,7 +304,7 @@ struct doctors_problem {
     int chain_slots = 0;            // > 0: chained or dataflow sweep with this many CTA slots
     bool use_flow = false;          // dataflow sweep (one launch per sweep, task queue)
     bool use_split = false;         // dataflow sweep with the transforms in separate passes
-    int flow_zp = 1;                // dataflow sweep: z planes per hyperplane step
+    int flow_gp = 1;                // dataflow sweep: groups per task
     int differencing = 0;           // DOCTORS_DIFF_STEP or DOCTORS_DIFF_DIAMOND
     int flow_slots = 0;             // CTA slots of the plain dataflow kernel (modes 1, 2 under split)
     float* d_qang = nullptr;        // [G][8][V][ABP] angular source (split)

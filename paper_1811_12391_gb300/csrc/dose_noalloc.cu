@@ -32,7 +32,9 @@ std::mutex g_symbol_mu;
 double* g_symbol_ptr[kMaxDevices] = {};
 
 // Device address of the factor array on the current device, looked up once
-// per device (with that device current) and cached.
+// per device (with that device current) and cached for the life of the
+// process: the cache assumes one context per device (a cudaDeviceReset would
+// leave a stale address).
 cudaError_t factor_table_address(int device, double** out) {
     if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_symbol_mu);

@@ -26,6 +26,7 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include "sweep_chain.cuh"
 
@@ -53,10 +54,14 @@ __device__ __forceinline__ int flow_stage_tiles(int s, int ntx, int nty) {
 // a.qang and writes its angular-fluence record a.pang, with no moments and
 // no reductions (mode 0 only).
 //
-// ZP = 2: each hyperplane step sweeps two consecutive z planes of a column
-// (the second takes the first's fluence as its z inflow), so a task takes
-// ceil(nz / 2) + tx + ty - 2 steps instead of nz + tx + ty - 2; the planes
-// hold both cells' fluxes per column and two face records per edge and step.
+// GP = 2: a task sweeps two groups of one (tile, octant) together.  At each
+// hyperplane step every thread updates its cell in both groups: two
+// independent cell solves per step under one barrier, with one set of
+// direction tables and one set of index computations, and half as many
+// tasks per sweep.  A column's plane record holds both groups' fluxes, and
+// the edge threads fetch both groups' face records.  With an odd number of
+// groups the last task of each (tile, octant) has one group.  Mode 0, step
+// differencing, moments in 16-byte quarters (P1, P3).
 //
 // DD = true: diamond differencing (no negative-flux fixup).  The direction
 // table then holds 2 c_x, 2 c_y, 2 c_z and their sum, so the cell solve
@@ -64,30 +69,32 @@ __device__ __forceinline__ int flow_stage_tiles(int s, int ntx, int nty) {
 // leaves with 2 psi - psi_in.  The x-going and y-going face fluxes of a cell
 // differ, so they are kept in two planes (x: buf, y: bufy), and the face
 // records and the leakage carry the face fluxes, not the cell flux.
-template <int AB, int M, int MODE, bool SPLIT = false, int ZP = 1, bool DD = false>
-__global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2)
+template <int AB, int M, int MODE, bool SPLIT = false, int GP = 1, bool DD = false>
+__global__ void __launch_bounds__(256, (!SPLIT && M % 4 == 0) ? (GP == 1 ? 3 : 2) : 2)
     k_sweep_flow(const SweepArgs a, const ChainDirTable dt) {
     static_assert(!SPLIT || MODE == 0, "split transforms sweep in mode 0 only");
-    static_assert(ZP == 1 || (ZP == 2 && !SPLIT), "two planes per step in the fused kernel only");
-    static_assert(!DD || (!SPLIT && ZP == 1), "diamond differencing in the fused one-plane kernel only");
+    static_assert(GP == 1 || (GP == 2 && !SPLIT && !DD && MODE == 0 && M % 4 == 0),
+                  "two groups per task: the fused step-differenced kernel in mode 0, P1 or P3");
+    static_assert(!DD || (!SPLIT && GP == 1), "diamond differencing in the fused one-group kernel only");
     constexpr int ABP = flow_abp(AB);
-    constexpr int RS = (ZP * AB) | 1;         // a column's record: ZP cells' fluxes (odd length)
+    constexpr int RS = (GP * AB) | 1;         // a column's record: GP groups' fluxes (odd length)
     // pipeline depths: face records are fetched PD steps before the step
     // that uses them, source values PDS steps (the split sweep's steps are
     // short, so one step does not cover the memory latency)
     constexpr int PD = 2;                     // face records
-    constexpr int PDS = (SPLIT || ZP == 2) ? 2 : 1;   // source values (registers)
-    // fused one-plane kernel: the next cell's source moments go to shared
-    // memory by cp.async (no registers held for them across the step)
-    constexpr bool SMEMPF = !SPLIT && ZP == 1 && M % 4 == 0;
+    constexpr int PDS = SPLIT ? 2 : 1;        // source values (registers)
+    // fused kernel with moments in 16-byte quarters: the next cell's source
+    // moments go to shared memory by cp.async (no registers held for them
+    // across the step)
+    constexpr bool SMEMPF = !SPLIT && M % 4 == 0;
     extern __shared__ float4 sm4[];
     if (a.skip && *a.skip) return;          // retired instance of a batched loop
     const int PX = chain_px(a.tx);
     const int P = PX * (a.ty + 1);
-    float4* momst = sm4;                                      // [2][blockDim][16] prefetched source moments
-    float4* landx = momst + 2 * blockDim.x * 4;               // [PD][ZP][ty][ABP/4] fetched x-face records
-    float4* landy = landx + PD * ZP * a.ty * (ABP / 4);       // [PD][ZP][tx][ABP/4] fetched y-face records
-    double* leak_s = reinterpret_cast<double*>(landy + PD * ZP * a.tx * (ABP / 4));   // [gcount]
+    float4* momst = sm4;                                      // [2][GP][blockDim][4] prefetched source moments
+    float4* landx = momst + 2 * GP * blockDim.x * 4;          // [PD][GP][ty][ABP/4] fetched x-face records
+    float4* landy = landx + PD * GP * a.ty * (ABP / 4);       // [PD][GP][tx][ABP/4] fetched y-face records
+    double* leak_s = reinterpret_cast<double*>(landy + PD * GP * a.tx * (ABP / 4));   // [gcount]
     float* buf = reinterpret_cast<float*>(leak_s + a.gcount);              // [2][P][RS]
     float* bufy = DD ? buf + 2 * P * RS : buf;                // [2][P][RS] y-going faces (diamond)
     float* sigt_s = buf + (DD ? 4 : 2) * P * RS;              // [gcount][nmat]
@@ -123,21 +130,27 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
     const int nst = a.ntx + a.nty - 1;
     const int ntxf = a.ntx > 1 ? a.ntx - 1 : 0, ntyf = a.nty > 1 ? a.nty - 1 : 0;
     const size_t xslab = (size_t)a.ny * a.nz * ABP, yslab = (size_t)a.nx * a.nz * ABP;
+    // face records of consecutive groups are ntxf (ntyf) slabs apart
+    const size_t xgs = (size_t)ntxf * xslab, ygs = (size_t)ntyf * yslab;
+    const int ngp = (a.gcount + GP - 1) / GP;     // group blocks
     int ntasks = 0;
-    for (int s = 0; s < nst; ++s) ntasks += flow_stage_tiles(s, a.ntx, a.nty) * 8 * a.gcount;
-    // this thread's landing slot for the record used at step st
-    auto land_x = [&](int st, int zz) { return landx + (((st & (PD - 1)) * ZP + zz) * a.ty + lj) * (ABP / 4); };
-    auto land_y = [&](int st, int zz) { return landy + (((st & (PD - 1)) * ZP + zz) * a.tx + li) * (ABP / 4); };
+    for (int s = 0; s < nst; ++s) ntasks += flow_stage_tiles(s, a.ntx, a.nty) * 8 * ngp;
+    // this thread's landing slot for the record of group slot gg used at step st
+    auto land_x = [&](int st, int gg) { return landx + (((st & (PD - 1)) * GP + gg) * a.ty + lj) * (ABP / 4); };
+    auto land_y = [&](int st, int gg) { return landy + (((st & (PD - 1)) * GP + gg) * a.tx + li) * (ABP / 4); };
     const float qnan = __int_as_float(0x7fffffff);
 
-    constexpr int NS = SPLIT ? ABP : M;       // prefetched source values per cell
-    float sn[NS], sn2[PDS == 2 ? NS : 1];     // next cell; the cell after (depth 2)
+    constexpr int NS = SPLIT ? ABP : M;       // prefetched source values per cell (register path)
+    float sn[SMEMPF ? 1 : NS], sn2[PDS == 2 ? NS : 1];   // next cell; the cell after (depth 2)
 #pragma unroll
-    for (int m = 0; m < NS; ++m) sn[m] = 0.0f;
+    for (int m = 0; m < (SMEMPF ? 1 : NS); ++m) sn[m] = 0.0f;
     float rho_n = 0.0f, rho_n2 = 0.0f;        // density and material of the prefetched cells: the cross
     int mat_n = 0, mat_n2 = 0;                // section is looked up when the cell is swept, not at the load
-    float zc[AB];
-    float lk = 0.0f;
+    float zc[GP][AB];                         // z inflow of each group's next cell (GP = 1)
+    float2 zc2[GP == 2 ? AB : 1];             // GP = 2: both groups' z inflow, (.x, .y)
+    float lk[GP];
+#pragma unroll
+    for (int gg = 0; gg < GP; ++gg) lk[gg] = 0.0f;
 
     for (;;) {
         __syncthreads();                        // previous task done with task_s and the planes
@@ -146,16 +159,17 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
         const int t = *task_s;
         if (t >= ntasks) break;
         const bool withhold = a.flow[3] == t + 1;   // test hook: this task owes no faces
-        // task t: stage, then tile fastest, octant, group
+        // task t: stage, then tile fastest, octant, group block
         int s = 0, r = t, ntiles = 1;
         for (; s < nst; ++s) {
             ntiles = flow_stage_tiles(s, a.ntx, a.nty);
-            if (r < ntiles * 8 * a.gcount) break;
-            r -= ntiles * 8 * a.gcount;
+            if (r < ntiles * 8 * ngp) break;
+            r -= ntiles * 8 * ngp;
         }
         const int ti = r % ntiles;
         r /= ntiles;
-        const int o = r & 7, gi = r >> 3;
+        const int o = r & 7, gi = GP * (r >> 3);
+        const int gn = (GP == 2 && gi + 1 < a.gcount) ? 2 : 1;    // groups of this task
         const int g = a.g0 + gi;
         const int at = max(0, s - (a.nty - 1)) + ti, bt = s - at;
         const int sx = (o & 1) ? -1 : 1, sy = (o & 2) ? -1 : 1, sz = (o & 4) ? -1 : 1;
@@ -166,11 +180,12 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
         const int i = sx > 0 ? ir : a.nx - 1 - ir;
         const int j = sy > 0 ? jr : a.ny - 1 - jr;
         const size_t vcol = (size_t)j * a.nx + i;
-        const size_t gV = (size_t)g * V;
+        const size_t gV = (size_t)g * V;             // group slot gg: gV + gg * V
         const bool xout = li == a.tx - 1 && at < a.ntx - 1 && !withhold;
         const bool yout = lj == a.ty - 1 && bt < a.nty - 1 && !withhold;
         const bool xleak = ir == a.nx - 1, yleak = jr == a.ny - 1;
         const size_t og = (size_t)o * a.G + g;
+        // group slot gg: + gg * xgs (ygs)
         float* const xo = a.xface + (og * ntxf + at) * xslab + (size_t)jr * a.nz * ABP;
         float* const yo = a.yface + (og * ntyf + bt) * yslab + (size_t)ir * a.nz * ABP;
         // incoming records (null on the mesh boundary: zero inflow)
@@ -179,7 +194,8 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
         const bool xedge = col && li == 0, yedge = col && lj == 0;
 
         const size_t ang0 = ((size_t)g * 8 + oe) * V;       // angular records of (group, direction octant)
-        // source values, density and material of plane kn into (dst, rho, mat)
+        // source values, density and material of plane kn into (dst, rho, mat);
+        // with SMEMPF the moments of every group slot go to shared memory
         auto fetch = [&](int kn, float* dst, float& rho, int& mt) {
             const int k = sz > 0 ? kn : a.nz - 1 - kn;
             const size_t v = (size_t)k * nxy + vcol;
@@ -191,10 +207,15 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                     dst[4 * c4] = t4.x; dst[4 * c4 + 1] = t4.y; dst[4 * c4 + 2] = t4.z; dst[4 * c4 + 3] = t4.w;
                 }
             } else if constexpr (SMEMPF) {
-                float4* slot = momst + ((kn & 1) * blockDim.x + threadIdx.x) * 4;
-                const float* srcm = a.src + (gV + v) * M;
 #pragma unroll
-                for (int c4 = 0; c4 < M / 4; ++c4) cp_async_cg16(slot + c4, srcm + 4 * c4);
+                for (int gg = 0; gg < GP; ++gg) {
+                    if (gg < gn) {
+                        float4* slot = momst + (((kn & 1) * GP + gg) * blockDim.x + threadIdx.x) * 4;
+                        const float* srcm = a.src + (gV + gg * V + v) * M;
+#pragma unroll
+                        for (int c4 = 0; c4 < M / 4; ++c4) cp_async_cg16(slot + c4, srcm + 4 * c4);
+                    }
+                }
                 (void)dst;
             } else {
                 float tmp[M];
@@ -205,7 +226,8 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
             rho = __ldg(a.rho + v);
             mt = __ldg(a.mat + v);
         };
-        // the cell after the one in (sn, rho_n, mat_n) moves up, plane kn is fetched behind it
+        // register path: the cell after the one in (sn, rho_n, mat_n) moves up,
+        // plane kn is fetched behind it
         auto prefetch = [&](int kn) {
             if constexpr (PDS == 2) {
 #pragma unroll
@@ -225,25 +247,34 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
         }
         if constexpr (SMEMPF) asm volatile("cp.async.commit_group;\n" ::: "memory");
 #pragma unroll
-        for (int q = 0; q < AB; ++q) zc[q] = 0.0f;
+        for (int gg = 0; gg < GP; ++gg) {
+#pragma unroll
+            for (int q = 0; q < AB; ++q) zc[gg][q] = 0.0f;
+        }
+        if constexpr (GP == 2) {
+#pragma unroll
+            for (int q = 0; q < AB; ++q) zc2[q] = make_float2(0.0f, 0.0f);
+        }
 
         // issue the fetch of the face records this thread uses at step st
-        // (plane st - d): one commit group per step for every thread
+        // (plane st - d), every group slot: one commit group per step for
+        // every thread
         auto issue_faces = [&](int st) {
-            const int pt = st - d;
+            const int kt = st - d;
+            if (col && kt >= 0 && kt < a.nz) {
 #pragma unroll
-            for (int zz = 0; zz < ZP; ++zz) {
-                const int kt = ZP * pt + zz;
-                if (col && pt >= 0 && kt < a.nz) {
-                    if (xedge && xi) {
+                for (int gg = 0; gg < GP; ++gg) {
+                    if (gg < gn) {
+                        if (xedge && xi) {
 #pragma unroll
-                        for (int c4 = 0; c4 < ABP / 4; ++c4)
-                            cp_async_cg16(land_x(st, zz) + c4, xi + (size_t)kt * ABP + 4 * c4);
-                    }
-                    if (yedge && yi) {
+                            for (int c4 = 0; c4 < ABP / 4; ++c4)
+                                cp_async_cg16(land_x(st, gg) + c4, xi + gg * xgs + (size_t)kt * ABP + 4 * c4);
+                        }
+                        if (yedge && yi) {
 #pragma unroll
-                        for (int c4 = 0; c4 < ABP / 4; ++c4)
-                            cp_async_cg16(land_y(st, zz) + c4, yi + (size_t)kt * ABP + 4 * c4);
+                            for (int c4 = 0; c4 < ABP / 4; ++c4)
+                                cp_async_cg16(land_y(st, gg) + c4, yi + gg * ygs + (size_t)kt * ABP + 4 * c4);
+                        }
                     }
                 }
             }
@@ -251,35 +282,56 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
         };
         // steps -PD .. -1 only fetch the first records
         for (int st = 0; st < PD - 1; ++st) issue_faces(st);
-        const int hend = (a.nz + ZP - 1) / ZP + a.tx + a.ty - 2;
+        const int hend = a.nz + a.tx + a.ty - 2;
+#pragma unroll 1
         for (int h = -1; h < hend; ++h) {
             const int cb = h & 1, pb = cb ^ 1;
-            float sig_cur = 0.0f;
+            float sig_cur[GP];
+#pragma unroll
+            for (int gg = 0; gg < GP; ++gg) sig_cur[gg] = 0.0f;
             if constexpr (SMEMPF) {
-                // this step's cross section, then the next cell's moments (their own
+                // this step's cross sections, then the next cell's moments (their own
                 // commit group, ahead of the face records of this step)
                 const int kr0 = h - d;
                 if (col && kr0 >= 0 && kr0 < a.nz) {
-                    sig_cur = rho_n * sigt_s[gi * a.nmat + mat_n];
+#pragma unroll
+                    for (int gg = 0; gg < GP; ++gg)
+                        sig_cur[gg] = gg < gn ? rho_n * sigt_s[(gi + gg) * a.nmat + mat_n] : 0.0f;
                     if (kr0 + 1 < a.nz) fetch(kr0 + 1, sn, rho_n, mat_n);
                 }
                 asm volatile("cp.async.commit_group;\n" ::: "memory");
             }
             issue_faces(h + PD);
-#pragma unroll
-          for (int zz = 0; zz < ZP; ++zz) {
-            const int kr = ZP * (h - d) + zz;
+            const int kr = h - d;
             const bool act = col && h >= d && kr < a.nz;
             if (act) {
                 const bool last = kr == a.nz - 1;
                 const int k = sz > 0 ? kr : a.nz - 1 - kr;
                 const size_t v = (size_t)k * nxy + vcol;
-                const size_t mo = (gV + v) * M;
+                float sig_reg = 0.0f;
+                if constexpr (!SMEMPF) {
+                    if constexpr (!SPLIT) {
+#pragma unroll
+                        for (int m = 0; m < NS; ++m) sn[m] *= octant_sign<M>(m, fx, fy, fz);
+                    }
+                    sig_reg = rho_n * sigt_s[gi * a.nmat + mat_n];
+                }
+                float sreg[SMEMPF ? 1 : NS];
+                if constexpr (!SMEMPF) {
+#pragma unroll
+                    for (int m = 0; m < NS; ++m) sreg[m] = sn[m];
+                    if (!last) prefetch(kr + PDS);
+                }
+              // one cell of group slot gg (a compile-time constant, so that the
+              // per-group state stays in registers)
+              auto cell = [&](auto ggc) {
+                constexpr int gg = decltype(ggc)::value;
+                const size_t mo = (gV + gg * V + v) * M;
                 float s[NS];
                 float sig;
                 if constexpr (SMEMPF) {
-                    sig = sig_cur;
-                    const float4* slot = momst + ((kr & 1) * blockDim.x + threadIdx.x) * 4;
+                    sig = sig_cur[gg];
+                    const float4* slot = momst + (((kr & 1) * GP + gg) * blockDim.x + threadIdx.x) * 4;
 #pragma unroll
                     for (int c4 = 0; c4 < M / 4; ++c4) {
                         const float4 t4 = slot[c4];
@@ -295,16 +347,11 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                     }
                     if constexpr (NS % 2 == 1) s[NS - 1] *= octant_sign<M>(NS - 1, fx, fy, fz);
                 } else {
-                    if constexpr (!SPLIT) {
+                    sig = sig_reg;
 #pragma unroll
-                        for (int m = 0; m < NS; ++m) sn[m] *= octant_sign<M>(m, fx, fy, fz);
-                    }
-                    sig = rho_n * sigt_s[gi * a.nmat + mat_n];
-#pragma unroll
-                    for (int m = 0; m < NS; ++m) s[m] = sn[m];
-                    if (!last) prefetch(kr + PDS);
+                    for (int m = 0; m < NS; ++m) s[m] = sreg[m];
                 }
-                const int zo = zz * AB;               // this cell's fluxes within the column record
+                const int zo = gg * AB;               // this group's fluxes within the column record
                 // moments -> directions (split: the record already holds them)
                 float psi[AB];
                 if constexpr (SPLIT) {
@@ -347,30 +394,30 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                         const float2 py2 = make_float2(pvy[ys + zo + q], pvy[ys + zo + q + 1]);
                         float2 n2 = __ffma2_rn(make_float2(dt.cx[q], dt.cx[q + 1]), px2, make_float2(psi[q], psi[q + 1]));
                         n2 = __ffma2_rn(make_float2(dt.cy[q], dt.cy[q + 1]), py2, n2);
-                        n2 = __ffma2_rn(make_float2(dt.cz[q], dt.cz[q + 1]), make_float2(zc[q], zc[q + 1]), n2);
+                        n2 = __ffma2_rn(make_float2(dt.cz[q], dt.cz[q + 1]), make_float2(zc[gg][q], zc[gg][q + 1]), n2);
                         const float2 d2 = __fadd2_rn(make_float2(sig, sig), make_float2(dt.csum[q], dt.csum[q + 1]));
                         const float2 p2 = make_float2(n2.x * rcp_approx(d2.x), n2.y * rcp_approx(d2.y));
                         psi[q] = p2.x;
                         psi[q + 1] = p2.y;
                         cv[os + zo + q] = p2.x;
                         cv[os + zo + q + 1] = p2.y;
-                        zc[q] = p2.x;
-                        zc[q + 1] = p2.y;
+                        zc[gg][q] = p2.x;
+                        zc[gg][q + 1] = p2.y;
                     }
                 }
 #pragma unroll
                 for (int q = DD ? 0 : (AB & ~1); q < AB; ++q) {
                     const float px = pv[xs + zo + q];
                     const float py = pvy[ys + zo + q];
-                    const float num = fmaf(dt.cz[q], zc[q], fmaf(dt.cy[q], py, fmaf(dt.cx[q], px, psi[q])));
+                    const float num = fmaf(dt.cz[q], zc[gg][q], fmaf(dt.cy[q], py, fmaf(dt.cx[q], px, psi[q])));
                     psi[q] = num * rcp_approx(sig + dt.csum[q]);
                     if constexpr (DD) {
                         cv[os + zo + q] = fmaf(2.0f, psi[q], -px);
                         cvy[os + zo + q] = fmaf(2.0f, psi[q], -py);
-                        zc[q] = fmaf(2.0f, psi[q], -zc[q]);
+                        zc[gg][q] = fmaf(2.0f, psi[q], -zc[gg][q]);
                     } else {
                         cv[os + zo + q] = psi[q];
-                        zc[q] = psi[q];
+                        zc[gg][q] = psi[q];
                     }
                 }
                 // stored angular fluence, laid out for this kernel as one 16-byte
@@ -422,9 +469,9 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                     if (xleak || yleak || last) {
 #pragma unroll
                         for (int q = 0; q < AB; ++q) {
-                            if (xleak) lk = fmaf(dt.lx[q], fxo[q], lk);
-                            if (yleak) lk = fmaf(dt.ly[q], fyo[q], lk);
-                            if (last) lk = fmaf(dt.lz[q], zc[q], lk);
+                            if (xleak) lk[gg] = fmaf(dt.lx[q], fxo[q], lk[gg]);
+                            if (yleak) lk[gg] = fmaf(dt.ly[q], fyo[q], lk[gg]);
+                            if (last) lk[gg] = fmaf(dt.lz[q], zc[gg][q], lk[gg]);
                         }
                     }
                 } else {
@@ -437,12 +484,12 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                                               4 * c4 + 2 < AB ? psi[4 * c4 + 2 < AB ? 4 * c4 + 2 : 0] : 0.0f,
                                               4 * c4 + 3 < AB ? psi[4 * c4 + 3 < AB ? 4 * c4 + 3 : 0] : 0.0f);
                     if (xout) {
-                        float4* dst = reinterpret_cast<float4*>(xo + (size_t)kr * ABP);
+                        float4* dst = reinterpret_cast<float4*>(xo + gg * xgs + (size_t)kr * ABP);
 #pragma unroll
                         for (int c4 = 0; c4 < ABP / 4; ++c4) dst[c4] = rec[c4];
                     }
                     if (yout) {
-                        float4* dst = reinterpret_cast<float4*>(yo + (size_t)kr * ABP);
+                        float4* dst = reinterpret_cast<float4*>(yo + gg * ygs + (size_t)kr * ABP);
 #pragma unroll
                         for (int c4 = 0; c4 < ABP / 4; ++c4) dst[c4] = rec[c4];
                     }
@@ -454,7 +501,7 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                         if (xleak) f += dt.lx[q];
                         if (yleak) f += dt.ly[q];
                         if (last) f += dt.lz[q];
-                        lk = fmaf(f, psi[q], lk);
+                        lk[gg] = fmaf(f, psi[q], lk[gg]);
                     }
                 }
                 }
@@ -498,13 +545,140 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                     }
                     add_moments<M>(a.mom + mo, acc);
                 }
-                if (last && lk != 0.0f) {
-                    atomicAdd(leak_s + gi, (double)lk);
-                    lk = 0.0f;
+                if (last && lk[gg] != 0.0f) {
+                    atomicAdd(leak_s + gi + gg, (double)lk[gg]);
+                    lk[gg] = 0.0f;
                 }
+              };
+              if constexpr (GP == 2) {
+                // both groups at once: every packed two-lane operation holds group
+                // slot 0 in .x and group slot 1 in .y with the same table constant
+                // in both lanes, so each table value is read once for the two cells
+                const bool two = gn == 2;
+                const float4* slot0 = momst + (((kr & 1) * GP + 0) * blockDim.x + threadIdx.x) * 4;
+                const float4* slot1 = momst + (((kr & 1) * GP + 1) * blockDim.x + threadIdx.x) * 4;
+                const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                float2 s2[M];
+#pragma unroll
+                for (int c4 = 0; c4 < M / 4; ++c4) {
+                    const float4 u = slot0[c4];
+                    const float4 w = two ? slot1[c4] : z4;
+                    s2[4 * c4] = make_float2(u.x, w.x);
+                    s2[4 * c4 + 1] = make_float2(u.y, w.y);
+                    s2[4 * c4 + 2] = make_float2(u.z, w.z);
+                    s2[4 * c4 + 3] = make_float2(u.w, w.w);
+                }
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    const float sg = octant_sign<M>(m, fx, fy, fz);
+                    s2[m] = __fmul2_rn(s2[m], make_float2(sg, sg));
+                }
+                // moments -> directions
+                float2 psi2[AB];
+#pragma unroll
+                for (int q = 0; q < AB; ++q) {
+                    float2 t2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        const float c = dt.mop[q * 16 + m];
+                        t2 = __ffma2_rn(make_float2(c, c), s2[m], t2);
+                    }
+                    psi2[q] = t2;
+                }
+                // step-differenced cell solve of both groups
+                const float* pv = buf + pb * P * RS;
+                float* cv = buf + cb * P * RS;
+                const float2 sig2 = make_float2(sig_cur[0], sig_cur[1]);
+#pragma unroll
+                for (int q = 0; q < AB; ++q) {
+                    const float2 px2 = make_float2(pv[xs + q], pv[xs + AB + q]);
+                    const float2 py2 = make_float2(pv[ys + q], pv[ys + AB + q]);
+                    float2 n2 = __ffma2_rn(make_float2(dt.cx[q], dt.cx[q]), px2, psi2[q]);
+                    n2 = __ffma2_rn(make_float2(dt.cy[q], dt.cy[q]), py2, n2);
+                    n2 = __ffma2_rn(make_float2(dt.cz[q], dt.cz[q]), zc2[q], n2);
+                    const float2 d2 = __fadd2_rn(sig2, make_float2(dt.csum[q], dt.csum[q]));
+                    const float2 p2 = __fmul2_rn(n2, make_float2(rcp_approx(d2.x), rcp_approx(d2.y)));
+                    psi2[q] = p2;
+                    zc2[q] = p2;
+                    cv[os + q] = p2.x;
+                    cv[os + AB + q] = p2.y;
+                }
+                // outgoing face records of plane kr, one per group
+                if (xout || yout) {
+                    float4 r0[ABP / 4], r1[ABP / 4];
+#pragma unroll
+                    for (int c4 = 0; c4 < ABP / 4; ++c4) {
+                        float e0[4], e1[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int q = 4 * c4 + e;
+                            e0[e] = q < AB ? psi2[q < AB ? q : 0].x : 0.0f;
+                            e1[e] = q < AB ? psi2[q < AB ? q : 0].y : 0.0f;
+                        }
+                        r0[c4] = make_float4(e0[0], e0[1], e0[2], e0[3]);
+                        r1[c4] = make_float4(e1[0], e1[1], e1[2], e1[3]);
+                    }
+                    if (xout) {
+                        float4* dst = reinterpret_cast<float4*>(xo + (size_t)kr * ABP);
+#pragma unroll
+                        for (int c4 = 0; c4 < ABP / 4; ++c4) dst[c4] = r0[c4];
+                        if (two) {
+                            float4* dst1 = reinterpret_cast<float4*>(xo + xgs + (size_t)kr * ABP);
+#pragma unroll
+                            for (int c4 = 0; c4 < ABP / 4; ++c4) dst1[c4] = r1[c4];
+                        }
+                    }
+                    if (yout) {
+                        float4* dst = reinterpret_cast<float4*>(yo + (size_t)kr * ABP);
+#pragma unroll
+                        for (int c4 = 0; c4 < ABP / 4; ++c4) dst[c4] = r0[c4];
+                        if (two) {
+                            float4* dst1 = reinterpret_cast<float4*>(yo + ygs + (size_t)kr * ABP);
+#pragma unroll
+                            for (int c4 = 0; c4 < ABP / 4; ++c4) dst1[c4] = r1[c4];
+                        }
+                    }
+                }
+                if (xleak || yleak || last) {
+                    float2 l2 = make_float2(lk[0], lk[1]);
+#pragma unroll
+                    for (int q = 0; q < AB; ++q) {
+                        float f = 0.0f;
+                        if (xleak) f += dt.lx[q];
+                        if (yleak) f += dt.ly[q];
+                        if (last) f += dt.lz[q];
+                        l2 = __ffma2_rn(make_float2(f, f), psi2[q], l2);
+                    }
+                    lk[0] = l2.x;
+                    lk[1] = l2.y;
+                }
+                // directions -> moments (Eq. 3 for lm = 00)
+                float acc0[M], acc1[M];
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    float2 t2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+                    for (int q = 0; q < AB; ++q) {
+                        const float c = dt.dop[m * kFlowMaxAB + q];
+                        t2 = __ffma2_rn(make_float2(c, c), psi2[q], t2);
+                    }
+                    const float sg = octant_sign<M>(m, fx, fy, fz);
+                    acc0[m] = t2.x * sg;
+                    acc1[m] = t2.y * sg;
+                }
+                add_moments<M>(a.mom + (gV + v) * M, acc0);
+                if (two) add_moments<M>(a.mom + (gV + V + v) * M, acc1);
+                if (last) {
+                    if (lk[0] != 0.0f) atomicAdd(leak_s + gi, (double)lk[0]);
+                    if (two && lk[1] != 0.0f) atomicAdd(leak_s + gi + 1, (double)lk[1]);
+                    lk[0] = 0.0f;
+                    lk[1] = 0.0f;
+                }
+              } else {
+                cell(std::integral_constant<int, 0>{});
+              }
             }
-          }
-            // incoming records of the planes swept next step (fetched PD steps
+            // incoming records of the plane swept next step (fetched PD steps
             // ago): wait until the producer has written every flux (no NaN
             // left), move them into the halo and hand the records back to the
             // next sweep as NaN; zero inflow on the mesh boundary
@@ -513,7 +687,7 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                 // the next cell's moments (and the faces fetched a step ago) have landed
                 asm volatile("cp.async.wait_group 1;\n" ::: "memory");
             }
-            if (col && pf >= 0 && ZP * pf < a.nz && (xedge || yedge)) {
+            if (col && pf >= 0 && pf < a.nz && (xedge || yedge)) {
                 if constexpr (PD == 2) {
                     asm volatile("cp.async.wait_group 1;\n" ::: "memory");
                 } else {
@@ -522,13 +696,12 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                 float* hbx = buf + cb * P * RS;
                 float* hby = bufy + cb * P * RS;
 #pragma unroll
-                for (int zz = 0; zz < ZP; ++zz) {
-                  const int kf = ZP * pf + zz;
-                  if (kf >= a.nz) break;
+                for (int gg = 0; gg < GP; ++gg) {
+                  if (gg >= gn) break;
                   for (int side = 0; side < 2; ++side) {
                     const bool edge = side == 0 ? xedge : yedge;
                     if (!edge) continue;
-                    const int hs = (side == 0 ? xs : ys) + zz * AB;
+                    const int hs = (side == 0 ? xs : ys) + gg * AB;
                     float* hb = side == 0 ? hbx : hby;
                     float* src = side == 0 ? xi : yi;
                     if (!src) {
@@ -536,9 +709,9 @@ __global__ void __launch_bounds__(256, (!SPLIT && ZP == 1 && M % 4 == 0) ? 3 : 2
                         for (int q = 0; q < AB; ++q) hb[hs + q] = 0.0f;
                         continue;
                     }
-                    float4* land = side == 0 ? land_x(h + 1, zz) : land_y(h + 1, zz);
+                    float4* land = side == 0 ? land_x(h + 1, gg) : land_y(h + 1, gg);
                     const float* lf = reinterpret_cast<const float*>(land);
-                    src += (size_t)kf * ABP;
+                    src += (side == 0 ? gg * xgs : gg * ygs) + (size_t)pf * ABP;
                     bool ok = false;
                     for (int it = 0; it < kFlowSpinLimit; ++it) {
                         ok = true;
@@ -663,7 +836,7 @@ __global__ void __launch_bounds__(256) k_split_d2m(const float* pang, float* mom
 }
 
 template <int M>
-int sweep_flow_blocks_per_sm(int ab, int threads, size_t smem, bool split, int zp, bool dd) {
+int sweep_flow_blocks_per_sm(int ab, int threads, size_t smem, bool split, int gp, bool dd) {
     int b = 0;
     cudaError_t e = cudaErrorInvalidValue;
     auto query = [&](auto kern) {
@@ -674,9 +847,10 @@ int sweep_flow_blocks_per_sm(int ab, int threads, size_t smem, bool split, int z
 #define DOCTORS_FLOW_OCC(AB)                                                            \
     case AB:                                                                            \
         if (split) query(k_sweep_flow<AB, M, 0, true>);                                  \
-        else if (zp == 2) query(k_sweep_flow<AB, M, 0, false, 2>);                       \
         else if (dd) query(k_sweep_flow<AB, M, 0, false, 1, true>);                      \
-        else query(k_sweep_flow<AB, M, 0>);                                              \
+        else if (gp == 2) {                                                             \
+            if constexpr (M % 4 == 0) query(k_sweep_flow<AB, M, 0, false, 2>);          \
+        } else query(k_sweep_flow<AB, M, 0>);                                            \
         break;
     switch (ab) {
         DOCTORS_FLOW_OCC(1)
@@ -737,17 +911,18 @@ template <int M, int MODE>
 cudaError_t launch_sweep_flow_m(const SweepArgs& a, cudaStream_t s) {
     if (a.gcount <= 0) return cudaSuccess;
     if (a.dir_table == nullptr || a.flow == nullptr || a.nab != 1) return cudaErrorInvalidValue;
+    const bool dd = a.dd != 0;
+    const int ngp = (MODE == 0 && a.gp == 2 && !dd && M % 4 == 0) ? (a.gcount + 1) / 2 : a.gcount;
     int ntasks = 0;
     for (int st = 0; st < a.ntx + a.nty - 1; ++st) {
         const int lo = st - (a.nty - 1) > 0 ? st - (a.nty - 1) : 0;
         const int hi = st < a.ntx - 1 ? st : a.ntx - 1;
-        ntasks += (hi - lo + 1) * 8 * a.gcount;
+        ntasks += (hi - lo + 1) * 8 * ngp;
     }
     const int grid = ntasks < a.chain_slots ? ntasks : a.chain_slots;
     const int T = a.tx * a.ty;
-    const bool dd = a.dd != 0;
-    const int zp = (MODE == 0 && a.zp == 2 && !dd) ? 2 : 1;
-    const size_t smem = sweep_flow_smem_bytes(a.ab, a.tx, a.ty, a.gcount, a.nmat, zp, dd);
+    const int gp = (MODE == 0 && a.gp == 2 && !dd && M % 4 == 0) ? 2 : 1;
+    const size_t smem = sweep_flow_smem_bytes(a.ab, a.tx, a.ty, a.gcount, a.nmat, gp, dd);
     cudaError_t e = cudaSuccess;
     auto launch = [&](auto kern) {
         if (smem > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -759,8 +934,8 @@ cudaError_t launch_sweep_flow_m(const SweepArgs& a, cudaStream_t s) {
             launch(k_sweep_flow<AB, M, MODE, false, 1, true>);                           \
             break;                                                                      \
         }                                                                               \
-        if constexpr (MODE == 0) {                                                      \
-            if (zp == 2) {                                                              \
+        if constexpr (MODE == 0 && M % 4 == 0) {                                        \
+            if (gp == 2) {                                                              \
                 launch(k_sweep_flow<AB, M, 0, false, 2>);                                \
                 break;                                                                  \
             }                                                                           \

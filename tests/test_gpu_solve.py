@@ -64,8 +64,9 @@ def cylinder_ref():
 def test_ragged_multitile_cylinder(dp, cylinder_ref, tile, ab, kernel):
     """Several sweep tiles with ragged tails in x and y, S8 P3, with the
     CUDA-core (1), tensor-core (2), chained (3), dataflow (4), dataflow
-    with split transforms (5) and dataflow with two z planes per step (6;
-    odd plane counts are in test_degenerate_meshes) sweeps."""
+    with split transforms (5) and dataflow with two groups per task (6; with
+    five groups the last task of every tile and octant has one group)
+    sweeps."""
     p, sol = cylinder_ref
     d = dp(p, tol=1e-6, max_iters=400, tile=tile, angles_per_block=ab, sweep_kernel=kernel)
     _compare(d, p, sol, f"cylinder tile={tile} ab={ab} kernel={kernel}")
