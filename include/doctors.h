@@ -108,7 +108,10 @@ typedef struct doctors_options {
                                 G x N(N+2) x V floats, padded),
                                 6 = dataflow with two groups per task: each thread updates its
                                 cell in two groups at every hyperplane step (same conditions as 4,
-                                and P1 or P3) */
+                                and P1 or P3),
+                                7 = dataflow with a face warp: one more warp per CTA fetches and
+                                waits for the incoming face fluxes, the column threads only sweep
+                                (same conditions as 4, P1 or P3, tile_x + tile_y <= 64) */
     int device_loop;         /* 1 = run the source iteration as one CUDA graph whose while loop is
                                 decided on the device (no host round trip per iteration) */
     int differencing;        /* spatial scheme of the sweep (the paper does not state one):
@@ -339,7 +342,8 @@ typedef struct doctors_tuning {
     int tile_x, tile_y;      /* tile of columns */
     int angles_per_block;    /* directions per CTA */
     int sweep_kernel;        /* 1 CUDA-core, 2 tensor-core, 3 chained, 4 dataflow, 5 dataflow with split
-                                transforms, 6 dataflow with two groups per task (as doctors_options) */
+                                transforms, 6 dataflow with two groups per task, 7 dataflow with a
+                                face warp (as doctors_options) */
     double ms_per_sweep;     /* measured time of one full sweep of this problem */
     int candidates;          /* schedules timed (0 if taken from the cache) */
 } doctors_tuning;

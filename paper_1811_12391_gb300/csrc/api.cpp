@@ -53,6 +53,7 @@ constexpr bool kDefaultChainedSweep = true;
 constexpr bool kDefaultDataflowSweep = true;
 constexpr bool kDefaultSplitSweep = false;
 constexpr bool kDefaultTwoGroupSweep = false;
+constexpr bool kDefaultFaceWarpSweep = false;
 
 int dalloc(void** p, size_t bytes, const char* what) {
     if (bytes == 0) bytes = 16;
@@ -213,6 +214,7 @@ SweepArgs sweep_args(const doctors_problem* p, int reverse, const float* src, fl
     a.qang = p->d_qang;
     a.pang = p->d_pang;
     a.gp = p->flow_gp;
+    a.hw = p->flow_hw ? 1 : 0;
     a.dd = p->differencing == DOCTORS_DIFF_DIAMOND ? 1 : 0;
     return a;
 }
@@ -224,7 +226,7 @@ cudaError_t launch_sweep(const doctors_problem* p, SweepArgs sw, int mode, cudaS
     if (p->use_flow || p->use_split) {
         // modes 1 and 2 (stored / paired angular fluence) of the split and two-group
         // paths use the plain dataflow kernel
-        if (p->use_split || (mode != 0 && p->flow_gp != 1)) sw.chain_slots = p->flow_slots;
+        if (p->use_split || (mode != 0 && (p->flow_gp != 1 || p->flow_hw))) sw.chain_slots = p->flow_slots;
         *count = 1;
         return launch_sweep_flow(sw, p->M, mode, s);
     }
@@ -530,16 +532,20 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
         set_error("angles_per_block must divide N(N+2)/8 and be one of 1,2,3,4,5,6,7,9,10,12");
         return DOCTORS_ERR_INVALID_ARG;
     }
-    if (kernel < 0 || kernel > 6) {
-        set_error("sweep_kernel must be 0 .. 6");
+    if (kernel < 0 || kernel > 7) {
+        set_error("sweep_kernel must be 0 .. 7");
         return DOCTORS_ERR_INVALID_ARG;
     }
     if (kernel >= 4 && !(p->A8 == ab && chain_const_table_ab(ab))) {
         set_error("dataflow sweep needs whole octants per CTA (angles_per_block = N(N+2)/8) of S2, S4, S6 or S8");
         return DOCTORS_ERR_INVALID_ARG;
     }
-    if (kernel == 6 && p->M % 4 != 0) {
-        set_error("the two-group dataflow sweep (sweep_kernel 6) needs P1 or P3 (legendre 1 or 3)");
+    if ((kernel == 6 || kernel == 7) && p->M % 4 != 0) {
+        set_error("the two-group and face-warp dataflow sweeps (sweep_kernel 6, 7) need P1 or P3 (legendre 1 or 3)");
+        return DOCTORS_ERR_INVALID_ARG;
+    }
+    if (kernel == 7 && tx + ty > 64) {
+        set_error("the face-warp dataflow sweep (sweep_kernel 7) needs tile_x + tile_y <= 64");
         return DOCTORS_ERR_INVALID_ARG;
     }
     const bool dd = p->differencing == DOCTORS_DIFF_DIAMOND;
@@ -564,9 +570,11 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
     const bool use_tc = kernel == 2 || (kernel == 0 && tc_ok && kDefaultTensorCoreSweep);
     const bool flow_ok = p->A8 == ab && chain_const_table_ab(ab);
     const bool use_split = kernel == 5 || (kernel == 0 && !use_tc && flow_ok && kDefaultSplitSweep);
-    const bool use_flow = !use_split && (kernel == 4 || kernel == 6 ||
+    const bool use_flow = !use_split && (kernel == 4 || kernel == 6 || kernel == 7 ||
                                          (kernel == 0 && !use_tc && flow_ok && kDefaultDataflowSweep));
     const int gp = kernel == 6 || (kernel == 0 && use_flow && kDefaultTwoGroupSweep && p->M % 4 == 0) ? 2 : 1;
+    const bool hw = gp == 1 && !dd && p->M % 4 == 0 && tx + ty <= 64 &&
+                    (kernel == 7 || (kernel == 0 && use_flow && kDefaultFaceWarpSweep));
     const bool use_chain = !use_tc && !use_flow && !use_split && (kernel == 3 || (kernel == 0 && kDefaultChainedSweep));
     const int ntx = (p->nx + tx - 1) / tx, nty = (p->ny + ty - 1) / ty;
     int chain_slots = 0, flow_slots = 0;
@@ -580,8 +588,11 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
         if (smem <= 227 * 1024) {
             const size_t smem1 = sweep_flow_smem_bytes(ab, tx, ty, p->G, kMaxMat, 1, dd);
             const int per_sm = sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem1, false, 1, dd);
+            const int hw_threads = ((tx * ty + 31) / 32 + 1) * 32;
             const int per_sm_main = use_split ? sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem, true, 1)
-                                  : gp == 2 ? sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem, false, 2) : per_sm;
+                                  : gp == 2 ? sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem, false, 2)
+                                  : hw ? sweep_flow_blocks_per_sm(ab, p->M, hw_threads, smem, false, 1, false, true)
+                                       : per_sm;
             if (per_sm < 1 || per_sm_main < 1) {
                 set_error("dataflow sweep cannot be resident with this tile");
                 return DOCTORS_ERR_INVALID_ARG;
@@ -665,6 +676,7 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
     p->use_flow = use_flow;
     p->use_split = use_split;
     p->flow_gp = use_flow ? gp : 1;
+    p->flow_hw = use_flow && hw;
     p->chain_slots = chain_slots;
     p->flow_slots = flow_slots;
     return DOCTORS_OK;
@@ -737,7 +749,7 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     p->nab = p->A8 / p->ab;
     p->ntx = (p->nx + p->tx - 1) / p->tx;
     p->nty = (p->ny + p->ty - 1) / p->ty;
-    if (opt->sweep_kernel < 0 || opt->sweep_kernel > 6) return fail(DOCTORS_ERR_INVALID_ARG, "sweep_kernel must be 0 .. 6");
+    if (opt->sweep_kernel < 0 || opt->sweep_kernel > 7) return fail(DOCTORS_ERR_INVALID_ARG, "sweep_kernel must be 0 .. 7");
     if (p->differencing == DOCTORS_DIFF_DIAMOND &&
         !((opt->sweep_kernel == 0 || opt->sweep_kernel == 4) && p->A8 == p->ab && chain_const_table_ab(p->ab)))
         return fail(DOCTORS_ERR_INVALID_ARG,
@@ -1180,11 +1192,11 @@ int doctors_autotune(doctors_problem* p, doctors_tuning* out) {
     best.ms_per_sweep = 1e30;
     int count = 0;
     const int saved[4] = {p->tx, p->ty, p->ab,
-                          p->use_tc ? 2 : p->use_split ? 5 : p->use_flow ? (p->flow_gp == 2 ? 6 : 4)
+                          p->use_tc ? 2 : p->use_split ? 5 : p->use_flow ? (p->flow_gp == 2 ? 6 : p->flow_hw ? 7 : 4)
                                                                           : (p->chain_slots > 0 ? 3 : 1)};
     for (const auto& t : tiles) {
         for (int ab : abs_ok) {
-            for (int kernel = 1; kernel <= 6; ++kernel) {
+            for (int kernel = 1; kernel <= 7; ++kernel) {
                 if (p->differencing == DOCTORS_DIFF_DIAMOND && kernel != 4) continue;
                 if (kernel == 2 && !sweep_tc_supported(ab, p->M, t[0], t[1])) continue;
                 if (kernel >= 4 && !(p->A8 == ab && chain_const_table_ab(ab))) continue;

@@ -185,6 +185,8 @@ struct SweepArgs {
     const float* qang;                 // split transforms: angular source [G][8][V][ABP] (direction octant)
     float* pang;                       // split transforms: angular fluence [G][8][V][ABP]
     int gp;                            // dataflow kernel: groups per task (1 or 2)
+    int hw;                            // dataflow kernel: 1 = a face warp per CTA takes the incoming
+                                       // face records (mode 0)
     int dd;                            // dataflow kernel: 1 = diamond differencing (dir_table holds 2c), 0 = step
     int* flow;                         // non-null: dataflow kernel; [0] task queue, [1] CTAs done, [2] wait timed out,
                                        // [3] test hook: task + 1 that writes no faces (0: none)
@@ -250,7 +252,8 @@ inline size_t sweep_flow_smem_bytes(int ab, int tx, int ty, int gcount, int nmat
            8 * (size_t)gcount +
            4 * ((size_t)(dd ? 4 : 2) * chain_rs(gp * ab) * chain_px(tx) * (ty + 1) + (size_t)gcount * nmat) + 16;
 }
-int sweep_flow_blocks_per_sm(int ab, int M, int threads, size_t smem, bool split = false, int gp = 1, bool dd = false);
+int sweep_flow_blocks_per_sm(int ab, int M, int threads, size_t smem, bool split = false, int gp = 1, bool dd = false,
+                             bool hw = false);
 cudaError_t launch_sweep_flow(const SweepArgs& a, int M, int mode, cudaStream_t s);
 // split transforms (whole octants of S2..S8): moments -> angular source for
 // all 8 octants, the dataflow sweep on angular records (a.qang -> a.pang),
@@ -305,6 +308,7 @@ struct doctors_problem {
     bool use_flow = false;          // dataflow sweep (one launch per sweep, task queue)
     bool use_split = false;         // dataflow sweep with the transforms in separate passes
     int flow_gp = 1;                // dataflow sweep: groups per task
+    bool flow_hw = false;           // dataflow sweep: a face warp per CTA
     int differencing = 0;           // DOCTORS_DIFF_STEP or DOCTORS_DIFF_DIAMOND
     int flow_slots = 0;             // CTA slots of the plain dataflow kernel (modes 1, 2 under split)
     float* d_qang = nullptr;        // [G][8][V][ABP] angular source (split)

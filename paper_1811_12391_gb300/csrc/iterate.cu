@@ -30,13 +30,13 @@ cudaError_t launch_sweep_flow_m1_entry(const SweepArgs& a, int mode, cudaStream_
 cudaError_t launch_sweep_flow_m4_entry(const SweepArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_sweep_flow_m9_entry(const SweepArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_sweep_flow_m16_entry(const SweepArgs& a, int mode, cudaStream_t s);
-int sweep_flow_blocks_m1(int ab, int threads, size_t smem, bool split, int gp, bool dd);
+int sweep_flow_blocks_m1(int ab, int threads, size_t smem, bool split, int gp, bool dd, bool hw);
 cudaError_t launch_split_sweep_m1_entry(const SweepArgs& a, cudaStream_t s, int* count);
-int sweep_flow_blocks_m4(int ab, int threads, size_t smem, bool split, int gp, bool dd);
+int sweep_flow_blocks_m4(int ab, int threads, size_t smem, bool split, int gp, bool dd, bool hw);
 cudaError_t launch_split_sweep_m4_entry(const SweepArgs& a, cudaStream_t s, int* count);
-int sweep_flow_blocks_m9(int ab, int threads, size_t smem, bool split, int gp, bool dd);
+int sweep_flow_blocks_m9(int ab, int threads, size_t smem, bool split, int gp, bool dd, bool hw);
 cudaError_t launch_split_sweep_m9_entry(const SweepArgs& a, cudaStream_t s, int* count);
-int sweep_flow_blocks_m16(int ab, int threads, size_t smem, bool split, int gp, bool dd);
+int sweep_flow_blocks_m16(int ab, int threads, size_t smem, bool split, int gp, bool dd, bool hw);
 cudaError_t launch_split_sweep_m16_entry(const SweepArgs& a, cudaStream_t s, int* count);
 
 cudaError_t upload_tables_m1(const float* R, const float* w);
@@ -100,12 +100,12 @@ int sweep_chain_blocks_per_sm(int ab, bool ct, int M, int threads, size_t smem) 
     }
 }
 
-int sweep_flow_blocks_per_sm(int ab, int M, int threads, size_t smem, bool split, int gp, bool dd) {
+int sweep_flow_blocks_per_sm(int ab, int M, int threads, size_t smem, bool split, int gp, bool dd, bool hw) {
     switch (M) {
-        case 1: return sweep_flow_blocks_m1(ab, threads, smem, split, gp, dd);
-        case 4: return sweep_flow_blocks_m4(ab, threads, smem, split, gp, dd);
-        case 9: return sweep_flow_blocks_m9(ab, threads, smem, split, gp, dd);
-        case 16: return sweep_flow_blocks_m16(ab, threads, smem, split, gp, dd);
+        case 1: return sweep_flow_blocks_m1(ab, threads, smem, split, gp, dd, hw);
+        case 4: return sweep_flow_blocks_m4(ab, threads, smem, split, gp, dd, hw);
+        case 9: return sweep_flow_blocks_m9(ab, threads, smem, split, gp, dd, hw);
+        case 16: return sweep_flow_blocks_m16(ab, threads, smem, split, gp, dd, hw);
         default: return 0;
     }
 }

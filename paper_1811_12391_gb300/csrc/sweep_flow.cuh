@@ -63,19 +63,27 @@ __device__ __forceinline__ int flow_stage_tiles(int s, int ntx, int nty) {
 // groups the last task of each (tile, octant) has one group.  Mode 0, step
 // differencing, moments in 16-byte quarters (P1, P3).
 //
+// HW = true: one more warp per CTA, the face warp, takes over the incoming
+// face records: it fetches them ahead, waits until each is complete, moves
+// it into the halo of the plane buffers and hands the record back as NaN.
+// The column threads then run no face code at all (in the plain kernel the
+// threads of the tile's first row and column do it, and their warps carry
+// that code at every step).  Mode 0.
+//
 // DD = true: diamond differencing (no negative-flux fixup).  The direction
 // table then holds 2 c_x, 2 c_y, 2 c_z and their sum, so the cell solve
 // (q + sum 2 c psi_in) / (sigma + 2 sum c) is the step formula's; each face
 // leaves with 2 psi - psi_in.  The x-going and y-going face fluxes of a cell
 // differ, so they are kept in two planes (x: buf, y: bufy), and the face
 // records and the leakage carry the face fluxes, not the cell flux.
-template <int AB, int M, int MODE, bool SPLIT = false, int GP = 1, bool DD = false>
-__global__ void __launch_bounds__(256, (!SPLIT && M % 4 == 0) ? (GP == 1 ? 3 : 2) : 2)
+template <int AB, int M, int MODE, bool SPLIT = false, int GP = 1, bool DD = false, bool HW = false>
+__global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP == 1 ? 3 : 2) : 2)
     k_sweep_flow(const SweepArgs a, const ChainDirTable dt) {
     static_assert(!SPLIT || MODE == 0, "split transforms sweep in mode 0 only");
     static_assert(GP == 1 || (GP == 2 && !SPLIT && !DD && MODE == 0 && M % 4 == 0),
                   "two groups per task: the fused step-differenced kernel in mode 0, P1 or P3");
     static_assert(!DD || (!SPLIT && GP == 1), "diamond differencing in the fused one-group kernel only");
+    static_assert(!HW || MODE == 0, "the face warp serves the mode-0 sweep");
     constexpr int ABP = flow_abp(AB);
     constexpr int RS = (GP * AB) | 1;         // a column's record: GP groups' fluxes (odd length)
     // pipeline depths: face records are fetched PD steps before the step
@@ -92,7 +100,8 @@ __global__ void __launch_bounds__(256, (!SPLIT && M % 4 == 0) ? (GP == 1 ? 3 : 2
     const int PX = chain_px(a.tx);
     const int P = PX * (a.ty + 1);
     float4* momst = sm4;                                      // [2][GP][blockDim][4] prefetched source moments
-    float4* landx = momst + 2 * GP * blockDim.x * 4;          // [PD][GP][ty][ABP/4] fetched x-face records
+    const int T = a.tx * a.ty;                                // column threads
+    float4* landx = momst + 2 * GP * T * 4;                   // [PD][GP][ty][ABP/4] fetched x-face records
     float4* landy = landx + PD * GP * a.ty * (ABP / 4);       // [PD][GP][tx][ABP/4] fetched y-face records
     double* leak_s = reinterpret_cast<double*>(landy + PD * GP * a.tx * (ABP / 4));   // [gcount]
     float* buf = reinterpret_cast<float*>(leak_s + a.gcount);              // [2][P][RS]
@@ -107,6 +116,10 @@ __global__ void __launch_bounds__(256, (!SPLIT && M % 4 == 0) ? (GP == 1 ? 3 : 2
 
     // threads own the tile's columns in diagonal order (li + lj ascending)
     const int tid = threadIdx.x;
+    // with the face warp: the warps after the column threads' warps
+    const int ncw = (T + 31) / 32;
+    const bool fw = HW && tid >= ncw * 32;
+    const bool colthread = tid < T;
     int li = 0, lj = 0;
     {
         int base = 0;
@@ -136,8 +149,10 @@ __global__ void __launch_bounds__(256, (!SPLIT && M % 4 == 0) ? (GP == 1 ? 3 : 2
     int ntasks = 0;
     for (int s = 0; s < nst; ++s) ntasks += flow_stage_tiles(s, a.ntx, a.nty) * 8 * ngp;
     // this thread's landing slot for the record of group slot gg used at step st
-    auto land_x = [&](int st, int gg) { return landx + (((st & (PD - 1)) * GP + gg) * a.ty + lj) * (ABP / 4); };
-    auto land_y = [&](int st, int gg) { return landy + (((st & (PD - 1)) * GP + gg) * a.tx + li) * (ABP / 4); };
+    auto land_xr = [&](int st, int gg, int row) { return landx + (((st & (PD - 1)) * GP + gg) * a.ty + row) * (ABP / 4); };
+    auto land_yr = [&](int st, int gg, int cl) { return landy + (((st & (PD - 1)) * GP + gg) * a.tx + cl) * (ABP / 4); };
+    auto land_x = [&](int st, int gg) { return land_xr(st, gg, lj); };
+    auto land_y = [&](int st, int gg) { return land_yr(st, gg, li); };
     const float qnan = __int_as_float(0x7fffffff);
 
     constexpr int NS = SPLIT ? ABP : M;       // prefetched source values per cell (register path)
@@ -176,7 +191,7 @@ __global__ void __launch_bounds__(256, (!SPLIT && M % 4 == 0) ? (GP == 1 ? 3 : 2
         const int oe = a.reverse ? (o ^ 7) : o;     // octant of the directions
         const float fx = (oe & 1) ? -1.0f : 1.0f, fy = (oe & 2) ? -1.0f : 1.0f, fz = (oe & 4) ? -1.0f : 1.0f;
         const int ir = at * a.tx + li, jr = bt * a.ty + lj;
-        const bool col = ir < a.nx && jr < a.ny;
+        const bool col = colthread && ir < a.nx && jr < a.ny;
         const int i = sx > 0 ? ir : a.nx - 1 - ir;
         const int j = sy > 0 ? jr : a.ny - 1 - jr;
         const size_t vcol = (size_t)j * a.nx + i;
@@ -191,7 +206,9 @@ __global__ void __launch_bounds__(256, (!SPLIT && M % 4 == 0) ? (GP == 1 ? 3 : 2
         // incoming records (null on the mesh boundary: zero inflow)
         float* const xi = (li == 0 && at > 0) ? a.xface + (og * ntxf + at - 1) * xslab + (size_t)jr * a.nz * ABP : nullptr;
         float* const yi = (lj == 0 && bt > 0) ? a.yface + (og * ntyf + bt - 1) * yslab + (size_t)ir * a.nz * ABP : nullptr;
-        const bool xedge = col && li == 0, yedge = col && lj == 0;
+        // the column threads of the first row and column fetch and wait for the
+        // incoming face records, unless the face warp does
+        const bool xedge = !HW && col && li == 0, yedge = !HW && col && lj == 0;
 
         const size_t ang0 = ((size_t)g * 8 + oe) * V;       // angular records of (group, direction octant)
         // source values, density and material of plane kn into (dst, rho, mat);
@@ -210,7 +227,7 @@ __global__ void __launch_bounds__(256, (!SPLIT && M % 4 == 0) ? (GP == 1 ? 3 : 2
 #pragma unroll
                 for (int gg = 0; gg < GP; ++gg) {
                     if (gg < gn) {
-                        float4* slot = momst + (((kn & 1) * GP + gg) * blockDim.x + threadIdx.x) * 4;
+                        float4* slot = momst + (((kn & 1) * GP + gg) * T + threadIdx.x) * 4;
                         const float* srcm = a.src + (gV + gg * V + v) * M;
 #pragma unroll
                         for (int c4 = 0; c4 < M / 4; ++c4) cp_async_cg16(slot + c4, srcm + 4 * c4);
@@ -280,12 +297,106 @@ __global__ void __launch_bounds__(256, (!SPLIT && M % 4 == 0) ? (GP == 1 ? 3 : 2
             }
             asm volatile("cp.async.commit_group;\n" ::: "memory");
         };
+        // the face warp's records: lane r owns x-face row r (r < ty: the
+        // record entering column (0, r)) and y-face column r - ty (entering
+        // column (r - ty, 0)), and again r + 32
+        const int lane = threadIdx.x & 31;
+        auto fw_rec = [&](int r, int& side, int& idx, bool& ok, float*& src) {
+            if (r < a.ty) {
+                side = 0;
+                idx = r;
+                const int jr2 = bt * a.ty + r;
+                ok = jr2 < a.ny;
+                src = at > 0 ? a.xface + (og * ntxf + at - 1) * xslab + (size_t)jr2 * a.nz * ABP : nullptr;
+            } else {
+                side = 1;
+                idx = r - a.ty;
+                const int ir2 = at * a.tx + idx;
+                ok = ir2 < a.nx;
+                src = bt > 0 ? a.yface + (og * ntyf + bt - 1) * yslab + (size_t)ir2 * a.nz * ABP : nullptr;
+            }
+        };
+        // fetch the records used at step st (plane st - idx of each edge column)
+        auto fw_issue = [&](int st) {
+            for (int r = lane; r < a.tx + a.ty; r += 32) {
+                int side, idx;
+                bool ok;
+                float* src;
+                fw_rec(r, side, idx, ok, src);
+                const int pf = st - idx;
+                if (ok && src && pf >= 0 && pf < a.nz) {
+#pragma unroll
+                    for (int gg = 0; gg < GP; ++gg) {
+                        if (gg >= gn) break;
+                        float4* land = side == 0 ? land_xr(st, gg, idx) : land_yr(st, gg, idx);
+                        const float* s0 = src + (side == 0 ? gg * xgs : gg * ygs) + (size_t)pf * ABP;
+#pragma unroll
+                        for (int c4 = 0; c4 < ABP / 4; ++c4) cp_async_cg16(land + c4, s0 + 4 * c4);
+                    }
+                }
+            }
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+        };
+        // the records of step st (fetched PD steps ago): wait until complete,
+        // move into the halo of plane buffer cbf, hand back as NaN; zero
+        // inflow on the mesh boundary
+        auto fw_fill = [&](int st, int cbf) {
+            for (int r = lane; r < a.tx + a.ty; r += 32) {
+                int side, idx;
+                bool ok;
+                float* src;
+                fw_rec(r, side, idx, ok, src);
+                const int pf = st - idx;
+                if (!ok || pf < 0 || pf >= a.nz) continue;
+                const int hs0 = side == 0 ? (idx + 1) * PX * RS : (idx + 1) * RS;
+                float* hb = (side == 0 ? buf : bufy) + cbf * P * RS;
+#pragma unroll
+                for (int gg = 0; gg < GP; ++gg) {
+                    if (gg >= gn) break;
+                    const int hs = hs0 + gg * AB;
+                    if (!src) {
+#pragma unroll
+                        for (int q = 0; q < AB; ++q) hb[hs + q] = 0.0f;
+                        continue;
+                    }
+                    float4* land = side == 0 ? land_xr(st, gg, idx) : land_yr(st, gg, idx);
+                    const float* lf = reinterpret_cast<const float*>(land);
+                    float* s0 = src + (side == 0 ? gg * xgs : gg * ygs) + (size_t)pf * ABP;
+                    bool got = false;
+                    for (int it = 0; it < kFlowSpinLimit; ++it) {
+                        got = true;
+#pragma unroll
+                        for (int q = 0; q < AB; ++q) got = got && !isnan(lf[q]);
+                        if (got) break;
+                        if ((it & 63) == 63 && *reinterpret_cast<volatile int*>(a.flow + 2)) break;
+                        __nanosleep(100);
+#pragma unroll
+                        for (int c4 = 0; c4 < ABP / 4; ++c4) cp_async_cg16(land + c4, s0 + 4 * c4);
+                        cp_async_wait_all();
+                    }
+                    if (!got) atomicExch(a.flow + 2, 1);
+#pragma unroll
+                    for (int q = 0; q < AB; ++q) hb[hs + q] = got ? lf[q] : 0.0f;
+                    float4* back = reinterpret_cast<float4*>(s0);
+#pragma unroll
+                    for (int c4 = 0; c4 < ABP / 4; ++c4) back[c4] = make_float4(qnan, qnan, qnan, qnan);
+                }
+            }
+        };
         // steps -PD .. -1 only fetch the first records
-        for (int st = 0; st < PD - 1; ++st) issue_faces(st);
+        for (int st = 0; st < PD - 1; ++st) {
+            if (HW && fw) fw_issue(st);
+            else issue_faces(st);
+        }
         const int hend = a.nz + a.tx + a.ty - 2;
 #pragma unroll 1
         for (int h = -1; h < hend; ++h) {
             const int cb = h & 1, pb = cb ^ 1;
+          if (HW && fw) {
+            fw_issue(h + PD);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+            fw_fill(h + 1, cb);
+          } else {
             float sig_cur[GP];
 #pragma unroll
             for (int gg = 0; gg < GP; ++gg) sig_cur[gg] = 0.0f;
@@ -301,7 +412,7 @@ __global__ void __launch_bounds__(256, (!SPLIT && M % 4 == 0) ? (GP == 1 ? 3 : 2
                 }
                 asm volatile("cp.async.commit_group;\n" ::: "memory");
             }
-            issue_faces(h + PD);
+            if constexpr (!HW) issue_faces(h + PD);
             const int kr = h - d;
             const bool act = col && h >= d && kr < a.nz;
             if (act) {
@@ -331,7 +442,7 @@ __global__ void __launch_bounds__(256, (!SPLIT && M % 4 == 0) ? (GP == 1 ? 3 : 2
                 float sig;
                 if constexpr (SMEMPF) {
                     sig = sig_cur[gg];
-                    const float4* slot = momst + (((kr & 1) * GP + gg) * blockDim.x + threadIdx.x) * 4;
+                    const float4* slot = momst + (((kr & 1) * GP + gg) * T + threadIdx.x) * 4;
 #pragma unroll
                     for (int c4 = 0; c4 < M / 4; ++c4) {
                         const float4 t4 = slot[c4];
@@ -555,8 +666,8 @@ __global__ void __launch_bounds__(256, (!SPLIT && M % 4 == 0) ? (GP == 1 ? 3 : 2
                 // slot 0 in .x and group slot 1 in .y with the same table constant
                 // in both lanes, so each table value is read once for the two cells
                 const bool two = gn == 2;
-                const float4* slot0 = momst + (((kr & 1) * GP + 0) * blockDim.x + threadIdx.x) * 4;
-                const float4* slot1 = momst + (((kr & 1) * GP + 1) * blockDim.x + threadIdx.x) * 4;
+                const float4* slot0 = momst + (((kr & 1) * GP + 0) * T + threadIdx.x) * 4;
+                const float4* slot1 = momst + (((kr & 1) * GP + 1) * T + threadIdx.x) * 4;
                 const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 float2 s2[M];
 #pragma unroll
@@ -685,7 +796,8 @@ __global__ void __launch_bounds__(256, (!SPLIT && M % 4 == 0) ? (GP == 1 ? 3 : 2
             const int pf = h + 1 - d;
             if constexpr (SMEMPF) {
                 // the next cell's moments (and the faces fetched a step ago) have landed
-                asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+                if constexpr (HW) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+                else asm volatile("cp.async.wait_group 1;\n" ::: "memory");
             }
             if (col && pf >= 0 && pf < a.nz && (xedge || yedge)) {
                 if constexpr (PD == 2) {
@@ -734,6 +846,7 @@ __global__ void __launch_bounds__(256, (!SPLIT && M % 4 == 0) ? (GP == 1 ? 3 : 2
                   }
                 }
             }
+          }
             __syncthreads();
         }
     }
@@ -836,7 +949,7 @@ __global__ void __launch_bounds__(256) k_split_d2m(const float* pang, float* mom
 }
 
 template <int M>
-int sweep_flow_blocks_per_sm(int ab, int threads, size_t smem, bool split, int gp, bool dd) {
+int sweep_flow_blocks_per_sm(int ab, int threads, size_t smem, bool split, int gp, bool dd, bool hw) {
     int b = 0;
     cudaError_t e = cudaErrorInvalidValue;
     auto query = [&](auto kern) {
@@ -848,7 +961,9 @@ int sweep_flow_blocks_per_sm(int ab, int threads, size_t smem, bool split, int g
     case AB:                                                                            \
         if (split) query(k_sweep_flow<AB, M, 0, true>);                                  \
         else if (dd) query(k_sweep_flow<AB, M, 0, false, 1, true>);                      \
-        else if (gp == 2) {                                                             \
+        else if (hw) {                                                                  \
+            if constexpr (M % 4 == 0) query(k_sweep_flow<AB, M, 0, false, 1, false, true>); \
+        } else if (gp == 2) {                                                           \
             if constexpr (M % 4 == 0) query(k_sweep_flow<AB, M, 0, false, 2>);          \
         } else query(k_sweep_flow<AB, M, 0>);                                            \
         break;
@@ -920,8 +1035,10 @@ cudaError_t launch_sweep_flow_m(const SweepArgs& a, cudaStream_t s) {
         ntasks += (hi - lo + 1) * 8 * ngp;
     }
     const int grid = ntasks < a.chain_slots ? ntasks : a.chain_slots;
-    const int T = a.tx * a.ty;
     const int gp = (MODE == 0 && a.gp == 2 && !dd && M % 4 == 0) ? 2 : 1;
+    const bool hw = MODE == 0 && a.hw != 0 && !dd && gp == 1 && M % 4 == 0;
+    // column threads, plus the face warp
+    const int T = hw ? ((a.tx * a.ty + 31) / 32 + 1) * 32 : a.tx * a.ty;
     const size_t smem = sweep_flow_smem_bytes(a.ab, a.tx, a.ty, a.gcount, a.nmat, gp, dd);
     cudaError_t e = cudaSuccess;
     auto launch = [&](auto kern) {
@@ -935,6 +1052,10 @@ cudaError_t launch_sweep_flow_m(const SweepArgs& a, cudaStream_t s) {
             break;                                                                      \
         }                                                                               \
         if constexpr (MODE == 0 && M % 4 == 0) {                                        \
+            if (hw) {                                                                   \
+                launch(k_sweep_flow<AB, M, 0, false, 1, false, true>);                   \
+                break;                                                                  \
+            }                                                                           \
             if (gp == 2) {                                                              \
                 launch(k_sweep_flow<AB, M, 0, false, 2>);                                \
                 break;                                                                  \

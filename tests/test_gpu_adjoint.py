@@ -46,8 +46,8 @@ def grad_ref():
     return p, roi, osv.gradients(p, roi, tol=1e-12)
 
 
-@pytest.mark.parametrize("L,kernel", [(1, 1), (1, 3), (1, 4), (1, 5), (1, 6), (3, 1), (3, 2), (3, 3), (3, 4), (3, 5),
-                                      (3, 6)])
+@pytest.mark.parametrize("L,kernel", [(1, 1), (1, 3), (1, 4), (1, 5), (1, 6), (1, 7), (3, 1), (3, 2), (3, 3), (3, 4),
+                                      (3, 5), (3, 6), (3, 7)])
 def test_adjoint_fluence_and_gradients_match_oracle(env, grad_ref, L, kernel):
     torch, C, DoctorsProblem = env
     if L == 1:

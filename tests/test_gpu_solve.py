@@ -60,13 +60,15 @@ def cylinder_ref():
                                             ((16, 16), 10, 4), ((16, 8), 10, 4), ((5, 7), 10, 4), ((8, 4), 10, 4),
                                             ((8, 8), 10, 4), ((8, 8), 10, 0),
                                             ((8, 8), 10, 5), ((16, 8), 10, 5), ((5, 7), 10, 5),
-                                            ((8, 8), 10, 6), ((16, 8), 10, 6), ((5, 7), 10, 6)])
+                                            ((8, 8), 10, 6), ((16, 8), 10, 6), ((5, 7), 10, 6),
+                                            ((8, 8), 10, 7), ((16, 8), 10, 7), ((5, 7), 10, 7), ((32, 8), 10, 7)])
 def test_ragged_multitile_cylinder(dp, cylinder_ref, tile, ab, kernel):
     """Several sweep tiles with ragged tails in x and y, S8 P3, with the
     CUDA-core (1), tensor-core (2), chained (3), dataflow (4), dataflow
-    with split transforms (5) and dataflow with two groups per task (6; with
-    five groups the last task of every tile and octant has one group)
-    sweeps."""
+    with split transforms (5), dataflow with two groups per task (6; with
+    five groups the last task of every tile and octant has one group) and
+    dataflow with a face warp (7; 5x7 leaves a partly used column warp, 32x8
+    gives the face warp 40 records) sweeps."""
     p, sol = cylinder_ref
     d = dp(p, tol=1e-6, max_iters=400, tile=tile, angles_per_block=ab, sweep_kernel=kernel)
     _compare(d, p, sol, f"cylinder tile={tile} ab={ab} kernel={kernel}")
@@ -89,12 +91,12 @@ def test_sweep_kernels_agree(dp):
     cylinder (one sweep from the first-collision source)."""
     p = ph.water_cylinder()
     outs = []
-    for kernel in (1, 2, 3, 4, 5, 6):
+    for kernel in (1, 2, 3, 4, 5, 6, 7):
         d = dp(p, tol=1e-6, max_iters=1, sweep_kernel=kernel, angles_per_block=10)
         d.solve(allow_not_converged=True)
         outs.append(d.fluence_host(1))
         d.close()
-    for k in (1, 2, 3, 4, 5):
+    for k in (1, 2, 3, 4, 5, 6):
         assert max_rel(outs[k], outs[0]) <= 2e-5
 
 
@@ -122,7 +124,7 @@ def test_infinite_medium_volume_source(dp):
     d.close()
 
 
-@pytest.mark.parametrize("kernel", [1, 3, 4, 5, 6])
+@pytest.mark.parametrize("kernel", [1, 3, 4, 5, 6, 7])
 def test_degenerate_meshes(dp, kernel):
     """Single voxel, single column and single plane meshes."""
     for dims in ((1, 1, 1), (1, 1, 7), (5, 1, 1), (4, 6, 1)):
@@ -180,7 +182,7 @@ def test_iteration_cap_reports_not_converged(dp):
     from paper_1811_12391_gb300 import _lib as C
     p = ph.tiny_cube(n=8)
     ref = osv.solve(p, tol=1e-11)
-    for device_loop, kernel in ((0, 0), (1, 0), (1, 4), (0, 5), (1, 5), (0, 6), (1, 6)):
+    for device_loop, kernel in ((0, 0), (1, 0), (1, 4), (0, 5), (1, 5), (0, 6), (1, 6), (0, 7), (1, 7)):
         d = dp(p, tol=1e-6, max_iters=3, device_loop=device_loop, sweep_kernel=kernel, angles_per_block=3)
         with pytest.raises(C.DoctorsError) as e:
             d.solve()
@@ -197,16 +199,18 @@ def test_iteration_cap_reports_not_converged(dp):
         d.close()
 
 
-def test_dataflow_wait_times_out_and_recovers(dp):
+@pytest.mark.parametrize("kernel", [4, 7])
+def test_dataflow_wait_times_out_and_recovers(dp, kernel):
     """The dataflow sweep's waits are bounded: with one task withholding the
-    faces it owes (test hook), the downstream waits give up, the solve
-    returns DOCTORS_ERR_TIMEOUT, and after the hook is cleared the same
-    problem solves to the oracle again."""
+    faces it owes (test hook), the downstream waits give up (in the column
+    threads of kernel 4, in the face warp of kernel 7), the solve returns
+    DOCTORS_ERR_TIMEOUT, and after the hook is cleared the same problem
+    solves to the oracle again."""
     import time
     from paper_1811_12391_gb300 import _lib as C
     p = ph.tiny_cube(n=8)
     ref = osv.solve(p, tol=1e-11)
-    d = dp(p, tol=1e-6, max_iters=3, tile=(4, 4), sweep_kernel=4, angles_per_block=3)
+    d = dp(p, tol=1e-6, max_iters=3, tile=(4, 4), sweep_kernel=kernel, angles_per_block=3)
     C.check(C.doctors_debug_withhold_faces(d.h, 0))
     t0 = time.time()
     with pytest.raises(C.DoctorsError) as e:
@@ -215,7 +219,7 @@ def test_dataflow_wait_times_out_and_recovers(dp):
     assert time.time() - t0 < 30.0
     C.check(C.doctors_debug_withhold_faces(d.h, -1))
     d.close()
-    d = dp(p, tol=1e-6, max_iters=300, tile=(4, 4), sweep_kernel=4, angles_per_block=3)
+    d = dp(p, tol=1e-6, max_iters=300, tile=(4, 4), sweep_kernel=kernel, angles_per_block=3)
     C.check(C.doctors_debug_withhold_faces(d.h, 5))
     with pytest.raises(C.DoctorsError):
         d.solve(allow_not_converged=True)
