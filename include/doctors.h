@@ -111,7 +111,9 @@ typedef struct doctors_options {
                                 and P1 or P3),
                                 7 = dataflow with a face warp: one more warp per CTA fetches and
                                 waits for the incoming face fluxes, the column threads only sweep
-                                (same conditions as 4, P1 or P3, tile_x + tile_y <= 64) */
+                                (same conditions as 4, P1 or P3, tile_x + tile_y <= 64),
+                                8 = as 5 with the two transform passes on the tensor cores
+                                (tcgen05, 3xTF32 with FP32 accumulation; P3 only) */
     int device_loop;         /* 1 = run the source iteration as one CUDA graph whose while loop is
                                 decided on the device (no host round trip per iteration) */
     int differencing;        /* spatial scheme of the sweep (the paper does not state one):
@@ -343,7 +345,7 @@ typedef struct doctors_tuning {
     int angles_per_block;    /* directions per CTA */
     int sweep_kernel;        /* 1 CUDA-core, 2 tensor-core, 3 chained, 4 dataflow, 5 dataflow with split
                                 transforms, 6 dataflow with two groups per task, 7 dataflow with a
-                                face warp (as doctors_options) */
+                                face warp, 8 split transforms on the tensor cores (as doctors_options) */
     double ms_per_sweep;     /* measured time of one full sweep of this problem */
     int candidates;          /* schedules timed (0 if taken from the cache) */
 } doctors_tuning;

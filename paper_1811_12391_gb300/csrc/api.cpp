@@ -85,7 +85,7 @@ void free_problem(doctors_problem* p) {
                     p->d_emit, p->d_iso, p->d_xface, p->d_yface, p->d_red,
                     p->d_Z, p->d_Qa, p->d_T, p->d_rf, p->d_r, p->d_acc, p->d_grad, p->d_H,
                     p->d_ones, p->d_psi, p->d_prod, p->d_flow, p->d_qang, p->d_pang,
-                    p->d_k, p->d_roi, p->d_part};
+                    p->d_k, p->d_roi, p->d_part, p->d_tcb};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (p->h_red) cudaFreeHost(p->h_red);
@@ -215,6 +215,8 @@ SweepArgs sweep_args(const doctors_problem* p, int reverse, const float* src, fl
     a.pang = p->d_pang;
     a.gp = p->flow_gp;
     a.hw = p->flow_hw ? 1 : 0;
+    a.tc_b1 = (p->use_split && p->split_tc) ? p->d_tcb : nullptr;
+    a.tc_b2 = (p->use_split && p->split_tc) ? p->d_tcb + p->tcb1_floats : nullptr;
     a.dd = p->differencing == DOCTORS_DIFF_DIAMOND ? 1 : 0;
     return a;
 }
@@ -451,6 +453,10 @@ int graph_iterate(doctors_problem** ps, int n, int reverse, const float* const* 
             if (e == cudaSuccess) e = launch_zero(p->d_red, 5 * (size_t)p->G, skip, cs);
             SweepArgs sw = sweep_args(p, reverse, p->d_src, moms[q]);
             sw.skip = skip;
+            // the branches' dataflow sweeps share the resident CTA slots, so
+            // instances sweep side by side and one's wavefront fill and drain
+            // overlap another's full stages
+            sw.slot_share = nb;
             int nl = 0;
             if (e == cudaSuccess) e = launch_sweep(p, sw, 0, cs, &nl);
             if (e == cudaSuccess) e = launch_residual(p->V, p->G, p->M, moms[q], p->d_prev, p->d_red + p->G, cs, skip);
@@ -532,8 +538,8 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
         set_error("angles_per_block must divide N(N+2)/8 and be one of 1,2,3,4,5,6,7,9,10,12");
         return DOCTORS_ERR_INVALID_ARG;
     }
-    if (kernel < 0 || kernel > 7) {
-        set_error("sweep_kernel must be 0 .. 7");
+    if (kernel < 0 || kernel > 8) {
+        set_error("sweep_kernel must be 0 .. 8");
         return DOCTORS_ERR_INVALID_ARG;
     }
     if (kernel >= 4 && !(p->A8 == ab && chain_const_table_ab(ab))) {
@@ -542,6 +548,10 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
     }
     if ((kernel == 6 || kernel == 7) && p->M % 4 != 0) {
         set_error("the two-group and face-warp dataflow sweeps (sweep_kernel 6, 7) need P1 or P3 (legendre 1 or 3)");
+        return DOCTORS_ERR_INVALID_ARG;
+    }
+    if (kernel == 8 && p->M != 16) {
+        set_error("the tensor-core transforms (sweep_kernel 8) need P3 (legendre 3)");
         return DOCTORS_ERR_INVALID_ARG;
     }
     if (kernel == 7 && tx + ty > 64) {
@@ -569,7 +579,8 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
     }
     const bool use_tc = kernel == 2 || (kernel == 0 && tc_ok && kDefaultTensorCoreSweep);
     const bool flow_ok = p->A8 == ab && chain_const_table_ab(ab);
-    const bool use_split = kernel == 5 || (kernel == 0 && !use_tc && flow_ok && kDefaultSplitSweep);
+    const bool use_split = kernel == 5 || kernel == 8 || (kernel == 0 && !use_tc && flow_ok && kDefaultSplitSweep);
+    const bool split_tc = kernel == 8 && p->M == 16;
     const bool use_flow = !use_split && (kernel == 4 || kernel == 6 || kernel == 7 ||
                                          (kernel == 0 && !use_tc && flow_ok && kDefaultDataflowSweep));
     const int gp = kernel == 6 || (kernel == 0 && use_flow && kDefaultTwoGroupSweep && p->M % 4 == 0) ? 2 : 1;
@@ -662,6 +673,16 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
             p->ang_floats = nang;
         }
     }
+    if (split_tc && !p->d_tcb) {
+        // operand tables of the tensor-core transforms (the first octant's rows are fixed per problem)
+        std::vector<float> b1, b2;
+        build_tc_transform_tables(p->dir_table, p->A8, b1, b2);
+        int rc = dalloc_t(&p->d_tcb, b1.size() + b2.size(), "tensor-core transform tables");
+        if (rc) return rc;
+        CU(cudaMemcpy(p->d_tcb, b1.data(), b1.size() * sizeof(float), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(p->d_tcb + b1.size(), b2.data(), b2.size() * sizeof(float), cudaMemcpyHostToDevice));
+        p->tcb1_floats = b1.size();
+    }
     if (use_flow || use_split) {
         // every face record starts as NaN (not yet written); the queue at zero
         if (!p->d_flow) {
@@ -675,6 +696,7 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
     p->tx = tx; p->ty = ty; p->ab = ab; p->nab = p->A8 / ab; p->ntx = ntx; p->nty = nty; p->use_tc = use_tc;
     p->use_flow = use_flow;
     p->use_split = use_split;
+    p->split_tc = use_split && split_tc;
     p->flow_gp = use_flow ? gp : 1;
     p->flow_hw = use_flow && hw;
     p->chain_slots = chain_slots;
@@ -749,7 +771,7 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     p->nab = p->A8 / p->ab;
     p->ntx = (p->nx + p->tx - 1) / p->tx;
     p->nty = (p->ny + p->ty - 1) / p->ty;
-    if (opt->sweep_kernel < 0 || opt->sweep_kernel > 7) return fail(DOCTORS_ERR_INVALID_ARG, "sweep_kernel must be 0 .. 7");
+    if (opt->sweep_kernel < 0 || opt->sweep_kernel > 8) return fail(DOCTORS_ERR_INVALID_ARG, "sweep_kernel must be 0 .. 8");
     if (p->differencing == DOCTORS_DIFF_DIAMOND &&
         !((opt->sweep_kernel == 0 || opt->sweep_kernel == 4) && p->A8 == p->ab && chain_const_table_ab(p->ab)))
         return fail(DOCTORS_ERR_INVALID_ARG,
@@ -1192,11 +1214,11 @@ int doctors_autotune(doctors_problem* p, doctors_tuning* out) {
     best.ms_per_sweep = 1e30;
     int count = 0;
     const int saved[4] = {p->tx, p->ty, p->ab,
-                          p->use_tc ? 2 : p->use_split ? 5 : p->use_flow ? (p->flow_gp == 2 ? 6 : p->flow_hw ? 7 : 4)
+                          p->use_tc ? 2 : p->use_split ? (p->split_tc ? 8 : 5) : p->use_flow ? (p->flow_gp == 2 ? 6 : p->flow_hw ? 7 : 4)
                                                                           : (p->chain_slots > 0 ? 3 : 1)};
     for (const auto& t : tiles) {
         for (int ab : abs_ok) {
-            for (int kernel = 1; kernel <= 7; ++kernel) {
+            for (int kernel = 1; kernel <= 8; ++kernel) {
                 if (p->differencing == DOCTORS_DIFF_DIAMOND && kernel != 4) continue;
                 if (kernel == 2 && !sweep_tc_supported(ab, p->M, t[0], t[1])) continue;
                 if (kernel >= 4 && !(p->A8 == ab && chain_const_table_ab(ab))) continue;

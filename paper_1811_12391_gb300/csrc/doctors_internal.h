@@ -181,12 +181,16 @@ struct SweepArgs {
     float* prod;                       // [G][V]: mode 2 accumulator
     const int* skip;                   // if non-null and *skip != 0 the kernel does nothing
     int chain_slots;                   // > 0: chained kernel, at most this many CTAs per stage launch
+    int slot_share;                    // dataflow kernels: use chain_slots / slot_share CTAs (> 1 when
+                                       // that many instances sweep concurrently; 0 or 1: all)
     const struct ChainDirTable* dir_table;   // host copy of the first-octant direction table (chained kernel)
     const float* qang;                 // split transforms: angular source [G][8][V][ABP] (direction octant)
     float* pang;                       // split transforms: angular fluence [G][8][V][ABP]
     int gp;                            // dataflow kernel: groups per task (1 or 2)
     int hw;                            // dataflow kernel: 1 = a face warp per CTA takes the incoming
                                        // face records (mode 0)
+    const float* tc_b1;                // split transforms on the tensor cores (P3): moments -> directions
+    const float* tc_b2;                // and directions -> moments operand tables, or null
     int dd;                            // dataflow kernel: 1 = diamond differencing (dir_table holds 2c), 0 = step
     int* flow;                         // non-null: dataflow kernel; [0] task queue, [1] CTAs done, [2] wait timed out,
                                        // [3] test hook: task + 1 that writes no faces (0: none)
@@ -263,6 +267,13 @@ cudaError_t launch_split_sweep(const SweepArgs& a, int M, cudaStream_t s, int* c
 // once per device; returns the first table row of order N in *base.
 cudaError_t ensure_direction_tables(int device, int N, int* base);
 
+// split transforms on the tensor cores (P3, whole octants of S2..S8):
+// transform_tc.cu.  The operand tables (TF32 hi and lo parts in the kernels'
+// shared-memory layout) are built on the host from the first-octant rows.
+void build_tc_transform_tables(const ChainDirTable& dt, int AB, std::vector<float>& b1, std::vector<float>& b2);
+cudaError_t launch_m2d_tc(const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_d2m_tc(const SweepArgs& a, cudaStream_t s);
+
 // tensor-core sweep (P3): sweep_tc.cu
 bool sweep_tc_supported(int ab, int M, int tx, int ty);
 size_t sweep_tc_smem_bytes(int ab, int tx, int ty, int nz, int nmat);
@@ -307,12 +318,15 @@ struct doctors_problem {
     int chain_slots = 0;            // > 0: chained or dataflow sweep with this many CTA slots
     bool use_flow = false;          // dataflow sweep (one launch per sweep, task queue)
     bool use_split = false;         // dataflow sweep with the transforms in separate passes
+    bool split_tc = false;          // ... those passes on the tensor cores (P3)
     int flow_gp = 1;                // dataflow sweep: groups per task
     bool flow_hw = false;           // dataflow sweep: a face warp per CTA
     int differencing = 0;           // DOCTORS_DIFF_STEP or DOCTORS_DIFF_DIAMOND
     int flow_slots = 0;             // CTA slots of the plain dataflow kernel (modes 1, 2 under split)
     float* d_qang = nullptr;        // [G][8][V][ABP] angular source (split)
     float* d_pang = nullptr;        // [G][8][V][ABP] angular fluence (split)
+    float* d_tcb = nullptr;         // split transforms on the tensor cores: operand tables b1, b2
+    size_t tcb1_floats = 0;         // floats of b1 (b2 follows)
     size_t ang_floats = 0;
     int* d_flow = nullptr;          // [4] dataflow queue, done count, timeout flag
     doctors::ChainDirTable dir_table{};   // first-octant direction table of the chained sweep

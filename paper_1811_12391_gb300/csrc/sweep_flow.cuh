@@ -993,13 +993,21 @@ cudaError_t launch_split_sweep_m(const SweepArgs& a, cudaStream_t s, int* count)
         const int hi = st < a.ntx - 1 ? st : a.ntx - 1;
         ntasks += (hi - lo + 1) * 8 * a.gcount;
     }
-    const int grid = ntasks < a.chain_slots ? ntasks : a.chain_slots;
+    // persistent CTAs: every resident slot, or its share when several instances sweep at once
+    const int slots = std::max(1, a.chain_slots / std::max(1, a.slot_share));
+    const int grid = ntasks < slots ? ntasks : slots;
     const int T = a.tx * a.ty;
     const size_t smem = sweep_flow_smem_bytes(a.ab, a.tx, a.ty, a.gcount, a.nmat);
     cudaError_t e = cudaSuccess;
+    // P3: the transforms on the tensor cores when the problem holds their tables
+    const bool tc = M == 16 && a.tc_b1 && a.tc_b2;
     auto run = [&](auto m2d, auto sweep, auto d2m) {
-        m2d<<<tgrid, 256, 0, s>>>(a.src, const_cast<float*>(a.qang), V, a.g0, a.gcount, a.skip);
-        e = cudaGetLastError();
+        if (tc) {
+            e = launch_m2d_tc(a, s);
+        } else {
+            m2d<<<tgrid, 256, 0, s>>>(a.src, const_cast<float*>(a.qang), V, a.g0, a.gcount, a.skip);
+            e = cudaGetLastError();
+        }
         if (e == cudaSuccess && smem > 48 * 1024)
             e = cudaFuncSetAttribute(sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess) {
@@ -1007,8 +1015,12 @@ cudaError_t launch_split_sweep_m(const SweepArgs& a, cudaStream_t s, int* count)
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) {
-            d2m<<<tgrid, 256, 0, s>>>(a.pang, a.mom, V, a.g0, a.gcount, a.skip);
-            e = cudaGetLastError();
+            if (tc) {
+                e = launch_d2m_tc(a, s);
+            } else {
+                d2m<<<tgrid, 256, 0, s>>>(a.pang, a.mom, V, a.g0, a.gcount, a.skip);
+                e = cudaGetLastError();
+            }
         }
     };
     switch (a.ab) {
@@ -1034,7 +1046,9 @@ cudaError_t launch_sweep_flow_m(const SweepArgs& a, cudaStream_t s) {
         const int hi = st < a.ntx - 1 ? st : a.ntx - 1;
         ntasks += (hi - lo + 1) * 8 * ngp;
     }
-    const int grid = ntasks < a.chain_slots ? ntasks : a.chain_slots;
+    // persistent CTAs: every resident slot, or its share when several instances sweep at once
+    const int slots = std::max(1, a.chain_slots / std::max(1, a.slot_share));
+    const int grid = ntasks < slots ? ntasks : slots;
     const int gp = (MODE == 0 && a.gp == 2 && !dd && M % 4 == 0) ? 2 : 1;
     const bool hw = MODE == 0 && a.hw != 0 && !dd && gp == 1 && M % 4 == 0;
     // column threads, plus the face warp

@@ -30,3 +30,10 @@ def max_rel(gpu, ref, floor=FLOOR):
 # 4.9e-4 at S4 P3, 2.7e-3 at S16 P1; above 1e-4 of the maximum at most
 # 5.4e-5).
 DENSITY_GRAD_TOL = 5e-3
+
+# Sweep kernel 8 runs the split sweep's P3 moment transforms on the tensor cores as 3xTF32
+# (about 2^-21 relative error per transform, against 2^-24 in FP32).  In the
+# density gradient's cancellations that shows as up to 1.3e-4 (measured) on
+# entries between 1e-4 and 1e-3 of the largest gradient, so for that path the
+# REL_TOL bar on density gradients starts at this fraction of the maximum.
+TF32X3_DENSITY_FLOOR = 1e-3

@@ -8,7 +8,7 @@ import pytest
 
 from oracle import solver as osv
 from synth import phantoms as ph
-from tests.parity import DENSITY_GRAD_TOL, REL_TOL, max_rel
+from tests.parity import DENSITY_GRAD_TOL, REL_TOL, TF32X3_DENSITY_FLOOR, max_rel
 
 pytestmark = pytest.mark.gpu
 
@@ -47,7 +47,7 @@ def grad_ref():
 
 
 @pytest.mark.parametrize("L,kernel", [(1, 1), (1, 3), (1, 4), (1, 5), (1, 6), (1, 7), (3, 1), (3, 2), (3, 3), (3, 4),
-                                      (3, 5), (3, 6), (3, 7)])
+                                      (3, 5), (3, 6), (3, 7), (3, 8)])
 def test_adjoint_fluence_and_gradients_match_oracle(env, grad_ref, L, kernel):
     torch, C, DoctorsProblem = env
     if L == 1:
@@ -77,7 +77,11 @@ def test_adjoint_fluence_and_gradients_match_oracle(env, grad_ref, L, kernel):
     explicit = (roi[None, :] * p.k_dep[p.mat].T * ref["forward"].phi).sum(axis=0)
     gd = g["density"].cpu().numpy() + explicit
     rd = ref["d_density"]
-    assert max_rel(gd, rd, floor=1e-4) <= REL_TOL
+    # kernel 8 runs the split sweep's P3 transforms on the tensor cores as
+    # 3xTF32 (about 2^-21 relative error per transform against 2^-24 in FP32):
+    # its bar for 1e-4 starts at 1e-3 of the largest gradient
+    floor = TF32X3_DENSITY_FLOOR if kernel == 8 else 1e-4
+    assert max_rel(gd, rd, floor=floor) <= REL_TOL
     assert max_rel(gd, rd, floor=1e-6) <= DENSITY_GRAD_TOL
     d.close()
 

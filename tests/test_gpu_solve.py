@@ -61,14 +61,16 @@ def cylinder_ref():
                                             ((8, 8), 10, 4), ((8, 8), 10, 0),
                                             ((8, 8), 10, 5), ((16, 8), 10, 5), ((5, 7), 10, 5),
                                             ((8, 8), 10, 6), ((16, 8), 10, 6), ((5, 7), 10, 6),
-                                            ((8, 8), 10, 7), ((16, 8), 10, 7), ((5, 7), 10, 7), ((32, 8), 10, 7)])
+                                            ((8, 8), 10, 7), ((16, 8), 10, 7), ((5, 7), 10, 7), ((32, 8), 10, 7),
+                                            ((8, 8), 10, 8), ((5, 7), 10, 8)])
 def test_ragged_multitile_cylinder(dp, cylinder_ref, tile, ab, kernel):
     """Several sweep tiles with ragged tails in x and y, S8 P3, with the
     CUDA-core (1), tensor-core (2), chained (3), dataflow (4), dataflow
     with split transforms (5), dataflow with two groups per task (6; with
     five groups the last task of every tile and octant has one group) and
     dataflow with a face warp (7; 5x7 leaves a partly used column warp, 32x8
-    gives the face warp 40 records) sweeps."""
+    gives the face warp 40 records) and split transforms on the tensor cores
+    (8; 3xTF32) sweeps."""
     p, sol = cylinder_ref
     d = dp(p, tol=1e-6, max_iters=400, tile=tile, angles_per_block=ab, sweep_kernel=kernel)
     _compare(d, p, sol, f"cylinder tile={tile} ab={ab} kernel={kernel}")
@@ -91,12 +93,12 @@ def test_sweep_kernels_agree(dp):
     cylinder (one sweep from the first-collision source)."""
     p = ph.water_cylinder()
     outs = []
-    for kernel in (1, 2, 3, 4, 5, 6, 7):
+    for kernel in (1, 2, 3, 4, 5, 6, 7, 8):
         d = dp(p, tol=1e-6, max_iters=1, sweep_kernel=kernel, angles_per_block=10)
         d.solve(allow_not_converged=True)
         outs.append(d.fluence_host(1))
         d.close()
-    for k in (1, 2, 3, 4, 5, 6):
+    for k in (1, 2, 3, 4, 5, 6, 7):
         assert max_rel(outs[k], outs[0]) <= 2e-5
 
 
