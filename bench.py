@@ -59,7 +59,8 @@ SWEEP_TRAFFIC = {
     (16, 16, 5, 1): (1687.6e6, "sweep_impl.cuh", "592eff4d10129e1bde8b55aecdf9fbf52f768e8c"),
     (16, 16, 10, 2): (2121.9e6, "sweep_tc.cu", "79ec5703826b205c1bdc9d4f7ff57c205fec428a"),
     (16, 8, 10, 3): (2534.9e6, "sweep_chain.cuh", "3502773d12d37fb58b50dbc1187553785b1df685"),
-    (8, 8, 10, 4): (3154.0e6, "sweep_flow.cuh", "6057ed04a3eed69e65ed21239fae6fc7df83e2ca"),
+    (8, 8, 10, 4): (3145.0e6, "sweep_flow.cuh", "6b1fe4aa291235b10dec1bd55ee276001b8734ed"),
+    (8, 8, 10, 7): (3134.6e6, "sweep_flow.cuh", "6b1fe4aa291235b10dec1bd55ee276001b8734ed"),
 }
 
 # sweep kernel by the library's sweep_kernel code

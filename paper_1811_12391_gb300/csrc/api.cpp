@@ -453,10 +453,12 @@ int graph_iterate(doctors_problem** ps, int n, int reverse, const float* const* 
             if (e == cudaSuccess) e = launch_zero(p->d_red, 5 * (size_t)p->G, skip, cs);
             SweepArgs sw = sweep_args(p, reverse, p->d_src, moms[q]);
             sw.skip = skip;
-            // the branches' dataflow sweeps share the resident CTA slots, so
-            // instances sweep side by side and one's wavefront fill and drain
-            // overlap another's full stages
-            sw.slot_share = nb;
+            // two instances' dataflow sweeps share the resident CTA slots, so
+            // one's wavefront fill and drain overlap the other's full stages
+            // (measured on the axial-scan batch: sharing among 2, 4 and 8 took
+            // 2025, 2058 and 2233 ms against 2038 ms without sharing; more
+            // instances at once spill each other's working sets out of L2)
+            sw.slot_share = std::min(nb, 2);
             int nl = 0;
             if (e == cudaSuccess) e = launch_sweep(p, sw, 0, cs, &nl);
             if (e == cudaSuccess) e = launch_residual(p->V, p->G, p->M, moms[q], p->d_prev, p->d_red + p->G, cs, skip);
