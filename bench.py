@@ -165,7 +165,8 @@ def oracle_solve_sample(p, groups, threads):
     """Time the FP64 oracle's forward solve (ray trace, first-collision source,
     Gauss-Seidel source iteration to TOL) of the first `groups` groups of p on
     `threads` host threads (0: all).  Returns (cell updates/s, cell updates,
-    seconds, threads used)."""
+    seconds, threads used); the sweeps per group are left in
+    oracle_solve_sample.iters."""
     from oracle import solver as osv
     from oracle import transport as tr
     used = tr.set_threads(threads if threads > 0 else (os.cpu_count() or 1))
@@ -174,6 +175,7 @@ def oracle_solve_sample(p, groups, threads):
     sol = osv.solve(q, tol=TOL)
     el = time.perf_counter() - t0
     cells = q.V * q.n_angles * sum(sol.iters)
+    oracle_solve_sample.iters = list(sol.iters)
     return cells / el, cells, el, used
 
 
@@ -204,21 +206,27 @@ def _max_rel(a, b):
     return worst
 
 
-def golden_parity(name, phi, dose):
-    """Error of a solve's total fluence [G][V] and dose [V] against the FP64
-    oracle values stored for seeded voxels of workload `name` (largest
-    relative error over groups on values above 1e-6 of the group's maximum)
-    and against the stored per-group fluence totals; None if none stored."""
+def golden_parity(name, phi, dose, phi_u=None, phi_c=None):
+    """Error of a solve's total fluence [G][V] and dose [V] (and, if given,
+    its uncollided and collided fluence) against the FP64 oracle values
+    stored for seeded voxels of workload `name` (largest relative error over
+    groups on values above 1e-6 of the group's maximum) and against the
+    stored per-group fluence totals; None if none stored."""
     import numpy as np
     gold = os.path.join(ROOT, "tests", "golden", f"{name}_samples.npz")
     if not os.path.exists(gold):
         return None
     ref = np.load(gold)
     idx = ref["voxels"]
-    return {"voxels": int(idx.size), "max_rel_phi": _max_rel(phi[:, idx], ref["phi"]),
-            "max_rel_dose": _max_rel(dose[idx], ref["dose"]),
-            "max_rel_group_totals": float(np.abs(phi.astype(np.float64).sum(axis=1) / ref["phi_total"] - 1.0).max()),
-            "tolerance": 1e-4}
+    out = {"voxels": int(idx.size), "max_rel_phi": _max_rel(phi[:, idx], ref["phi"]),
+           "max_rel_dose": _max_rel(dose[idx], ref["dose"]),
+           "max_rel_group_totals": float(np.abs(phi.astype(np.float64).sum(axis=1) / ref["phi_total"] - 1.0).max()),
+           "tolerance": 1e-4}
+    if phi_u is not None:
+        out["max_rel_phi_u"] = _max_rel(phi_u[:, idx], ref["phi_u"])
+    if phi_c is not None:
+        out["max_rel_phi_c"] = _max_rel(phi_c[:, idx], ref["phi_c"])
+    return out
 
 
 def ray_visits(p, src):
@@ -263,7 +271,7 @@ def bench_abdomen(torch, DoctorsProblem, ph, stream, sm_mhz, hbm_peak):
     voxel visits and the error against stored FP64 oracle samples."""
     p = ph.config_problem("abdomen")
     d, r, t = _timed_solve(DoctorsProblem, p, stream)
-    par = golden_parity("abdomen", d.fluence_host(2), d.dose_host(p.k_dep))
+    par = golden_parity("abdomen", d.fluence_host(2), d.dose_host(p.k_dep), d.fluence_host(0), d.fluence_host(1))
     d.close()
     return {"ms_per_solve": r["ms_total"], "cell_updates_per_s": r["cell_updates"] / (r["ms_total"] / 1e3),
             "iterations": r["iterations"], "converged": bool(r["converged"]), "schedule": _schedule(t),
@@ -452,7 +460,7 @@ def cpu_baselines(p, ph, seconds):
         k, rec = 1, None
         while k <= p.G:
             v, c, el, used = oracle_solve_sample(p, k, threads)
-            rec = {"value": v, "cores": used, "groups": k, "seconds": el}
+            rec = {"value": v, "cores": used, "groups": k, "seconds": el, "iterations": oracle_solve_sample.iters}
             if el >= seconds / 4 or threads == 1:
                 break
             k *= 2
@@ -548,7 +556,7 @@ def main():
         h2d = p.V * 1 + p.V * 4
         d2h = phi.nbytes + dose.nbytes
         # the last end-to-end solve against stored FP64 oracle values
-        parity = golden_parity(WORKLOAD, phi, dose) if world == 1 else None
+        parity = golden_parity(WORKLOAD, phi, dose, d.fluence_host(0), d.fluence_host(1)) if world == 1 else None
 
         # adjoint (backward) solve: gradients of the mean dose in a central region
         adjoint = None

@@ -91,8 +91,8 @@ typedef struct doctors_options {
     int tile_x, tile_y;      /* sweep tile in voxels (0 = default: 8 x 8 for the dataflow sweep, else
                                 16 x 16); tile_x*tile_y <= 256 */
     int angles_per_block;    /* directions per sweep block (0 = default); must divide N(N+2)/8 */
-    int sweep_kernel;        /* 0 = default (the fastest measured: dataflow where it applies, else
-                                chained),
+    int sweep_kernel;        /* 0 = default (the fastest measured: dataflow with a face warp (7) where
+                                it applies, else plain dataflow (4), else chained (3)),
                                 1 = CUDA-core transforms, one task (tile, octant, direction block,
                                 group) per CTA, 2 = tensor-core (3xTF32 mma) moment transforms
                                 (P3 only), 3 = CUDA-core transforms, each CTA running a chain of

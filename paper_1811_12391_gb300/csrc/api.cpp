@@ -53,7 +53,7 @@ constexpr bool kDefaultChainedSweep = true;
 constexpr bool kDefaultDataflowSweep = true;
 constexpr bool kDefaultSplitSweep = false;
 constexpr bool kDefaultTwoGroupSweep = false;
-constexpr bool kDefaultFaceWarpSweep = false;
+constexpr bool kDefaultFaceWarpSweep = true;
 
 int dalloc(void** p, size_t bytes, const char* what) {
     if (bytes == 0) bytes = 16;
@@ -85,7 +85,7 @@ void free_problem(doctors_problem* p) {
                     p->d_emit, p->d_iso, p->d_xface, p->d_yface, p->d_red,
                     p->d_Z, p->d_Qa, p->d_T, p->d_rf, p->d_r, p->d_acc, p->d_grad, p->d_H,
                     p->d_ones, p->d_psi, p->d_prod, p->d_flow, p->d_qang, p->d_pang,
-                    p->d_k, p->d_roi, p->d_part, p->d_tcb};
+                    p->d_k, p->d_roi, p->d_part, p->d_tcb, p->d_emit_all, p->d_dose_stage};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (p->h_red) cudaFreeHost(p->h_red);
@@ -151,9 +151,21 @@ int first_collision(doctors_problem* p) {
     std::vector<float> emit_all((size_t)p->srcs.size() * p->G);
     for (size_t s = 0; s < p->srcs.size(); ++s)
         for (int g = 0; g < p->G; ++g) emit_all[s * p->G + g] = (float)(p->srcs[s].weight * p->spectra[s][g]);
-    float* d_emit_all = nullptr;
-    int rc = dalloc_t(&d_emit_all, emit_all.size(), "source emission table");
-    if (rc) return rc;
+    // the emission table stays allocated between solves (grown when the
+    // source list grows); copies from pageable host memory are staged before
+    // they return, and the table is only read by launches on this stream
+    if (p->emit_cap < emit_all.size()) {
+        if (p->d_emit_all) {
+            CU(cudaStreamSynchronize(p->stream));
+            cudaFree(p->d_emit_all);
+            p->d_emit_all = nullptr;
+            p->emit_cap = 0;
+        }
+        int rc = dalloc_t(&p->d_emit_all, emit_all.size(), "source emission table");
+        if (rc) return rc;
+        p->emit_cap = emit_all.size();
+    }
+    float* d_emit_all = p->d_emit_all;
     cudaError_t e = cudaMemcpyAsync(d_emit_all, emit_all.data(), emit_all.size() * sizeof(float),
                                     cudaMemcpyHostToDevice, p->stream);
     for (size_t s = 0; s < p->srcs.size() && e == cudaSuccess; ++s) {
@@ -187,10 +199,6 @@ int first_collision(doctors_problem* p) {
         e = launch_scatter(sa, p->stream);
         ++p->launches;
     }
-    // the emission table must outlive the launches that read it
-    cudaError_t e2 = cudaStreamSynchronize(p->stream);
-    cudaFree(d_emit_all);
-    if (e == cudaSuccess) e = e2;
     if (e != cudaSuccess) {
         set_error(std::string("first-collision source: ") + cudaGetErrorString(e));
         return DOCTORS_ERR_CUDA;
@@ -393,6 +401,14 @@ int graph_iterate(doctors_problem** ps, int n, int reverse, const float* const* 
         ctl[q].tol = std::max(ps[q]->opt.tol, kTolFloor);
         ctl[q].resid = 0.0;
         ctl[q].res = ps[q]->d_red + ps[q]->G;
+        ctl[q].reverse = reverse;
+        // the dataflow sweeps (and the scattering source, zeroing and residual
+        // around them) follow a device-side active-group window; the other
+        // sweep kernels sweep every group at every iteration
+        ctl[q].use_window = ps[q]->use_flow ? 1 : 0;
+        ctl[q].win[0] = 0;
+        ctl[q].win[1] = ps[q]->G;
+        ctl[q].group_sweeps = 0;
     }
     LoopCtl* d_ctl = nullptr;
     int rc = dalloc_t(&d_ctl, (size_t)n, "loop control");
@@ -448,11 +464,21 @@ int graph_iterate(doctors_problem** ps, int n, int reverse, const float* const* 
             sa.V = p->V; sa.G = p->G; sa.M = p->M; sa.L = p->L; sa.nmat = p->nmat; sa.transpose = reverse;
             sa.mat = p->d_mat; sa.rho = p->d_rho; sa.sigs = p->d_sigs;
             sa.base = Qs[q]; sa.phi = moms[q]; sa.out = p->d_src; sa.skip = skip;
+            const int* win = p->use_flow ? d_ctl[q].win : nullptr;
+            sa.win = win;
             e = launch_scatter(sa, cs);
-            if (e == cudaSuccess && !p->use_split) e = launch_zero(moms[q], (size_t)p->G * p->V * p->M, skip, cs);
-            if (e == cudaSuccess) e = launch_zero(p->d_red, 5 * (size_t)p->G, skip, cs);
+            if (e == cudaSuccess && win)
+                e = launch_zero_window(moms[q], (size_t)p->V * p->M, p->G, win, skip, cs);
+            else if (e == cudaSuccess && !p->use_split)
+                e = launch_zero(moms[q], (size_t)p->G * p->V * p->M, skip, cs);
+            // leakage [G] (a retired group keeps its last sweep's, for the balance),
+            // then the residual and balance sums [4G]
+            if (e == cudaSuccess && win) e = launch_zero_window(p->d_red, 1, p->G, win, skip, cs);
+            else if (e == cudaSuccess) e = launch_zero(p->d_red, (size_t)p->G, skip, cs);
+            if (e == cudaSuccess) e = launch_zero(p->d_red + p->G, 4 * (size_t)p->G, skip, cs);
             SweepArgs sw = sweep_args(p, reverse, p->d_src, moms[q]);
             sw.skip = skip;
+            sw.win = win;
             // two instances' dataflow sweeps share the resident CTA slots, so
             // one's wavefront fill and drain overlap the other's full stages
             // (measured on the axial-scan batch: sharing among 2, 4 and 8 took
@@ -461,7 +487,8 @@ int graph_iterate(doctors_problem** ps, int n, int reverse, const float* const* 
             sw.slot_share = std::min(nb, 2);
             int nl = 0;
             if (e == cudaSuccess) e = launch_sweep(p, sw, 0, cs, &nl);
-            if (e == cudaSuccess) e = launch_residual(p->V, p->G, p->M, moms[q], p->d_prev, p->d_red + p->G, cs, skip);
+            if (e == cudaSuccess)
+                e = launch_residual(p->V, p->G, p->M, moms[q], p->d_prev, p->d_red + p->G, cs, skip, 0, -1, win);
             per_iter_launches += 4 + nl;
         }
         if (nb > 1) {
@@ -521,7 +548,7 @@ int graph_iterate(doctors_problem** ps, int n, int reverse, const float* const* 
             r.residual = ctl[q].resid;
             r.balance_rel = gain != 0.0 ? std::fabs(gain - loss) / std::fabs(gain) : 0.0;
             r.tol_used = ctl[q].tol;
-            r.cell_updates = (double)ctl[q].iters * (double)p->V * p->A * p->G;
+            r.cell_updates = (double)ctl[q].group_sweeps * (double)p->V * p->A;
             r.ms_sweep = -1.0;   // not separable inside the graph
         }
         p->launches += (long long)max_it * per_iter_launches / n + 1;
@@ -1045,27 +1072,18 @@ int doctors_dose(doctors_problem* p, const double* k, double* dose, int mem) {
         return DOCTORS_ERR_STATE;
     }
     for (int q = 0; q < p->nmat * p->G; ++q) CHECK_ARG(std::isfinite(k[q]), "k must be finite");
-    double* d_k = nullptr;
-    double* d_out = nullptr;
-    rc = dalloc_t(&d_k, (size_t)p->nmat * p->G, "dose factors");
+    // the factor table and the host-output staging stay allocated between calls
+    if (!p->d_k) rc = dalloc_t(&p->d_k, (size_t)kMaxMat * p->G, "dose factors");
+    if (!rc && mem == DOCTORS_MEM_HOST && !p->d_dose_stage) rc = dalloc_t(&p->d_dose_stage, p->V, "dose staging");
     if (rc) return rc;
-    if (mem == DOCTORS_MEM_HOST) {
-        rc = dalloc_t(&d_out, p->V, "dose staging");
-        if (rc) {
-            cudaFree(d_k);
-            return rc;
-        }
-    }
-    cudaError_t e = cudaMemcpyAsync(d_k, k, (size_t)p->nmat * p->G * sizeof(double), cudaMemcpyHostToDevice,
+    cudaError_t e = cudaMemcpyAsync(p->d_k, k, (size_t)p->nmat * p->G * sizeof(double), cudaMemcpyHostToDevice,
                                     p->stream);
-    double* dst = mem == DOCTORS_MEM_HOST ? d_out : dose;
-    if (e == cudaSuccess) e = launch_dose(p->V, p->G, p->M, p->d_mat, p->d_rho, d_k, p->d_phiu, p->d_mom, dst, p->stream);
+    double* dst = mem == DOCTORS_MEM_HOST ? p->d_dose_stage : dose;
+    if (e == cudaSuccess)
+        e = launch_dose(p->V, p->G, p->M, p->d_mat, p->d_rho, p->d_k, p->d_phiu, p->d_mom, dst, p->stream);
     if (e == cudaSuccess && mem == DOCTORS_MEM_HOST)
-        e = cudaMemcpyAsync(dose, d_out, p->V * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
-    // the factor table (and staging) must outlive the kernel
+        e = cudaMemcpyAsync(dose, p->d_dose_stage, p->V * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
-    cudaFree(d_k);
-    if (d_out) cudaFree(d_out);
     if (e != cudaSuccess) {
         set_error(std::string("dose: ") + cudaGetErrorString(e));
         return DOCTORS_ERR_CUDA;

@@ -122,12 +122,17 @@ struct ScatterArgs {
     float* out;                        // [G][V][M]
     const int* skip;                   // if non-null and *skip != 0 the kernel does nothing
     int g0, g1;                        // destination groups updated: g0 .. g1 - 1 (g1 = 0: all)
+    const int* win;                    // non-null: the window [win[0], win[1]) in device memory instead
 };
 cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s);
 
 // residual: res[g][0] += sum_v (phi00 - prev)^2, res[g][1] += sum_v phi00^2; prev = phi00
 cudaError_t launch_residual(size_t V, int G, int M, const float* mom, float* prev, double* res,
-                            cudaStream_t s, const int* skip = nullptr, int g0 = 0, int gcount = -1);
+                            cudaStream_t s, const int* skip = nullptr, int g0 = 0, int gcount = -1,
+                            const int* win = nullptr);
+// zero groups [win[0], win[1]) of a [G][per_group] float array unless *skip
+cudaError_t launch_zero_window(float* p, size_t per_group, int G, const int* win, const int* skip, cudaStream_t s);
+cudaError_t launch_zero_window(double* p, size_t per_group, int G, const int* win, const int* skip, cudaStream_t s);
 // zero n floats (or doubles) unless *skip
 cudaError_t launch_zero(float* p, size_t n, const int* skip, cudaStream_t s);
 cudaError_t launch_zero(double* p, size_t n, const int* skip, cudaStream_t s);
@@ -141,6 +146,10 @@ struct LoopCtl {
     double tol;
     double resid;                      // max over groups of the last relative change
     const double* res;                 // [G][2] residual sums of the instance
+    int reverse;                       // adjoint: the window's trailing groups retire
+    int use_window;                    // the instance's kernels follow win (else all groups, every sweep)
+    int win[2];                        // active group window [win[0], win[1])
+    long long group_sweeps;            // sum over iterations of the groups swept
 };
 // Retire converged instances; end the while loop when all are retired.
 cudaError_t launch_decide(LoopCtl* ctl, int n, unsigned long long cond_handle, cudaStream_t s);
@@ -181,6 +190,8 @@ struct SweepArgs {
     float* prod;                       // [G][V]: mode 2 accumulator
     const int* skip;                   // if non-null and *skip != 0 the kernel does nothing
     int chain_slots;                   // > 0: chained kernel, at most this many CTAs per stage launch
+    const int* win;                    // dataflow kernels: non-null: sweep the groups [win[0], win[1]) read from
+                                       // device memory (g0, gcount then give only the buffer layout)
     int slot_share;                    // dataflow kernels: use chain_slots / slot_share CTAs (> 1 when
                                        // that many instances sweep concurrently; 0 or 1: all)
     const struct ChainDirTable* dir_table;   // host copy of the first-octant direction table (chained kernel)
@@ -355,6 +366,8 @@ struct doctors_problem {
     float* d_src2 = nullptr;       // [G][V][M] the next iteration's source (formed ahead)
     float* d_prev = nullptr;       // [G][V]
     float* d_emit = nullptr;       // [G]
+    float* d_emit_all = nullptr;   // [n_src][G] weight * spectrum of every source
+    size_t emit_cap = 0;           // floats allocated in d_emit_all
     float* d_iso = nullptr;        // [G]
     float* d_xface = nullptr;
     float* d_yface = nullptr;
@@ -378,6 +391,7 @@ struct doctors_problem {
     double* d_k = nullptr;         // [kMaxMat][G] dose factors
     double* d_roi = nullptr;       // [V] ROI weights (staged from host memory)
     double* d_part = nullptr;      // [kRoiPartials + 1] partial sums of J, then J
+    double* d_dose_stage = nullptr;  // [V] dose staging for host-memory output
     bool solved = false;
     bool adjoint_done = false;
     cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};

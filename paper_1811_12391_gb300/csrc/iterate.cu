@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kScatterThreads, 3) k_scatter(const ScatterArg
         __syncthreads();
     }
     const size_t VM = a.V * a.M;
-    const int g_beg = a.g0, g_end = a.g1 > 0 ? a.g1 : G;
+    const int g_beg = a.win ? a.win[0] : a.g0, g_end = a.win ? a.win[1] : (a.g1 > 0 ? a.g1 : G);
     // no barrier below: threads leave the grid-stride loop independently
     for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < VM; t += (size_t)gridDim.x * blockDim.x) {
         const size_t v = t / a.M;
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(kScatterThreads, GMAX <= 24 ? 3 : GMAX <= 32 ?
     }
     __syncthreads();
     const unsigned VM = (unsigned)(a.V * a.M), M = (unsigned)a.M;
-    const int g_beg = a.g0, g_end = a.g1 > 0 ? a.g1 : G;
+    const int g_beg = a.win ? a.win[0] : a.g0, g_end = a.win ? a.win[1] : (a.g1 > 0 ? a.g1 : G);
     const int L1 = a.L + 1;
     // no barrier below: threads leave the grid-stride loop independently
     for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < VM; t += gridDim.x * blockDim.x) {
@@ -345,9 +345,10 @@ __device__ __forceinline__ void block_reduce_add(double (&x)[NV], double* dst) {
 // and the blocks are summed in FP64, so that few FP64 operations are issued:
 // their rate on this part is a small fraction of the FP32 rate.
 __global__ void __launch_bounds__(256) k_residual(size_t V, int M, const float* mom, float* prev,
-                                                  double* res, const int* skip, int g0) {
+                                                  double* res, const int* skip, int g0, const int* win) {
     if (skip && *skip) return;
     const int g = g0 + blockIdx.y;
+    if (win && (g < win[0] || g >= win[1])) return;      // retired group (whole block)
     double x[2] = {0.0, 0.0};
     // four voxels per thread and pass, their loads issued together
     const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -440,10 +441,35 @@ __global__ void k_decide(LoopCtl* ctl, int n, cudaGraphConditionalHandle h) {
         }
         c.iters += 1;
         c.resid = eps;
-        if (eps < c.tol || c.iters >= c.max_iters) c.done = 1;
-        else all = false;
+        c.group_sweeps += c.use_window ? c.win[1] - c.win[0] : c.G;
+        if (eps < c.tol || c.iters >= c.max_iters) {
+            c.done = 1;
+        } else {
+            all = false;
+            // shrink the active group window as the host loop does: a group whose
+            // relative change is below tol and whose sources are all final is
+            // final too (forward: leading groups, adjoint: trailing groups)
+            if (c.use_window) {
+                auto eps_of = [&](int g) {
+                    const double num = c.res[2 * g], den = c.res[2 * g + 1];
+                    return den > 0.0 ? sqrt(num / den) : 0.0;
+                };
+                if (!c.reverse)
+                    while (c.win[0] < c.win[1] - 1 && eps_of(c.win[0]) < c.tol) ++c.win[0];
+                else
+                    while (c.win[1] - 1 > c.win[0] && eps_of(c.win[1] - 1) < c.tol) --c.win[1];
+            }
+        }
     }
     if (all) cudaGraphSetConditional(h, 0);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_zero_window(T* p, size_t per_group, const int* win, const int* skip) {
+    if (skip && *skip) return;
+    const size_t beg = (size_t)win[0] * per_group, end = (size_t)win[1] * per_group;
+    for (size_t t = beg + (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < end; t += (size_t)gridDim.x * blockDim.x)
+        p[t] = T(0);
 }
 
 unsigned blocks_for(size_t n, int bs, unsigned cap = 0) {
@@ -505,10 +531,20 @@ cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_residual(size_t V, int G, int M, const float* mom, float* prev, double* res,
-                            cudaStream_t s, const int* skip, int g0, int gcount) {
+                            cudaStream_t s, const int* skip, int g0, int gcount, const int* win) {
     // sixteen voxels per thread (four passes)
     dim3 grid(blocks_for((V + 15) / 16, 256, 152), gcount < 0 ? G : gcount);
-    k_residual<<<grid, 256, 0, s>>>(V, M, mom, prev, res, skip, g0);
+    k_residual<<<grid, 256, 0, s>>>(V, M, mom, prev, res, skip, g0, win);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_window(float* p, size_t per_group, int G, const int* win, const int* skip, cudaStream_t s) {
+    k_zero_window<float><<<blocks_for((per_group * G + 3) / 4, 256, 152 * 16), 256, 0, s>>>(p, per_group, win, skip);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_window(double* p, size_t per_group, int G, const int* win, const int* skip, cudaStream_t s) {
+    k_zero_window<double><<<blocks_for((per_group * G + 3) / 4, 256, 152 * 16), 256, 0, s>>>(p, per_group, win, skip);
     return cudaGetLastError();
 }
 

@@ -109,9 +109,16 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
     float* sigt_s = buf + (DD ? 4 : 2) * P * RS;              // [gcount][nmat]
     int* task_s = reinterpret_cast<int*>(sigt_s + a.gcount * a.nmat);
 
-    for (int e = threadIdx.x; e < a.gcount * a.nmat; e += blockDim.x)
-        sigt_s[e] = a.sigt[(e % a.nmat) * a.G + a.g0 + e / a.nmat];
-    for (int e = threadIdx.x; e < a.gcount; e += blockDim.x) leak_s[e] = 0.0;
+    // groups swept: [g0, g0 + gcount), from device memory in a batched
+    // graph loop (a.g0, a.gcount then size the buffers only)
+    int g0 = a.g0, gcount = a.gcount;
+    if (a.win) {
+        g0 = a.win[0];
+        gcount = a.win[1] - a.win[0];
+    }
+    for (int e = threadIdx.x; e < gcount * a.nmat; e += blockDim.x)
+        sigt_s[e] = a.sigt[(e % a.nmat) * a.G + g0 + e / a.nmat];
+    for (int e = threadIdx.x; e < gcount; e += blockDim.x) leak_s[e] = 0.0;
     for (int e = threadIdx.x; e < (DD ? 4 : 2) * P * RS; e += blockDim.x) buf[e] = 0.0f;
 
     // threads own the tile's columns in diagonal order (li + lj ascending)
@@ -145,7 +152,7 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
     const size_t xslab = (size_t)a.ny * a.nz * ABP, yslab = (size_t)a.nx * a.nz * ABP;
     // face records of consecutive groups are ntxf (ntyf) slabs apart
     const size_t xgs = (size_t)ntxf * xslab, ygs = (size_t)ntyf * yslab;
-    const int ngp = (a.gcount + GP - 1) / GP;     // group blocks
+    const int ngp = (gcount + GP - 1) / GP;       // group blocks
     int ntasks = 0;
     for (int s = 0; s < nst; ++s) ntasks += flow_stage_tiles(s, a.ntx, a.nty) * 8 * ngp;
     // this thread's landing slot for the record of group slot gg used at step st
@@ -184,8 +191,8 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
         const int ti = r % ntiles;
         r /= ntiles;
         const int o = r & 7, gi = GP * (r >> 3);
-        const int gn = (GP == 2 && gi + 1 < a.gcount) ? 2 : 1;    // groups of this task
-        const int g = a.g0 + gi;
+        const int gn = (GP == 2 && gi + 1 < gcount) ? 2 : 1;      // groups of this task
+        const int g = g0 + gi;
         const int at = max(0, s - (a.nty - 1)) + ti, bt = s - at;
         const int sx = (o & 1) ? -1 : 1, sy = (o & 2) ? -1 : 1, sz = (o & 4) ? -1 : 1;
         const int oe = a.reverse ? (o ^ 7) : o;     // octant of the directions
@@ -850,8 +857,8 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
             __syncthreads();
         }
     }
-    for (int e = threadIdx.x; e < a.gcount; e += blockDim.x)
-        if (leak_s[e] != 0.0) atomicAdd(a.leak + a.g0 + e, leak_s[e]);
+    for (int e = threadIdx.x; e < gcount; e += blockDim.x)
+        if (leak_s[e] != 0.0) atomicAdd(a.leak + g0 + e, leak_s[e]);
     // the last CTA out resets the queue for the next sweep
     if (threadIdx.x == 0) {
         __threadfence();
