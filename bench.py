@@ -57,15 +57,16 @@ TOL = 1e-6
 SWEEP_TRAFFIC = {
     (16, 16, 10, 1): (2246.4e6, "sweep_impl.cuh", "592eff4d10129e1bde8b55aecdf9fbf52f768e8c"),
     (16, 16, 5, 1): (1687.6e6, "sweep_impl.cuh", "592eff4d10129e1bde8b55aecdf9fbf52f768e8c"),
-    (16, 16, 10, 2): (2121.9e6, "sweep_tc.cu", "79ec5703826b205c1bdc9d4f7ff57c205fec428a"),
     (16, 8, 10, 3): (2534.9e6, "sweep_chain.cuh", "3502773d12d37fb58b50dbc1187553785b1df685"),
     (8, 8, 10, 4): (3145.0e6, "sweep_flow.cuh", "6b1fe4aa291235b10dec1bd55ee276001b8734ed"),
-    (8, 8, 10, 7): (3134.6e6, "sweep_flow.cuh", "6b1fe4aa291235b10dec1bd55ee276001b8734ed"),
+    (8, 8, 10, 7): (2989.8e6, "sweep_flow.cuh", "3e88a62cb6244deb8d1b5affff5df3003400e9be"),
+    (16, 16, 10, 7): (2619.1e6, "sweep_flow.cuh", "3e88a62cb6244deb8d1b5affff5df3003400e9be"),
 }
 
 # sweep kernel by the library's sweep_kernel code
-SWEEP_KERNELS = {1: "k_sweep", 2: "k_sweep_tc", 3: "k_sweep_chain", 4: "k_sweep_flow",
-                 5: "k_split_m2d + k_sweep_flow<split> + k_split_d2m", 6: "k_sweep_flow<two groups per task>"}
+SWEEP_KERNELS = {1: "k_sweep", 3: "k_sweep_chain", 4: "k_sweep_flow",
+                 5: "k_split_m2d + k_sweep_flow<split> + k_split_d2m", 7: "k_sweep_flow<face warp>",
+                 8: "k_m2d_tc + k_sweep_flow<split> + k_d2m_tc"}
 
 # FP32 lanes per SM and SMs of a GB300 (the ALU roofline of the CUDA-core sweep)
 FP32_LANES_PER_SM = 128

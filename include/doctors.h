@@ -94,8 +94,7 @@ typedef struct doctors_options {
     int sweep_kernel;        /* 0 = default (the fastest measured: dataflow with a face warp (7) where
                                 it applies, else plain dataflow (4), else chained (3)),
                                 1 = CUDA-core transforms, one task (tile, octant, direction block,
-                                group) per CTA, 2 = tensor-core (3xTF32 mma) moment transforms
-                                (P3 only), 3 = CUDA-core transforms, each CTA running a chain of
+                                group) per CTA, 3 = CUDA-core transforms, each CTA running a chain of
                                 tasks of a stage back to back in one hyperplane pipeline,
                                 4 = dataflow: one launch per sweep, CTAs take tasks from a queue and
                                 wait (bounded) on their upstream tiles' face fluxes plane by plane;
@@ -106,14 +105,15 @@ typedef struct doctors_options {
                                 writes one angular record per cell, a pass turns the angular fluence
                                 back into moments (same conditions as 4; two more arrays of
                                 G x N(N+2) x V floats, padded),
-                                6 = dataflow with two groups per task: each thread updates its
-                                cell in two groups at every hyperplane step (same conditions as 4,
-                                and P1 or P3),
                                 7 = dataflow with a face warp: one more warp per CTA fetches and
                                 waits for the incoming face fluxes, the column threads only sweep
                                 (same conditions as 4, P1 or P3, tile_x + tile_y <= 64),
                                 8 = as 5 with the two transform passes on the tensor cores
-                                (tcgen05, 3xTF32 with FP32 accumulation; P3 only) */
+                                (tcgen05, 3xTF32 with FP32 accumulation; P3 only).
+                                2 and 6 are not offered (DOCTORS_ERR_INVALID_ARG): a sweep with
+                                the transforms on mma.sync tensor cores and a dataflow sweep of two
+                                groups per task, both measured slower than 1, 3, 4 and 7 on
+                                every workload, were taken out */
     int device_loop;         /* 1 = run the source iteration as one CUDA graph whose while loop is
                                 decided on the device (no host round trip per iteration) */
     int differencing;        /* spatial scheme of the sweep (the paper does not state one):
@@ -343,9 +343,9 @@ int doctors_solve_batch(doctors_problem **problems, int n, doctors_result *resul
 typedef struct doctors_tuning {
     int tile_x, tile_y;      /* tile of columns */
     int angles_per_block;    /* directions per CTA */
-    int sweep_kernel;        /* 1 CUDA-core, 2 tensor-core, 3 chained, 4 dataflow, 5 dataflow with split
-                                transforms, 6 dataflow with two groups per task, 7 dataflow with a
-                                face warp, 8 split transforms on the tensor cores (as doctors_options) */
+    int sweep_kernel;        /* 1 CUDA-core, 3 chained, 4 dataflow, 5 dataflow with split transforms,
+                                7 dataflow with a face warp, 8 split transforms on the tensor cores
+                                (as doctors_options) */
     double ms_per_sweep;     /* measured time of one full sweep of this problem */
     int candidates;          /* schedules timed (0 if taken from the cache) */
 } doctors_tuning;

@@ -1,6 +1,6 @@
 """Command line: solve a named synthetic workload and print the report.
 
-  python -m paper_1811_12391_gb300 <workload> [--iters N] [--tol T] [--tile X Y] [--ab K] [--kernel 1..6]
+  python -m paper_1811_12391_gb300 <workload> [--iters N] [--tol T] [--tile X Y] [--ab K] [--kernel 0..8]
                                    [--device-loop] [--diamond] [--adjoint] [--autotune] [--repeat R]
 
 Workloads: tiny_cube, water_cylinder, abdomen, axial_scan, differentiable_abdomen
@@ -23,7 +23,8 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--tile", type=int, nargs=2, default=(0, 0))
     ap.add_argument("--ab", type=int, default=0)
-    ap.add_argument("--kernel", type=int, default=0, help="sweep kernel: 0 default, 1 CUDA-core, 2 tensor-core, 3 chained CUDA-core, 4 dataflow, 5 dataflow with split transforms, 6 dataflow with two groups per task")
+    ap.add_argument("--kernel", type=int, default=0, help="sweep kernel: 0 default, 1 CUDA-core, 3 chained CUDA-core, 4 dataflow, 5 dataflow with split "
+                    "transforms, 7 dataflow with a face warp, 8 split transforms on the tensor cores")
     ap.add_argument("--device-loop", action="store_true",
                     help="run the source iteration as one CUDA graph with a device-side while loop")
     ap.add_argument("--diamond", action="store_true", help="diamond differencing (dataflow sweep)")

@@ -48,11 +48,9 @@ using namespace doctors;
 namespace {
 
 // default choice of the moment-transform path of the sweep for P3 problems
-constexpr bool kDefaultTensorCoreSweep = false;
 constexpr bool kDefaultChainedSweep = true;
 constexpr bool kDefaultDataflowSweep = true;
 constexpr bool kDefaultSplitSweep = false;
-constexpr bool kDefaultTwoGroupSweep = false;
 constexpr bool kDefaultFaceWarpSweep = true;
 
 int dalloc(void** p, size_t bytes, const char* what) {
@@ -216,12 +214,11 @@ SweepArgs sweep_args(const doctors_problem* p, int reverse, const float* src, fl
     a.A = p->A;
     a.g0 = 0;
     a.gcount = p->G;
-    a.chain_slots = p->use_tc ? 0 : p->chain_slots;
+    a.chain_slots = p->chain_slots;
     a.dir_table = &p->dir_table;
     a.flow = (p->use_flow || p->use_split) ? p->d_flow : nullptr;
     a.qang = p->d_qang;
     a.pang = p->d_pang;
-    a.gp = p->flow_gp;
     a.hw = p->flow_hw ? 1 : 0;
     a.tc_b1 = (p->use_split && p->split_tc) ? p->d_tcb : nullptr;
     a.tc_b2 = (p->use_split && p->split_tc) ? p->d_tcb + p->tcb1_floats : nullptr;
@@ -234,16 +231,16 @@ SweepArgs sweep_args(const doctors_problem* p, int reverse, const float* src, fl
 cudaError_t launch_sweep(const doctors_problem* p, SweepArgs sw, int mode, cudaStream_t s, int* count) {
     if (p->use_split && mode == 0) return launch_split_sweep(sw, p->M, s, count);
     if (p->use_flow || p->use_split) {
-        // modes 1 and 2 (stored / paired angular fluence) of the split and two-group
+        // modes 1 and 2 (stored / paired angular fluence) of the split and face-warp
         // paths use the plain dataflow kernel
-        if (p->use_split || (mode != 0 && (p->flow_gp != 1 || p->flow_hw))) sw.chain_slots = p->flow_slots;
+        if (p->use_split || (mode != 0 && p->flow_hw)) sw.chain_slots = p->flow_slots;
         *count = 1;
         return launch_sweep_flow(sw, p->M, mode, s);
     }
     *count = 0;
     for (int st = 0; st < p->ntx + p->nty - 1; ++st) {
         sw.stage = st;
-        cudaError_t e = p->use_tc ? launch_sweep_tc(sw, mode, s) : launch_sweep_stage(sw, p->M, mode, s);
+        cudaError_t e = launch_sweep_stage(sw, p->M, mode, s);
         if (e != cudaSuccess) return e;
         ++*count;
     }
@@ -567,16 +564,17 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
         set_error("angles_per_block must divide N(N+2)/8 and be one of 1,2,3,4,5,6,7,9,10,12");
         return DOCTORS_ERR_INVALID_ARG;
     }
-    if (kernel < 0 || kernel > 8) {
-        set_error("sweep_kernel must be 0 .. 8");
+    if (kernel < 0 || kernel > 8 || kernel == 2 || kernel == 6) {
+        set_error("sweep_kernel must be 0, 1, 3, 4, 5, 7 or 8 (2 and 6 are not offered: both measured slower "
+                  "on every workload)");
         return DOCTORS_ERR_INVALID_ARG;
     }
     if (kernel >= 4 && !(p->A8 == ab && chain_const_table_ab(ab))) {
         set_error("dataflow sweep needs whole octants per CTA (angles_per_block = N(N+2)/8) of S2, S4, S6 or S8");
         return DOCTORS_ERR_INVALID_ARG;
     }
-    if ((kernel == 6 || kernel == 7) && p->M % 4 != 0) {
-        set_error("the two-group and face-warp dataflow sweeps (sweep_kernel 6, 7) need P1 or P3 (legendre 1 or 3)");
+    if (kernel == 7 && p->M % 4 != 0) {
+        set_error("the face-warp dataflow sweep (sweep_kernel 7) needs P1 or P3 (legendre 1 or 3)");
         return DOCTORS_ERR_INVALID_ARG;
     }
     if (kernel == 8 && p->M != 16) {
@@ -601,37 +599,26 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
         }
         kernel = 4;
     }
-    const bool tc_ok = sweep_tc_supported(ab, p->M, tx, ty);
-    if (kernel == 2 && !tc_ok) {
-        set_error("tensor-core sweep needs P3, <= 16 directions per block and a 16x16, 32x8, 16x8, 8x16, 8x8 or 8x4 tile");
-        return DOCTORS_ERR_INVALID_ARG;
-    }
-    const bool use_tc = kernel == 2 || (kernel == 0 && tc_ok && kDefaultTensorCoreSweep);
     const bool flow_ok = p->A8 == ab && chain_const_table_ab(ab);
-    const bool use_split = kernel == 5 || kernel == 8 || (kernel == 0 && !use_tc && flow_ok && kDefaultSplitSweep);
+    const bool use_split = kernel == 5 || kernel == 8 || (kernel == 0 && flow_ok && kDefaultSplitSweep);
     const bool split_tc = kernel == 8 && p->M == 16;
-    const bool use_flow = !use_split && (kernel == 4 || kernel == 6 || kernel == 7 ||
-                                         (kernel == 0 && !use_tc && flow_ok && kDefaultDataflowSweep));
-    const int gp = kernel == 6 || (kernel == 0 && use_flow && kDefaultTwoGroupSweep && p->M % 4 == 0) ? 2 : 1;
-    const bool hw = gp == 1 && !dd && p->M % 4 == 0 && tx + ty <= 64 &&
+    const bool use_flow = !use_split && (kernel == 4 || kernel == 7 ||
+                                         (kernel == 0 && flow_ok && kDefaultDataflowSweep));
+    const bool hw = !dd && p->M % 4 == 0 && tx + ty <= 64 &&
                     (kernel == 7 || (kernel == 0 && use_flow && kDefaultFaceWarpSweep));
-    const bool use_chain = !use_tc && !use_flow && !use_split && (kernel == 3 || (kernel == 0 && kDefaultChainedSweep));
+    const bool use_chain = !use_flow && !use_split && (kernel == 3 || (kernel == 0 && kDefaultChainedSweep));
     const int ntx = (p->nx + tx - 1) / tx, nty = (p->ny + ty - 1) / ty;
     int chain_slots = 0, flow_slots = 0;
     size_t smem = 0;
-    if (use_tc) {
-        smem = sweep_tc_smem_bytes(ab, tx, ty, p->nz, kMaxMat);
-    } else if (use_flow || use_split) {
+    if (use_flow || use_split) {
         int sms = 0;
         CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-        smem = sweep_flow_smem_bytes(ab, tx, ty, p->G, kMaxMat, gp, dd);
+        smem = sweep_flow_smem_bytes(ab, tx, ty, p->G, kMaxMat, dd);
         if (smem <= 227 * 1024) {
-            const size_t smem1 = sweep_flow_smem_bytes(ab, tx, ty, p->G, kMaxMat, 1, dd);
-            const int per_sm = sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem1, false, 1, dd);
+            const int per_sm = sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem, false, dd);
             const int hw_threads = ((tx * ty + 31) / 32 + 1) * 32;
-            const int per_sm_main = use_split ? sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem, true, 1)
-                                  : gp == 2 ? sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem, false, 2)
-                                  : hw ? sweep_flow_blocks_per_sm(ab, p->M, hw_threads, smem, false, 1, false, true)
+            const int per_sm_main = use_split ? sweep_flow_blocks_per_sm(ab, p->M, tx * ty, smem, true)
+                                  : hw ? sweep_flow_blocks_per_sm(ab, p->M, hw_threads, smem, false, false, true)
                                        : per_sm;
             if (per_sm < 1 || per_sm_main < 1) {
                 set_error("dataflow sweep cannot be resident with this tile");
@@ -722,11 +709,10 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
         if (p->xface_bytes) CU(cudaMemsetAsync(p->d_xface, 0xff, p->xface_bytes, p->stream));
         if (p->yface_bytes) CU(cudaMemsetAsync(p->d_yface, 0xff, p->yface_bytes, p->stream));
     }
-    p->tx = tx; p->ty = ty; p->ab = ab; p->nab = p->A8 / ab; p->ntx = ntx; p->nty = nty; p->use_tc = use_tc;
+    p->tx = tx; p->ty = ty; p->ab = ab; p->nab = p->A8 / ab; p->ntx = ntx; p->nty = nty;
     p->use_flow = use_flow;
     p->use_split = use_split;
     p->split_tc = use_split && split_tc;
-    p->flow_gp = use_flow ? gp : 1;
     p->flow_hw = use_flow && hw;
     p->chain_slots = chain_slots;
     p->flow_slots = flow_slots;
@@ -800,14 +786,15 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     p->nab = p->A8 / p->ab;
     p->ntx = (p->nx + p->tx - 1) / p->tx;
     p->nty = (p->ny + p->ty - 1) / p->ty;
-    if (opt->sweep_kernel < 0 || opt->sweep_kernel > 8) return fail(DOCTORS_ERR_INVALID_ARG, "sweep_kernel must be 0 .. 8");
+    if (opt->sweep_kernel < 0 || opt->sweep_kernel > 8)
+        return fail(DOCTORS_ERR_INVALID_ARG, "sweep_kernel must be 0, 1, 3, 4, 5, 7 or 8");
+    if (opt->sweep_kernel == 2 || opt->sweep_kernel == 6)
+        return fail(DOCTORS_ERR_INVALID_ARG, "sweep_kernel 2 and 6 are not offered (both measured slower on every workload)");
     if (p->differencing == DOCTORS_DIFF_DIAMOND &&
         !((opt->sweep_kernel == 0 || opt->sweep_kernel == 4) && p->A8 == p->ab && chain_const_table_ab(p->ab)))
         return fail(DOCTORS_ERR_INVALID_ARG,
                     "diamond differencing runs on the dataflow sweep: sweep_kernel 0 or 4, angles_per_block = "
                     "N(N+2)/8 and N <= 8");
-    if (opt->sweep_kernel == 2 && !sweep_tc_supported(p->ab, p->M, p->tx, p->ty))
-        return fail(DOCTORS_ERR_INVALID_ARG, "tensor-core sweep needs P3, <= 16 directions per block and a 16x16, 32x8, 16x8, 8x16, 8x8 or 8x4 tile");
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) return fail(DOCTORS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
 
@@ -1234,13 +1221,13 @@ int doctors_autotune(doctors_problem* p, doctors_tuning* out) {
     best.ms_per_sweep = 1e30;
     int count = 0;
     const int saved[4] = {p->tx, p->ty, p->ab,
-                          p->use_tc ? 2 : p->use_split ? (p->split_tc ? 8 : 5) : p->use_flow ? (p->flow_gp == 2 ? 6 : p->flow_hw ? 7 : 4)
+                          p->use_split ? (p->split_tc ? 8 : 5) : p->use_flow ? (p->flow_hw ? 7 : 4)
                                                                           : (p->chain_slots > 0 ? 3 : 1)};
     for (const auto& t : tiles) {
         for (int ab : abs_ok) {
             for (int kernel = 1; kernel <= 8; ++kernel) {
                 if (p->differencing == DOCTORS_DIFF_DIAMOND && kernel != 4) continue;
-                if (kernel == 2 && !sweep_tc_supported(ab, p->M, t[0], t[1])) continue;
+                if (kernel == 2 || kernel == 6) continue;
                 if (kernel >= 4 && !(p->A8 == ab && chain_const_table_ab(ab))) continue;
                 if (configure_sweep(p, t[0], t[1], ab, kernel) != DOCTORS_OK) continue;
                 SweepArgs sw = sweep_args(p, 0, p->d_Q, p->d_mom);

@@ -21,11 +21,10 @@ constexpr double kTolFloor = 1e-6;   // FP32 sweep: relative-change floor
 void set_error(const std::string& msg);
 
 // Storage order of the flux moments of one cell.  For P3 (16 moments) the
-// record is stored as the 4 x 4 transpose of the (l, m) order, so that the
-// tensor-core sweep loads a lane's A-operand fragment and stores its
-// accumulator fragment as one float4 each: position p holds moment
-// lm = p / 4 + 4 (p % 4) (position 0 is still lm = 00).  Other orders are
-// stored in (l, m) order.
+// record is stored as the 4 x 4 transpose of the (l, m) order: position p
+// holds moment lm = p / 4 + 4 (p % 4) (position 0 is still lm = 00).  Other
+// orders are stored in (l, m) order.  Every kernel's moment tables and the
+// host's staging go through lm_of_pos, so the order is a layout choice only.
 __host__ __device__ constexpr int lm_of_pos(int p, int M) { return M == 16 ? (p >> 2) + 4 * (p & 3) : p; }
 __host__ __device__ constexpr int degree_of_lm(int lm) { return lm >= 9 ? 3 : lm >= 4 ? 2 : lm >= 1 ? 1 : 0; }
 
@@ -197,7 +196,6 @@ struct SweepArgs {
     const struct ChainDirTable* dir_table;   // host copy of the first-octant direction table (chained kernel)
     const float* qang;                 // split transforms: angular source [G][8][V][ABP] (direction octant)
     float* pang;                       // split transforms: angular fluence [G][8][V][ABP]
-    int gp;                            // dataflow kernel: groups per task (1 or 2)
     int hw;                            // dataflow kernel: 1 = a face warp per CTA takes the incoming
                                        // face records (mode 0)
     const float* tc_b1;                // split transforms on the tensor cores (P3): moments -> directions
@@ -257,17 +255,16 @@ inline size_t sweep_chain_smem_bytes(int ab, int tx, int ty, int cmax, int gcoun
 // tile's first row and column, per-group leakage, the two halo-padded
 // hyperplanes, sigma_t of the swept groups and the task slot
 inline int flow_abp_host(int ab) { return (ab + 3) & ~3; }
-inline size_t sweep_flow_smem_bytes(int ab, int tx, int ty, int gcount, int nmat, int gp = 1, bool dd = false) {
-    // prefetched source moments (2 slots of 16 floats per thread and group of
-    // the task), two landing slots (pipeline depth 2) of gp records per edge
-    // column (one per group of the task), the leakage per
+inline size_t sweep_flow_smem_bytes(int ab, int tx, int ty, int gcount, int nmat, bool dd = false) {
+    // prefetched source moments (2 slots of 16 floats per thread), two landing
+    // slots (pipeline depth 2) of one record per edge column, the leakage per
     // group, two planes of column records (diamond differencing: x-going and
     // y-going face fluxes in separate planes), the cross sections and the task slot
-    return 2 * (size_t)gp * 16 * 4 * (size_t)tx * ty + 2 * (size_t)gp * 4 * (tx + ty) * flow_abp_host(ab) +
+    return 2 * (size_t)16 * 4 * (size_t)tx * ty + 2 * (size_t)4 * (tx + ty) * flow_abp_host(ab) +
            8 * (size_t)gcount +
-           4 * ((size_t)(dd ? 4 : 2) * chain_rs(gp * ab) * chain_px(tx) * (ty + 1) + (size_t)gcount * nmat) + 16;
+           4 * ((size_t)(dd ? 4 : 2) * chain_rs(ab) * chain_px(tx) * (ty + 1) + (size_t)gcount * nmat) + 16;
 }
-int sweep_flow_blocks_per_sm(int ab, int M, int threads, size_t smem, bool split = false, int gp = 1, bool dd = false,
+int sweep_flow_blocks_per_sm(int ab, int M, int threads, size_t smem, bool split = false, bool dd = false,
                              bool hw = false);
 cudaError_t launch_sweep_flow(const SweepArgs& a, int M, int mode, cudaStream_t s);
 // split transforms (whole octants of S2..S8): moments -> angular source for
@@ -285,11 +282,6 @@ void build_tc_transform_tables(const ChainDirTable& dt, int AB, std::vector<floa
 cudaError_t launch_m2d_tc(const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_d2m_tc(const SweepArgs& a, cudaStream_t s);
 
-// tensor-core sweep (P3): sweep_tc.cu
-bool sweep_tc_supported(int ab, int M, int tx, int ty);
-size_t sweep_tc_smem_bytes(int ab, int tx, int ty, int nz, int nmat);
-cudaError_t launch_sweep_tc(const SweepArgs& a, int mode, cudaStream_t s);
-cudaError_t upload_tables_tc(const float* R, const float* w);
 
 // ---------------------------------------------------------------------------
 // region-of-interest dose and its gradient terms (roi.cu)
@@ -325,12 +317,10 @@ struct doctors_problem {
     std::vector<double> dirs, w;
     // sweep tiling
     int tx = 16, ty = 16, ntx = 1, nty = 1, ab = 1, nab = 1;
-    bool use_tc = false;            // tensor-core transforms in the sweep
     int chain_slots = 0;            // > 0: chained or dataflow sweep with this many CTA slots
     bool use_flow = false;          // dataflow sweep (one launch per sweep, task queue)
     bool use_split = false;         // dataflow sweep with the transforms in separate passes
     bool split_tc = false;          // ... those passes on the tensor cores (P3)
-    int flow_gp = 1;                // dataflow sweep: groups per task
     bool flow_hw = false;           // dataflow sweep: a face warp per CTA
     int differencing = 0;           // DOCTORS_DIFF_STEP or DOCTORS_DIFF_DIAMOND
     int flow_slots = 0;             // CTA slots of the plain dataflow kernel (modes 1, 2 under split)

@@ -30,13 +30,13 @@ cudaError_t launch_sweep_flow_m1_entry(const SweepArgs& a, int mode, cudaStream_
 cudaError_t launch_sweep_flow_m4_entry(const SweepArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_sweep_flow_m9_entry(const SweepArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_sweep_flow_m16_entry(const SweepArgs& a, int mode, cudaStream_t s);
-int sweep_flow_blocks_m1(int ab, int threads, size_t smem, bool split, int gp, bool dd, bool hw);
+int sweep_flow_blocks_m1(int ab, int threads, size_t smem, bool split, bool dd, bool hw);
 cudaError_t launch_split_sweep_m1_entry(const SweepArgs& a, cudaStream_t s, int* count);
-int sweep_flow_blocks_m4(int ab, int threads, size_t smem, bool split, int gp, bool dd, bool hw);
+int sweep_flow_blocks_m4(int ab, int threads, size_t smem, bool split, bool dd, bool hw);
 cudaError_t launch_split_sweep_m4_entry(const SweepArgs& a, cudaStream_t s, int* count);
-int sweep_flow_blocks_m9(int ab, int threads, size_t smem, bool split, int gp, bool dd, bool hw);
+int sweep_flow_blocks_m9(int ab, int threads, size_t smem, bool split, bool dd, bool hw);
 cudaError_t launch_split_sweep_m9_entry(const SweepArgs& a, cudaStream_t s, int* count);
-int sweep_flow_blocks_m16(int ab, int threads, size_t smem, bool split, int gp, bool dd, bool hw);
+int sweep_flow_blocks_m16(int ab, int threads, size_t smem, bool split, bool dd, bool hw);
 cudaError_t launch_split_sweep_m16_entry(const SweepArgs& a, cudaStream_t s, int* count);
 
 cudaError_t upload_tables_m1(const float* R, const float* w);
@@ -78,7 +78,6 @@ cudaError_t ensure_direction_tables(int device, int N, int* base) {
     if (e == cudaSuccess) e = upload_tables_m4(R.data(), w.data());
     if (e == cudaSuccess) e = upload_tables_m9(R.data(), w.data());
     if (e == cudaSuccess) e = upload_tables_m16(R.data(), w.data());
-    if (e == cudaSuccess) e = upload_tables_tc(R.data(), w.data());
     if (e == cudaSuccess) g_table_done[device] = true;
     return e;
 }
@@ -100,12 +99,12 @@ int sweep_chain_blocks_per_sm(int ab, bool ct, int M, int threads, size_t smem) 
     }
 }
 
-int sweep_flow_blocks_per_sm(int ab, int M, int threads, size_t smem, bool split, int gp, bool dd, bool hw) {
+int sweep_flow_blocks_per_sm(int ab, int M, int threads, size_t smem, bool split, bool dd, bool hw) {
     switch (M) {
-        case 1: return sweep_flow_blocks_m1(ab, threads, smem, split, gp, dd, hw);
-        case 4: return sweep_flow_blocks_m4(ab, threads, smem, split, gp, dd, hw);
-        case 9: return sweep_flow_blocks_m9(ab, threads, smem, split, gp, dd, hw);
-        case 16: return sweep_flow_blocks_m16(ab, threads, smem, split, gp, dd, hw);
+        case 1: return sweep_flow_blocks_m1(ab, threads, smem, split, dd, hw);
+        case 4: return sweep_flow_blocks_m4(ab, threads, smem, split, dd, hw);
+        case 9: return sweep_flow_blocks_m9(ab, threads, smem, split, dd, hw);
+        case 16: return sweep_flow_blocks_m16(ab, threads, smem, split, dd, hw);
         default: return 0;
     }
 }

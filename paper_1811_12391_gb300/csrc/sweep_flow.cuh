@@ -26,7 +26,6 @@
 #pragma once
 
 #include <algorithm>
-#include <type_traits>
 
 #include "sweep_chain.cuh"
 
@@ -54,15 +53,6 @@ __device__ __forceinline__ int flow_stage_tiles(int s, int ntx, int nty) {
 // a.qang and writes its angular-fluence record a.pang, with no moments and
 // no reductions (mode 0 only).
 //
-// GP = 2: a task sweeps two groups of one (tile, octant) together.  At each
-// hyperplane step every thread updates its cell in both groups: two
-// independent cell solves per step under one barrier, with one set of
-// direction tables and one set of index computations, and half as many
-// tasks per sweep.  A column's plane record holds both groups' fluxes, and
-// the edge threads fetch both groups' face records.  With an odd number of
-// groups the last task of each (tile, octant) has one group.  Mode 0, step
-// differencing, moments in 16-byte quarters (P1, P3).
-//
 // HW = true: one more warp per CTA, the face warp, takes over the incoming
 // face records: it fetches them ahead, waits until each is complete, moves
 // it into the halo of the plane buffers and hands the record back as NaN.
@@ -76,16 +66,14 @@ __device__ __forceinline__ int flow_stage_tiles(int s, int ntx, int nty) {
 // leaves with 2 psi - psi_in.  The x-going and y-going face fluxes of a cell
 // differ, so they are kept in two planes (x: buf, y: bufy), and the face
 // records and the leakage carry the face fluxes, not the cell flux.
-template <int AB, int M, int MODE, bool SPLIT = false, int GP = 1, bool DD = false, bool HW = false>
-__global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP == 1 ? 3 : 2) : 2)
+template <int AB, int M, int MODE, bool SPLIT = false, bool DD = false, bool HW = false>
+__global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? 3 : 2)
     k_sweep_flow(const SweepArgs a, const ChainDirTable dt) {
     static_assert(!SPLIT || MODE == 0, "split transforms sweep in mode 0 only");
-    static_assert(GP == 1 || (GP == 2 && !SPLIT && !DD && MODE == 0 && M % 4 == 0),
-                  "two groups per task: the fused step-differenced kernel in mode 0, P1 or P3");
-    static_assert(!DD || (!SPLIT && GP == 1), "diamond differencing in the fused one-group kernel only");
+    static_assert(!DD || !SPLIT, "diamond differencing in the fused kernel only");
     static_assert(!HW || MODE == 0, "the face warp serves the mode-0 sweep");
     constexpr int ABP = flow_abp(AB);
-    constexpr int RS = (GP * AB) | 1;         // a column's record: GP groups' fluxes (odd length)
+    constexpr int RS = AB | 1;                // a column's record of fluxes (odd length)
     // pipeline depths: face records are fetched PD steps before the step
     // that uses them, source values PDS steps (the split sweep's steps are
     // short, so one step does not cover the memory latency)
@@ -99,11 +87,11 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
     if (a.skip && *a.skip) return;          // retired instance of a batched loop
     const int PX = chain_px(a.tx);
     const int P = PX * (a.ty + 1);
-    float4* momst = sm4;                                      // [2][GP][blockDim][4] prefetched source moments
+    float4* momst = sm4;                                      // [2][column threads][4] prefetched source moments
     const int T = a.tx * a.ty;                                // column threads
-    float4* landx = momst + 2 * GP * T * 4;                   // [PD][GP][ty][ABP/4] fetched x-face records
-    float4* landy = landx + PD * GP * a.ty * (ABP / 4);       // [PD][GP][tx][ABP/4] fetched y-face records
-    double* leak_s = reinterpret_cast<double*>(landy + PD * GP * a.tx * (ABP / 4));   // [gcount]
+    float4* landx = momst + 2 * T * 4;                        // [PD][ty][ABP/4] fetched x-face records
+    float4* landy = landx + PD * a.ty * (ABP / 4);            // [PD][tx][ABP/4] fetched y-face records
+    double* leak_s = reinterpret_cast<double*>(landy + PD * a.tx * (ABP / 4));   // [gcount]
     float* buf = reinterpret_cast<float*>(leak_s + a.gcount);              // [2][P][RS]
     float* bufy = DD ? buf + 2 * P * RS : buf;                // [2][P][RS] y-going faces (diamond)
     float* sigt_s = buf + (DD ? 4 : 2) * P * RS;              // [gcount][nmat]
@@ -150,16 +138,13 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
     const int nst = a.ntx + a.nty - 1;
     const int ntxf = a.ntx > 1 ? a.ntx - 1 : 0, ntyf = a.nty > 1 ? a.nty - 1 : 0;
     const size_t xslab = (size_t)a.ny * a.nz * ABP, yslab = (size_t)a.nx * a.nz * ABP;
-    // face records of consecutive groups are ntxf (ntyf) slabs apart
-    const size_t xgs = (size_t)ntxf * xslab, ygs = (size_t)ntyf * yslab;
-    const int ngp = (gcount + GP - 1) / GP;       // group blocks
     int ntasks = 0;
-    for (int s = 0; s < nst; ++s) ntasks += flow_stage_tiles(s, a.ntx, a.nty) * 8 * ngp;
-    // this thread's landing slot for the record of group slot gg used at step st
-    auto land_xr = [&](int st, int gg, int row) { return landx + (((st & (PD - 1)) * GP + gg) * a.ty + row) * (ABP / 4); };
-    auto land_yr = [&](int st, int gg, int cl) { return landy + (((st & (PD - 1)) * GP + gg) * a.tx + cl) * (ABP / 4); };
-    auto land_x = [&](int st, int gg) { return land_xr(st, gg, lj); };
-    auto land_y = [&](int st, int gg) { return land_yr(st, gg, li); };
+    for (int s = 0; s < nst; ++s) ntasks += flow_stage_tiles(s, a.ntx, a.nty) * 8 * gcount;
+    // landing slot of the x (y) record of row (column) i used at step st; this thread's
+    auto land_xr = [&](int st, int row) { return landx + ((st & (PD - 1)) * a.ty + row) * (ABP / 4); };
+    auto land_yr = [&](int st, int cl) { return landy + ((st & (PD - 1)) * a.tx + cl) * (ABP / 4); };
+    auto land_x = [&](int st) { return land_xr(st, lj); };
+    auto land_y = [&](int st) { return land_yr(st, li); };
     const float qnan = __int_as_float(0x7fffffff);
 
     constexpr int NS = SPLIT ? ABP : M;       // prefetched source values per cell (register path)
@@ -168,11 +153,8 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
     for (int m = 0; m < (SMEMPF ? 1 : NS); ++m) sn[m] = 0.0f;
     float rho_n = 0.0f, rho_n2 = 0.0f;        // density and material of the prefetched cells: the cross
     int mat_n = 0, mat_n2 = 0;                // section is looked up when the cell is swept, not at the load
-    float zc[GP][AB];                         // z inflow of each group's next cell (GP = 1)
-    float2 zc2[GP == 2 ? AB : 1];             // GP = 2: both groups' z inflow, (.x, .y)
-    float lk[GP];
-#pragma unroll
-    for (int gg = 0; gg < GP; ++gg) lk[gg] = 0.0f;
+    float zc[AB];                             // z inflow of the column's next cell
+    float lk = 0.0f;
 
     for (;;) {
         __syncthreads();                        // previous task done with task_s and the planes
@@ -185,13 +167,12 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
         int s = 0, r = t, ntiles = 1;
         for (; s < nst; ++s) {
             ntiles = flow_stage_tiles(s, a.ntx, a.nty);
-            if (r < ntiles * 8 * ngp) break;
-            r -= ntiles * 8 * ngp;
+            if (r < ntiles * 8 * gcount) break;
+            r -= ntiles * 8 * gcount;
         }
         const int ti = r % ntiles;
         r /= ntiles;
-        const int o = r & 7, gi = GP * (r >> 3);
-        const int gn = (GP == 2 && gi + 1 < gcount) ? 2 : 1;      // groups of this task
+        const int o = r & 7, gi = r >> 3;
         const int g = g0 + gi;
         const int at = max(0, s - (a.nty - 1)) + ti, bt = s - at;
         const int sx = (o & 1) ? -1 : 1, sy = (o & 2) ? -1 : 1, sz = (o & 4) ? -1 : 1;
@@ -202,12 +183,11 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
         const int i = sx > 0 ? ir : a.nx - 1 - ir;
         const int j = sy > 0 ? jr : a.ny - 1 - jr;
         const size_t vcol = (size_t)j * a.nx + i;
-        const size_t gV = (size_t)g * V;             // group slot gg: gV + gg * V
+        const size_t gV = (size_t)g * V;
         const bool xout = li == a.tx - 1 && at < a.ntx - 1 && !withhold;
         const bool yout = lj == a.ty - 1 && bt < a.nty - 1 && !withhold;
         const bool xleak = ir == a.nx - 1, yleak = jr == a.ny - 1;
         const size_t og = (size_t)o * a.G + g;
-        // group slot gg: + gg * xgs (ygs)
         float* const xo = a.xface + (og * ntxf + at) * xslab + (size_t)jr * a.nz * ABP;
         float* const yo = a.yface + (og * ntyf + bt) * yslab + (size_t)ir * a.nz * ABP;
         // incoming records (null on the mesh boundary: zero inflow)
@@ -219,7 +199,7 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
 
         const size_t ang0 = ((size_t)g * 8 + oe) * V;       // angular records of (group, direction octant)
         // source values, density and material of plane kn into (dst, rho, mat);
-        // with SMEMPF the moments of every group slot go to shared memory
+        // with SMEMPF the moments go to shared memory
         auto fetch = [&](int kn, float* dst, float& rho, int& mt) {
             const int k = sz > 0 ? kn : a.nz - 1 - kn;
             const size_t v = (size_t)k * nxy + vcol;
@@ -231,15 +211,10 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
                     dst[4 * c4] = t4.x; dst[4 * c4 + 1] = t4.y; dst[4 * c4 + 2] = t4.z; dst[4 * c4 + 3] = t4.w;
                 }
             } else if constexpr (SMEMPF) {
+                float4* slot = momst + ((kn & 1) * T + threadIdx.x) * 4;
+                const float* srcm = a.src + (gV + v) * M;
 #pragma unroll
-                for (int gg = 0; gg < GP; ++gg) {
-                    if (gg < gn) {
-                        float4* slot = momst + (((kn & 1) * GP + gg) * T + threadIdx.x) * 4;
-                        const float* srcm = a.src + (gV + gg * V + v) * M;
-#pragma unroll
-                        for (int c4 = 0; c4 < M / 4; ++c4) cp_async_cg16(slot + c4, srcm + 4 * c4);
-                    }
-                }
+                for (int c4 = 0; c4 < M / 4; ++c4) cp_async_cg16(slot + c4, srcm + 4 * c4);
                 (void)dst;
             } else {
                 float tmp[M];
@@ -271,35 +246,22 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
         }
         if constexpr (SMEMPF) asm volatile("cp.async.commit_group;\n" ::: "memory");
 #pragma unroll
-        for (int gg = 0; gg < GP; ++gg) {
-#pragma unroll
-            for (int q = 0; q < AB; ++q) zc[gg][q] = 0.0f;
-        }
-        if constexpr (GP == 2) {
-#pragma unroll
-            for (int q = 0; q < AB; ++q) zc2[q] = make_float2(0.0f, 0.0f);
-        }
+        for (int q = 0; q < AB; ++q) zc[q] = 0.0f;
 
         // issue the fetch of the face records this thread uses at step st
-        // (plane st - d), every group slot: one commit group per step for
-        // every thread
+        // (plane st - d): one commit group per step for every thread
         auto issue_faces = [&](int st) {
             const int kt = st - d;
             if (col && kt >= 0 && kt < a.nz) {
+                if (xedge && xi) {
 #pragma unroll
-                for (int gg = 0; gg < GP; ++gg) {
-                    if (gg < gn) {
-                        if (xedge && xi) {
+                    for (int c4 = 0; c4 < ABP / 4; ++c4)
+                        cp_async_cg16(land_x(st) + c4, xi + (size_t)kt * ABP + 4 * c4);
+                }
+                if (yedge && yi) {
 #pragma unroll
-                            for (int c4 = 0; c4 < ABP / 4; ++c4)
-                                cp_async_cg16(land_x(st, gg) + c4, xi + gg * xgs + (size_t)kt * ABP + 4 * c4);
-                        }
-                        if (yedge && yi) {
-#pragma unroll
-                            for (int c4 = 0; c4 < ABP / 4; ++c4)
-                                cp_async_cg16(land_y(st, gg) + c4, yi + gg * ygs + (size_t)kt * ABP + 4 * c4);
-                        }
-                    }
+                    for (int c4 = 0; c4 < ABP / 4; ++c4)
+                        cp_async_cg16(land_y(st) + c4, yi + (size_t)kt * ABP + 4 * c4);
                 }
             }
             asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -332,14 +294,10 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
                 fw_rec(r, side, idx, ok, src);
                 const int pf = st - idx;
                 if (ok && src && pf >= 0 && pf < a.nz) {
+                    float4* land = side == 0 ? land_xr(st, idx) : land_yr(st, idx);
+                    const float* s0 = src + (size_t)pf * ABP;
 #pragma unroll
-                    for (int gg = 0; gg < GP; ++gg) {
-                        if (gg >= gn) break;
-                        float4* land = side == 0 ? land_xr(st, gg, idx) : land_yr(st, gg, idx);
-                        const float* s0 = src + (side == 0 ? gg * xgs : gg * ygs) + (size_t)pf * ABP;
-#pragma unroll
-                        for (int c4 = 0; c4 < ABP / 4; ++c4) cp_async_cg16(land + c4, s0 + 4 * c4);
-                    }
+                    for (int c4 = 0; c4 < ABP / 4; ++c4) cp_async_cg16(land + c4, s0 + 4 * c4);
                 }
             }
             asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -355,39 +313,34 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
                 fw_rec(r, side, idx, ok, src);
                 const int pf = st - idx;
                 if (!ok || pf < 0 || pf >= a.nz) continue;
-                const int hs0 = side == 0 ? (idx + 1) * PX * RS : (idx + 1) * RS;
+                const int hs = side == 0 ? (idx + 1) * PX * RS : (idx + 1) * RS;
                 float* hb = (side == 0 ? buf : bufy) + cbf * P * RS;
+                if (!src) {
 #pragma unroll
-                for (int gg = 0; gg < GP; ++gg) {
-                    if (gg >= gn) break;
-                    const int hs = hs0 + gg * AB;
-                    if (!src) {
-#pragma unroll
-                        for (int q = 0; q < AB; ++q) hb[hs + q] = 0.0f;
-                        continue;
-                    }
-                    float4* land = side == 0 ? land_xr(st, gg, idx) : land_yr(st, gg, idx);
-                    const float* lf = reinterpret_cast<const float*>(land);
-                    float* s0 = src + (side == 0 ? gg * xgs : gg * ygs) + (size_t)pf * ABP;
-                    bool got = false;
-                    for (int it = 0; it < kFlowSpinLimit; ++it) {
-                        got = true;
-#pragma unroll
-                        for (int q = 0; q < AB; ++q) got = got && !isnan(lf[q]);
-                        if (got) break;
-                        if ((it & 63) == 63 && *reinterpret_cast<volatile int*>(a.flow + 2)) break;
-                        __nanosleep(100);
-#pragma unroll
-                        for (int c4 = 0; c4 < ABP / 4; ++c4) cp_async_cg16(land + c4, s0 + 4 * c4);
-                        cp_async_wait_all();
-                    }
-                    if (!got) atomicExch(a.flow + 2, 1);
-#pragma unroll
-                    for (int q = 0; q < AB; ++q) hb[hs + q] = got ? lf[q] : 0.0f;
-                    float4* back = reinterpret_cast<float4*>(s0);
-#pragma unroll
-                    for (int c4 = 0; c4 < ABP / 4; ++c4) back[c4] = make_float4(qnan, qnan, qnan, qnan);
+                    for (int q = 0; q < AB; ++q) hb[hs + q] = 0.0f;
+                    continue;
                 }
+                float4* land = side == 0 ? land_xr(st, idx) : land_yr(st, idx);
+                const float* lf = reinterpret_cast<const float*>(land);
+                float* s0 = src + (size_t)pf * ABP;
+                bool got = false;
+                for (int it = 0; it < kFlowSpinLimit; ++it) {
+                    got = true;
+#pragma unroll
+                    for (int q = 0; q < AB; ++q) got = got && !isnan(lf[q]);
+                    if (got) break;
+                    if ((it & 63) == 63 && *reinterpret_cast<volatile int*>(a.flow + 2)) break;
+                    __nanosleep(100);
+#pragma unroll
+                    for (int c4 = 0; c4 < ABP / 4; ++c4) cp_async_cg16(land + c4, s0 + 4 * c4);
+                    cp_async_wait_all();
+                }
+                if (!got) atomicExch(a.flow + 2, 1);
+#pragma unroll
+                for (int q = 0; q < AB; ++q) hb[hs + q] = got ? lf[q] : 0.0f;
+                float4* back = reinterpret_cast<float4*>(s0);
+#pragma unroll
+                for (int c4 = 0; c4 < ABP / 4; ++c4) back[c4] = make_float4(qnan, qnan, qnan, qnan);
             }
         };
         // steps -PD .. -1 only fetch the first records
@@ -404,17 +357,13 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
             asm volatile("cp.async.wait_group 1;\n" ::: "memory");
             fw_fill(h + 1, cb);
           } else {
-            float sig_cur[GP];
-#pragma unroll
-            for (int gg = 0; gg < GP; ++gg) sig_cur[gg] = 0.0f;
+            float sig_cur = 0.0f;
             if constexpr (SMEMPF) {
-                // this step's cross sections, then the next cell's moments (their own
+                // this step's cross section, then the next cell's moments (their own
                 // commit group, ahead of the face records of this step)
                 const int kr0 = h - d;
                 if (col && kr0 >= 0 && kr0 < a.nz) {
-#pragma unroll
-                    for (int gg = 0; gg < GP; ++gg)
-                        sig_cur[gg] = gg < gn ? rho_n * sigt_s[(gi + gg) * a.nmat + mat_n] : 0.0f;
+                    sig_cur = rho_n * sigt_s[gi * a.nmat + mat_n];
                     if (kr0 + 1 < a.nz) fetch(kr0 + 1, sn, rho_n, mat_n);
                 }
                 asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -440,16 +389,12 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
                     for (int m = 0; m < NS; ++m) sreg[m] = sn[m];
                     if (!last) prefetch(kr + PDS);
                 }
-              // one cell of group slot gg (a compile-time constant, so that the
-              // per-group state stays in registers)
-              auto cell = [&](auto ggc) {
-                constexpr int gg = decltype(ggc)::value;
-                const size_t mo = (gV + gg * V + v) * M;
+                const size_t mo = (gV + v) * M;
                 float s[NS];
                 float sig;
                 if constexpr (SMEMPF) {
-                    sig = sig_cur[gg];
-                    const float4* slot = momst + (((kr & 1) * GP + gg) * T + threadIdx.x) * 4;
+                    sig = sig_cur;
+                    const float4* slot = momst + ((kr & 1) * T + threadIdx.x) * 4;
 #pragma unroll
                     for (int c4 = 0; c4 < M / 4; ++c4) {
                         const float4 t4 = slot[c4];
@@ -469,7 +414,6 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
 #pragma unroll
                     for (int m = 0; m < NS; ++m) s[m] = sreg[m];
                 }
-                const int zo = gg * AB;               // this group's fluxes within the column record
                 // moments -> directions (split: the record already holds them)
                 float psi[AB];
                 if constexpr (SPLIT) {
@@ -508,34 +452,34 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
                     // two directions per packed operation
 #pragma unroll
                     for (int q = 0; q + 1 < AB; q += 2) {
-                        const float2 px2 = make_float2(pv[xs + zo + q], pv[xs + zo + q + 1]);
-                        const float2 py2 = make_float2(pvy[ys + zo + q], pvy[ys + zo + q + 1]);
+                        const float2 px2 = make_float2(pv[xs + q], pv[xs + q + 1]);
+                        const float2 py2 = make_float2(pvy[ys + q], pvy[ys + q + 1]);
                         float2 n2 = __ffma2_rn(make_float2(dt.cx[q], dt.cx[q + 1]), px2, make_float2(psi[q], psi[q + 1]));
                         n2 = __ffma2_rn(make_float2(dt.cy[q], dt.cy[q + 1]), py2, n2);
-                        n2 = __ffma2_rn(make_float2(dt.cz[q], dt.cz[q + 1]), make_float2(zc[gg][q], zc[gg][q + 1]), n2);
+                        n2 = __ffma2_rn(make_float2(dt.cz[q], dt.cz[q + 1]), make_float2(zc[q], zc[q + 1]), n2);
                         const float2 d2 = __fadd2_rn(make_float2(sig, sig), make_float2(dt.csum[q], dt.csum[q + 1]));
                         const float2 p2 = make_float2(n2.x * rcp_approx(d2.x), n2.y * rcp_approx(d2.y));
                         psi[q] = p2.x;
                         psi[q + 1] = p2.y;
-                        cv[os + zo + q] = p2.x;
-                        cv[os + zo + q + 1] = p2.y;
-                        zc[gg][q] = p2.x;
-                        zc[gg][q + 1] = p2.y;
+                        cv[os + q] = p2.x;
+                        cv[os + q + 1] = p2.y;
+                        zc[q] = p2.x;
+                        zc[q + 1] = p2.y;
                     }
                 }
 #pragma unroll
                 for (int q = DD ? 0 : (AB & ~1); q < AB; ++q) {
-                    const float px = pv[xs + zo + q];
-                    const float py = pvy[ys + zo + q];
-                    const float num = fmaf(dt.cz[q], zc[gg][q], fmaf(dt.cy[q], py, fmaf(dt.cx[q], px, psi[q])));
+                    const float px = pv[xs + q];
+                    const float py = pvy[ys + q];
+                    const float num = fmaf(dt.cz[q], zc[q], fmaf(dt.cy[q], py, fmaf(dt.cx[q], px, psi[q])));
                     psi[q] = num * rcp_approx(sig + dt.csum[q]);
                     if constexpr (DD) {
-                        cv[os + zo + q] = fmaf(2.0f, psi[q], -px);
-                        cvy[os + zo + q] = fmaf(2.0f, psi[q], -py);
-                        zc[gg][q] = fmaf(2.0f, psi[q], -zc[gg][q]);
+                        cv[os + q] = fmaf(2.0f, psi[q], -px);
+                        cvy[os + q] = fmaf(2.0f, psi[q], -py);
+                        zc[q] = fmaf(2.0f, psi[q], -zc[q]);
                     } else {
-                        cv[os + zo + q] = psi[q];
-                        zc[gg][q] = psi[q];
+                        cv[os + q] = psi[q];
+                        zc[q] = psi[q];
                     }
                 }
                 // stored angular fluence, laid out for this kernel as one 16-byte
@@ -566,8 +510,8 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
                 // outgoing face records of plane kr
                 if constexpr (DD) {
                     // the x and y face fluxes, read back from this thread's plane entries
-                    const float* fxo = cv + os + zo;
-                    const float* fyo = cvy + os + zo;
+                    const float* fxo = cv + os;
+                    const float* fyo = cvy + os;
                     if (xout) {
                         float4* dst = reinterpret_cast<float4*>(xo + (size_t)kr * ABP);
 #pragma unroll
@@ -587,9 +531,9 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
                     if (xleak || yleak || last) {
 #pragma unroll
                         for (int q = 0; q < AB; ++q) {
-                            if (xleak) lk[gg] = fmaf(dt.lx[q], fxo[q], lk[gg]);
-                            if (yleak) lk[gg] = fmaf(dt.ly[q], fyo[q], lk[gg]);
-                            if (last) lk[gg] = fmaf(dt.lz[q], zc[gg][q], lk[gg]);
+                            if (xleak) lk = fmaf(dt.lx[q], fxo[q], lk);
+                            if (yleak) lk = fmaf(dt.ly[q], fyo[q], lk);
+                            if (last) lk = fmaf(dt.lz[q], zc[q], lk);
                         }
                     }
                 } else {
@@ -602,12 +546,12 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
                                               4 * c4 + 2 < AB ? psi[4 * c4 + 2 < AB ? 4 * c4 + 2 : 0] : 0.0f,
                                               4 * c4 + 3 < AB ? psi[4 * c4 + 3 < AB ? 4 * c4 + 3 : 0] : 0.0f);
                     if (xout) {
-                        float4* dst = reinterpret_cast<float4*>(xo + gg * xgs + (size_t)kr * ABP);
+                        float4* dst = reinterpret_cast<float4*>(xo + (size_t)kr * ABP);
 #pragma unroll
                         for (int c4 = 0; c4 < ABP / 4; ++c4) dst[c4] = rec[c4];
                     }
                     if (yout) {
-                        float4* dst = reinterpret_cast<float4*>(yo + gg * ygs + (size_t)kr * ABP);
+                        float4* dst = reinterpret_cast<float4*>(yo + (size_t)kr * ABP);
 #pragma unroll
                         for (int c4 = 0; c4 < ABP / 4; ++c4) dst[c4] = rec[c4];
                     }
@@ -619,7 +563,7 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
                         if (xleak) f += dt.lx[q];
                         if (yleak) f += dt.ly[q];
                         if (last) f += dt.lz[q];
-                        lk[gg] = fmaf(f, psi[q], lk[gg]);
+                        lk = fmaf(f, psi[q], lk);
                     }
                 }
                 }
@@ -663,138 +607,10 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
                     }
                     add_moments<M>(a.mom + mo, acc);
                 }
-                if (last && lk[gg] != 0.0f) {
-                    atomicAdd(leak_s + gi + gg, (double)lk[gg]);
-                    lk[gg] = 0.0f;
+                if (last && lk != 0.0f) {
+                    atomicAdd(leak_s + gi, (double)lk);
+                    lk = 0.0f;
                 }
-              };
-              if constexpr (GP == 2) {
-                // both groups at once: every packed two-lane operation holds group
-                // slot 0 in .x and group slot 1 in .y with the same table constant
-                // in both lanes, so each table value is read once for the two cells
-                const bool two = gn == 2;
-                const float4* slot0 = momst + (((kr & 1) * GP + 0) * T + threadIdx.x) * 4;
-                const float4* slot1 = momst + (((kr & 1) * GP + 1) * T + threadIdx.x) * 4;
-                const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                float2 s2[M];
-#pragma unroll
-                for (int c4 = 0; c4 < M / 4; ++c4) {
-                    const float4 u = slot0[c4];
-                    const float4 w = two ? slot1[c4] : z4;
-                    s2[4 * c4] = make_float2(u.x, w.x);
-                    s2[4 * c4 + 1] = make_float2(u.y, w.y);
-                    s2[4 * c4 + 2] = make_float2(u.z, w.z);
-                    s2[4 * c4 + 3] = make_float2(u.w, w.w);
-                }
-#pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    const float sg = octant_sign<M>(m, fx, fy, fz);
-                    s2[m] = __fmul2_rn(s2[m], make_float2(sg, sg));
-                }
-                // moments -> directions
-                float2 psi2[AB];
-#pragma unroll
-                for (int q = 0; q < AB; ++q) {
-                    float2 t2 = make_float2(0.0f, 0.0f);
-#pragma unroll
-                    for (int m = 0; m < M; ++m) {
-                        const float c = dt.mop[q * 16 + m];
-                        t2 = __ffma2_rn(make_float2(c, c), s2[m], t2);
-                    }
-                    psi2[q] = t2;
-                }
-                // step-differenced cell solve of both groups
-                const float* pv = buf + pb * P * RS;
-                float* cv = buf + cb * P * RS;
-                const float2 sig2 = make_float2(sig_cur[0], sig_cur[1]);
-#pragma unroll
-                for (int q = 0; q < AB; ++q) {
-                    const float2 px2 = make_float2(pv[xs + q], pv[xs + AB + q]);
-                    const float2 py2 = make_float2(pv[ys + q], pv[ys + AB + q]);
-                    float2 n2 = __ffma2_rn(make_float2(dt.cx[q], dt.cx[q]), px2, psi2[q]);
-                    n2 = __ffma2_rn(make_float2(dt.cy[q], dt.cy[q]), py2, n2);
-                    n2 = __ffma2_rn(make_float2(dt.cz[q], dt.cz[q]), zc2[q], n2);
-                    const float2 d2 = __fadd2_rn(sig2, make_float2(dt.csum[q], dt.csum[q]));
-                    const float2 p2 = __fmul2_rn(n2, make_float2(rcp_approx(d2.x), rcp_approx(d2.y)));
-                    psi2[q] = p2;
-                    zc2[q] = p2;
-                    cv[os + q] = p2.x;
-                    cv[os + AB + q] = p2.y;
-                }
-                // outgoing face records of plane kr, one per group
-                if (xout || yout) {
-                    float4 r0[ABP / 4], r1[ABP / 4];
-#pragma unroll
-                    for (int c4 = 0; c4 < ABP / 4; ++c4) {
-                        float e0[4], e1[4];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int q = 4 * c4 + e;
-                            e0[e] = q < AB ? psi2[q < AB ? q : 0].x : 0.0f;
-                            e1[e] = q < AB ? psi2[q < AB ? q : 0].y : 0.0f;
-                        }
-                        r0[c4] = make_float4(e0[0], e0[1], e0[2], e0[3]);
-                        r1[c4] = make_float4(e1[0], e1[1], e1[2], e1[3]);
-                    }
-                    if (xout) {
-                        float4* dst = reinterpret_cast<float4*>(xo + (size_t)kr * ABP);
-#pragma unroll
-                        for (int c4 = 0; c4 < ABP / 4; ++c4) dst[c4] = r0[c4];
-                        if (two) {
-                            float4* dst1 = reinterpret_cast<float4*>(xo + xgs + (size_t)kr * ABP);
-#pragma unroll
-                            for (int c4 = 0; c4 < ABP / 4; ++c4) dst1[c4] = r1[c4];
-                        }
-                    }
-                    if (yout) {
-                        float4* dst = reinterpret_cast<float4*>(yo + (size_t)kr * ABP);
-#pragma unroll
-                        for (int c4 = 0; c4 < ABP / 4; ++c4) dst[c4] = r0[c4];
-                        if (two) {
-                            float4* dst1 = reinterpret_cast<float4*>(yo + ygs + (size_t)kr * ABP);
-#pragma unroll
-                            for (int c4 = 0; c4 < ABP / 4; ++c4) dst1[c4] = r1[c4];
-                        }
-                    }
-                }
-                if (xleak || yleak || last) {
-                    float2 l2 = make_float2(lk[0], lk[1]);
-#pragma unroll
-                    for (int q = 0; q < AB; ++q) {
-                        float f = 0.0f;
-                        if (xleak) f += dt.lx[q];
-                        if (yleak) f += dt.ly[q];
-                        if (last) f += dt.lz[q];
-                        l2 = __ffma2_rn(make_float2(f, f), psi2[q], l2);
-                    }
-                    lk[0] = l2.x;
-                    lk[1] = l2.y;
-                }
-                // directions -> moments (Eq. 3 for lm = 00)
-                float acc0[M], acc1[M];
-#pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    float2 t2 = make_float2(0.0f, 0.0f);
-#pragma unroll
-                    for (int q = 0; q < AB; ++q) {
-                        const float c = dt.dop[m * kFlowMaxAB + q];
-                        t2 = __ffma2_rn(make_float2(c, c), psi2[q], t2);
-                    }
-                    const float sg = octant_sign<M>(m, fx, fy, fz);
-                    acc0[m] = t2.x * sg;
-                    acc1[m] = t2.y * sg;
-                }
-                add_moments<M>(a.mom + (gV + v) * M, acc0);
-                if (two) add_moments<M>(a.mom + (gV + V + v) * M, acc1);
-                if (last) {
-                    if (lk[0] != 0.0f) atomicAdd(leak_s + gi, (double)lk[0]);
-                    if (two && lk[1] != 0.0f) atomicAdd(leak_s + gi + 1, (double)lk[1]);
-                    lk[0] = 0.0f;
-                    lk[1] = 0.0f;
-                }
-              } else {
-                cell(std::integral_constant<int, 0>{});
-              }
             }
             // incoming records of the plane swept next step (fetched PD steps
             // ago): wait until the producer has written every flux (no NaN
@@ -814,13 +630,11 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
                 }
                 float* hbx = buf + cb * P * RS;
                 float* hby = bufy + cb * P * RS;
-#pragma unroll
-                for (int gg = 0; gg < GP; ++gg) {
-                  if (gg >= gn) break;
+                {
                   for (int side = 0; side < 2; ++side) {
                     const bool edge = side == 0 ? xedge : yedge;
                     if (!edge) continue;
-                    const int hs = (side == 0 ? xs : ys) + gg * AB;
+                    const int hs = side == 0 ? xs : ys;
                     float* hb = side == 0 ? hbx : hby;
                     float* src = side == 0 ? xi : yi;
                     if (!src) {
@@ -828,9 +642,9 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? (GP =
                         for (int q = 0; q < AB; ++q) hb[hs + q] = 0.0f;
                         continue;
                     }
-                    float4* land = side == 0 ? land_x(h + 1, gg) : land_y(h + 1, gg);
+                    float4* land = side == 0 ? land_x(h + 1) : land_y(h + 1);
                     const float* lf = reinterpret_cast<const float*>(land);
-                    src += (side == 0 ? gg * xgs : gg * ygs) + (size_t)pf * ABP;
+                    src += (size_t)pf * ABP;
                     bool ok = false;
                     for (int it = 0; it < kFlowSpinLimit; ++it) {
                         ok = true;
@@ -956,7 +770,7 @@ __global__ void __launch_bounds__(256) k_split_d2m(const float* pang, float* mom
 }
 
 template <int M>
-int sweep_flow_blocks_per_sm(int ab, int threads, size_t smem, bool split, int gp, bool dd, bool hw) {
+int sweep_flow_blocks_per_sm(int ab, int threads, size_t smem, bool split, bool dd, bool hw) {
     int b = 0;
     cudaError_t e = cudaErrorInvalidValue;
     auto query = [&](auto kern) {
@@ -967,11 +781,9 @@ int sweep_flow_blocks_per_sm(int ab, int threads, size_t smem, bool split, int g
 #define DOCTORS_FLOW_OCC(AB)                                                            \
     case AB:                                                                            \
         if (split) query(k_sweep_flow<AB, M, 0, true>);                                  \
-        else if (dd) query(k_sweep_flow<AB, M, 0, false, 1, true>);                      \
+        else if (dd) query(k_sweep_flow<AB, M, 0, false, true>);                         \
         else if (hw) {                                                                  \
-            if constexpr (M % 4 == 0) query(k_sweep_flow<AB, M, 0, false, 1, false, true>); \
-        } else if (gp == 2) {                                                           \
-            if constexpr (M % 4 == 0) query(k_sweep_flow<AB, M, 0, false, 2>);          \
+            if constexpr (M % 4 == 0) query(k_sweep_flow<AB, M, 0, false, false, true>); \
         } else query(k_sweep_flow<AB, M, 0>);                                            \
         break;
     switch (ab) {
@@ -1046,21 +858,19 @@ cudaError_t launch_sweep_flow_m(const SweepArgs& a, cudaStream_t s) {
     if (a.gcount <= 0) return cudaSuccess;
     if (a.dir_table == nullptr || a.flow == nullptr || a.nab != 1) return cudaErrorInvalidValue;
     const bool dd = a.dd != 0;
-    const int ngp = (MODE == 0 && a.gp == 2 && !dd && M % 4 == 0) ? (a.gcount + 1) / 2 : a.gcount;
     int ntasks = 0;
     for (int st = 0; st < a.ntx + a.nty - 1; ++st) {
         const int lo = st - (a.nty - 1) > 0 ? st - (a.nty - 1) : 0;
         const int hi = st < a.ntx - 1 ? st : a.ntx - 1;
-        ntasks += (hi - lo + 1) * 8 * ngp;
+        ntasks += (hi - lo + 1) * 8 * a.gcount;
     }
     // persistent CTAs: every resident slot, or its share when several instances sweep at once
     const int slots = std::max(1, a.chain_slots / std::max(1, a.slot_share));
     const int grid = ntasks < slots ? ntasks : slots;
-    const int gp = (MODE == 0 && a.gp == 2 && !dd && M % 4 == 0) ? 2 : 1;
-    const bool hw = MODE == 0 && a.hw != 0 && !dd && gp == 1 && M % 4 == 0;
+    const bool hw = MODE == 0 && a.hw != 0 && !dd && M % 4 == 0;
     // column threads, plus the face warp
     const int T = hw ? ((a.tx * a.ty + 31) / 32 + 1) * 32 : a.tx * a.ty;
-    const size_t smem = sweep_flow_smem_bytes(a.ab, a.tx, a.ty, a.gcount, a.nmat, gp, dd);
+    const size_t smem = sweep_flow_smem_bytes(a.ab, a.tx, a.ty, a.gcount, a.nmat, dd);
     cudaError_t e = cudaSuccess;
     auto launch = [&](auto kern) {
         if (smem > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1069,16 +879,12 @@ cudaError_t launch_sweep_flow_m(const SweepArgs& a, cudaStream_t s) {
 #define DOCTORS_FLOW_CASE(AB)                                                           \
     case AB:                                                                            \
         if (dd) {                                                                       \
-            launch(k_sweep_flow<AB, M, MODE, false, 1, true>);                           \
+            launch(k_sweep_flow<AB, M, MODE, false, true>);                              \
             break;                                                                      \
         }                                                                               \
         if constexpr (MODE == 0 && M % 4 == 0) {                                        \
             if (hw) {                                                                   \
-                launch(k_sweep_flow<AB, M, 0, false, 1, false, true>);                   \
-                break;                                                                  \
-            }                                                                           \
-            if (gp == 2) {                                                              \
-                launch(k_sweep_flow<AB, M, 0, false, 2>);                                \
+                launch(k_sweep_flow<AB, M, 0, false, false, true>);                      \
                 break;                                                                  \
             }                                                                           \
         }                                                                               \

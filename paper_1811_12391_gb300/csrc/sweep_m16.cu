@@ -28,8 +28,8 @@ cudaError_t launch_sweep_flow_m16_entry(const SweepArgs& a, int mode, cudaStream
         default: return cudaErrorInvalidValue;
     }
 }
-int sweep_flow_blocks_m16(int ab, int threads, size_t smem, bool split, int gp, bool dd, bool hw) {
-    return sweep_flow_blocks_per_sm<16>(ab, threads, smem, split, gp, dd, hw);
+int sweep_flow_blocks_m16(int ab, int threads, size_t smem, bool split, bool dd, bool hw) {
+    return sweep_flow_blocks_per_sm<16>(ab, threads, smem, split, dd, hw);
 }
 cudaError_t launch_split_sweep_m16_entry(const SweepArgs& a, cudaStream_t s, int* count) {
     return launch_split_sweep_m<16>(a, s, count);

@@ -95,6 +95,18 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib):
         assert C.doctors_create_problem(ctypes.byref(mesh), ctypes.byref(opt), None, ctypes.byref(h)) == \
             C.DOCTORS_ERR_INVALID_ARG
         assert "diamond" in C.last_error()
+    opt.differencing = C.DOCTORS_DIFF_STEP
+    for kernel in (2, 6):
+        # taken out (both measured slower than the kernels kept), rejected before any device call
+        opt.sweep_kernel = kernel
+        assert C.doctors_create_problem(ctypes.byref(mesh), ctypes.byref(opt), None, ctypes.byref(h)) == \
+            C.DOCTORS_ERR_INVALID_ARG
+        assert "not offered" in C.last_error()
+    for kernel in (-1, 9):
+        opt.sweep_kernel = kernel
+        assert C.doctors_create_problem(ctypes.byref(mesh), ctypes.byref(opt), None, ctypes.byref(h)) == \
+            C.DOCTORS_ERR_INVALID_ARG
+        assert "sweep_kernel" in C.last_error()
     opt.sweep_kernel, opt.sn_order = 0, 4
     opt.reserved[0] = 1
     assert C.doctors_create_problem(ctypes.byref(mesh), ctypes.byref(opt), None, ctypes.byref(h)) == \

@@ -46,8 +46,8 @@ def grad_ref():
     return p, roi, osv.gradients(p, roi, tol=1e-12)
 
 
-@pytest.mark.parametrize("L,kernel", [(1, 1), (1, 3), (1, 4), (1, 5), (1, 6), (1, 7), (3, 1), (3, 2), (3, 3), (3, 4),
-                                      (3, 5), (3, 6), (3, 7), (3, 8)])
+@pytest.mark.parametrize("L,kernel", [(1, 1), (1, 3), (1, 4), (1, 5), (1, 7), (3, 1), (3, 3), (3, 4),
+                                      (3, 5), (3, 7), (3, 8)])
 def test_adjoint_fluence_and_gradients_match_oracle(env, grad_ref, L, kernel):
     torch, C, DoctorsProblem = env
     if L == 1:
@@ -145,7 +145,7 @@ def test_autograd_roi_dose_matches_finite_differences(env):
         assert abs(fd - gr[v]) <= 2e-2 * abs(fd) + noise, (v, fd, gr[v], noise)
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("kernel", [1, 3, 4, 5, 7])
 def test_gradients_satisfy_euler_identity(env, kernel):
     """J is linear in every view weight and in every spectrum entry, so
     sum_s w_s dJ/dw_s = J and sum_g chi_g dJ/dchi_g = J (Euler's identity for

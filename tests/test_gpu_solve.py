@@ -54,30 +54,27 @@ def cylinder_ref():
     return p, osv.solve(p, tol=1e-11)
 
 
-@pytest.mark.parametrize("tile,ab,kernel", [((16, 16), 0, 1), ((16, 16), 0, 2), ((16, 16), 0, 3), ((8, 4), 5, 1),
-                                            ((8, 4), 5, 2), ((8, 4), 5, 3), ((5, 7), 2, 1), ((5, 7), 2, 3),
-                                            ((32, 8), 10, 2), ((32, 8), 10, 3), ((8, 16), 10, 2), ((16, 2), 1, 3),
+@pytest.mark.parametrize("tile,ab,kernel", [((16, 16), 0, 1), ((16, 16), 0, 3), ((8, 4), 5, 1),
+                                            ((8, 4), 5, 3), ((5, 7), 2, 1), ((5, 7), 2, 3),
+                                            ((32, 8), 10, 1), ((32, 8), 10, 3), ((8, 16), 10, 1), ((16, 2), 1, 3),
                                             ((16, 16), 10, 4), ((16, 8), 10, 4), ((5, 7), 10, 4), ((8, 4), 10, 4),
                                             ((8, 8), 10, 4), ((8, 8), 10, 0),
                                             ((8, 8), 10, 5), ((16, 8), 10, 5), ((5, 7), 10, 5),
-                                            ((8, 8), 10, 6), ((16, 8), 10, 6), ((5, 7), 10, 6),
                                             ((8, 8), 10, 7), ((16, 8), 10, 7), ((5, 7), 10, 7), ((32, 8), 10, 7),
                                             ((8, 8), 10, 8), ((5, 7), 10, 8)])
 def test_ragged_multitile_cylinder(dp, cylinder_ref, tile, ab, kernel):
     """Several sweep tiles with ragged tails in x and y, S8 P3, with the
-    CUDA-core (1), tensor-core (2), chained (3), dataflow (4), dataflow
-    with split transforms (5), dataflow with two groups per task (6; with
-    five groups the last task of every tile and octant has one group) and
-    dataflow with a face warp (7; 5x7 leaves a partly used column warp, 32x8
-    gives the face warp 40 records) and split transforms on the tensor cores
-    (8; 3xTF32) sweeps."""
+    CUDA-core (1), chained (3), dataflow (4), dataflow with split
+    transforms (5), dataflow with a face warp (7; 5x7 leaves a partly used
+    column warp, 32x8 gives the face warp 40 records) and split transforms on
+    the tensor cores (8; 3xTF32) sweeps."""
     p, sol = cylinder_ref
     d = dp(p, tol=1e-6, max_iters=400, tile=tile, angles_per_block=ab, sweep_kernel=kernel)
     _compare(d, p, sol, f"cylinder tile={tile} ab={ab} kernel={kernel}")
     d.close()
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3])
+@pytest.mark.parametrize("kernel", [1, 3])
 def test_abdomen_s16_multi_angle_block(dp, kernel):
     """Heterogeneous abdomen-like phantom, S16 (three direction blocks per
     octant), P3, five materials."""
@@ -89,16 +86,16 @@ def test_abdomen_s16_multi_angle_block(dp, kernel):
 
 
 def test_sweep_kernels_agree(dp):
-    """The three sweep kernels give the same fluence on the full-size water
+    """Every sweep kernel gives the same fluence on the full-size water
     cylinder (one sweep from the first-collision source)."""
     p = ph.water_cylinder()
     outs = []
-    for kernel in (1, 2, 3, 4, 5, 6, 7, 8):
+    for kernel in (1, 3, 4, 5, 7, 8):
         d = dp(p, tol=1e-6, max_iters=1, sweep_kernel=kernel, angles_per_block=10)
         d.solve(allow_not_converged=True)
         outs.append(d.fluence_host(1))
         d.close()
-    for k in (1, 2, 3, 4, 5, 6, 7):
+    for k in range(1, len(outs)):
         assert max_rel(outs[k], outs[0]) <= 2e-5
 
 
@@ -126,7 +123,7 @@ def test_infinite_medium_volume_source(dp):
     d.close()
 
 
-@pytest.mark.parametrize("kernel", [1, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("kernel", [1, 3, 4, 5, 7])
 def test_degenerate_meshes(dp, kernel):
     """Single voxel, single column and single plane meshes."""
     for dims in ((1, 1, 1), (1, 1, 7), (5, 1, 1), (4, 6, 1)):
@@ -184,7 +181,7 @@ def test_iteration_cap_reports_not_converged(dp):
     from paper_1811_12391_gb300 import _lib as C
     p = ph.tiny_cube(n=8)
     ref = osv.solve(p, tol=1e-11)
-    for device_loop, kernel in ((0, 0), (1, 0), (1, 4), (0, 5), (1, 5), (0, 6), (1, 6), (0, 7), (1, 7)):
+    for device_loop, kernel in ((0, 0), (1, 0), (1, 4), (0, 5), (1, 5), (0, 7), (1, 7)):
         d = dp(p, tol=1e-6, max_iters=3, device_loop=device_loop, sweep_kernel=kernel, angles_per_block=3)
         with pytest.raises(C.DoctorsError) as e:
             d.solve()
