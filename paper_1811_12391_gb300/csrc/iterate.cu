@@ -259,16 +259,34 @@ __device__ __forceinline__ float ldg_if(const float* p, bool pred) {
     return x;
 }
 
+// staged table of k_scatter_fast: per (material, degree) block GMAX rows of
+// GMAX entries, row g holding the entries destination group g sums over in
+// ascending source order (forward: sigma(g' -> g) for g' = 0..GMAX-1, the
+// table's column g; adjoint: sigma(g -> g'), its row g), so that a thread
+// reads them as 16-byte vectors.  The block pitch GMAX^2 + 4 is 4 or 20 mod
+// 32 words for every GMAX used, so eight consecutive blocks (the degrees of
+// two voxels of neighbouring materials, as one warp reads them) start in
+// distinct 16-byte bank groups.
+template <int GMAX>
+__host__ __device__ constexpr int scatter_fast_pitch() { return GMAX * GMAX + 4; }
+template <int GMAX>
+size_t scatter_fast_table_bytes(const ScatterArgs& a) {
+    return (size_t)a.nmat * (a.L + 1) * scatter_fast_pitch<GMAX>() * sizeof(float);
+}
+
 template <int GMAX, bool TR, bool HAS_BASE, bool ISO = false>
-__global__ void __launch_bounds__(kScatterThreads, GMAX <= 24 ? 3 : GMAX <= 32 ? 2 : 1) k_scatter_fast(const ScatterArgs a) {
-    extern __shared__ float tab_s[];
+__global__ void __launch_bounds__(kScatterThreads, GMAX <= 24 ? 2 : 1) k_scatter_fast(const ScatterArgs a) {
+    extern __shared__ float4 tab4_s[];
+    float* tab_s = reinterpret_cast<float*>(tab4_s);
+    static_assert(GMAX % 4 == 0, "rows of whole 16-byte vectors");
     if (a.skip && *a.skip) return;
     const int G = a.G;
-    constexpr int BP = scatter_block_pitch<GMAX>();
+    constexpr int BP = scatter_fast_pitch<GMAX>();
     const int nblk = a.nmat * (a.L + 1);
     for (int e = threadIdx.x; e < nblk * BP; e += blockDim.x) {
-        const int blk = e / BP, r = e % BP, i = r / GMAX, j = r % GMAX;
-        tab_s[e] = (r < GMAX * GMAX && i < G && j < G) ? __ldg(a.sigs + ((size_t)blk * G + i) * G + j) : 0.0f;
+        const int blk = e / BP, r = e % BP, i = r / GMAX, j = r % GMAX;   // row i, entry j
+        const int from = TR ? i : j, to = TR ? j : i;
+        tab_s[e] = (r < GMAX * GMAX && i < G && j < G) ? __ldg(a.sigs + ((size_t)blk * G + from) * G + to) : 0.0f;
     }
     __syncthreads();
     const unsigned VM = (unsigned)(a.V * a.M), M = (unsigned)a.M;
@@ -296,17 +314,23 @@ __global__ void __launch_bounds__(kScatterThreads, GMAX <= 24 ? 3 : GMAX <= 32 ?
             for (int g = 0; g < GMAX; ++g)
                 if (g < G) qb[g] += __ldg(a.iso + g);
         }
-        const float* ts = tab_s + mb * BP;
+        const float4* ts4 = reinterpret_cast<const float4*>(tab_s + mb * BP);
         float* po = a.out + t;
 #pragma unroll
         for (int g = 0; g < GMAX; ++g) {
+            // the same sums as k_scatter, source groups ascending: forward
+            // g' = 0..g, adjoint g' = g..GMAX-1, read four entries at a time
             float acc = 0.0f;
-            if (!TR) {
+            constexpr int R4 = GMAX / 4;
 #pragma unroll
-                for (int gp = 0; gp <= g; ++gp) acc = fmaf(ts[gp * GMAX + g], ph[gp], acc);
-            } else {
+            for (int c = TR ? g / 4 : 0; c < (TR ? R4 : g / 4 + 1); ++c) {
+                const float4 t4 = ts4[g * R4 + c];
+                const float tv[4] = {t4.x, t4.y, t4.z, t4.w};
 #pragma unroll
-                for (int gp = g; gp < GMAX; ++gp) acc = fmaf(ts[g * GMAX + gp], ph[gp], acc);
+                for (int k = 0; k < 4; ++k) {
+                    const int gp = 4 * c + k;
+                    if (TR ? gp >= g : gp <= g) acc = fmaf(tv[k], ph[gp], acc);
+                }
             }
             const float out = fmaf(r, acc, qb[g]);
             if (g >= g_beg && g < g_end) po[(size_t)g * VM] = out;
@@ -502,14 +526,16 @@ cudaError_t launch_scatter_g(const ScatterArgs& a, cudaStream_t s) {
     const size_t tab_bytes = scatter_table_bytes<GMAX>(a);
     const int staged = tab_bytes <= kScatterTableSmem ? 1 : 0;
     const size_t smem = staged ? tab_bytes : 0;
-    if (staged && a.phi && a.iso && !a.iso_field && !a.transpose && !a.base && a.V * a.M < ((size_t)1 << 31))
-        return launch_scatter_fast<GMAX, false, false, true>(a, smem, s);
-    if (staged && a.phi && !a.iso && !a.iso_field && a.V * a.M < ((size_t)1 << 31)) {
+    const size_t fast_bytes = scatter_fast_table_bytes<GMAX>(a);
+    const bool fast = fast_bytes <= kScatterTableSmem && a.phi && !a.iso_field && a.V * a.M < ((size_t)1 << 31);
+    if (fast && a.iso && !a.transpose && !a.base)
+        return launch_scatter_fast<GMAX, false, false, true>(a, fast_bytes, s);
+    if (fast && !a.iso) {
         if (a.transpose)
-            return a.base ? launch_scatter_fast<GMAX, true, true>(a, smem, s)
-                          : launch_scatter_fast<GMAX, true, false>(a, smem, s);
-        return a.base ? launch_scatter_fast<GMAX, false, true>(a, smem, s)
-                      : launch_scatter_fast<GMAX, false, false>(a, smem, s);
+            return a.base ? launch_scatter_fast<GMAX, true, true>(a, fast_bytes, s)
+                          : launch_scatter_fast<GMAX, true, false>(a, fast_bytes, s);
+        return a.base ? launch_scatter_fast<GMAX, false, true>(a, fast_bytes, s)
+                      : launch_scatter_fast<GMAX, false, false>(a, fast_bytes, s);
     }
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_scatter<GMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
