@@ -98,13 +98,14 @@ typedef struct doctors_options {
                                 tasks of a stage back to back in one hyperplane pipeline,
                                 4 = dataflow: one launch per sweep, CTAs take tasks from a queue and
                                 wait (bounded) on their upstream tiles' face fluxes plane by plane;
-                                needs angles_per_block = N(N+2)/8 and N <= 8.  A wait that gives up
-                                makes the solve return DOCTORS_ERR_TIMEOUT,
+                                needs angles_per_block = N(N+2)/8 and N <= 8, or angles_per_block
+                                = 12 at S16 (one launch per block of 12 directions).  A wait that
+                                gives up makes the solve return DOCTORS_ERR_TIMEOUT,
                                 5 = dataflow with the transforms split out: a pass turns the source
                                 moments into angular sources of all directions, the sweep reads and
                                 writes one angular record per cell, a pass turns the angular fluence
-                                back into moments (same conditions as 4; two more arrays of
-                                G x N(N+2) x V floats, padded),
+                                back into moments (whole octants of S2..S8 only; two more arrays
+                                of G x N(N+2) x V floats, padded),
                                 7 = dataflow with a face warp: one more warp per CTA fetches and
                                 waits for the incoming face fluxes, the column threads only sweep
                                 (same conditions as 4, P1 or P3, tile_x + tile_y <= 64),

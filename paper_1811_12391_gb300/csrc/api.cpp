@@ -77,6 +77,39 @@ int default_ab(int A8) {
     return 1;
 }
 
+// Direction table of the first octant's directions j0 .. j0+n-1: step and
+// boundary coefficients and weights (n <= kMaxA8) and, for the first
+// kFlowMaxAB of them, the moment <-> direction rows.  Diamond differencing
+// stores 2 c (the dataflow kernel's cell solve then has the step form).
+ChainDirTable make_dir_table(const doctors_problem* p, int j0, int n) {
+    ChainDirTable t{};
+    const double dx = p->mesh.dx, dy = p->mesh.dy, dz = p->mesh.dz;
+    const float cf = p->differencing == DOCTORS_DIFF_DIAMOND ? 2.0f : 1.0f;
+    double Rb[16];
+    for (int jl = 0; jl < n && jl < kMaxA8; ++jl) {
+        const int j = j0 + jl;
+        const double x = p->dirs[3 * j], y = p->dirs[3 * j + 1], z = p->dirs[3 * j + 2];
+        const double ox = std::fabs(x), oy = std::fabs(y), oz = std::fabs(z), wj = p->w[j];
+        if (jl < kFlowMaxAB) {
+            real_harmonics(3, x, y, z, Rb);
+            for (int m = 0; m < p->M; ++m) {
+                const int lm = lm_of_pos(m, p->M);
+                t.mop[jl * 16 + m] = (float)((2 * degree_of_lm(lm) + 1) / (4.0 * M_PI) * Rb[lm]);
+                t.dop[m * kFlowMaxAB + jl] = (float)(wj * Rb[lm]);
+            }
+        }
+        t.cx[jl] = cf * (float)(ox / dx);
+        t.cy[jl] = cf * (float)(oy / dy);
+        t.cz[jl] = cf * (float)(oz / dz);
+        t.csum[jl] = cf * (float)(ox / dx + oy / dy + oz / dz);
+        t.lx[jl] = (float)(wj * ox * dy * dz);
+        t.ly[jl] = (float)(wj * oy * dx * dz);
+        t.lz[jl] = (float)(wj * oz * dx * dy);
+        t.w[jl] = (float)wj;
+    }
+    return t;
+}
+
 void free_problem(doctors_problem* p) {
     void* ptrs[] = {p->d_coef, p->d_mat, p->d_rho, p->d_sigt, p->d_sigs,
                     p->d_phiu_src, p->d_phiu, p->d_U, p->d_Q, p->d_mom, p->d_src, p->d_src2, p->d_prev,
@@ -223,6 +256,7 @@ SweepArgs sweep_args(const doctors_problem* p, int reverse, const float* src, fl
     a.tc_b1 = (p->use_split && p->split_tc) ? p->d_tcb : nullptr;
     a.tc_b2 = (p->use_split && p->split_tc) ? p->d_tcb + p->tcb1_floats : nullptr;
     a.dd = p->differencing == DOCTORS_DIFF_DIAMOND ? 1 : 0;
+    a.blk = 0;
     return a;
 }
 
@@ -234,8 +268,21 @@ cudaError_t launch_sweep(const doctors_problem* p, SweepArgs sw, int mode, cudaS
         // modes 1 and 2 (stored / paired angular fluence) of the split and face-warp
         // paths use the plain dataflow kernel
         if (p->use_split || (mode != 0 && p->flow_hw)) sw.chain_slots = p->flow_slots;
-        *count = 1;
-        return launch_sweep_flow(sw, p->M, mode, s);
+        if (p->nab == 1) {
+            *count = 1;
+            return launch_sweep_flow(sw, p->M, mode, s);
+        }
+        // direction blocks (S16): one launch per block, each with its own table;
+        // the blocks only share the moments (vector reductions) and the leakage
+        *count = 0;
+        for (int b = 0; b < p->nab; ++b) {
+            sw.blk = b;
+            sw.dir_table = &p->dir_blk[b];
+            cudaError_t e = launch_sweep_flow(sw, p->M, mode, s);
+            if (e != cudaSuccess) return e;
+            ++*count;
+        }
+        return cudaSuccess;
     }
     *count = 0;
     for (int st = 0; st < p->ntx + p->nty - 1; ++st) {
@@ -569,8 +616,15 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
                   "on every workload)");
         return DOCTORS_ERR_INVALID_ARG;
     }
-    if (kernel >= 4 && !(p->A8 == ab && chain_const_table_ab(ab))) {
-        set_error("dataflow sweep needs whole octants per CTA (angles_per_block = N(N+2)/8) of S2, S4, S6 or S8");
+    const bool whole_octant = p->A8 == ab && chain_const_table_ab(ab);
+    if ((kernel == 5 || kernel == 8) && !whole_octant) {
+        set_error("the split dataflow sweeps (sweep_kernel 5, 8) need whole octants per CTA "
+                  "(angles_per_block = N(N+2)/8) of S2, S4, S6 or S8");
+        return DOCTORS_ERR_INVALID_ARG;
+    }
+    if ((kernel == 4 || kernel == 7) && !flow_block_ab(p->A8, ab)) {
+        set_error("the dataflow sweep (sweep_kernel 4, 7) needs whole octants per CTA (angles_per_block = "
+                  "N(N+2)/8) of S2, S4, S6 or S8, or blocks of 12 directions (S16)");
         return DOCTORS_ERR_INVALID_ARG;
     }
     if (kernel == 7 && p->M % 4 != 0) {
@@ -592,14 +646,16 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
             set_error("diamond differencing runs on the dataflow sweep (sweep_kernel 0 or 4)");
             return DOCTORS_ERR_INVALID_ARG;
         }
-        if (!(p->A8 == ab && chain_const_table_ab(ab))) {
+        if (!whole_octant) {
             set_error("diamond differencing needs the dataflow sweep: whole octants per CTA "
                       "(angles_per_block = N(N+2)/8) of S2, S4, S6 or S8");
             return DOCTORS_ERR_INVALID_ARG;
         }
         kernel = 4;
     }
-    const bool flow_ok = p->A8 == ab && chain_const_table_ab(ab);
+    // the default (sweep_kernel 0) takes the dataflow kernels for whole octants
+    // of S2..S8 and for S16 in blocks of 12 directions
+    const bool flow_ok = flow_block_ab(p->A8, ab);
     const bool use_split = kernel == 5 || kernel == 8 || (kernel == 0 && flow_ok && kDefaultSplitSweep);
     const bool split_tc = kernel == 8 && p->M == 16;
     const bool use_flow = !use_split && (kernel == 4 || kernel == 7 ||
@@ -710,6 +766,9 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
         if (p->yface_bytes) CU(cudaMemsetAsync(p->d_yface, 0xff, p->yface_bytes, p->stream));
     }
     p->tx = tx; p->ty = ty; p->ab = ab; p->nab = p->A8 / ab; p->ntx = ntx; p->nty = nty;
+    p->dir_blk.clear();
+    if (use_flow && p->nab > 1)
+        for (int b = 0; b < p->nab; ++b) p->dir_blk.push_back(make_dir_table(p, b * ab, ab));
     p->use_flow = use_flow;
     p->use_split = use_split;
     p->split_tc = use_split && split_tc;
@@ -766,11 +825,10 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     p->stream = (cudaStream_t)cuda_stream;
     p->differencing = opt->differencing;
     p->ab = opt->angles_per_block > 0 ? opt->angles_per_block : default_ab(p->A8);
-    // default tile: 8 x 8 for the dataflow sweep (whole octants of S2..S8),
-    // 16 x 16 for the stage kernels (the fastest measured shapes)
+    // default tile: 8 x 8 for the dataflow sweep (whole octants of S2..S8,
+    // S16 in blocks of 12), 16 x 16 for the stage kernels (the fastest measured shapes)
     const bool flow_default = opt->sweep_kernel >= 4 || p->differencing == DOCTORS_DIFF_DIAMOND ||
-                              (opt->sweep_kernel == 0 && kDefaultDataflowSweep && p->A8 == p->ab &&
-                               chain_const_table_ab(p->ab));
+                              (opt->sweep_kernel == 0 && kDefaultDataflowSweep && flow_block_ab(p->A8, p->ab));
     const int tdef = flow_default ? 8 : 16;
     p->tx = opt->tile_x > 0 ? opt->tile_x : std::min(tdef, p->nx);
     p->ty = opt->tile_y > 0 ? opt->tile_y : std::min(tdef, p->ny);
@@ -829,26 +887,7 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
                     return fail(DOCTORS_ERR_INVALID_ARG, "quadrature octants are not reflections of the first");
             }
         }
-        // diamond differencing: the dataflow kernel's cell solve takes 2 c
-        const float cf = p->differencing == DOCTORS_DIFF_DIAMOND ? 2.0f : 1.0f;
-        for (int j = 0; j < p->A8 && j < kFlowMaxAB; ++j) {
-            real_harmonics(3, dirs[3 * j], dirs[3 * j + 1], dirs[3 * j + 2], Rb);
-            for (int m = 0; m < p->M; ++m) {
-                const int lm = lm_of_pos(m, p->M);
-                t.mop[j * 16 + m] = (float)((2 * degree_of_lm(lm) + 1) / (4.0 * M_PI) * Rb[lm]);
-                t.dop[m * kFlowMaxAB + j] = (float)(w[j] * Rb[lm]);
-            }
-        }
-        for (int j = 0; j < p->A8; ++j) {
-            t.cx[j] = cf * coef[j * 8 + 0];
-            t.cy[j] = cf * coef[j * 8 + 1];
-            t.cz[j] = cf * coef[j * 8 + 2];
-            t.csum[j] = cf * coef[j * 8 + 3];
-            t.lx[j] = coef[j * 8 + 4];
-            t.ly[j] = coef[j * 8 + 5];
-            t.lz[j] = coef[j * 8 + 6];
-            t.w[j] = coef[j * 8 + 7];
-        }
+        t = make_dir_table(p, 0, p->A8);
     }
     const size_t GV = (size_t)p->G * p->V, GVM = GV * M;
     int rc = 0;
@@ -1228,7 +1267,8 @@ int doctors_autotune(doctors_problem* p, doctors_tuning* out) {
             for (int kernel = 1; kernel <= 8; ++kernel) {
                 if (p->differencing == DOCTORS_DIFF_DIAMOND && kernel != 4) continue;
                 if (kernel == 2 || kernel == 6) continue;
-                if (kernel >= 4 && !(p->A8 == ab && chain_const_table_ab(ab))) continue;
+                if ((kernel == 5 || kernel == 8) && !(p->A8 == ab && chain_const_table_ab(ab))) continue;
+                if ((kernel == 4 || kernel == 7) && !flow_block_ab(p->A8, ab)) continue;
                 if (configure_sweep(p, t[0], t[1], ab, kernel) != DOCTORS_OK) continue;
                 SweepArgs sw = sweep_args(p, 0, p->d_Q, p->d_mom);
                 float total = 0.0f;

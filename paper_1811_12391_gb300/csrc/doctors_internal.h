@@ -201,6 +201,8 @@ struct SweepArgs {
     const float* tc_b1;                // split transforms on the tensor cores (P3): moments -> directions
     const float* tc_b2;                // and directions -> moments operand tables, or null
     int dd;                            // dataflow kernel: 1 = diamond differencing (dir_table holds 2c), 0 = step
+    int blk;                           // dataflow kernel: the direction block this launch sweeps (0 .. nab-1;
+                                       // dir_table holds that block's rows)
     int* flow;                         // non-null: dataflow kernel; [0] task queue, [1] CTAs done, [2] wait timed out,
                                        // [3] test hook: task + 1 that writes no faces (0: none)
 };
@@ -212,7 +214,7 @@ struct SweepArgs {
 // builds them that way), and R_lm of a reflected direction is R_lm of the
 // original times (-1) to the number of reflected axes in which R_lm is odd.
 constexpr int kMaxA8 = 36;             // S16
-constexpr int kFlowMaxAB = 10;         // whole octants of S2..S8
+constexpr int kFlowMaxAB = 12;         // whole octants of S2..S8, blocks of 12 directions of S16
 struct ChainDirTable {
     float cx[kMaxA8], cy[kMaxA8], cz[kMaxA8], csum[kMaxA8];   // |Omega_q| / d_q and their sum
     float lx[kMaxA8], ly[kMaxA8], lz[kMaxA8];                  // boundary current per face (w |Omega_q| area)
@@ -232,6 +234,11 @@ constexpr unsigned kOddZ = (1u << 2) | (1u << 5) | (1u << 7) | (1u << 10) | (1u 
 // chained kernels with the direction table in the constant bank exist for
 // these directions per CTA (whole octants of S2, S4, S6, S8)
 inline bool chain_const_table_ab(int ab) { return ab == 1 || ab == 3 || ab == 6 || ab == 10; }
+// direction blocks the dataflow kernels sweep (one launch per block, its
+// table in the constant bank): whole octants of S2..S8, or blocks of 12
+// directions (S16: three per octant; a block's face and stored angular
+// records are then exactly its 12 fluxes, no padding)
+inline bool flow_block_ab(int A8, int ab) { return (A8 == ab && chain_const_table_ab(ab)) || (ab == 12 && A8 % 12 == 0); }
 // mode 0: plain; 1: store psi; 2: accumulate sum_n w_n psi_n psi_stored_n into prod
 cudaError_t launch_sweep_stage(const SweepArgs& a, int M, int mode, cudaStream_t s);
 bool sweep_supported(int ab, int M);
@@ -331,6 +338,7 @@ struct doctors_problem {
     size_t ang_floats = 0;
     int* d_flow = nullptr;          // [4] dataflow queue, done count, timeout flag
     doctors::ChainDirTable dir_table{};   // first-octant direction table of the chained sweep
+    std::vector<doctors::ChainDirTable> dir_blk;   // dataflow sweep: the table of each direction block
     // device tables
     float* d_coef = nullptr;
     int table_base = 0;

@@ -2,7 +2,8 @@
 // k_sweep_chain (whole octants per CTA; the first octant's direction rows,
 // coefficients and moment tables are kernel parameters, read through the
 // constant bank at compile-time offsets) with the tile stages replaced by a
-// task queue in one launch.
+// task queue in one launch.  S16 runs as three launches, one per block of
+// 12 directions of every octant, each with that block's table.
 //
 // The tasks (tile, octant, group) are numbered stage by stage (the tile
 // diagonal of the octant's reflected tile grid).  Each CTA takes the next
@@ -483,10 +484,10 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? 3 : 2
                     }
                 }
                 // stored angular fluence, laid out for this kernel as one 16-byte
-                // aligned record of ABP floats per (group, voxel, direction octant):
-                // [G][V][8][ABP] (the stage kernels use [G][V][A])
+                // aligned record of ABP floats per (group, voxel, direction octant,
+                // direction block): [G][V][8][nab][ABP] (the stage kernels use [G][V][A])
                 if constexpr (MODE == 1) {
-                    float4* rec = reinterpret_cast<float4*>(a.psi + (((size_t)g * V + v) * 8 + oe) * ABP);
+                    float4* rec = reinterpret_cast<float4*>(a.psi + ((((size_t)g * V + v) * 8 + oe) * a.nab + a.blk) * ABP);
 #pragma unroll
                     for (int c4 = 0; c4 < ABP / 4; ++c4)
                         rec[c4] = make_float4(4 * c4 < AB ? psi[4 * c4 < AB ? 4 * c4 : 0] : 0.0f,
@@ -495,7 +496,8 @@ __global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? 3 : 2
                                               4 * c4 + 3 < AB ? psi[4 * c4 + 3 < AB ? 4 * c4 + 3 : 0] : 0.0f);
                 }
                 if constexpr (MODE == 2) {
-                    const float4* rec = reinterpret_cast<const float4*>(a.psi + (((size_t)g * V + v) * 8 + oe) * ABP);
+                    const float4* rec =
+                        reinterpret_cast<const float4*>(a.psi + ((((size_t)g * V + v) * 8 + oe) * a.nab + a.blk) * ABP);
                     float pacc = 0.0f;
 #pragma unroll
                     for (int c4 = 0; c4 < ABP / 4; ++c4) {
@@ -791,6 +793,7 @@ int sweep_flow_blocks_per_sm(int ab, int threads, size_t smem, bool split, bool 
         DOCTORS_FLOW_OCC(3)
         DOCTORS_FLOW_OCC(6)
         DOCTORS_FLOW_OCC(10)
+        DOCTORS_FLOW_OCC(12)
         default: break;
     }
 #undef DOCTORS_FLOW_OCC
@@ -856,7 +859,8 @@ cudaError_t launch_split_sweep_m(const SweepArgs& a, cudaStream_t s, int* count)
 template <int M, int MODE>
 cudaError_t launch_sweep_flow_m(const SweepArgs& a, cudaStream_t s) {
     if (a.gcount <= 0) return cudaSuccess;
-    if (a.dir_table == nullptr || a.flow == nullptr || a.nab != 1) return cudaErrorInvalidValue;
+    if (a.dir_table == nullptr || a.flow == nullptr || a.blk < 0 || a.blk >= a.nab || a.ab * a.nab != a.A8)
+        return cudaErrorInvalidValue;
     const bool dd = a.dd != 0;
     int ntasks = 0;
     for (int st = 0; st < a.ntx + a.nty - 1; ++st) {
@@ -895,6 +899,7 @@ cudaError_t launch_sweep_flow_m(const SweepArgs& a, cudaStream_t s) {
         DOCTORS_FLOW_CASE(3)
         DOCTORS_FLOW_CASE(6)
         DOCTORS_FLOW_CASE(10)
+        DOCTORS_FLOW_CASE(12)
         default: return cudaErrorInvalidValue;
     }
 #undef DOCTORS_FLOW_CASE

@@ -169,12 +169,13 @@ def test_gradients_satisfy_euler_identity(env, kernel):
     d.close()
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 3, 4, 7])
 def test_adjoint_gradients_s16_direction_blocks(env, kernel):
-    """S16 (three blocks of 12 directions per octant): the chained (default)
-    and tile-stage kernels store and pair the angular fluence in 16-byte runs
-    of a voxel's directions; adjoint fluence and all gradients against the
-    oracle."""
+    """S16 (three blocks of 12 directions per octant): the tile-stage and
+    chained kernels store and pair the angular fluence in 16-byte runs of a
+    voxel's directions, the dataflow kernels (4, 7 and the default; one
+    launch per block) in one 12-float record per (voxel, octant, block);
+    adjoint fluence and all gradients against the oracle."""
     torch, C, DoctorsProblem = env
     p = ph.abdomen(nx=16, ny=14, nz=4, d=2.0, dz=2.0, G=2, sn=16, L=1)
     rng = np.random.default_rng(7)

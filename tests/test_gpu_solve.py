@@ -74,15 +74,29 @@ def test_ragged_multitile_cylinder(dp, cylinder_ref, tile, ab, kernel):
     d.close()
 
 
-@pytest.mark.parametrize("kernel", [1, 3])
-def test_abdomen_s16_multi_angle_block(dp, kernel):
+@pytest.mark.parametrize("kernel,tile", [(1, (0, 0)), (3, (0, 0)), (4, (0, 0)), (7, (0, 0)), (4, (5, 7)), (7, (16, 8))])
+def test_abdomen_s16_multi_angle_block(dp, kernel, tile):
     """Heterogeneous abdomen-like phantom, S16 (three direction blocks per
-    octant), P3, five materials."""
+    octant), P3, five materials: the stage and chained kernels, and the
+    dataflow kernels as one launch per block of 12 directions (ragged 5x7
+    tiles, a 16x8 face-warp tile)."""
     p = ph.abdomen(nx=32, ny=32, nz=6, d=1.0, dz=2.0, G=3, sn=16, L=3)
     sol = osv.solve(p, tol=1e-11)
-    d = dp(p, tol=1e-6, max_iters=400, sweep_kernel=kernel)
-    _compare(d, p, sol, f"abdomen S16 kernel={kernel}")
+    d = dp(p, tol=1e-6, max_iters=400, sweep_kernel=kernel, tile=tile)
+    _compare(d, p, sol, f"abdomen S16 kernel={kernel} tile={tile}")
     d.close()
+
+
+def test_s16_dataflow_block_checks(dp):
+    """S16 reaches the dataflow kernels only in blocks of 12 directions: other
+    blocks, and the split-transform kernels (whole octants only), are
+    rejected with DOCTORS_ERR_INVALID_ARG."""
+    from paper_1811_12391_gb300 import _lib as C
+    p = ph.abdomen(nx=8, ny=8, nz=2, d=1.0, dz=2.0, G=2, sn=16, L=1)
+    for kernel, ab in ((4, 6), (7, 9), (5, 12), (8, 12)):
+        with pytest.raises(C.DoctorsError) as e:
+            dp(p, tol=1e-6, max_iters=10, sweep_kernel=kernel, angles_per_block=ab)
+        assert e.value.code == C.DOCTORS_ERR_INVALID_ARG
 
 
 def test_sweep_kernels_agree(dp):
