@@ -90,7 +90,9 @@ typedef struct doctors_options {
     int max_iters;           /* source-iteration cap, >= 1 */
     int tile_x, tile_y;      /* sweep tile in voxels (0 = default: 8 x 8 for the dataflow sweep, else
                                 16 x 16); tile_x*tile_y <= 256 */
-    int angles_per_block;    /* directions per sweep block (0 = default); must divide N(N+2)/8 */
+    int angles_per_block;    /* directions per sweep block (0 = default: whole octants on the dataflow
+                                sweep, else the largest of 12, 10, 9, 7, ... dividing it); must divide
+                                N(N+2)/8; 36 (whole S16 octants) on the dataflow sweep only */
     int sweep_kernel;        /* 0 = default (the fastest measured: dataflow with a face warp (7) where
                                 it applies, else plain dataflow (4), else chained (3)),
                                 1 = CUDA-core transforms, one task (tile, octant, direction block,
@@ -98,9 +100,10 @@ typedef struct doctors_options {
                                 tasks of a stage back to back in one hyperplane pipeline,
                                 4 = dataflow: one launch per sweep, CTAs take tasks from a queue and
                                 wait (bounded) on their upstream tiles' face fluxes plane by plane;
-                                needs angles_per_block = N(N+2)/8 and N <= 8, or angles_per_block
-                                = 12 at S16 (one launch per block of 12 directions).  A wait that
-                                gives up makes the solve return DOCTORS_ERR_TIMEOUT,
+                                needs angles_per_block = N(N+2)/8 with N <= 8 or N = 16 (whole
+                                octants), or angles_per_block = 12 at S16 (one launch per block of
+                                12 directions).  A wait that gives up makes the solve return
+                                DOCTORS_ERR_TIMEOUT,
                                 5 = dataflow with the transforms split out: a pass turns the source
                                 moments into angular sources of all directions, the sweep reads and
                                 writes one angular record per cell, a pass turns the angular fluence
@@ -124,7 +127,8 @@ typedef struct doctors_options {
                                 psi = (q + 2 sum_d c_d psi_in,d) / (sigma_t + 2 sum_d c_d) and
                                 psi_out,d = 2 psi - psi_in,d, with no negative-flux fixup
                                 (c_d = |Omega_d| / delta_d).  Diamond differencing runs on the dataflow
-                                sweep only: sweep_kernel 0 or 4, angles_per_block = N(N+2)/8, N <= 8 */
+                                sweep only: sweep_kernel 0 or 4, angles_per_block = N(N+2)/8, N <= 8
+                                or N = 16 */
     int reserved[5];         /* must be zero */
 } doctors_options;
 

@@ -70,7 +70,9 @@ int dalloc_t(T** p, size_t count, const char* what) {
     return dalloc(reinterpret_cast<void**>(p), count * sizeof(T), what);
 }
 
-int default_ab(int A8) {
+int default_ab(int A8, int kernel) {
+    // the dataflow kernels (the default where they apply) sweep whole octants
+    if ((kernel == 0 || kernel == 4 || kernel == 7) && flow_octant_ab(A8)) return A8;
     const int cand[] = {12, 10, 9, 7, 6, 5, 4, 3, 2, 1};
     for (int c : cand)
         if (A8 % c == 0) return c;
@@ -607,8 +609,9 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
         set_error("tile_x * tile_y must be 1..256");
         return DOCTORS_ERR_INVALID_ARG;
     }
-    if (p->A8 % ab != 0 || !sweep_supported(ab, p->M)) {
-        set_error("angles_per_block must divide N(N+2)/8 and be one of 1,2,3,4,5,6,7,9,10,12");
+    if (p->A8 % ab != 0 || !(sweep_supported(ab, p->M) || flow_block_ab(p->A8, ab))) {
+        set_error("angles_per_block must divide N(N+2)/8 and be one of 1,2,3,4,5,6,7,9,10,12 "
+                  "(or 36 at S16, dataflow sweep only)");
         return DOCTORS_ERR_INVALID_ARG;
     }
     if (kernel < 0 || kernel > 8 || kernel == 2 || kernel == 6) {
@@ -616,7 +619,7 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
                   "on every workload)");
         return DOCTORS_ERR_INVALID_ARG;
     }
-    const bool whole_octant = p->A8 == ab && chain_const_table_ab(ab);
+    const bool whole_octant = p->A8 == ab && chain_const_table_ab(ab);   // S2..S8
     if ((kernel == 5 || kernel == 8) && !whole_octant) {
         set_error("the split dataflow sweeps (sweep_kernel 5, 8) need whole octants per CTA "
                   "(angles_per_block = N(N+2)/8) of S2, S4, S6 or S8");
@@ -624,7 +627,7 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
     }
     if ((kernel == 4 || kernel == 7) && !flow_block_ab(p->A8, ab)) {
         set_error("the dataflow sweep (sweep_kernel 4, 7) needs whole octants per CTA (angles_per_block = "
-                  "N(N+2)/8) of S2, S4, S6 or S8, or blocks of 12 directions (S16)");
+                  "N(N+2)/8) of S2, S4, S6, S8 or S16, or blocks of 12 directions (S16)");
         return DOCTORS_ERR_INVALID_ARG;
     }
     if (kernel == 7 && p->M % 4 != 0) {
@@ -646,15 +649,15 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
             set_error("diamond differencing runs on the dataflow sweep (sweep_kernel 0 or 4)");
             return DOCTORS_ERR_INVALID_ARG;
         }
-        if (!whole_octant) {
+        if (!(p->A8 == ab && flow_octant_ab(ab))) {
             set_error("diamond differencing needs the dataflow sweep: whole octants per CTA "
-                      "(angles_per_block = N(N+2)/8) of S2, S4, S6 or S8");
+                      "(angles_per_block = N(N+2)/8) of S2, S4, S6, S8 or S16");
             return DOCTORS_ERR_INVALID_ARG;
         }
         kernel = 4;
     }
     // the default (sweep_kernel 0) takes the dataflow kernels for whole octants
-    // of S2..S8 and for S16 in blocks of 12 directions
+    // of S2..S8 and S16 and for S16 in blocks of 12 directions
     const bool flow_ok = flow_block_ab(p->A8, ab);
     const bool use_split = kernel == 5 || kernel == 8 || (kernel == 0 && flow_ok && kDefaultSplitSweep);
     const bool split_tc = kernel == 8 && p->M == 16;
@@ -663,6 +666,10 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
     const bool hw = !dd && p->M % 4 == 0 && tx + ty <= 64 &&
                     (kernel == 7 || (kernel == 0 && use_flow && kDefaultFaceWarpSweep));
     const bool use_chain = !use_flow && !use_split && (kernel == 3 || (kernel == 0 && kDefaultChainedSweep));
+    if (!use_flow && !use_split && !sweep_supported(ab, p->M)) {
+        set_error("angles_per_block = 36 (whole S16 octants) runs on the dataflow sweep only (sweep_kernel 0, 4, 7)");
+        return DOCTORS_ERR_INVALID_ARG;
+    }
     const int ntx = (p->nx + tx - 1) / tx, nty = (p->ny + ty - 1) / ty;
     int chain_slots = 0, flow_slots = 0;
     size_t smem = 0;
@@ -824,7 +831,7 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     p->dirs = dirs; p->w = w;
     p->stream = (cudaStream_t)cuda_stream;
     p->differencing = opt->differencing;
-    p->ab = opt->angles_per_block > 0 ? opt->angles_per_block : default_ab(p->A8);
+    p->ab = opt->angles_per_block > 0 ? opt->angles_per_block : default_ab(p->A8, opt->sweep_kernel);
     // default tile: 8 x 8 for the dataflow sweep (whole octants of S2..S8,
     // S16 in blocks of 12), 16 x 16 for the stage kernels (the fastest measured shapes)
     const bool flow_default = opt->sweep_kernel >= 4 || p->differencing == DOCTORS_DIFF_DIAMOND ||
@@ -839,8 +846,12 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
         return code;
     };
     if (p->tx * p->ty > 256 || p->tx < 1 || p->ty < 1) return fail(DOCTORS_ERR_INVALID_ARG, "tile_x * tile_y must be 1..256");
-    if (p->A8 % p->ab != 0 || !sweep_supported(p->ab, p->M))
-        return fail(DOCTORS_ERR_INVALID_ARG, "angles_per_block must divide N(N+2)/8 and be one of 1,2,3,4,5,6,7,9,10,12");
+    if (p->A8 % p->ab != 0 || !(sweep_supported(p->ab, p->M) || flow_block_ab(p->A8, p->ab)))
+        return fail(DOCTORS_ERR_INVALID_ARG, "angles_per_block must divide N(N+2)/8 and be one of "
+                                             "1,2,3,4,5,6,7,9,10,12 (or 36 at S16, dataflow sweep only)");
+    if ((opt->sweep_kernel == 1 || opt->sweep_kernel == 3) && !sweep_supported(p->ab, p->M))
+        return fail(DOCTORS_ERR_INVALID_ARG,
+                    "angles_per_block = 36 (whole S16 octants) runs on the dataflow sweep only (sweep_kernel 0, 4, 7)");
     p->nab = p->A8 / p->ab;
     p->ntx = (p->nx + p->tx - 1) / p->tx;
     p->nty = (p->ny + p->ty - 1) / p->ty;
@@ -849,10 +860,10 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     if (opt->sweep_kernel == 2 || opt->sweep_kernel == 6)
         return fail(DOCTORS_ERR_INVALID_ARG, "sweep_kernel 2 and 6 are not offered (both measured slower on every workload)");
     if (p->differencing == DOCTORS_DIFF_DIAMOND &&
-        !((opt->sweep_kernel == 0 || opt->sweep_kernel == 4) && p->A8 == p->ab && chain_const_table_ab(p->ab)))
+        !((opt->sweep_kernel == 0 || opt->sweep_kernel == 4) && p->A8 == p->ab && flow_octant_ab(p->ab)))
         return fail(DOCTORS_ERR_INVALID_ARG,
                     "diamond differencing runs on the dataflow sweep: sweep_kernel 0 or 4, angles_per_block = "
-                    "N(N+2)/8 and N <= 8");
+                    "N(N+2)/8 and N <= 8 or N = 16");
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) return fail(DOCTORS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
 
@@ -1252,7 +1263,7 @@ int doctors_autotune(doctors_problem* p, doctors_tuning* out) {
     rc = first_collision(p);
     if (rc) return rc;
     const int tiles[][2] = {{16, 16}, {32, 8}, {16, 8}, {8, 16}, {8, 8}, {32, 4}, {16, 4}, {8, 4}, {4, 8}};
-    const int abs_c[] = {12, 10, 9, 7, 6, 5, 4, 3, 2, 1};
+    const int abs_c[] = {36, 12, 10, 9, 7, 6, 5, 4, 3, 2, 1};
     std::vector<int> abs_ok;
     for (int ab : abs_c)
         if (p->A8 % ab == 0 && (int)abs_ok.size() < 3) abs_ok.push_back(ab);
@@ -1267,6 +1278,7 @@ int doctors_autotune(doctors_problem* p, doctors_tuning* out) {
             for (int kernel = 1; kernel <= 8; ++kernel) {
                 if (p->differencing == DOCTORS_DIFF_DIAMOND && kernel != 4) continue;
                 if (kernel == 2 || kernel == 6) continue;
+                if ((kernel == 1 || kernel == 3) && !sweep_supported(ab, p->M)) continue;
                 if ((kernel == 5 || kernel == 8) && !(p->A8 == ab && chain_const_table_ab(ab))) continue;
                 if ((kernel == 4 || kernel == 7) && !flow_block_ab(p->A8, ab)) continue;
                 if (configure_sweep(p, t[0], t[1], ab, kernel) != DOCTORS_OK) continue;

@@ -2,8 +2,9 @@
 // k_sweep_chain (whole octants per CTA; the first octant's direction rows,
 // coefficients and moment tables are kernel parameters, read through the
 // constant bank at compile-time offsets) with the tile stages replaced by a
-// task queue in one launch.  S16 runs as three launches, one per block of
-// 12 directions of every octant, each with that block's table.
+// task queue in one launch.  S16 runs as whole octants (36 directions per
+// cell step), or as three launches, one per block of 12 directions of
+// every octant, each with that block's table.
 //
 // The tasks (tile, octant, group) are numbered stage by stage (the tile
 // diagonal of the octant's reflected tile grid).  Each CTA takes the next
@@ -68,7 +69,7 @@ __device__ __forceinline__ int flow_stage_tiles(int s, int ntx, int nty) {
 // differ, so they are kept in two planes (x: buf, y: bufy), and the face
 // records and the leakage carry the face fluxes, not the cell flux.
 template <int AB, int M, int MODE, bool SPLIT = false, bool DD = false, bool HW = false>
-__global__ void __launch_bounds__(HW ? 288 : 256, (!SPLIT && M % 4 == 0) ? 3 : 2)
+__global__ void __launch_bounds__(HW ? 288 : 256, AB > 12 ? 1 : ((!SPLIT && M % 4 == 0) ? 3 : 2))
     k_sweep_flow(const SweepArgs a, const ChainDirTable dt) {
     static_assert(!SPLIT || MODE == 0, "split transforms sweep in mode 0 only");
     static_assert(!DD || !SPLIT, "diamond differencing in the fused kernel only");
@@ -794,6 +795,7 @@ int sweep_flow_blocks_per_sm(int ab, int threads, size_t smem, bool split, bool 
         DOCTORS_FLOW_OCC(6)
         DOCTORS_FLOW_OCC(10)
         DOCTORS_FLOW_OCC(12)
+        DOCTORS_FLOW_OCC(36)
         default: break;
     }
 #undef DOCTORS_FLOW_OCC
@@ -900,6 +902,7 @@ cudaError_t launch_sweep_flow_m(const SweepArgs& a, cudaStream_t s) {
         DOCTORS_FLOW_CASE(6)
         DOCTORS_FLOW_CASE(10)
         DOCTORS_FLOW_CASE(12)
+        DOCTORS_FLOW_CASE(36)
         default: return cudaErrorInvalidValue;
     }
 #undef DOCTORS_FLOW_CASE

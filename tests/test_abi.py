@@ -90,12 +90,20 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib):
         C.DOCTORS_ERR_INVALID_ARG
     assert "differencing" in C.last_error()
     opt.differencing = C.DOCTORS_DIFF_DIAMOND
-    for kernel, sn in ((1, 4), (3, 4), (5, 4), (0, 16)):
-        opt.sweep_kernel, opt.sn_order = kernel, sn
+    # diamond differencing: dataflow kernels on whole octants only (S16 in blocks of 12 is refused)
+    for kernel, sn, ab in ((1, 4, 0), (3, 4, 0), (5, 4, 0), (0, 16, 12)):
+        opt.sweep_kernel, opt.sn_order, opt.angles_per_block = kernel, sn, ab
         assert C.doctors_create_problem(ctypes.byref(mesh), ctypes.byref(opt), None, ctypes.byref(h)) == \
             C.DOCTORS_ERR_INVALID_ARG
         assert "diamond" in C.last_error()
+    opt.angles_per_block = 0
     opt.differencing = C.DOCTORS_DIFF_STEP
+    for kernel in (1, 3):
+        # whole S16 octants run on the dataflow kernels only
+        opt.sweep_kernel, opt.sn_order, opt.angles_per_block = kernel, 16, 36
+        assert C.doctors_create_problem(ctypes.byref(mesh), ctypes.byref(opt), None, ctypes.byref(h)) == \
+            C.DOCTORS_ERR_INVALID_ARG
+    opt.angles_per_block = 0
     for kernel in (2, 6):
         # taken out (both measured slower than the kernels kept), rejected before any device call
         opt.sweep_kernel = kernel

@@ -169,13 +169,13 @@ def test_gradients_satisfy_euler_identity(env, kernel):
     d.close()
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 3, 4, 7])
-def test_adjoint_gradients_s16_direction_blocks(env, kernel):
-    """S16 (three blocks of 12 directions per octant): the tile-stage and
-    chained kernels store and pair the angular fluence in 16-byte runs of a
-    voxel's directions, the dataflow kernels (4, 7 and the default; one
-    launch per block) in one 12-float record per (voxel, octant, block);
-    adjoint fluence and all gradients against the oracle."""
+@pytest.mark.parametrize("kernel,ab", [(0, 0), (1, 12), (3, 12), (4, 12), (7, 12), (4, 36)])
+def test_adjoint_gradients_s16_direction_blocks(env, kernel, ab):
+    """S16: the tile-stage and chained kernels (blocks of 12 directions) store
+    and pair the angular fluence in 16-byte runs of a voxel's directions, the
+    dataflow kernels in one record per (voxel, octant, block) of 12
+    directions (one launch per block) or of the whole octant's 36 (the
+    default); adjoint fluence and all gradients against the oracle."""
     torch, C, DoctorsProblem = env
     p = ph.abdomen(nx=16, ny=14, nz=4, d=2.0, dz=2.0, G=2, sn=16, L=1)
     rng = np.random.default_rng(7)
@@ -183,7 +183,7 @@ def test_adjoint_gradients_s16_direction_blocks(env, kernel):
     roi = np.zeros(p.V)
     roi.reshape(p.nz, p.ny, p.nx)[1:3, 5:9, 5:9] = 1.0 / 32.0
     ref = osv.gradients(p, roi, tol=1e-12)
-    d = DoctorsProblem(p, tol=1e-6, max_iters=400, sweep_kernel=kernel, angles_per_block=12)
+    d = DoctorsProblem(p, tol=1e-6, max_iters=400, sweep_kernel=kernel, angles_per_block=ab)
     d.solve()
     r = osv.response_from_roi(p, roi)
     g = d.adjoint(torch.as_tensor(r, device="cuda"))

@@ -164,6 +164,19 @@ def test_diamond_full_size_cylinder(env):
     assert np.abs(sums[1] / sums[0] - 1).max() < 0.03
 
 
+@pytest.mark.parametrize("tile", [(8, 8), (5, 7)])
+def test_diamond_s16_whole_octants(env, tile):
+    """S16 P1 (36 directions per octant, one cell step for all of them),
+    heterogeneous abdomen, diamond differencing, against the oracle."""
+    torch, C, DoctorsProblem = env
+    p = ph.abdomen(nx=20, ny=18, nz=5, d=1.0, dz=2.0, G=2, sn=16, L=1)
+    p.differencing = 1
+    sol = osv.solve(p, tol=1e-11)
+    d = DoctorsProblem(p, tol=1e-6, max_iters=400, tile=tile)
+    _compare(d, p, sol, f"diamond S16 tile={tile}")
+    d.close()
+
+
 def test_diamond_option_checks(env):
     torch, C, DoctorsProblem = env
     p = ph.water_cylinder(nx=8, ny=8, nz=4, dx=2.0, dy=2.0, dz=2.0, diameter=12, G=2, sn=4, L=1)
@@ -174,8 +187,8 @@ def test_diamond_option_checks(env):
         assert ei.value.code == C.DOCTORS_ERR_INVALID_ARG
     q = ph.abdomen(nx=16, ny=16, nz=4, d=1.0, dz=2.0, G=2, sn=16, L=1)
     q.differencing = 1
-    with pytest.raises(C.DoctorsError) as ei:
-        DoctorsProblem(q, tol=1e-6, max_iters=10)
+    with pytest.raises(C.DoctorsError) as ei:     # S16 in blocks of 12: whole octants only
+        DoctorsProblem(q, tol=1e-6, max_iters=10, angles_per_block=12)
     assert ei.value.code == C.DOCTORS_ERR_INVALID_ARG
     p.differencing = 2
     with pytest.raises(C.DoctorsError) as ei:

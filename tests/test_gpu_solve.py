@@ -74,26 +74,34 @@ def test_ragged_multitile_cylinder(dp, cylinder_ref, tile, ab, kernel):
     d.close()
 
 
-@pytest.mark.parametrize("kernel,tile", [(1, (0, 0)), (3, (0, 0)), (4, (0, 0)), (7, (0, 0)), (4, (5, 7)), (7, (16, 8))])
-def test_abdomen_s16_multi_angle_block(dp, kernel, tile):
-    """Heterogeneous abdomen-like phantom, S16 (three direction blocks per
-    octant), P3, five materials: the stage and chained kernels, and the
-    dataflow kernels as one launch per block of 12 directions (ragged 5x7
-    tiles, a 16x8 face-warp tile)."""
+@pytest.fixture(scope="module")
+def s16_abdomen():
     p = ph.abdomen(nx=32, ny=32, nz=6, d=1.0, dz=2.0, G=3, sn=16, L=3)
-    sol = osv.solve(p, tol=1e-11)
-    d = dp(p, tol=1e-6, max_iters=400, sweep_kernel=kernel, tile=tile)
-    _compare(d, p, sol, f"abdomen S16 kernel={kernel} tile={tile}")
+    return p, osv.solve(p, tol=1e-11)
+
+
+@pytest.mark.parametrize("kernel,tile,ab", [(1, (0, 0), 0), (3, (0, 0), 0), (0, (0, 0), 0), (4, (0, 0), 36),
+                                            (7, (5, 7), 36), (7, (16, 8), 36), (4, (5, 7), 12), (7, (16, 8), 12)])
+def test_abdomen_s16_multi_angle_block(dp, s16_abdomen, kernel, tile, ab):
+    """Heterogeneous abdomen-like phantom, S16, P3, five materials: the stage
+    and chained kernels (three blocks of 12 directions per octant), the
+    dataflow kernels on whole octants (36 directions per cell step; the
+    default) and as one launch per block of 12 directions, on ragged 5x7 and
+    16x8 face-warp tiles."""
+    p, sol = s16_abdomen
+    d = dp(p, tol=1e-6, max_iters=400, sweep_kernel=kernel, tile=tile, angles_per_block=ab)
+    _compare(d, p, sol, f"abdomen S16 kernel={kernel} tile={tile} ab={ab}")
     d.close()
 
 
 def test_s16_dataflow_block_checks(dp):
-    """S16 reaches the dataflow kernels only in blocks of 12 directions: other
-    blocks, and the split-transform kernels (whole octants only), are
-    rejected with DOCTORS_ERR_INVALID_ARG."""
+    """S16 reaches the dataflow kernels as whole octants or in blocks of 12
+    directions: other blocks, whole octants on the stage and chained
+    kernels, and the split-transform kernels (S2..S8 only) are rejected with
+    DOCTORS_ERR_INVALID_ARG."""
     from paper_1811_12391_gb300 import _lib as C
     p = ph.abdomen(nx=8, ny=8, nz=2, d=1.0, dz=2.0, G=2, sn=16, L=1)
-    for kernel, ab in ((4, 6), (7, 9), (5, 12), (8, 12)):
+    for kernel, ab in ((4, 6), (7, 9), (5, 12), (8, 12), (5, 36), (1, 36), (3, 36)):
         with pytest.raises(C.DoctorsError) as e:
             dp(p, tol=1e-6, max_iters=10, sweep_kernel=kernel, angles_per_block=ab)
         assert e.value.code == C.DOCTORS_ERR_INVALID_ARG
