@@ -58,10 +58,10 @@ SWEEP_TRAFFIC = {
     (16, 16, 10, 1): (2246.4e6, "sweep_impl.cuh", "592eff4d10129e1bde8b55aecdf9fbf52f768e8c"),
     (16, 16, 5, 1): (1687.6e6, "sweep_impl.cuh", "592eff4d10129e1bde8b55aecdf9fbf52f768e8c"),
     (16, 8, 10, 3): (2534.9e6, "sweep_chain.cuh", "3502773d12d37fb58b50dbc1187553785b1df685"),
-    (8, 8, 10, 4): (3143.4e6, "sweep_flow.cuh", "1a74a4fb6b2cfaa26a20c6f6c71ea076fb240cd2"),
-    (16, 8, 10, 7): (2803.7e6, "sweep_flow.cuh", "1a74a4fb6b2cfaa26a20c6f6c71ea076fb240cd2"),
-    (8, 8, 10, 7): (2992.4e6, "sweep_flow.cuh", "1a74a4fb6b2cfaa26a20c6f6c71ea076fb240cd2"),
-    (16, 16, 10, 7): (2636.4e6, "sweep_flow.cuh", "1a74a4fb6b2cfaa26a20c6f6c71ea076fb240cd2"),
+    (8, 8, 10, 4): (3142.2e6, "sweep_flow.cuh", "a84c39f5d482ec32d8739ce528d0fc6ed21b177b"),
+    (16, 8, 10, 7): (2800.1e6, "sweep_flow.cuh", "a84c39f5d482ec32d8739ce528d0fc6ed21b177b"),
+    (8, 8, 10, 7): (2987.8e6, "sweep_flow.cuh", "a84c39f5d482ec32d8739ce528d0fc6ed21b177b"),
+    (16, 16, 10, 7): (2618.0e6, "sweep_flow.cuh", "a84c39f5d482ec32d8739ce528d0fc6ed21b177b"),
 }
 
 # sweep kernel by the library's sweep_kernel code
