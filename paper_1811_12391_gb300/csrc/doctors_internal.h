@@ -227,6 +227,9 @@ struct ChainDirTable {
     // moment) are adjacent kernel-parameter words
     float mop[kFlowMaxAB * 16], dop[16 * kFlowMaxAB];
 };
+// the dataflow and chained kernels take SweepArgs and the table by value: the
+// parameter block (up to 32764 bytes on this architecture) must hold both
+static_assert(sizeof(SweepArgs) + sizeof(ChainDirTable) < 32764, "kernel parameter block too large");
 // R_lm odd in x, y, z (bit lm)
 constexpr unsigned kOddX = (1u << 3) | (1u << 4) | (1u << 7) | (1u << 10) | (1u << 13) | (1u << 15);
 constexpr unsigned kOddY = (1u << 1) | (1u << 4) | (1u << 5) | (1u << 9) | (1u << 10) | (1u << 11);
