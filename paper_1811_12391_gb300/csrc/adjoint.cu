@@ -34,6 +34,21 @@ __device__ __forceinline__ void harmonics_scaled(float x, float y, float z, floa
     }
 }
 
+// a voxel's M moments as 16-byte vector loads (records are 16-byte aligned when M % 4 == 0)
+template <int M>
+__device__ __forceinline__ void load_record(const float* p, float (&t)[M]) {
+    if constexpr (M % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < M / 4; ++q) {
+            const float4 v4 = __ldg(reinterpret_cast<const float4*>(p) + q);
+            t[4 * q] = v4.x; t[4 * q + 1] = v4.y; t[4 * q + 2] = v4.z; t[4 * q + 3] = v4.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < M; ++q) t[q] = __ldg(p + q);
+    }
+}
+
 template <int M>
 __global__ void __launch_bounds__(256) k_source_grad(const SourceGradArgs a) {
     __shared__ double s_acc[kMaxG];
@@ -41,7 +56,11 @@ __global__ void __launch_bounds__(256) k_source_grad(const SourceGradArgs a) {
     __syncthreads();
     const size_t V = (size_t)a.nx * a.ny * a.nz;
     const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v < V) {
+    const bool in = v < V;
+    float R[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) R[m] = 0.0f;
+    if (in) {
         const int i = (int)(v % a.nx);
         const int j = (int)((v / a.nx) % a.ny);
         const int k = (int)(v / ((size_t)a.nx * a.ny));
@@ -49,20 +68,25 @@ __global__ void __launch_bounds__(256) k_source_grad(const SourceGradArgs a) {
         float y = a.oy + (j + 0.5f) * a.dy - a.sy;
         float z = a.oz + (k + 0.5f) * a.dz - a.sz;
         const float rn = rsqrtf(x * x + y * y + z * z);
-        float R[M];
         harmonics_scaled<M>(x * rn, y * rn, z * rn, R);
-        float h[kMaxMat];
+    }
+    float h[kMaxMat];
 #pragma unroll
-        for (int m = 0; m < kMaxMat; ++m) h[m] = 0.0f;
-        for (int g = 0; g < a.G; ++g) {
-            const float u = a.u[(size_t)g * V + v];
-            if (u == 0.0f) continue;
-            const float* t = a.T + ((size_t)g * V + v) * M;
+    for (int m = 0; m < kMaxMat; ++m) h[m] = 0.0f;
+    // per group: this voxel's term, summed over the warp by shuffles and added
+    // to the block's total by one shared-memory atomic per warp (every thread
+    // of the block takes part in every shuffle)
+    for (int g = 0; g < a.G; ++g) {
+        double term = 0.0;
+        const float u = in ? a.u[(size_t)g * V + v] : 0.0f;
+        if (u != 0.0f) {
+            float t[M];
+            load_record<M>(a.T + ((size_t)g * V + v) * M, t);
             float imp = 0.0f;
 #pragma unroll
             for (int pm = 0; pm < M; ++pm) imp = fmaf(R[lm_of_pos(pm, M)], t[pm], imp);
             const double impd = a.r[(size_t)g * V + v] + (double)imp;
-            atomicAdd(&s_acc[g], (double)u * impd);
+            term = (double)u * impd;
             if (a.H) {
                 const float w = (float)impd * __ldg(a.emit + g) * u;
 #pragma unroll
@@ -70,11 +94,14 @@ __global__ void __launch_bounds__(256) k_source_grad(const SourceGradArgs a) {
                     if (m < a.nmat) h[m] = fmaf(__ldg(a.sigt + m * a.G + g), w, h[m]);
             }
         }
-        if (a.H)
 #pragma unroll
-            for (int m = 0; m < kMaxMat; ++m)
-                if (m < a.nmat) a.H[(size_t)m * V + v] = h[m];
+        for (int off = 16; off > 0; off >>= 1) term += __shfl_down_sync(0xffffffffu, term, off);
+        if ((threadIdx.x & 31) == 0 && term != 0.0) atomicAdd(&s_acc[g], term);
     }
+    if (in && a.H)
+#pragma unroll
+        for (int m = 0; m < kMaxMat; ++m)
+            if (m < a.nmat) a.H[(size_t)m * V + v] = h[m];
     __syncthreads();
     for (int g = threadIdx.x; g < a.G; g += blockDim.x)
         if (s_acc[g] != 0.0) atomicAdd(a.acc + g, s_acc[g]);
