@@ -123,6 +123,8 @@ void free_problem(doctors_problem* p) {
         if (q) cudaFree(q);
     if (p->h_red) cudaFreeHost(p->h_red);
     if (p->h_acc) cudaFreeHost(p->h_acc);
+    if (p->d_acc_src) cudaFree(p->d_acc_src);
+    if (p->h_acc_src) cudaFreeHost(p->h_acc_src);
     for (auto& e : p->ev)
         if (e) cudaEventDestroy(e);
 }
@@ -1380,6 +1382,27 @@ int ensure_adjoint_buffers(doctors_problem* p, bool density) {
             return DOCTORS_ERR_OOM;
         }
     }
+    // per-source sums of the view-weight and spectrum terms, read back once
+    const size_t na = std::max<size_t>(1, p->srcs.size()) * p->G;
+    if (p->acc_src_cap < na) {
+        if (p->d_acc_src) {
+            CU(cudaStreamSynchronize(p->stream));
+            cudaFree(p->d_acc_src);
+            p->d_acc_src = nullptr;
+        }
+        if (p->h_acc_src) cudaFreeHost(p->h_acc_src);
+        p->h_acc_src = nullptr;
+        p->acc_src_cap = 0;
+        rc = dalloc_t(&p->d_acc_src, na, "per-source gradient sums");
+        if (rc) return rc;
+        if (cudaMallocHost(&p->h_acc_src, na * sizeof(double)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            p->h_acc_src = nullptr;
+            set_error("pinned host allocation failed");
+            return DOCTORS_ERR_OOM;
+        }
+        p->acc_src_cap = na;
+    }
     return DOCTORS_OK;
 }
 
@@ -1468,11 +1491,14 @@ int adjoint_impl(doctors_problem* p, const double* response, int mem, const RoiT
     // 6. per-source view-weight, spectrum and ray terms
     std::vector<double> gw(p->srcs.size(), 0.0), gs(p->G, 0.0);
     if (density) CU(cudaMemsetAsync(p->d_grad, 0, p->V * sizeof(double), p->stream));
-    bool have_z00 = false;
+    // the point sources' sums stay on the device until all are done (one
+    // readback, no host round trip per source)
+    CU(cudaMemsetAsync(p->d_acc_src, 0, p->srcs.size() * (size_t)p->G * sizeof(double), p->stream));
+    bool have_z00 = false, any_point = false;
     for (size_t s = 0; s < p->srcs.size(); ++s) {
         const doctors_source& src = p->srcs[s];
-        CU(cudaMemsetAsync(p->d_acc, 0, 2 * (size_t)p->G * sizeof(double), p->stream));
         if (src.kind == DOCTORS_SRC_VOLUME) {
+            CU(cudaMemsetAsync(p->d_acc, 0, 2 * (size_t)p->G * sizeof(double), p->stream));
             // J depends on a volume source through <q00 / (4 pi), Z00>
             if (!have_z00) {
                 CU(launch_sum00(p->V, p->G, p->M, p->d_Z, p->d_acc + p->G, p->stream));
@@ -1489,9 +1515,7 @@ int adjoint_impl(doctors_problem* p, const double* response, int mem, const RoiT
             }
             continue;
         }
-        std::vector<float> emit(p->G);
-        for (int g = 0; g < p->G; ++g) emit[g] = (float)(src.weight * p->spectra[s][g]);
-        CU(cudaMemcpyAsync(p->d_iso, emit.data(), p->G * sizeof(float), cudaMemcpyHostToDevice, p->stream));
+        any_point = true;
         RayArgs ra = ray_args(p, src, p->d_ones);
         ra.phi_tot = nullptr;
         CU(launch_raytrace(ra, p->stream));
@@ -1500,19 +1524,27 @@ int adjoint_impl(doctors_problem* p, const double* response, int mem, const RoiT
         ga.nx = p->nx; ga.ny = p->ny; ga.nz = p->nz; ga.G = p->G; ga.M = p->M; ga.nmat = p->nmat;
         ga.ox = ra.ox; ga.oy = ra.oy; ga.oz = ra.oz; ga.dx = ra.dx; ga.dy = ra.dy; ga.dz = ra.dz;
         ga.sx = ra.sx; ga.sy = ra.sy; ga.sz = ra.sz;
-        ga.r = p->d_r; ga.T = p->d_T; ga.u = p->d_phiu_src; ga.emit = p->d_iso; ga.sigt = p->d_sigt;
-        ga.acc = p->d_acc; ga.H = density ? p->d_H : nullptr;
+        // emission w_s chi_g of this source: the forward solve's table
+        ga.r = p->d_r; ga.T = p->d_T; ga.u = p->d_phiu_src; ga.emit = p->d_emit_all + s * p->G; ga.sigt = p->d_sigt;
+        ga.acc = p->d_acc_src + s * p->G; ga.H = density ? p->d_H : nullptr;
         CU(launch_source_grad(ga, p->stream));
         ++p->launches;
         if (density) {
             CU(launch_backproject(ra, p->d_H, p->d_grad, p->stream));
             ++p->launches;
         }
-        CU(cudaMemcpyAsync(p->h_acc, p->d_acc, (size_t)p->G * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    }
+    if (any_point) {
+        CU(cudaMemcpyAsync(p->h_acc_src, p->d_acc_src, p->srcs.size() * (size_t)p->G * sizeof(double),
+                           cudaMemcpyDeviceToHost, p->stream));
         CU(cudaStreamSynchronize(p->stream));
-        for (int g = 0; g < p->G; ++g) {
-            gw[s] += p->spectra[s][g] * p->h_acc[g];
-            gs[g] += src.weight * p->h_acc[g];
+        for (size_t s = 0; s < p->srcs.size(); ++s) {
+            if (p->srcs[s].kind == DOCTORS_SRC_VOLUME) continue;
+            const double* acc = p->h_acc_src + s * p->G;
+            for (int g = 0; g < p->G; ++g) {
+                gw[s] += p->spectra[s][g] * acc[g];
+                gs[g] += p->srcs[s].weight * acc[g];
+            }
         }
     }
     // 7. collision and scattering terms of the density gradient

@@ -391,6 +391,9 @@ struct doctors_problem {
     float* d_psi = nullptr;        // stored forward angular fluence ([G][V][A], or the dataflow layout)
     float* d_prod = nullptr;       // [G][V] angular product
     double* h_acc = nullptr;       // pinned [2G]
+    double* d_acc_src = nullptr;   // [S][G] per-source gradient sums (adjoint)
+    double* h_acc_src = nullptr;   // pinned copy of it
+    size_t acc_src_cap = 0;        // doubles in both
     // region-of-interest dose (allocated on first use)
     double* d_k = nullptr;         // [kMaxMat][G] dose factors
     double* d_roi = nullptr;       // [V] ROI weights (staged from host memory)
