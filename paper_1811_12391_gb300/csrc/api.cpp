@@ -118,7 +118,7 @@ void free_problem(doctors_problem* p) {
                     p->d_emit, p->d_iso, p->d_xface, p->d_yface, p->d_red,
                     p->d_Z, p->d_Qa, p->d_T, p->d_rf, p->d_r, p->d_acc, p->d_grad, p->d_H,
                     p->d_ones, p->d_psi, p->d_prod, p->d_flow, p->d_qang, p->d_pang,
-                    p->d_k, p->d_roi, p->d_part, p->d_tcb, p->d_emit_all, p->d_dose_stage};
+                    p->d_k, p->d_roi, p->d_part, p->d_tcb, p->d_emit_all, p->d_dose_stage, p->d_sig};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (p->h_red) cudaFreeHost(p->h_red);
@@ -261,6 +261,7 @@ SweepArgs sweep_args(const doctors_problem* p, int reverse, const float* src, fl
     a.tc_b2 = (p->use_split && p->split_tc) ? p->d_tcb + p->tcb1_floats : nullptr;
     a.dd = p->differencing == DOCTORS_DIFF_DIAMOND ? 1 : 0;
     a.blk = 0;
+    a.sig = p->d_sig;
     return a;
 }
 
@@ -907,6 +908,7 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     rc = rc ? rc : dalloc_t(&p->d_coef, coef.size(), "tables");
     rc = rc ? rc : dalloc_t(&p->d_mat, p->V, "materials");
     rc = rc ? rc : dalloc_t(&p->d_rho, p->V, "densities");
+    rc = rc ? rc : dalloc_t(&p->d_sig, (size_t)p->G * p->V, "total cross sections per cell");
     rc = rc ? rc : dalloc_t(&p->d_sigt, (size_t)kMaxMat * p->G, "sigma_t");
     rc = rc ? rc : dalloc_t(&p->d_sigs, (size_t)kMaxMat * (p->L + 1) * p->G * p->G, "sigma_s");
     rc = rc ? rc : dalloc_t(&p->d_phiu_src, GV, "uncollided (source)");
@@ -982,6 +984,7 @@ int doctors_set_materials(doctors_problem* p, int n_mat, const uint8_t* mat, con
     CU(cudaMemcpyAsync(p->d_rho, hr.data(), p->V * sizeof(float), cudaMemcpyHostToDevice, p->stream));
     CU(cudaMemcpyAsync(p->d_sigt, st.data(), st.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream));
     CU(cudaMemcpyAsync(p->d_sigs, ss.data(), ss.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream));
+    CU(launch_total_xs(p->V, G, p->d_mat, p->d_rho, p->d_sigt, p->d_sig, p->stream));
     CU(cudaStreamSynchronize(p->stream));
     p->nmat = n_mat;
     p->h_sigt.assign(sigma_t, sigma_t + (size_t)n_mat * G);

@@ -131,6 +131,9 @@ cudaError_t launch_residual(size_t V, int G, int M, const float* mom, float* pre
                             const int* win = nullptr);
 // zero groups [win[0], win[1]) of a [G][per_group] float array unless *skip
 cudaError_t launch_zero_window(float* p, size_t per_group, int G, const int* win, const int* skip, cudaStream_t s);
+// out[g][v] = rho[v] * sigt[mat[v]][g] (FP32, the product the sweep forms)
+cudaError_t launch_total_xs(size_t V, int G, const uint8_t* mat, const float* rho, const float* sigt, float* out,
+                            cudaStream_t s);
 cudaError_t launch_zero_window(double* p, size_t per_group, int G, const int* win, const int* skip, cudaStream_t s);
 // zero n floats (or doubles) unless *skip
 cudaError_t launch_zero(float* p, size_t n, const int* skip, cudaStream_t s);
@@ -203,6 +206,7 @@ struct SweepArgs {
     int dd;                            // dataflow kernel: 1 = diamond differencing (dir_table holds 2c), 0 = step
     int blk;                           // dataflow kernel: the direction block this launch sweeps (0 .. nab-1;
                                        // dir_table holds that block's rows)
+    const float* sig;                  // dataflow kernel: [G][V] rho sigma_t of every cell and group
     int* flow;                         // non-null: dataflow kernel; [0] task queue, [1] CTAs done, [2] wait timed out,
                                        // [3] test hook: task + 1 that writes no faces (0: none)
 };
@@ -393,6 +397,7 @@ struct doctors_problem {
     double* h_acc = nullptr;       // pinned [2G]
     double* d_acc_src = nullptr;   // [S][G] per-source gradient sums (adjoint)
     double* h_acc_src = nullptr;   // pinned copy of it
+    float* d_sig = nullptr;        // [G][V] rho * sigma_t per cell and group (the dataflow sweep's one load)
     size_t acc_src_cap = 0;        // doubles in both
     // region-of-interest dose (allocated on first use)
     double* d_k = nullptr;         // [kMaxMat][G] dose factors

@@ -367,6 +367,16 @@ __device__ __forceinline__ void block_reduce_add(double (&x)[NV], double* dst) {
 // is compared against tolerances of 1e-6 and above); the passes, the threads
 // and the blocks are summed in FP64, so that few FP64 operations are issued:
 // their rate on this part is a small fraction of the FP32 rate.
+// rho sigma_t of every cell and group, the product the sweep would form per cell step
+__global__ void __launch_bounds__(256) k_total_xs(size_t V, int G, const uint8_t* mat, const float* rho,
+                                                  const float* sigt, float* out) {
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (size_t)gridDim.x * blockDim.x) {
+        const float r = rho[v];
+        const int m = mat[v];
+        for (int g = 0; g < G; ++g) out[(size_t)g * V + v] = r * __ldg(sigt + m * G + g);
+    }
+}
+
 __global__ void __launch_bounds__(256) k_residual(size_t V, int M, const float* mom, float* prev,
                                                   double* res, const int* skip, int g0, const int* win) {
     if (skip && *skip) return;
@@ -560,6 +570,12 @@ cudaError_t launch_residual(size_t V, int G, int M, const float* mom, float* pre
     // sixteen voxels per thread (four passes)
     dim3 grid(blocks_for((V + 15) / 16, 256, 152), gcount < 0 ? G : gcount);
     k_residual<<<grid, 256, 0, s>>>(V, M, mom, prev, res, skip, g0, win);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_total_xs(size_t V, int G, const uint8_t* mat, const float* rho, const float* sigt, float* out,
+                            cudaStream_t s) {
+    k_total_xs<<<blocks_for(V, 256, 152 * 16), 256, 0, s>>>(V, G, mat, rho, sigt, out);
     return cudaGetLastError();
 }
 

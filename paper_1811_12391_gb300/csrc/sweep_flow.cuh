@@ -76,6 +76,13 @@ __global__ void __launch_bounds__(HW ? 288 : 256, AB > 12 ? 1 : ((!SPLIT && M % 
     static_assert(!HW || MODE == 0, "the face warp serves the mode-0 sweep");
     constexpr int ABP = flow_abp(AB);
     constexpr int RS = AB | 1;                // a column's record of fluxes (odd length)
+    // Total cross section of a cell: in the plain and split step-differenced
+    // kernels one load from the per-cell table a.sig (rho sigma_t of every cell
+    // and group, formed when the materials are set: one memory request per cell
+    // step fewer, 5-7 % per sweep); the face-warp and diamond kernels keep the
+    // density and material loads and the staged table (with the table load they
+    // spill: the face warp's 72 registers at three 288-thread CTAs per SM)
+    constexpr bool XS = !HW && !DD;
     // pipeline depths: face records are fetched PD steps before the step
     // that uses them, source values PDS steps (the split sweep's steps are
     // short, so one step does not cover the memory latency)
@@ -106,8 +113,9 @@ __global__ void __launch_bounds__(HW ? 288 : 256, AB > 12 ? 1 : ((!SPLIT && M % 
         g0 = a.win[0];
         gcount = a.win[1] - a.win[0];
     }
-    for (int e = threadIdx.x; e < gcount * a.nmat; e += blockDim.x)
-        sigt_s[e] = a.sigt[(e % a.nmat) * a.G + g0 + e / a.nmat];
+    if constexpr (!XS)   // rho sigma_t formed from the staged table
+        for (int e = threadIdx.x; e < gcount * a.nmat; e += blockDim.x)
+            sigt_s[e] = a.sigt[(e % a.nmat) * a.G + g0 + e / a.nmat];
     for (int e = threadIdx.x; e < gcount; e += blockDim.x) leak_s[e] = 0.0;
     for (int e = threadIdx.x; e < (DD ? 4 : 2) * P * RS; e += blockDim.x) buf[e] = 0.0f;
 
@@ -153,8 +161,8 @@ __global__ void __launch_bounds__(HW ? 288 : 256, AB > 12 ? 1 : ((!SPLIT && M % 
     float sn[SMEMPF ? 1 : NS], sn2[PDS == 2 ? NS : 1];   // next cell; the cell after (depth 2)
 #pragma unroll
     for (int m = 0; m < (SMEMPF ? 1 : NS); ++m) sn[m] = 0.0f;
-    float rho_n = 0.0f, rho_n2 = 0.0f;        // density and material of the prefetched cells: the cross
-    int mat_n = 0, mat_n2 = 0;                // section is looked up when the cell is swept, not at the load
+    float rho_n = 0.0f, rho_n2 = 0.0f;        // density (XS: rho sigma_t) and material of the prefetched
+    int mat_n = 0, mat_n2 = 0;                // cells; the cross section is formed when the cell is swept
     float zc[AB];                             // z inflow of the column's next cell
     float lk = 0.0f;
 
@@ -224,8 +232,13 @@ __global__ void __launch_bounds__(HW ? 288 : 256, AB > 12 ? 1 : ((!SPLIT && M % 
 #pragma unroll
                 for (int m = 0; m < M; ++m) dst[m] = tmp[m];
             }
-            rho = __ldg(a.rho + v);
-            mt = __ldg(a.mat + v);
+            if constexpr (XS) {
+                rho = __ldg(a.sig + gV + v);
+                (void)mt;
+            } else {
+                rho = __ldg(a.rho + v);
+                mt = __ldg(a.mat + v);
+            }
         };
         // register path: the cell after the one in (sn, rho_n, mat_n) moves up,
         // plane kn is fetched behind it
@@ -365,7 +378,7 @@ __global__ void __launch_bounds__(HW ? 288 : 256, AB > 12 ? 1 : ((!SPLIT && M % 
                 // commit group, ahead of the face records of this step)
                 const int kr0 = h - d;
                 if (col && kr0 >= 0 && kr0 < a.nz) {
-                    sig_cur = rho_n * sigt_s[gi * a.nmat + mat_n];
+                    sig_cur = XS ? rho_n : rho_n * sigt_s[gi * a.nmat + mat_n];
                     if (kr0 + 1 < a.nz) fetch(kr0 + 1, sn, rho_n, mat_n);
                 }
                 asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -383,7 +396,7 @@ __global__ void __launch_bounds__(HW ? 288 : 256, AB > 12 ? 1 : ((!SPLIT && M % 
 #pragma unroll
                         for (int m = 0; m < NS; ++m) sn[m] *= octant_sign<M>(m, fx, fy, fz);
                     }
-                    sig_reg = rho_n * sigt_s[gi * a.nmat + mat_n];
+                    sig_reg = XS ? rho_n : rho_n * sigt_s[gi * a.nmat + mat_n];
                 }
                 float sreg[SMEMPF ? 1 : NS];
                 if constexpr (!SMEMPF) {
@@ -807,7 +820,8 @@ template <int M>
 cudaError_t launch_split_sweep_m(const SweepArgs& a, cudaStream_t s, int* count) {
     *count = 0;
     if (a.gcount <= 0) return cudaSuccess;
-    if (a.dir_table == nullptr || a.flow == nullptr || a.nab != 1 || !a.qang || !a.pang) return cudaErrorInvalidValue;
+    if (a.dir_table == nullptr || a.flow == nullptr || a.sig == nullptr || a.nab != 1 || !a.qang || !a.pang)
+        return cudaErrorInvalidValue;
     const size_t V = (size_t)a.nx * a.ny * a.nz;
     const size_t n = (size_t)a.gcount * V;
     const unsigned tgrid = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 8);
@@ -861,7 +875,8 @@ cudaError_t launch_split_sweep_m(const SweepArgs& a, cudaStream_t s, int* count)
 template <int M, int MODE>
 cudaError_t launch_sweep_flow_m(const SweepArgs& a, cudaStream_t s) {
     if (a.gcount <= 0) return cudaSuccess;
-    if (a.dir_table == nullptr || a.flow == nullptr || a.blk < 0 || a.blk >= a.nab || a.ab * a.nab != a.A8)
+    if (a.dir_table == nullptr || a.flow == nullptr || a.sig == nullptr || a.blk < 0 || a.blk >= a.nab ||
+        a.ab * a.nab != a.A8)
         return cudaErrorInvalidValue;
     const bool dd = a.dd != 0;
     int ntasks = 0;
