@@ -85,6 +85,7 @@ int default_ab(int A8, int kernel) {
 // stores 2 c (the dataflow kernel's cell solve then has the step form).
 ChainDirTable make_dir_table(const doctors_problem* p, int j0, int n) {
     ChainDirTable t{};
+    t.sig = p->d_sig;
     const double dx = p->mesh.dx, dy = p->mesh.dy, dz = p->mesh.dz;
     const float cf = p->differencing == DOCTORS_DIFF_DIAMOND ? 2.0f : 1.0f;
     double Rb[16];
@@ -261,7 +262,6 @@ SweepArgs sweep_args(const doctors_problem* p, int reverse, const float* src, fl
     a.tc_b2 = (p->use_split && p->split_tc) ? p->d_tcb + p->tcb1_floats : nullptr;
     a.dd = p->differencing == DOCTORS_DIFF_DIAMOND ? 1 : 0;
     a.blk = 0;
-    a.sig = p->d_sig;
     return a;
 }
 
@@ -920,6 +920,7 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     rc = rc ? rc : dalloc_t(&p->d_src2, GVM, "sweep source (next iteration)");
     rc = rc ? rc : dalloc_t(&p->d_prev, GV, "previous scalar fluence");
     rc = rc ? rc : dalloc_t(&p->d_iso, (size_t)p->G, "volume source");
+    p->dir_table.sig = p->d_sig;   // the whole-octant table also carries the per-cell cross sections
     rc = rc ? rc : configure_sweep(p, p->tx, p->ty, p->ab, opt->sweep_kernel);
     rc = rc ? rc : dalloc_t(&p->d_red, 5 * (size_t)p->G, "reductions");
     if (rc) return fail(rc, "");

@@ -206,7 +206,6 @@ struct SweepArgs {
     int dd;                            // dataflow kernel: 1 = diamond differencing (dir_table holds 2c), 0 = step
     int blk;                           // dataflow kernel: the direction block this launch sweeps (0 .. nab-1;
                                        // dir_table holds that block's rows)
-    const float* sig;                  // dataflow kernel: [G][V] rho sigma_t of every cell and group
     int* flow;                         // non-null: dataflow kernel; [0] task queue, [1] CTAs done, [2] wait timed out,
                                        // [3] test hook: task + 1 that writes no faces (0: none)
 };
@@ -230,6 +229,9 @@ struct ChainDirTable {
     // packed two-lane FMA (two moments of one direction, two directions of one
     // moment) are adjacent kernel-parameter words
     float mop[kFlowMaxAB * 16], dop[16 * kFlowMaxAB];
+    // the problem's [G][V] rho sigma_t of every cell and group (dataflow kernels);
+    // last, so that the tables above keep their parameter offsets
+    const float* sig;
 };
 // the dataflow and chained kernels take SweepArgs and the table by value: the
 // parameter block (up to 32764 bytes on this architecture) must hold both

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(HW ? 288 : 256, AB > 12 ? 1 : ((!SPLIT && M % 
     constexpr int ABP = flow_abp(AB);
     constexpr int RS = AB | 1;                // a column's record of fluxes (odd length)
     // Total cross section of a cell: in the plain and split step-differenced
-    // kernels one load from the per-cell table a.sig (rho sigma_t of every cell
+    // kernels one load from the per-cell table dt.sig (rho sigma_t of every cell
     // and group, formed when the materials are set: one memory request per cell
     // step fewer, 5-7 % per sweep); the face-warp and diamond kernels keep the
     // density and material loads and the staged table (with the table load they
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(HW ? 288 : 256, AB > 12 ? 1 : ((!SPLIT && M % 
                 for (int m = 0; m < M; ++m) dst[m] = tmp[m];
             }
             if constexpr (XS) {
-                rho = __ldg(a.sig + gV + v);
+                rho = __ldg(dt.sig + gV + v);
                 (void)mt;
             } else {
                 rho = __ldg(a.rho + v);
@@ -820,7 +820,8 @@ template <int M>
 cudaError_t launch_split_sweep_m(const SweepArgs& a, cudaStream_t s, int* count) {
     *count = 0;
     if (a.gcount <= 0) return cudaSuccess;
-    if (a.dir_table == nullptr || a.flow == nullptr || a.sig == nullptr || a.nab != 1 || !a.qang || !a.pang)
+    if (a.dir_table == nullptr || a.flow == nullptr || a.dir_table->sig == nullptr || a.nab != 1 || !a.qang ||
+        !a.pang)
         return cudaErrorInvalidValue;
     const size_t V = (size_t)a.nx * a.ny * a.nz;
     const size_t n = (size_t)a.gcount * V;
@@ -875,7 +876,7 @@ cudaError_t launch_split_sweep_m(const SweepArgs& a, cudaStream_t s, int* count)
 template <int M, int MODE>
 cudaError_t launch_sweep_flow_m(const SweepArgs& a, cudaStream_t s) {
     if (a.gcount <= 0) return cudaSuccess;
-    if (a.dir_table == nullptr || a.flow == nullptr || a.sig == nullptr || a.blk < 0 || a.blk >= a.nab ||
+    if (a.dir_table == nullptr || a.flow == nullptr || a.dir_table->sig == nullptr || a.blk < 0 || a.blk >= a.nab ||
         a.ab * a.nab != a.A8)
         return cudaErrorInvalidValue;
     const bool dd = a.dd != 0;
