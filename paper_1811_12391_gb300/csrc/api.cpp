@@ -835,8 +835,9 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     p->stream = (cudaStream_t)cuda_stream;
     p->differencing = opt->differencing;
     p->ab = opt->angles_per_block > 0 ? opt->angles_per_block : default_ab(p->A8, opt->sweep_kernel);
-    // default tile: 8 x 8 for the dataflow sweep (whole octants of S2..S8,
-    // S16 in blocks of 12), 16 x 16 for the stage kernels (the fastest measured shapes)
+    // default tile: 8 x 8 for the dataflow sweep (whole octants of S2..S8 and
+    // S16, or S16 in blocks of 12), 16 x 16 for the stage kernels (the fastest
+    // measured shapes)
     const bool flow_default = opt->sweep_kernel >= 4 || p->differencing == DOCTORS_DIFF_DIAMOND ||
                               (opt->sweep_kernel == 0 && kDefaultDataflowSweep && flow_block_ab(p->A8, p->ab));
     const int tdef = flow_default ? 8 : 16;
