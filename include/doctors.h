@@ -92,7 +92,7 @@ typedef struct doctors_options {
                                 16 x 16); tile_x*tile_y <= 256 */
     int angles_per_block;    /* directions per sweep block (0 = default: whole octants on the dataflow
                                 sweep, else the largest of 12, 10, 9, 7, ... dividing it); must divide
-                                N(N+2)/8; 36 (whole S16 octants) on the dataflow sweep only */
+                                N(N+2)/8; 21 and 36 (whole S12, S16 octants) on the dataflow sweep only */
     int sweep_kernel;        /* 0 = default (the fastest measured: dataflow with a face warp (7) where
                                 it applies, else plain dataflow (4), else chained (3)),
                                 1 = CUDA-core transforms, one task (tile, octant, direction block,
@@ -100,7 +100,7 @@ typedef struct doctors_options {
                                 tasks of a stage back to back in one hyperplane pipeline,
                                 4 = dataflow: one launch per sweep, CTAs take tasks from a queue and
                                 wait (bounded) on their upstream tiles' face fluxes plane by plane;
-                                needs angles_per_block = N(N+2)/8 with N <= 8 or N = 16 (whole
+                                needs angles_per_block = N(N+2)/8 with N <= 8, 12 or 16 (whole
                                 octants), or angles_per_block = 12 at S16 (one launch per block of
                                 12 directions).  A wait that gives up makes the solve return
                                 DOCTORS_ERR_TIMEOUT,
@@ -128,7 +128,7 @@ typedef struct doctors_options {
                                 psi_out,d = 2 psi - psi_in,d, with no negative-flux fixup
                                 (c_d = |Omega_d| / delta_d).  Diamond differencing runs on the dataflow
                                 sweep only: sweep_kernel 0 or 4, angles_per_block = N(N+2)/8, N <= 8
-                                or N = 16 */
+                                or N = 12, 16 */
     int reserved[5];         /* must be zero */
 } doctors_options;
 

@@ -614,7 +614,7 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
     }
     if (p->A8 % ab != 0 || !(sweep_supported(ab, p->M) || flow_block_ab(p->A8, ab))) {
         set_error("angles_per_block must divide N(N+2)/8 and be one of 1,2,3,4,5,6,7,9,10,12 "
-                  "(or 36 at S16, dataflow sweep only)");
+                  "(or 21 at S12, 36 at S16: whole octants, dataflow sweep only)");
         return DOCTORS_ERR_INVALID_ARG;
     }
     if (kernel < 0 || kernel > 8 || kernel == 2 || kernel == 6) {
@@ -630,7 +630,7 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
     }
     if ((kernel == 4 || kernel == 7) && !flow_block_ab(p->A8, ab)) {
         set_error("the dataflow sweep (sweep_kernel 4, 7) needs whole octants per CTA (angles_per_block = "
-                  "N(N+2)/8) of S2, S4, S6, S8 or S16, or blocks of 12 directions (S16)");
+                  "N(N+2)/8) of S2, S4, S6, S8, S12 or S16, or blocks of 12 directions (S16)");
         return DOCTORS_ERR_INVALID_ARG;
     }
     if (kernel == 7 && p->M % 4 != 0) {
@@ -654,13 +654,13 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
         }
         if (!(p->A8 == ab && flow_octant_ab(ab))) {
             set_error("diamond differencing needs the dataflow sweep: whole octants per CTA "
-                      "(angles_per_block = N(N+2)/8) of S2, S4, S6, S8 or S16");
+                      "(angles_per_block = N(N+2)/8) of S2, S4, S6, S8, S12 or S16");
             return DOCTORS_ERR_INVALID_ARG;
         }
         kernel = 4;
     }
     // the default (sweep_kernel 0) takes the dataflow kernels for whole octants
-    // of S2..S8 and S16 and for S16 in blocks of 12 directions
+    // of S2..S8, S12 and S16 and for S16 in blocks of 12 directions
     const bool flow_ok = flow_block_ab(p->A8, ab);
     const bool use_split = kernel == 5 || kernel == 8 || (kernel == 0 && flow_ok && kDefaultSplitSweep);
     const bool split_tc = kernel == 8 && p->M == 16;
@@ -670,7 +670,8 @@ int configure_sweep(doctors_problem* p, int tx, int ty, int ab, int kernel) {
                     (kernel == 7 || (kernel == 0 && use_flow && kDefaultFaceWarpSweep));
     const bool use_chain = !use_flow && !use_split && (kernel == 3 || (kernel == 0 && kDefaultChainedSweep));
     if (!use_flow && !use_split && !sweep_supported(ab, p->M)) {
-        set_error("angles_per_block = 36 (whole S16 octants) runs on the dataflow sweep only (sweep_kernel 0, 4, 7)");
+        set_error("whole S12 or S16 octants (angles_per_block 21, 36) run on the dataflow sweep only "
+                  "(sweep_kernel 0, 4, 7)");
         return DOCTORS_ERR_INVALID_ARG;
     }
     const int ntx = (p->nx + tx - 1) / tx, nty = (p->ny + ty - 1) / ty;
@@ -836,7 +837,7 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     p->differencing = opt->differencing;
     p->ab = opt->angles_per_block > 0 ? opt->angles_per_block : default_ab(p->A8, opt->sweep_kernel);
     // default tile: 8 x 8 for the dataflow sweep (whole octants of S2..S8 and
-    // S16, or S16 in blocks of 12), 16 x 16 for the stage kernels (the fastest
+    // S12, S16, or S16 in blocks of 12), 16 x 16 for the stage kernels (the fastest
     // measured shapes)
     const bool flow_default = opt->sweep_kernel >= 4 || p->differencing == DOCTORS_DIFF_DIAMOND ||
                               (opt->sweep_kernel == 0 && kDefaultDataflowSweep && flow_block_ab(p->A8, p->ab));
@@ -852,10 +853,11 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
     if (p->tx * p->ty > 256 || p->tx < 1 || p->ty < 1) return fail(DOCTORS_ERR_INVALID_ARG, "tile_x * tile_y must be 1..256");
     if (p->A8 % p->ab != 0 || !(sweep_supported(p->ab, p->M) || flow_block_ab(p->A8, p->ab)))
         return fail(DOCTORS_ERR_INVALID_ARG, "angles_per_block must divide N(N+2)/8 and be one of "
-                                             "1,2,3,4,5,6,7,9,10,12 (or 36 at S16, dataflow sweep only)");
+                                             "1,2,3,4,5,6,7,9,10,12 (or 21 at S12, 36 at S16: whole octants, dataflow sweep only)");
     if ((opt->sweep_kernel == 1 || opt->sweep_kernel == 3) && !sweep_supported(p->ab, p->M))
         return fail(DOCTORS_ERR_INVALID_ARG,
-                    "angles_per_block = 36 (whole S16 octants) runs on the dataflow sweep only (sweep_kernel 0, 4, 7)");
+                    "whole S12 or S16 octants (angles_per_block 21, 36) run on the dataflow sweep only "
+                    "(sweep_kernel 0, 4, 7)");
     p->nab = p->A8 / p->ab;
     p->ntx = (p->nx + p->tx - 1) / p->tx;
     p->nty = (p->ny + p->ty - 1) / p->ty;
@@ -867,7 +869,7 @@ int doctors_create_problem(const doctors_mesh* mesh, const doctors_options* opt,
         !((opt->sweep_kernel == 0 || opt->sweep_kernel == 4) && p->A8 == p->ab && flow_octant_ab(p->ab)))
         return fail(DOCTORS_ERR_INVALID_ARG,
                     "diamond differencing runs on the dataflow sweep: sweep_kernel 0 or 4, angles_per_block = "
-                    "N(N+2)/8 and N <= 8 or N = 16");
+                    "N(N+2)/8 and N <= 8, N = 12 or N = 16");
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) return fail(DOCTORS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
 

@@ -217,7 +217,7 @@ struct SweepArgs {
 // builds them that way), and R_lm of a reflected direction is R_lm of the
 // original times (-1) to the number of reflected axes in which R_lm is odd.
 constexpr int kMaxA8 = 36;             // S16
-constexpr int kFlowMaxAB = 36;         // whole octants of S2..S8 and S16
+constexpr int kFlowMaxAB = 36;         // whole octants of S2..S8, S12 and S16
 struct ChainDirTable {
     float cx[kMaxA8], cy[kMaxA8], cz[kMaxA8], csum[kMaxA8];   // |Omega_q| / d_q and their sum
     float lx[kMaxA8], ly[kMaxA8], lz[kMaxA8];                  // boundary current per face (w |Omega_q| area)
@@ -244,8 +244,8 @@ constexpr unsigned kOddZ = (1u << 2) | (1u << 5) | (1u << 7) | (1u << 10) | (1u 
 // these directions per CTA (whole octants of S2, S4, S6, S8)
 inline bool chain_const_table_ab(int ab) { return ab == 1 || ab == 3 || ab == 6 || ab == 10; }
 // whole octants the dataflow kernels sweep with their table in the constant
-// bank: S2, S4, S6, S8 and S16
-inline bool flow_octant_ab(int ab) { return chain_const_table_ab(ab) || ab == 36; }
+// bank: S2, S4, S6, S8, S12 and S16
+inline bool flow_octant_ab(int ab) { return chain_const_table_ab(ab) || ab == 21 || ab == 36; }
 // direction blocks the dataflow kernels sweep (one launch per block, its
 // table in the constant bank): whole octants, or blocks of 12 directions
 // (S16: three per octant; a block's face and stored angular records are

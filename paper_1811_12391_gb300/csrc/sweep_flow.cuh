@@ -2,9 +2,9 @@
 // k_sweep_chain (whole octants per CTA; the first octant's direction rows,
 // coefficients and moment tables are kernel parameters, read through the
 // constant bank at compile-time offsets) with the tile stages replaced by a
-// task queue in one launch.  S16 runs as whole octants (36 directions per
-// cell step), or as three launches, one per block of 12 directions of
-// every octant, each with that block's table.
+// task queue in one launch.  S12 and S16 run as whole octants (21 and 36
+// directions per cell step); S16 also as three launches, one per block of
+// 12 directions of every octant, each with that block's table.
 //
 // The tasks (tile, octant, group) are numbered stage by stage (the tile
 // diagonal of the octant's reflected tile grid).  Each CTA takes the next
@@ -808,6 +808,7 @@ int sweep_flow_blocks_per_sm(int ab, int threads, size_t smem, bool split, bool 
         DOCTORS_FLOW_OCC(6)
         DOCTORS_FLOW_OCC(10)
         DOCTORS_FLOW_OCC(12)
+        DOCTORS_FLOW_OCC(21)
         DOCTORS_FLOW_OCC(36)
         default: break;
     }
@@ -918,6 +919,7 @@ cudaError_t launch_sweep_flow_m(const SweepArgs& a, cudaStream_t s) {
         DOCTORS_FLOW_CASE(6)
         DOCTORS_FLOW_CASE(10)
         DOCTORS_FLOW_CASE(12)
+        DOCTORS_FLOW_CASE(21)
         DOCTORS_FLOW_CASE(36)
         default: return cudaErrorInvalidValue;
     }

@@ -169,15 +169,18 @@ def test_gradients_satisfy_euler_identity(env, kernel):
     d.close()
 
 
-@pytest.mark.parametrize("kernel,ab", [(0, 0), (1, 12), (3, 12), (4, 12), (7, 12), (4, 36)])
-def test_adjoint_gradients_s16_direction_blocks(env, kernel, ab):
+@pytest.mark.parametrize("sn,kernel,ab", [(16, 0, 0), (16, 1, 12), (16, 3, 12), (16, 4, 12), (16, 7, 12),
+                                           (16, 4, 36), (12, 0, 0), (12, 3, 7)])
+def test_adjoint_gradients_s16_direction_blocks(env, sn, kernel, ab):
     """S16: the tile-stage and chained kernels (blocks of 12 directions) store
     and pair the angular fluence in 16-byte runs of a voxel's directions, the
     dataflow kernels in one record per (voxel, octant, block) of 12
     directions (one launch per block) or of the whole octant's 36 (the
-    default); adjoint fluence and all gradients against the oracle."""
+    default); S12 whole octants (21 directions, records padded to 24) and the
+    chained kernel's blocks of 7; adjoint fluence and all gradients against
+    the oracle."""
     torch, C, DoctorsProblem = env
-    p = ph.abdomen(nx=16, ny=14, nz=4, d=2.0, dz=2.0, G=2, sn=16, L=1)
+    p = ph.abdomen(nx=16, ny=14, nz=4, d=2.0, dz=2.0, G=2, sn=sn, L=1)
     rng = np.random.default_rng(7)
     p.density[:] = (p.density * rng.uniform(0.9, 1.1, size=p.V)).astype(np.float32)
     roi = np.zeros(p.V)

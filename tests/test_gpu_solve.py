@@ -94,6 +94,24 @@ def test_abdomen_s16_multi_angle_block(dp, s16_abdomen, kernel, tile, ab):
     d.close()
 
 
+@pytest.fixture(scope="module")
+def s12_cylinder():
+    p = ph.water_cylinder(nx=20, ny=18, nz=5, dx=1.5, dy=1.5, dz=2.0, diameter=24.0, G=3, sn=12, L=3)
+    return p, osv.solve(p, tol=1e-11)
+
+
+@pytest.mark.parametrize("kernel,tile,ab", [(0, (0, 0), 0), (4, (5, 7), 21), (7, (8, 8), 21), (3, (0, 0), 7),
+                                            (1, (0, 0), 7)])
+def test_s12_whole_octants_and_blocks(dp, s12_cylinder, kernel, tile, ab):
+    """S12 (21 directions per octant), P3: the dataflow kernels on whole
+    octants (the default, a ragged 5x7 tile, the face warp) and the chained and
+    stage kernels in blocks of 7, against the oracle."""
+    p, sol = s12_cylinder
+    d = dp(p, tol=1e-6, max_iters=400, sweep_kernel=kernel, tile=tile, angles_per_block=ab)
+    _compare(d, p, sol, f"cylinder S12 kernel={kernel} tile={tile} ab={ab}")
+    d.close()
+
+
 def test_s16_dataflow_block_checks(dp):
     """S16 reaches the dataflow kernels as whole octants or in blocks of 12
     directions: other blocks, whole octants on the stage and chained
