@@ -58,10 +58,10 @@ SWEEP_TRAFFIC = {
     (16, 16, 10, 1): (2246.4e6, "sweep_impl.cuh", "592eff4d10129e1bde8b55aecdf9fbf52f768e8c"),
     (16, 16, 5, 1): (1687.6e6, "sweep_impl.cuh", "592eff4d10129e1bde8b55aecdf9fbf52f768e8c"),
     (16, 8, 10, 3): (2534.9e6, "sweep_chain.cuh", "3502773d12d37fb58b50dbc1187553785b1df685"),
-    (8, 8, 10, 4): (3332.9e6, "sweep_flow.cuh", "1ae62cb7c9fbc12c7b179ce145fa3d3271ae1d55"),
-    (16, 8, 10, 7): (2801.9e6, "sweep_flow.cuh", "1ae62cb7c9fbc12c7b179ce145fa3d3271ae1d55"),
-    (8, 8, 10, 7): (2995.7e6, "sweep_flow.cuh", "1ae62cb7c9fbc12c7b179ce145fa3d3271ae1d55"),
-    (16, 16, 10, 7): (2644.0e6, "sweep_flow.cuh", "1ae62cb7c9fbc12c7b179ce145fa3d3271ae1d55"),
+    (8, 8, 10, 4): (3338.1e6, "sweep_flow.cuh", "19e106b753eb9e515798e72f9e5fe72303e29839"),
+    (16, 8, 10, 7): (2806.1e6, "sweep_flow.cuh", "19e106b753eb9e515798e72f9e5fe72303e29839"),
+    (8, 8, 10, 7): (3000.1e6, "sweep_flow.cuh", "19e106b753eb9e515798e72f9e5fe72303e29839"),
+    (16, 16, 10, 7): (2619.2e6, "sweep_flow.cuh", "19e106b753eb9e515798e72f9e5fe72303e29839"),
 }
 
 # sweep kernel by the library's sweep_kernel code
