@@ -1,7 +1,8 @@
 """Command line: solve a named synthetic workload and print the report.
 
   python -m paper_1811_12391_gb300 <workload> [--iters N] [--tol T] [--tile X Y] [--ab K] [--kernel 0..8]
-                                   [--device-loop] [--diamond] [--adjoint] [--autotune] [--repeat R]
+                                   [--sn N] [--legendre L] [--device-loop] [--diamond] [--adjoint]
+                                   [--autotune] [--repeat R]
 
 Workloads: tiny_cube, water_cylinder, abdomen, axial_scan, differentiable_abdomen
 (see synth/phantoms.py).  Used as the profiled command in profiles/.
@@ -25,6 +26,8 @@ def main():
     ap.add_argument("--ab", type=int, default=0)
     ap.add_argument("--kernel", type=int, default=0, help="sweep kernel: 0 default, 1 CUDA-core, 3 chained CUDA-core, 4 dataflow, 5 dataflow with split "
                     "transforms, 7 dataflow with a face warp, 8 split transforms on the tensor cores")
+    ap.add_argument("--sn", type=int, default=None, help="quadrature order (tiny_cube, water_cylinder, abdomen)")
+    ap.add_argument("--legendre", type=int, default=None, help="Legendre order (tiny_cube, water_cylinder, abdomen)")
     ap.add_argument("--device-loop", action="store_true",
                     help="run the source iteration as one CUDA graph with a device-side while loop")
     ap.add_argument("--diamond", action="store_true", help="diamond differencing (dataflow sweep)")
@@ -38,7 +41,7 @@ def main():
     from paper_1811_12391_gb300.solver import DoctorsProblem
     from synth import phantoms as ph
 
-    p = ph.config_problem(args.workload)
+    p = ph.config_problem(args.workload, sn=args.sn, L=args.legendre)
     if args.diamond:
         p.differencing = 1
     d = DoctorsProblem(p, tol=args.tol, max_iters=args.iters, tile=tuple(args.tile), angles_per_block=args.ab,

@@ -425,14 +425,19 @@ def infinite_medium_cube(seed: int = 5, n: int = 16, G: int = 3, sigma_t: float 
                    sources=[src], k_dep=deposition_weights(sigt, sigs, e_mid), e_mid=e_mid)
 
 
-def config_problem(name: str) -> Problem:
-    """The named full-size workloads (single-problem forms)."""
+def config_problem(name: str, sn: Optional[int] = None, L: Optional[int] = None) -> Problem:
+    """The named full-size workloads (single-problem forms); `sn` and `L`
+    override the quadrature order and the Legendre order of the tiny cube,
+    the water cylinder and the abdomen."""
+    kw = {k: v for k, v in (("sn", sn), ("L", L)) if v is not None}
     if name == "tiny_cube":
-        return tiny_cube()
+        return tiny_cube(**kw)
     if name == "water_cylinder":
-        return water_cylinder()
+        return water_cylinder(**kw)
     if name == "abdomen":
-        return abdomen()
+        return abdomen(**kw)
+    if kw:
+        raise ValueError(f"sn and L overrides apply to tiny_cube, water_cylinder and abdomen, not {name}")
     if name == "axial_scan":
         p = water_cylinder()
         return p.with_sources(axial_scan_sources(p, 64), name="axial_scan")
